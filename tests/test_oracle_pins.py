@@ -1,0 +1,448 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+values, exact discrete identities, convergence orders, symmetries, brute-force
+dense solves.  A plausible slip (dropped term, wrong sign, wrong staggering
+offset, transposed operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import ib_workloads as W
+from oracle import ib_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- delta kernels (sec. 2.2)
+
+def _golden_delta():
+    rows = []
+    with open(os.path.join(GOLDEN, "delta_kernels.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, r, v = line.split()[:3]
+            rows.append((k, float(r), float(v)))
+    return rows
+
+
+def test_delta_golden_values():
+    rows = _golden_delta()
+    assert len(rows) == 13
+    for k, r, v in rows:
+        phi = O.KERNELS[k]
+        assert abs(float(phi(np.array([r]))[0]) - v) < 1e-15, (k, r)
+        assert abs(float(phi(np.array([-r]))[0]) - v) < 1e-15, (k, -r)
+
+
+@pytest.mark.parametrize("kernel", ["peskin4", "cos4"])
+def test_delta_moment_conditions(kernel):
+    phi = O.KERNELS[kernel]
+    j = np.arange(-4, 5)
+    for r in np.linspace(0.0, 1.0, 41):
+        w = phi(r - j)
+        assert abs(w.sum() - 1.0) < 1e-14                      # partition of unity
+        assert abs(w[j % 2 == 0].sum() - 0.5) < 1e-14          # even/odd split
+        assert abs((w * w).sum() - 3.0 / 8.0) < 1e-14          # sum of squares
+        assert np.count_nonzero(w) <= 4                        # 4-point support
+        m1 = ((r - j) * w).sum()
+        if kernel == "peskin4":
+            assert abs(m1) < 1e-14                             # exact first moment
+        else:
+            assert abs(m1) < 0.022                             # cos4: bounded, not zero
+    if kernel == "cos4":
+        r = np.linspace(0, 1, 401)
+        m1 = np.array([((x - j) * phi(x - j)).sum() for x in r])
+        assert 0.02 < np.abs(m1).max() < 0.0215
+
+
+# ---------------------------------------------------------------- spreading / interpolation
+
+def _small_problem(N=32, n=40, kappa=10.0, rest=None, seed=0, **kw):
+    p = W.single_ellipse(N=N, n_points=n, kappa=kappa, a=0.23, b=0.17,
+                         center=(0.47, 0.53), rest=rest, **kw)
+    return p
+
+
+@pytest.mark.parametrize("kernel", ["peskin4", "cos4"])
+def test_spread_conserves_force_and_interp_reproduces_constants(kernel):
+    p = _small_problem()
+    N, h = p.N, p.h
+    S = O.spread_matrix(p.X, N, p.L, kernel)
+    Ss = O.interp_matrix(S, h)
+    F = W.random_points_field(p.n_points, 3)
+    Fv = np.concatenate([F[:, 0], F[:, 1]])
+    f = S @ Fv
+    n2 = N * N
+    # total force is conserved: h^2 sum_x f(x) = sum_k F_k (per component)
+    assert abs(h * h * f[:n2].sum() - F[:, 0].sum()) < 1e-12
+    assert abs(h * h * f[n2:].sum() - F[:, 1].sum()) < 1e-12
+    # constants interpolate exactly
+    u = np.concatenate([np.full(n2, 2.5), np.full(n2, -1.25)])
+    U = Ss @ u
+    assert np.allclose(U[: p.n_points], 2.5, atol=1e-13)
+    assert np.allclose(U[p.n_points:], -1.25, atol=1e-13)
+
+
+def test_interp_linear_exact_peskin4_pins_staggering():
+    """Peskin4 has a zero first moment, so interpolating a linear field is exact,
+    which fails if a face is placed at the wrong half-cell offset."""
+    N, L = 32, 1.0
+    h = L / N
+    X = np.array([[0.431, 0.517], [0.55, 0.47], [0.5 + 0.25 * h, 0.5 - 0.375 * h]])
+    S = O.spread_matrix(X, N, L, "peskin4")
+    Ss = O.interp_matrix(S, h)
+    i = np.arange(N)
+    xu, yu = np.meshgrid(i * h, (i + 0.5) * h, indexing="xy")
+    xv, yv = np.meshgrid((i + 0.5) * h, i * h, indexing="xy")
+    u = 1.0 + 3.0 * xu - 2.0 * yu
+    v = -0.5 + 0.7 * xv + 1.9 * yv
+    U = Ss @ np.concatenate([u.ravel(), v.ravel()])
+    n = X.shape[0]
+    assert np.allclose(U[:n], 1.0 + 3.0 * X[:, 0] - 2.0 * X[:, 1], atol=1e-13)
+    assert np.allclose(U[n:], -0.5 + 0.7 * X[:, 0] + 1.9 * X[:, 1], atol=1e-13)
+    # and the spread force has its first moment at the point positions
+    F = np.array([[1.0, 2.0], [-0.5, 0.3], [0.25, -1.0]])
+    f = S @ np.concatenate([F[:, 0], F[:, 1]])
+    n2 = N * N
+    assert abs(h * h * (f[:n2] * xu.ravel()).sum() - (F[:, 0] * X[:, 0]).sum()) < 1e-13
+    assert abs(h * h * (f[n2:] * yv.ravel()).sum() - (F[:, 1] * X[:, 1]).sum()) < 1e-13
+
+
+def test_interp_of_smooth_field_second_order():
+    """S* u approximates u(X) with O(h^2) error (pins offsets for both kernels)."""
+    for kernel in ("peskin4", "cos4"):
+        errs = []
+        X = np.array([[0.3127, 0.6711], [0.7, 0.21]])
+        for N in (32, 64, 128):
+            h = 1.0 / N
+            i = np.arange(N)
+            xu, yu = np.meshgrid(i * h, (i + 0.5) * h, indexing="xy")
+            xv, yv = np.meshgrid((i + 0.5) * h, i * h, indexing="xy")
+            u = np.sin(2 * np.pi * xu) * np.cos(2 * np.pi * yu)
+            v = np.cos(2 * np.pi * xv + 0.3) * np.sin(4 * np.pi * yv)
+            S = O.spread_matrix(X, N, 1.0, kernel)
+            U = O.interp_matrix(S, h) @ np.concatenate([u.ravel(), v.ravel()])
+            ue = np.sin(2 * np.pi * X[:, 0]) * np.cos(2 * np.pi * X[:, 1])
+            ve = np.cos(2 * np.pi * X[:, 0] + 0.3) * np.sin(4 * np.pi * X[:, 1])
+            errs.append(max(np.abs(U[:2] - ue).max(), np.abs(U[2:] - ve).max()))
+        assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, (kernel, errs)
+
+
+def test_spread_interp_adjoint_and_sts_psd():
+    p = _small_problem(N=16, n=24)
+    h = p.h
+    S = O.spread_matrix(p.X, p.N, p.L, "peskin4")
+    Ss = O.interp_matrix(S, h)
+    rng = np.random.default_rng(1)
+    F = rng.standard_normal(2 * p.n_points)
+    u = rng.standard_normal(2 * p.N * p.N)
+    # <S F, u>_h = h^2 sum (S F) u  equals  <F, S* u>
+    assert abs(h * h * (S @ F) @ u - F @ (Ss @ u)) < 1e-11 * np.abs(F).sum() * np.abs(u).max()
+    M = (Ss @ S).toarray()
+    assert np.allclose(M, M.T, atol=1e-12)
+    assert np.linalg.eigvalsh(M).min() > -1e-12
+
+
+# ---------------------------------------------------------------- springs
+
+def test_spring_force_sums_to_zero_and_jacobian_matches_fd():
+    p = _small_problem(n=20, kappa=7.0, rest=0.03)
+    F = O.spring_force(p.X, p.springs, p.kappa, p.rest, p.L)
+    assert np.abs(F.sum(axis=0)).max() < 1e-12
+    Jx = O.spring_jacobian(p.X, p.springs, p.kappa, p.rest, p.L, clamped=False).toarray()
+    n = p.n_points
+    eps = 1e-6
+    Jfd = np.zeros((2 * n, 2 * n))
+    for c in range(2):
+        for k in range(n):
+            Xp = p.X.copy()
+            Xm = p.X.copy()
+            Xp[k, c] += eps
+            Xm[k, c] -= eps
+            dF = (O.spring_force(Xp, p.springs, p.kappa, p.rest, p.L)
+                  - O.spring_force(Xm, p.springs, p.kappa, p.rest, p.L)) / (2 * eps)
+            Jfd[:, c * n + k] = np.concatenate([dF[:, 0], dF[:, 1]])
+    assert np.abs(Jx - Jfd).max() < 1e-6 * np.abs(Jx).max()
+    assert np.allclose(Jx, Jx.T, atol=1e-12)
+
+
+def test_clamped_jacobian_nsd_and_zero_rest_length_is_kappa_af():
+    p = _small_problem(n=24, kappa=3.0, rest=0.06)   # compressed springs: exact J indefinite
+    Jc = O.spring_jacobian(p.X, p.springs, p.kappa, p.rest, p.L, clamped=True).toarray()
+    Je = O.spring_jacobian(p.X, p.springs, p.kappa, p.rest, p.L, clamped=False).toarray()
+    assert np.linalg.eigvalsh(Jc).max() < 1e-12
+    assert np.linalg.eigvalsh(Je).max() > 1e-3
+    # zero rest length: J = kappa * A_f (x) I_2 with A_f the closed-curve second difference
+    q = _small_problem(n=24, kappa=3.0, rest=0.0)
+    J0 = O.spring_jacobian(q.X, q.springs, q.kappa, q.rest, q.L, clamped=True).toarray()
+    n = q.n_points
+    Af = -2.0 * np.eye(n) + np.roll(np.eye(n), 1, axis=1) + np.roll(np.eye(n), -1, axis=1)
+    ref = np.kron(np.eye(2), 3.0 * Af)
+    assert np.abs(J0 - ref).max() < 1e-12
+    # and F = kappa A_f X for zero rest length
+    F = O.spring_force(q.X, q.springs, q.kappa, q.rest, q.L)
+    assert np.abs(F - 3.0 * Af @ q.X).max() < 1e-12
+
+
+# ---------------------------------------------------------------- Stokes operator (sec. 2.2)
+
+def _mms(N, mu=1.0):
+    h = 1.0 / N
+    i = np.arange(N)
+    tp = 2 * np.pi
+    xu, yu = np.meshgrid(i * h, (i + 0.5) * h, indexing="xy")
+    xv, yv = np.meshgrid((i + 0.5) * h, i * h, indexing="xy")
+    xp, yp = np.meshgrid((i + 0.5) * h, (i + 0.5) * h, indexing="xy")
+    u = np.sin(tp * xu) * np.cos(tp * yu)
+    v = -np.cos(tp * xv) * np.sin(tp * yv)
+    p = np.sin(tp * xp) * np.sin(tp * yp)
+    # continuous mu Lap u - grad p and div u at the same points
+    fu = -2 * tp * tp * mu * u - tp * np.cos(tp * xu) * np.sin(tp * yu)
+    fv = -2 * tp * tp * mu * v - tp * np.sin(tp * xv) * np.cos(tp * yv)
+    w = np.concatenate([u.ravel(), v.ravel(), p.ravel()])
+    exact = np.concatenate([fu.ravel(), fv.ravel(), np.zeros(N * N)])
+    return w, exact
+
+
+def test_stokes_manufactured_second_order():
+    errs = []
+    for N in (16, 32, 64, 128):
+        A = O.stokes_matrix(N, 1.0 / N, 1.0, 0.0, 1.0)
+        w, ex = _mms(N)
+        errs.append(np.abs(A @ w - ex).max() / np.abs(ex).max())
+    rates = [errs[k] / errs[k + 1] for k in range(3)]
+    assert all(3.5 < r < 4.5 for r in rates), (errs, rates)
+
+
+def test_stokes_unsteady_term_and_symmetry():
+    N = 16
+    h = 1.0 / N
+    A0 = O.stokes_matrix(N, h, 1.3, 0.0, 0.1)
+    A1 = O.stokes_matrix(N, h, 1.3, 2.0, 0.1)
+    D = (A1 - A0).toarray()
+    n = N * N
+    assert np.allclose(np.diag(D)[: 2 * n], -20.0) and np.allclose(np.diag(D)[2 * n:], 0.0)
+    assert np.abs(D - np.diag(np.diag(D))).max() == 0.0
+    # [[K, -G], [D, 0]] with D = -G^T is symmetric
+    assert abs(A1 - A1.T).max() < 1e-12
+
+
+def test_stokes_divergence_free_solution_check():
+    """A solve with a manufactured forcing gives an O(h^2)-accurate, exactly
+    (discretely) divergence-free field."""
+    errs = []
+    for N in (16, 32, 64):
+        A = O.stokes_matrix(N, 1.0 / N, 1.0, 0.0, 1.0)
+        w, ex = _mms(N)
+        sol = O.direct_solve(A, ex, N, 0.0) if N <= 32 else None
+        if sol is None:
+            import scipy.sparse.linalg as sla
+            Z = O.nullspace_basis(N, 0.0)
+            M = sp.bmat([[A, sp.csr_matrix(Z)], [sp.csr_matrix(Z.T), None]], format="csc")
+            sol = sla.spsolve(M, np.concatenate([ex, np.zeros(3)]))[: 3 * N * N]
+        n = N * N
+        sol[2 * n:] -= sol[2 * n:].mean()
+        div = (A @ sol)[2 * n:]
+        assert np.abs(div).max() < 1e-9
+        errs.append(np.abs(sol[: 2 * n] - w[: 2 * n]).max())
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+# ---------------------------------------------------------------- transfers (sec. 3.1)
+
+def test_transfer_constants_and_pressure_identity():
+    Nf = 16
+    R = O.restriction_matrix(Nf)
+    P = O.prolongation_matrix(Nf // 2)
+    assert np.allclose(np.asarray(R.sum(axis=1)).ravel(), 1.0)
+    assert np.allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0)
+    nc = (Nf // 2) ** 2
+    Rp = R[2 * nc:, 2 * Nf * Nf:]
+    Pp = P[2 * Nf * Nf:, 2 * nc:]
+    assert abs(Rp @ Pp - sp.identity(nc)).max() < 1e-15
+    # the u stencil is 1/8 [1 2 1; 1 2 1]: 6 fine faces, weights sum 1
+    row = R[0].toarray().ravel()
+    assert sorted(np.round(row[row != 0] * 8).tolist()) == [1, 1, 1, 1, 2, 2]
+
+
+def _staggered_fields(N, f):
+    h = 1.0 / N
+    i = np.arange(N)
+    xu, yu = np.meshgrid(i * h, (i + 0.5) * h, indexing="xy")
+    xv, yv = np.meshgrid((i + 0.5) * h, i * h, indexing="xy")
+    xp, yp = np.meshgrid((i + 0.5) * h, (i + 0.5) * h, indexing="xy")
+    return np.concatenate([f(xu, yu, 0).ravel(), f(xv, yv, 1).ravel(), f(xp, yp, 2).ravel()])
+
+
+def test_transfers_second_order_at_staggered_positions():
+    """R and P of a smooth field match the field at the target points to O(h^2);
+    a wrong staggering offset would leave an O(h) error."""
+    def f(x, y, c):
+        return np.sin(2 * np.pi * x + 0.4 * c) * np.cos(2 * np.pi * y - 0.3 * c)
+    er, ep = [], []
+    for N in (16, 32, 64, 128):
+        R = O.restriction_matrix(N)
+        P = O.prolongation_matrix(N // 2)
+        fine = _staggered_fields(N, f)
+        coarse = _staggered_fields(N // 2, f)
+        n2 = 2 * N * N
+        nc2 = 2 * (N // 2) ** 2
+        er.append(np.abs((R @ fine)[:nc2] - coarse[:nc2]).max())
+        ep.append(np.abs((P @ coarse)[:n2] - fine[:n2]).max())
+    for e in (er, ep):
+        assert all(e[k] / e[k + 1] > 3.5 for k in range(3)), e
+
+
+# ---------------------------------------------------------------- elasticity operator, hierarchy
+
+def test_elasticity_symmetric_nsd_and_kills_translations():
+    p = _small_problem(N=16, n=24, kappa=50.0, rest=0.04)
+    levels, ops = O.build_hierarchy(p)
+    E0 = levels[0].E.toarray()
+    assert np.allclose(E0, E0.T, atol=1e-9 * np.abs(E0).max())
+    assert np.linalg.eigvalsh(0.5 * (E0 + E0.T)).max() < 1e-9 * np.abs(E0).max()
+    for lev in levels:
+        n2 = lev.N * lev.N
+        c = np.concatenate([np.full(n2, 1.0), np.full(n2, -2.0)])
+        assert np.abs(lev.E @ c).max() < 1e-9 * abs(lev.E).max()
+
+
+def test_box_sizes_colours_and_free_boxes():
+    p = _small_problem(N=32, n=30, kappa=100.0)
+    levels, _ = O.build_hierarchy(p)
+    for b in (1, 2, 4, 8):
+        lev = levels[0]
+        bx = O.prepare_boxes(lev, b)
+        nb = 2 * b * (b + 1) + b * b
+        assert bx["lex"].shape[1] == nb
+        assert [5, 16, 56, 208][[1, 2, 4, 8].index(b)] == nb
+        for c in range(4):
+            idx = bx["color"][c][0]
+            assert len(np.unique(idx)) == idx.size       # same-colour boxes share no unknowns
+        # boxes away from the structure all carry the same matrix (sec. 8 remark)
+        nbx = lev.N // b
+        E = lev.E
+        touched = set(np.nonzero(np.asarray(abs(E).sum(axis=1)).ravel())[0].tolist())
+        free = [k for k in range(nbx * nbx) if not (set(bx["lex"][k].tolist()) & touched)]
+        assert len(free) > 4
+        A0 = bx["lexA"][free[0]]
+        for k in free[1:]:
+            assert np.array_equal(bx["lexA"][k], A0)
+        # every unknown belongs to some box
+        assert len(np.unique(bx["lex"])) == 3 * lev.N * lev.N
+
+
+# ---------------------------------------------------------------- V-cycle and solves
+
+def test_vcycle_stokes_contraction():
+    """Without structure, one V(1,1) cycle contracts the error by well under 1/2."""
+    p = _small_problem(N=64, n=8, kappa=0.0)
+    levels, _ = O.build_hierarchy(p)
+    for lev in levels[:-1]:
+        O.prepare_boxes(lev, 1)
+    rng = np.random.default_rng(5)
+    b = levels[0].A @ rng.standard_normal(3 * 64 * 64)
+    for order in ("color4", "lex"):
+        w = np.zeros_like(b)
+        r0 = np.linalg.norm(b)
+        rs = []
+        for _ in range(6):
+            w = O.vcycle(levels, b, w, 1, 1, p.rho, order)
+            rs.append(np.linalg.norm(b - levels[0].A @ w))
+        rate = (rs[-1] / rs[1]) ** (1 / 4)
+        assert rs[0] < r0 and rate < 0.35, (order, rate)
+
+
+def test_fgmres_matches_dense_direct_solve_16():
+    for rho, kap, rest in ((1.0, 1e3, None), (0.0, 1e2, 0.0)):
+        p = W.single_ellipse(N=16, n_points=24, kappa=kap, dt=1e-2, rho=rho, rest=rest,
+                             a=0.28, b=0.22)
+        res = O.solve_step(p)
+        levels, _ = O.build_hierarchy(p)
+        xd = O.remove_pressure_mean(O.direct_solve(levels[0].A, res.b, p.N, rho), p.N)
+        if rho == 0.0:
+            n = p.N * p.N
+            xd[:n] -= xd[:n].mean()
+            xd[n:2 * n] -= xd[n:2 * n].mean()
+            w = res.w.copy()
+            w[:n] -= w[:n].mean()
+            w[n:2 * n] -= w[n:2 * n].mean()
+        else:
+            w = res.w
+        assert res.solve.converged and res.solve.rel_res_true <= 1e-8
+        assert np.linalg.norm(w - xd) <= 1e-6 * np.linalg.norm(xd)
+        n = p.N * p.N
+        div = (levels[0].A @ res.w)[2 * n:]
+        assert np.linalg.norm(div) <= 1e-8 * np.linalg.norm(res.b)
+
+
+def test_iterations_flat_under_refinement_and_rise_with_stiffness():
+    its = []
+    for N in (32, 64, 128):
+        p = W.single_ellipse(N=N, n_points=2 * N, kappa=1e2, dt=1e-2)
+        its.append(O.solve_step(p).solve.iters)
+    assert max(its) - min(its) <= 2, its
+    soft = O.solve_step(W.single_ellipse(N=32, n_points=64, kappa=1.0, dt=1e-2)).solve.iters
+    stiff = O.solve_step(W.single_ellipse(N=32, n_points=64, kappa=1e6, dt=1e-2)).solve.iters
+    assert stiff > soft, (soft, stiff)
+
+
+def test_translation_by_one_cell_shifts_solution():
+    N = 32
+    p = W.single_ellipse(N=N, n_points=48, kappa=1e3, center=(0.45, 0.52))
+    q = W.single_ellipse(N=N, n_points=48, kappa=1e3, center=(0.45 + 1.0 / N, 0.52))
+    a = O.solve_step(p)
+    b = O.solve_step(q)
+    for c in range(3):
+        fa = a.w[c * N * N:(c + 1) * N * N].reshape(N, N)
+        fb = b.w[c * N * N:(c + 1) * N * N].reshape(N, N)
+        assert np.abs(np.roll(fa, 1, axis=1) - fb).max() < 1e-7 * np.abs(fa).max()
+    assert np.abs(a.X + np.array([1.0 / N, 0.0]) - b.X).max() < 1e-10
+
+
+def test_mirror_symmetry():
+    """Reflecting the geometry x -> 1 - x mirrors u (with a sign) and v, p."""
+    N = 32
+    p = W.single_ellipse(N=N, n_points=48, kappa=1e3, center=(0.41, 0.52))
+    X = p.X
+    p.X = np.stack([0.5 + 0.09 * np.cos(np.arange(48) * 2 * np.pi / 48) + 0.02 * np.sin(
+        3 * np.arange(48) * 2 * np.pi / 48), X[:, 1]], axis=1)
+    q = W.single_ellipse(N=N, n_points=48, kappa=1e3)
+    q.X = np.stack([1.0 - p.X[:, 0], p.X[:, 1]], axis=1)
+    q.springs = p.springs[:, ::-1].copy()
+    a = O.solve_step(p)
+    b = O.solve_step(q)
+    n = N * N
+    ua = a.w[:n].reshape(N, N)
+    ub = b.w[:n].reshape(N, N)
+    # u face i at x = i h maps to x = 1 - i h = face (N - i) mod N
+    ua_m = -ua[:, (-np.arange(N)) % N]
+    assert np.abs(ua_m - ub).max() < 1e-7 * np.abs(ua).max()
+    va = a.w[n:2 * n].reshape(N, N)
+    vb = b.w[n:2 * n].reshape(N, N)
+    assert np.abs(va[:, ::-1] - vb).max() < 1e-7 * np.abs(va).max()
+    pa = a.w[2 * n:].reshape(N, N)
+    pb = b.w[2 * n:].reshape(N, N)
+    assert np.abs(pa[:, ::-1] - pb).max() < 1e-7 * np.abs(pa).max()
+
+
+def test_backward_euler_energy_decreases_for_any_dt():
+    """Zero rest length, steady Stokes (rho = 0): the lagged-S backward-Euler step is
+    unconditionally stable, so the elastic energy never increases (sec. 2.3)."""
+    for dt in (1e-3, 1e-1, 10.0):
+        p = W.single_ellipse(N=32, n_points=48, kappa=50.0, dt=dt, rho=0.0, rest=0.0)
+        e = [O.elastic_energy(p.X, p.springs, p.kappa, p.rest, p.L)]
+        X = p.X
+        for _ in range(3):
+            r = O.solve_step(p, X=X)
+            assert r.solve.converged
+            X = r.X
+            e.append(O.elastic_energy(X, p.springs, p.kappa, p.rest, p.L))
+        assert all(e[k + 1] <= e[k] * (1 + 1e-12) for k in range(3)), (dt, e)
+        assert e[-1] < e[0]
