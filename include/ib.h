@@ -1,0 +1,170 @@
+/*
+ * ib.h -- C ABI of the GB300 implicit immersed-boundary multigrid library.
+ *
+ * Method: Guy, Philip & Griffith, "Geometric multigrid for an implicit-time
+ * immersed boundary method".  One backward-Euler IB step with lagged
+ * spreading/interpolation (sec. 2.3, Eqs. 11-14) is reduced to a Stokes-type
+ * saddle-point system on a 2-D staggered (MAC) grid by eliminating the
+ * Lagrangian unknowns (Eqs. 15-16, the block system of sec. 3):
+ *
+ *     [ mu*Lap_h - (rho/dt) I + dt * S J S^*   -grad_h ] [u]   [ -(rho/dt) u^n - S F(X^n) ]
+ *     [ div_h                                   0      ] [p] = [ 0                        ]
+ *
+ * where S is spreading with a 4-point regularised delta (sec. 2.2), S^* its
+ * adjoint (interpolation), F the spring force and J = dF/dX its Jacobian at
+ * X^n.  With rho = 0 and zero rest length this is exactly the paper's system
+ * with alpha S A_f S^* (alpha = gamma dt).  The system is solved by flexible
+ * GMRES (sec. 3.3) right-preconditioned by one geometric V-cycle (Algorithm 1)
+ * with the box / big-box smoother (secs. 5-6), re-discretised Stokes and
+ * Galerkin-coarsened elasticity on coarse levels (sec. 3.2), staggered
+ * transfers (sec. 3.1) and an exact solve on the N_c = max(4, box) grid
+ * (sec. 6.1).  Then X^{n+1} = X^n + dt S^* u^{n+1} (Eq. 14).
+ *
+ * Conventions for every entry point:
+ *  - Domain: periodic square of side L, N x N cells, h = L / N.
+ *  - Grid vectors have layout [u | v | p], each an N x N block, row-major with
+ *    x fastest (index j*N + i); u[j][i] sits at (i h, (j+1/2) h), v[j][i] at
+ *    ((i+1/2) h, j h), p[j][i] at the cell centre.  Level l vectors use
+ *    N_l = N / 2^l.
+ *  - Lagrangian arrays X are [n_points][2] (x, y), float64.
+ *  - "device" pointers are CUDA device memory on the current device; "host"
+ *    pointers are ordinary host memory.  All memory passed in is owned by the
+ *    caller and is only read/written for the duration of the call.
+ *  - Work is issued on the CUDA stream given at set-up; calls return after
+ *    their results are complete on that stream unless stated otherwise.
+ *  - Every function returns an ib_status code; nothing throws across the ABI
+ *    and nothing exits the process.  ib_last_error() gives a message for the
+ *    last failing call on the calling thread.
+ */
+#ifndef IB_H_
+#define IB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IB_API __attribute__((visibility("default")))
+#else
+#define IB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IB_OK = 0,
+  IB_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter failed validation */
+  IB_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  IB_ERR_OOM = 3,           /* device allocation failed */
+  IB_ERR_NOT_CONVERGED = 4, /* FGMRES hit max_iters above tol (results still written) */
+  IB_ERR_BREAKDOWN = 5,     /* non-finite value in the Krylov recurrence */
+  IB_ERR_SINGULAR = 6,      /* a zero pivot in a box or coarsest-level factorisation */
+  IB_ERR_TIMEOUT = 7        /* a bounded device-side wait ran out */
+} ib_status;
+
+enum { IB_DELTA_PESKIN4 = 0, IB_DELTA_COS4 = 1 };
+enum { IB_FP64 = 0, IB_FP32_PRECOND = 1 };
+enum { IB_JAC_CLAMPED = 0, IB_JAC_EXACT = 1 };
+
+/* Problem parameters (sec. 2: grid, fluid, time step; secs. 5-6: smoother). */
+typedef struct {
+  int32_t N;          /* cells per side: power of two, N >= 2 * max(4, box) */
+  double L;           /* domain side (> 0) */
+  double rho;         /* density (>= 0); 0 gives the paper's steady Stokes system */
+  double mu;          /* viscosity (> 0) */
+  double dt;          /* backward-Euler step (> 0) */
+  int32_t delta;      /* IB_DELTA_PESKIN4 or IB_DELTA_COS4 (sec. 2.2) */
+  int32_t box;        /* box size b in {1, 2, 4, 8} (sec. 6) */
+  int32_t nu1, nu2;   /* pre/post smoothing sweeps, 0..8 (Algorithm 1) */
+  int32_t precision;  /* IB_FP64 or IB_FP32_PRECOND (V-cycle in FP32, Krylov in FP64) */
+  int32_t jacobian;   /* IB_JAC_CLAMPED (default) or IB_JAC_EXACT spring Jacobian */
+  double tol;         /* relative residual target ||b - A x|| / ||b|| (> 0) */
+  int32_t max_iters;  /* FGMRES iteration cap, 1..512 (the paper stops at 100) */
+} ib_params;
+
+/* Statistics of one ib_solve_step call. */
+typedef struct {
+  int32_t iters;        /* FGMRES iterations (= V-cycles applied) */
+  int32_t restarts;     /* restarts after a failed true-residual check */
+  double rel_res_true;  /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
+  double rel_res_est;   /* FGMRES (Givens) estimate at the last iteration */
+  double t_setup_ms;    /* hierarchy set-up time (CUDA events) */
+  double t_solve_ms;    /* FGMRES time (CUDA events) */
+  int32_t n_struct_boxes; /* structure boxes (with elasticity), all levels */
+  int32_t status;       /* ib_status of the solve */
+} ib_stats;
+
+typedef struct ib_problem ib_problem;  /* opaque; owned by the library */
+
+/* Fill *p with the defaults: L=1, rho=1, mu=1, dt=1e-2, Peskin4, box 1, V(1,1),
+ * FP64, clamped Jacobian, tol 1e-8, max_iters 100.  N is set to 64. */
+IB_API void ib_default_params(ib_params* p);
+
+/* Create a problem: validates the parameters, allocates all device workspace
+ * (levels N, N/2, ..., N_c) and uploads the structure.
+ *   X        host [n_points][2] initial point positions (any real values; periodic)
+ *   springs  host [n_springs][2] point index pairs (i != j, 0 <= i, j < n_points)
+ *   kappa    host [n_springs] stiffness (>= 0);  rest  host [n_springs] rest length (>= 0)
+ *   stream   a cudaStream_t (NULL = legacy default stream) used by every later call
+ * n_points may be 0 (no structure; then n_springs must be 0).  The spring
+ * force law is F_i += kappa (1 - L0 / |d|) d with d = X_j - X_i (minimum image),
+ * the discrete tension law of sec. 2.2 generalised to rest length (sec. 7).
+ * On success *out receives the handle; on failure *out is NULL. */
+IB_API int ib_setup(const ib_params* params, int32_t n_points, const double* X,
+             int32_t n_springs, const int32_t* springs, const double* kappa,
+             const double* rest, void* stream, ib_problem** out);
+
+/* Replace the point positions by device X [n_points][2] and rebuild S, J, the
+ * coarse elasticity patches and all box factors (the per-step re-forming of
+ * S A_f S^* described in sec. 8). */
+IB_API int ib_update_points(ib_problem* prob, const double* X_dev);
+
+/* y = A_level w in FP64 (device pointers, 3 N_level^2 doubles each, must not
+ * alias).  A_0 is the fine operator of the system above; A_l (l >= 1) is the
+ * hybrid coarse operator of sec. 3.2: Stokes re-discretised with h_l plus
+ * dt * R E_{l-1} P.  level in [0, n_levels). */
+IB_API int ib_apply(ib_problem* prob, int32_t level, const double* w, double* y);
+
+/* One V-cycle (Algorithm 1, nu1/nu2 sweeps, zero initial guess) on the fine
+ * level: w = MGV(0, b).  device b, w: 3N^2 doubles (may not alias).  With
+ * IB_FP32_PRECOND the cycle runs in FP32 (structure boxes in FP64) and b, w are
+ * converted at entry and exit. */
+IB_API int ib_vcycle(ib_problem* prob, const double* b, double* w);
+
+/* b = [-(rho/dt) u^n - S F(X); 0] for the current points (device, 3N^2
+ * doubles).  u_n: device [2][N][N] doubles or NULL for a fluid at rest. */
+IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
+
+/* One implicit IB step (sec. 2.3):
+ *   u_n    device [2][N][N] velocity at t^n, or NULL (fluid at rest)
+ *   up     device [3][N][N] output: u, v, p at t^{n+1}, pressure with zero mean
+ *   X      device [n_points][2]: in X^n, out X^{n+1} = X^n + dt S^*(X^n) u^{n+1}
+ *   stats  host, may be NULL
+ * Re-forms S, J and the hierarchy from X^n, solves with MG-preconditioned
+ * FGMRES to params.tol, then moves the points.  Returns IB_ERR_NOT_CONVERGED
+ * if max_iters was reached (the best iterate is still written and X moved). */
+IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,
+                  ib_stats* stats);
+
+/* Number of levels in the hierarchy and the grid size of a level. */
+IB_API int ib_num_levels(const ib_problem* prob);
+IB_API int ib_level_size(const ib_problem* prob, int32_t level);
+
+/* Number of structure boxes (boxes whose block includes elasticity) on a level,
+ * as found by the last set-up. */
+IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
+
+/* Release all device memory of the problem.  NULL is ignored. */
+IB_API void ib_destroy(ib_problem* prob);
+
+/* Message for the last failing call on this thread ("" if none). */
+IB_API const char* ib_last_error(void);
+
+/* Library version string. */
+IB_API const char* ib_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IB_H_ */

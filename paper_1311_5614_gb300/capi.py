@@ -1,0 +1,262 @@
+"""ctypes binding of the C ABI in ``include/ib.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but check and convert arguments: torch CUDA tensors are passed as raw
+device pointers, numpy arrays as host pointers, the problem's CUDA stream is
+torch's current stream at set-up.  All arithmetic runs in ``libibmg.so``.
+If the library has not been built, loading it raises immediately; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibmg.so")
+
+IB_OK = 0
+IB_ERR_INVALID_ARG = 1
+IB_ERR_CUDA = 2
+IB_ERR_OOM = 3
+IB_ERR_NOT_CONVERGED = 4
+IB_ERR_BREAKDOWN = 5
+IB_ERR_SINGULAR = 6
+IB_ERR_TIMEOUT = 7
+STATUS_NAMES = {0: "IB_OK", 1: "IB_ERR_INVALID_ARG", 2: "IB_ERR_CUDA", 3: "IB_ERR_OOM",
+                4: "IB_ERR_NOT_CONVERGED", 5: "IB_ERR_BREAKDOWN", 6: "IB_ERR_SINGULAR",
+                7: "IB_ERR_TIMEOUT"}
+
+DELTA = {"peskin4": 0, "cos4": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+JACOBIAN = {"clamped": 0, "exact": 1}
+
+
+class ib_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_double), ("rho", ctypes.c_double),
+                ("mu", ctypes.c_double), ("dt", ctypes.c_double), ("delta", ctypes.c_int32),
+                ("box", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("jacobian", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int32)]
+
+
+class ib_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("rel_res_true", ctypes.c_double), ("rel_res_est", ctypes.c_double),
+                ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("n_struct_boxes", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "ib_default_params": (None, [ctypes.POINTER(ib_params)]),
+    "ib_setup": (ctypes.c_int, [ctypes.POINTER(ib_params), ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
+                                _P, _P, ctypes.POINTER(_P)]),
+    "ib_update_points": (ctypes.c_int, [_P, _P]),
+    "ib_apply": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "ib_vcycle": (ctypes.c_int, [_P, _P, _P]),
+    "ib_rhs": (ctypes.c_int, [_P, _P, _P]),
+    "ib_solve_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ib_stats)]),
+    "ib_num_levels": (ctypes.c_int, [_P]),
+    "ib_level_size": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_num_struct_boxes": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_destroy": (None, [_P]),
+    "ib_last_error": (ctypes.c_char_p, []),
+    "ib_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load ``libibmg.so`` (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libibmg.so is not built (run __graft_entry__.build()): " + LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != IB_OK:
+        raise IBError(code, lib().ib_last_error().decode())
+
+
+def _dev_ptr(t, numel, name):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 tensor" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ib_default_params():
+    p = ib_params()
+    lib().ib_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=1, nu2=1,
+                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100):
+    p = ib_default_params()
+    p.N, p.L, p.rho, p.mu, p.dt = int(N), float(L), float(rho), float(mu), float(dt)
+    p.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
+    p.box, p.nu1, p.nu2 = int(box), int(nu1), int(nu2)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.jacobian = JACOBIAN[jacobian] if isinstance(jacobian, str) else int(jacobian)
+    p.tol, p.max_iters = float(tol), int(max_iters)
+    return p
+
+
+def ib_setup(params, X, springs, kappa, rest, stream=None):
+    """Create a problem from host arrays; returns the opaque handle (c_void_p)."""
+    import torch
+
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 2)
+    springs = np.ascontiguousarray(springs, dtype=np.int32).reshape(-1, 2)
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64).ravel()
+    rest = np.ascontiguousarray(rest, dtype=np.float64).ravel()
+    if kappa.size != springs.shape[0] or rest.size != springs.shape[0]:
+        raise ValueError("kappa and rest need one value per spring")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    _check(lib().ib_setup(ctypes.byref(params), X.shape[0], X.ctypes.data_as(_P),
+                          springs.shape[0], springs.ctypes.data_as(_P), kappa.ctypes.data_as(_P),
+                          rest.ctypes.data_as(_P), ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out
+
+
+def ib_update_points(prob, X_dev, n_points):
+    _check(lib().ib_update_points(prob, _dev_ptr(X_dev, 2 * n_points, "X")))
+
+
+def ib_apply(prob, level, w, y):
+    n = ib_level_size(prob, level)
+    _check(lib().ib_apply(prob, int(level), _dev_ptr(w, 3 * n * n, "w"), _dev_ptr(y, 3 * n * n, "y")))
+
+
+def ib_vcycle(prob, b, w):
+    n = ib_level_size(prob, 0)
+    _check(lib().ib_vcycle(prob, _dev_ptr(b, 3 * n * n, "b"), _dev_ptr(w, 3 * n * n, "w")))
+
+
+def ib_rhs(prob, u_n, b):
+    n = ib_level_size(prob, 0)
+    _check(lib().ib_rhs(prob, _dev_ptr(u_n, 2 * n * n, "u_n"), _dev_ptr(b, 3 * n * n, "b")))
+
+
+def ib_solve_step(prob, u_n, up, X, n_points, raise_on_not_converged=False):
+    """One implicit step; returns the ib_stats as a dict (status included)."""
+    n = ib_level_size(prob, 0)
+    st = ib_stats()
+    code = lib().ib_solve_step(prob, _dev_ptr(u_n, 2 * n * n, "u_n"), _dev_ptr(up, 3 * n * n, "up"),
+                               _dev_ptr(X, 2 * n_points, "X") if n_points else None, ctypes.byref(st))
+    if code != IB_OK and (code != IB_ERR_NOT_CONVERGED or raise_on_not_converged):
+        _check(code)
+    return st.as_dict()
+
+
+def ib_num_levels(prob):
+    return lib().ib_num_levels(prob)
+
+
+def ib_level_size(prob, level):
+    return lib().ib_level_size(prob, int(level))
+
+
+def ib_num_struct_boxes(prob, level):
+    return lib().ib_num_struct_boxes(prob, int(level))
+
+
+def ib_destroy(prob):
+    if prob:
+        lib().ib_destroy(prob)
+
+
+def ib_last_error():
+    return lib().ib_last_error().decode()
+
+
+def ib_version():
+    return lib().ib_version().decode()
+
+
+class IBSolver:
+    """Owns one problem handle; methods forward to the functions above."""
+
+    def __init__(self, N, X, springs, kappa, rest, **kw):
+        self.params = make_params(N, **kw)
+        self.N = int(N)
+        self.n_points = int(np.asarray(X).reshape(-1, 2).shape[0])
+        self.handle = ib_setup(self.params, X, springs, kappa, rest)
+
+    @classmethod
+    def from_problem(cls, prob, **overrides):
+        kw = dict(L=prob.L, rho=prob.rho, mu=prob.mu, dt=prob.dt, delta=prob.delta, box=prob.box,
+                  nu1=prob.nu1, nu2=prob.nu2, tol=prob.tol, max_iters=prob.max_iters,
+                  jacobian="clamped" if prob.clamped else "exact")
+        kw.update(overrides)
+        return cls(prob.N, prob.X, prob.springs, prob.kappa, prob.rest, **kw)
+
+    @property
+    def n_levels(self):
+        return ib_num_levels(self.handle)
+
+    def level_size(self, level):
+        return ib_level_size(self.handle, level)
+
+    def struct_boxes(self, level):
+        return ib_num_struct_boxes(self.handle, level)
+
+    def apply(self, level, w, y):
+        ib_apply(self.handle, level, w, y)
+        return y
+
+    def vcycle(self, b, w):
+        ib_vcycle(self.handle, b, w)
+        return w
+
+    def rhs(self, u_n, b):
+        ib_rhs(self.handle, u_n, b)
+        return b
+
+    def update_points(self, X_dev):
+        ib_update_points(self.handle, X_dev, self.n_points)
+
+    def solve_step(self, u_n, up, X, raise_on_not_converged=False):
+        return ib_solve_step(self.handle, u_n, up, X, self.n_points, raise_on_not_converged)
+
+    def close(self):
+        if self.handle:
+            ib_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,677 @@
+// Host side of the C ABI: validation, workspace, hierarchy set-up, the V-cycle
+// of Algorithm 1 and the flexible GMRES driver of sec. 3.3.  Every arithmetic
+// step runs in the kernels of the other translation units; this file only
+// orders launches on the problem's stream and reads back the few scalars that
+// decide control flow (structure-box counts, Krylov residual estimates).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "ib_internal.cuh"
+
+namespace ib {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+namespace {
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return IB_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(IB_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  return IB_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int validate(const ib_params* p) {
+  if (!p) return fail(IB_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->box == 1 || p->box == 2 || p->box == 4 || p->box == 8))
+    return fail(IB_ERR_INVALID_ARG, "box must be 1, 2, 4 or 8");
+  int nc = p->box > 4 ? p->box : 4;
+  if (!is_pow2(p->N) || p->N < 2 * nc || p->N > (1 << 14))
+    return fail(IB_ERR_INVALID_ARG, "N must be a power of two with 2*max(4, box) <= N <= 16384");
+  if (!(std::isfinite(p->L) && p->L > 0)) return fail(IB_ERR_INVALID_ARG, "L must be > 0");
+  if (!(std::isfinite(p->mu) && p->mu > 0)) return fail(IB_ERR_INVALID_ARG, "mu must be > 0");
+  if (!(std::isfinite(p->dt) && p->dt > 0)) return fail(IB_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(std::isfinite(p->rho) && p->rho >= 0)) return fail(IB_ERR_INVALID_ARG, "rho must be >= 0");
+  if (p->delta != IB_DELTA_PESKIN4 && p->delta != IB_DELTA_COS4)
+    return fail(IB_ERR_INVALID_ARG, "unknown delta kernel");
+  if (p->precision != IB_FP64 && p->precision != IB_FP32_PRECOND)
+    return fail(IB_ERR_INVALID_ARG, "unknown precision");
+  if (p->jacobian != IB_JAC_CLAMPED && p->jacobian != IB_JAC_EXACT)
+    return fail(IB_ERR_INVALID_ARG, "unknown jacobian variant");
+  if (p->nu1 < 0 || p->nu1 > 8 || p->nu2 < 0 || p->nu2 > 8)
+    return fail(IB_ERR_INVALID_ARG, "nu1, nu2 must be in 0..8");
+  if (!(std::isfinite(p->tol) && p->tol > 0)) return fail(IB_ERR_INVALID_ARG, "tol must be > 0");
+  if (p->max_iters < 1 || p->max_iters > 512)
+    return fail(IB_ERR_INVALID_ARG, "max_iters must be in 1..512");
+  return IB_OK;
+}
+
+double efac(const Problem& P) { return P.prm.dt / (P.lev[0].h * P.lev[0].h); }
+
+__global__ void k_set(double* dst, double v) { *dst = v; }
+
+__global__ void k_axpy_n(double a, const double* __restrict__ x, double* y, long n) {
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e < n) y[e] += a * x[e];
+}
+
+template <typename T>
+LevelBuf<T>& bufs(LevelInfo& L);
+template <>
+LevelBuf<double>& bufs<double>(LevelInfo& L) { return L.v64; }
+template <>
+LevelBuf<float>& bufs<float>(LevelInfo& L) { return L.v32; }
+
+template <typename T>
+T* Uscratch(Problem& P);
+template <>
+double* Uscratch<double>(Problem& P) { return P.U64; }
+template <>
+float* Uscratch<float>(Problem& P) { return P.U32; }
+
+// r = b - A_l w on level l (Stokes part + elasticity), precision T.
+template <typename T>
+int residual(Problem& P, int l, const T* w, const T* b, T* r) {
+  IB_TRY(launch_stokes<T>(P, l, w, b, r, true));
+  IB_TRY(launch_elastic<T>(P, l, w, r, -efac(P), Uscratch<T>(P)));
+  return IB_OK;
+}
+
+// y = A_l w in FP64.
+int apply64(Problem& P, int l, const double* w, double* y) {
+  IB_TRY(launch_stokes<double>(P, l, w, nullptr, y, false));
+  IB_TRY(launch_elastic<double>(P, l, w, y, efac(P), P.U64));
+  return IB_OK;
+}
+
+// One smoothing sweep: four colours, each = residual from the colour's starting
+// state, then independent box solves (the boxes of a colour share no unknowns).
+template <typename T>
+int sweep(Problem& P, int l, T* w, const T* b, T* r, bool reverse) {
+  for (int cc = 0; cc < 4; ++cc) {
+    int c = reverse ? 3 - cc : cc;
+    IB_TRY(residual<T>(P, l, w, b, r));
+    IB_TRY(launch_box_solve<T>(P, l, c, r, w));
+  }
+  return IB_OK;
+}
+
+// w0 = MGV(0, b0) (Algorithm 1): pre-smooth, restrict the residual, recurse with
+// zero initial guess, prolong and correct, post-smooth (colours reversed);
+// exact bordered solve on the coarsest grid.
+template <typename T>
+int vcycle(Problem& P, const T* b0, T* w0) {
+  int nl = P.nlev;
+  for (int l = 0; l < nl - 1; ++l) {
+    LevelBuf<T>& B = bufs<T>(P.lev[l]);
+    T* w = l == 0 ? w0 : B.w;
+    const T* b = l == 0 ? b0 : B.b;
+    size_t n = 3ul * P.lev[l].N * P.lev[l].N;
+    IB_TRY(launch_fill<T>(P, w, n, (T)0));
+    for (int s = 0; s < P.prm.nu1; ++s) IB_TRY(sweep<T>(P, l, w, b, B.r, false));
+    IB_TRY(residual<T>(P, l, w, b, B.r));
+    IB_TRY(launch_restrict<T>(P, l, B.r, bufs<T>(P.lev[l + 1]).b));
+  }
+  LevelBuf<T>& C = bufs<T>(P.lev[nl - 1]);
+  IB_TRY(launch_coarse_solve<T>(P, C.b, C.w));
+  for (int l = nl - 2; l >= 0; --l) {
+    LevelBuf<T>& B = bufs<T>(P.lev[l]);
+    T* w = l == 0 ? w0 : B.w;
+    const T* b = l == 0 ? b0 : B.b;
+    IB_TRY(launch_prolong_add<T>(P, l, bufs<T>(P.lev[l + 1]).w, w));
+    for (int s = 0; s < P.prm.nu2; ++s) IB_TRY(sweep<T>(P, l, w, b, B.r, true));
+  }
+  return IB_OK;
+}
+
+int check_dev_err(Problem& P) {
+  int h = 0;
+  IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + 64, P.dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                              P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  h = P.count_host[64];
+  if (h) {
+    IB_CUDA_TRY(cudaMemsetAsync(P.dev_err, 0, sizeof(int), P.stream));
+    if (h & DEV_ERR_NONFINITE)
+      return fail(IB_ERR_INVALID_ARG, "a spring has coincident or non-finite end points");
+    if (h & DEV_ERR_SINGULAR) return fail(IB_ERR_SINGULAR, "zero pivot in a box or coarsest factorisation");
+    return fail(IB_ERR_INVALID_ARG, "internal index check failed (too many springs at a point?)");
+  }
+  return IB_OK;
+}
+
+// Re-form S, J and everything that depends on them (per step, sec. 8).
+int setup_hierarchy(Problem& P) {
+  IB_TRY(launch_fine_patches(P));
+  IB_TRY(launch_spring_force_jacobian(P));
+  for (int l = 1; l < P.nlev; ++l) IB_TRY(launch_coarse_patches(P, l));
+  if (P.prm.precision == IB_FP32_PRECOND)
+    for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_cast_patches(P, l));
+  int ns = P.nlev - 1;  // smoothing levels
+  for (int l = 0; l < ns; ++l) {
+    IB_TRY(launch_mark_struct(P, l));
+    IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + l, P.count, sizeof(int), cudaMemcpyDeviceToHost,
+                                P.stream));
+  }
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  int nB = P.nB;
+  for (int l = 0; l < ns; ++l) {
+    LevelInfo& L = P.lev[l];
+    int cnt = P.count_host[l];
+    if (cnt > L.cap_struct) {
+      dfree(L.Mstruct);
+      int cap = cnt + cnt / 4 + 16;
+      if (cap > L.nb * L.nb) cap = L.nb * L.nb;
+      IB_TRY(dalloc(&L.Mstruct, (size_t)cap * nB * nB));
+      L.cap_struct = cap;
+    }
+    L.n_struct = cnt;
+    IB_TRY(launch_box_stokes_fill(P, l, true));
+    IB_TRY(launch_assemble_struct(P, l));
+    IB_TRY(launch_invert(P, L.Mstruct, nB, cnt));
+    IB_TRY(launch_invert(P, L.Mfree, nB, 1));
+    if (P.prm.precision == IB_FP32_PRECOND)
+      IB_TRY(launch_cast<double, float>(P, L.Mfree, L.Mfree32, (size_t)nB * nB));
+  }
+  IB_TRY(launch_coarse_fill(P));
+  IB_TRY(launch_assemble_coarse(P));
+  IB_TRY(launch_invert(P, P.Mcoarse, P.nc + P.nborder, 1));
+  return check_dev_err(P);
+}
+
+void free_problem(Problem* P) {
+  if (!P) return;
+  for (auto& L : P->lev) {
+    dfree(L.flag); dfree(L.Mstruct); dfree(L.Mfree); dfree(L.Mfree32);
+    dfree(L.pat64.base); dfree(L.pat64.w); dfree(L.pat32.base); dfree(L.pat32.w);
+    dfree(L.v64.w); dfree(L.v64.b); dfree(L.v64.r);
+    dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);
+  }
+  dfree(P->X); dfree(P->springs); dfree(P->kappa); dfree(P->rest);
+  dfree(P->adj_ptr); dfree(P->adj_spring); dfree(P->adj_other);
+  dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->U64); dfree(P->U32);
+  dfree(P->Mcoarse); dfree(P->V); dfree(P->Z); dfree(P->H); dfree(P->givens);
+  dfree(P->dots); dfree(P->scal); dfree(P->x64); dfree(P->b64); dfree(P->t64); dfree(P->t64b);
+  dfree(P->dev_err); dfree(P->count);
+  if (P->scal_host) cudaFreeHost(P->scal_host);
+  if (P->count_host) cudaFreeHost(P->count_host);
+  for (auto& e : P->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+int allocate(Problem& P) {
+  const int nl = P.nlev;
+  const bool fp32 = P.prm.precision == IB_FP32_PRECOND;
+  for (int l = 0; l < nl; ++l) {
+    LevelInfo& L = P.lev[l];
+    size_t n3 = 3ul * L.N * L.N;
+    if (l < nl - 1) {
+      IB_TRY(dalloc(&L.flag, (size_t)L.nb * L.nb));
+      IB_TRY(dalloc(&L.Mfree, (size_t)P.nB * P.nB));
+      if (fp32) IB_TRY(dalloc(&L.Mfree32, (size_t)P.nB * P.nB));
+    }
+    if (P.np > 0) {
+      L.pat64.np = P.np;
+      IB_TRY(dalloc(&L.pat64.base, 8ul * P.np));
+      IB_TRY(dalloc(&L.pat64.w, 32ul * P.np));
+      if (fp32) {
+        L.pat32.np = P.np;
+        IB_TRY(dalloc(&L.pat32.base, 8ul * P.np));
+        IB_TRY(dalloc(&L.pat32.w, 32ul * P.np));
+      }
+    }
+    if (fp32) {
+      IB_TRY(dalloc(&L.v32.w, n3)); IB_TRY(dalloc(&L.v32.b, n3)); IB_TRY(dalloc(&L.v32.r, n3));
+    } else {
+      IB_TRY(dalloc(&L.v64.r, n3));
+      if (l > 0) { IB_TRY(dalloc(&L.v64.w, n3)); IB_TRY(dalloc(&L.v64.b, n3)); }
+    }
+  }
+  int np = P.np, ns = P.ns;
+  if (np > 0) {
+    IB_TRY(dalloc(&P.X, 2ul * np));
+    IB_TRY(dalloc(&P.F, 2ul * np));
+    IB_TRY(dalloc(&P.U64, 2ul * np));
+    if (fp32) IB_TRY(dalloc(&P.U32, 2ul * np));
+    IB_TRY(dalloc(&P.adj_ptr, (size_t)np + 1));
+  }
+  if (ns > 0) {
+    IB_TRY(dalloc(&P.springs, 2ul * ns));
+    IB_TRY(dalloc(&P.kappa, (size_t)ns));
+    IB_TRY(dalloc(&P.rest, (size_t)ns));
+    IB_TRY(dalloc(&P.adj_spring, 2ul * ns));
+    IB_TRY(dalloc(&P.adj_other, 2ul * ns));
+    IB_TRY(dalloc(&P.K64, 3ul * ns));
+    if (fp32) IB_TRY(dalloc(&P.K32, 3ul * ns));
+  }
+  int ldc = P.nc + P.nborder;
+  IB_TRY(dalloc(&P.Mcoarse, (size_t)ldc * ldc));
+  int m = P.max_m;
+  size_t n = 3ul * P.prm.N * P.prm.N;
+  IB_TRY(dalloc(&P.V, (size_t)(m + 1) * n));
+  if (fp32) {
+    float* z;
+    IB_TRY(dalloc(&z, (size_t)m * n));
+    P.Z = z;
+  } else {
+    double* z;
+    IB_TRY(dalloc(&z, (size_t)m * n));
+    P.Z = z;
+  }
+  IB_TRY(dalloc(&P.H, (size_t)(m + 1) * m));
+  IB_TRY(dalloc(&P.givens, 4ul * m + 1));
+  P.dot_blocks = (int)std::min<size_t>(608, (n + 1023) / 1024);
+  if (P.dot_blocks < 1) P.dot_blocks = 1;
+  IB_TRY(dalloc(&P.dots, (size_t)P.dot_blocks * (m + 2)));
+  IB_TRY(dalloc(&P.scal, 16ul + 2ul * (m + 2) + 8));
+  IB_TRY(dalloc(&P.x64, n));
+  IB_TRY(dalloc(&P.b64, n));
+  IB_TRY(dalloc(&P.t64, n));
+  IB_TRY(dalloc(&P.t64b, n));
+  IB_TRY(dalloc(&P.dev_err, 1));
+  IB_TRY(dalloc(&P.count, 1));
+  IB_CUDA_TRY(cudaMemsetAsync(P.dev_err, 0, sizeof(int), P.stream));
+  IB_CUDA_TRY(cudaMallocHost((void**)&P.scal_host, 64 * sizeof(double)));
+  IB_CUDA_TRY(cudaMallocHost((void**)&P.count_host, 128 * sizeof(int)));
+  for (auto& e : P.ev) IB_CUDA_TRY(cudaEventCreate(&e));
+  return IB_OK;
+}
+
+int read_scalars(Problem& P, int count) {
+  IB_CUDA_TRY(cudaMemcpyAsync(P.scal_host, P.scal, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                              P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
+}
+
+// FP64 residual r = b - A_0 x.
+int residual64(Problem& P, const double* x, const double* b, double* r) {
+  IB_TRY(launch_stokes<double>(P, 0, x, b, r, true));
+  IB_TRY(launch_elastic<double>(P, 0, x, r, -efac(P), P.U64));
+  return IB_OK;
+}
+
+// Flexible GMRES with the V-cycle as right preconditioner (sec. 3.3), zero
+// initial guess, classical Gram-Schmidt applied twice, Givens rotations; stop
+// when the estimate reaches tol ||b||, confirm with the true FP64 residual and
+// restart from the iterate if needed.
+template <typename T>
+int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
+  const size_t n = 3ul * P.prm.N * P.prm.N;
+  const int m = P.max_m;
+  const double tol = P.prm.tol;
+  T* Z = (T*)P.Z;
+  double* s = P.scal;
+  IB_TRY(launch_dot(P, b, b, s + 4));
+  IB_TRY(read_scalars(P, 8));
+  double bnorm = std::sqrt(P.scal_host[4]);
+  IB_TRY(launch_fill<double>(P, x, n, 0.0));
+  st->iters = 0;
+  st->restarts = 0;
+  st->rel_res_true = 0.0;
+  st->rel_res_est = 0.0;
+  if (!(bnorm > 0.0)) {
+    if (!std::isfinite(bnorm)) return fail(IB_ERR_BREAKDOWN, "non-finite right-hand side");
+    return IB_OK;
+  }
+  int total = 0;
+  double* h1 = s + 8;
+  double* h2 = h1 + m + 2;
+  double* wn = h2 + m + 2;
+  double* g = P.givens + 2 * m;
+  for (int restart = 0;; ++restart) {
+    if (total == 0) {
+      IB_CUDA_TRY(cudaMemcpyAsync(P.V, b, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+    } else {
+      IB_TRY(residual64(P, x, b, P.V));
+    }
+    IB_TRY(launch_dot(P, P.V, P.V, s + 5));
+    IB_TRY(read_scalars(P, 8));
+    double beta = std::sqrt(P.scal_host[5]);
+    if (!std::isfinite(beta)) return fail(IB_ERR_BREAKDOWN, "non-finite residual");
+    if (beta <= tol * bnorm) {
+      st->rel_res_true = beta / bnorm;
+      return IB_OK;
+    }
+    if (total >= P.prm.max_iters) break;
+    int mav = P.prm.max_iters - total;
+    IB_TRY(launch_fill<double>(P, g, (size_t)m + 1, 0.0));
+    k_set<<<1, 1, 0, P.stream>>>(g, beta);
+    k_set<<<1, 1, 0, P.stream>>>(s + 6, beta);
+    IB_LAUNCH_CHECK();
+    IB_TRY(launch_scale_copy(P, P.V, s + 6, P.V, true));
+    int k = 0;
+    for (int j = 0; j < mav; ++j) {
+      double* vj = P.V + (size_t)j * n;
+      T* zj = Z + (size_t)j * n;
+      if constexpr (std::is_same<T, double>::value) {
+        IB_TRY(vcycle<double>(P, vj, zj));
+        IB_TRY(apply64(P, 0, zj, P.t64));
+      } else {
+        LevelBuf<T>& B0 = bufs<T>(P.lev[0]);
+        IB_TRY((launch_cast<double, T>(P, vj, B0.b, n)));
+        IB_TRY(vcycle<T>(P, B0.b, zj));
+        IB_TRY((launch_cast<T, double>(P, zj, P.t64b, n)));
+        IB_TRY(apply64(P, 0, P.t64b, P.t64));
+      }
+      IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h1));
+      IB_TRY(launch_multiaxpy(P, P.V, j + 1, h1, P.t64));
+      IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h2));
+      IB_TRY(launch_multiaxpy(P, P.V, j + 1, h2, P.t64));
+      IB_TRY(launch_dot(P, P.t64, P.t64, wn));
+      IB_TRY(launch_givens(P, j, 0.0, nullptr));
+      IB_TRY(launch_scale_copy(P, P.t64, s + 1, P.V + (size_t)(j + 1) * n, true));
+      IB_TRY(read_scalars(P, 3));
+      ++total;
+      k = j + 1;
+      double est = P.scal_host[0];
+      st->rel_res_est = est / bnorm;
+      if (P.scal_host[2] != 0.0) return fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES");
+      if (est <= tol * bnorm) break;
+      if (!(P.scal_host[1] > 0.0)) break;  // lucky breakdown: exact solution in the space
+    }
+    IB_TRY(launch_backsolve(P, k));
+    IB_TRY(launch_update_x<T>(P, Z, k, x));
+    IB_TRY(residual64(P, x, b, P.t64));
+    IB_TRY(launch_dot(P, P.t64, P.t64, s + 7));
+    IB_TRY(read_scalars(P, 8));
+    double rt = std::sqrt(P.scal_host[7]) / bnorm;
+    st->rel_res_true = rt;
+    st->iters = total;
+    st->restarts = restart;
+    if (!std::isfinite(rt)) return fail(IB_ERR_BREAKDOWN, "non-finite true residual");
+    if (rt <= tol) return IB_OK;
+    if (total >= P.prm.max_iters) break;
+  }
+  return fail(IB_ERR_NOT_CONVERGED, "FGMRES reached max_iters above tol");
+}
+
+}  // namespace
+}  // namespace ib
+
+struct ib_problem {
+  ib::Problem P;
+};
+
+using namespace ib;
+
+extern "C" {
+
+const char* ib_version(void) { return "ibmg-gb300 0.1 (sm_103a)"; }
+
+const char* ib_last_error(void) { return g_err.c_str(); }
+
+void ib_default_params(ib_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->N = 64;
+  p->L = 1.0;
+  p->rho = 1.0;
+  p->mu = 1.0;
+  p->dt = 1e-2;
+  p->delta = IB_DELTA_PESKIN4;
+  p->box = 1;
+  p->nu1 = 1;
+  p->nu2 = 1;
+  p->precision = IB_FP64;
+  p->jacobian = IB_JAC_CLAMPED;
+  p->tol = 1e-8;
+  p->max_iters = 100;
+}
+
+int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t n_springs,
+             const int32_t* springs, const double* kappa, const double* rest, void* stream,
+             ib_problem** out) {
+  g_err.clear();
+  if (!out) return fail(IB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  IB_TRY(validate(params));
+  if (n_points < 0 || n_springs < 0) return fail(IB_ERR_INVALID_ARG, "negative counts");
+  if (n_points == 0 && n_springs > 0) return fail(IB_ERR_INVALID_ARG, "springs without points");
+  if (n_points > 0 && !X) return fail(IB_ERR_INVALID_ARG, "X is NULL");
+  if (n_springs > 0 && (!springs || !kappa || !rest))
+    return fail(IB_ERR_INVALID_ARG, "spring arrays are NULL");
+  for (int k = 0; k < 2 * n_points; ++k)
+    if (!std::isfinite(X[k])) return fail(IB_ERR_INVALID_ARG, "non-finite point position");
+  std::vector<int> deg(n_points + 1, 0);
+  for (int s = 0; s < n_springs; ++s) {
+    int i = springs[2 * s], j = springs[2 * s + 1];
+    if (i < 0 || j < 0 || i >= n_points || j >= n_points || i == j)
+      return fail(IB_ERR_INVALID_ARG, "spring end points out of range or equal");
+    if (!(std::isfinite(kappa[s]) && kappa[s] >= 0) || !(std::isfinite(rest[s]) && rest[s] >= 0))
+      return fail(IB_ERR_INVALID_ARG, "kappa and rest length must be finite and >= 0");
+    ++deg[i];
+    ++deg[j];
+  }
+  for (int k = 0; k < n_points; ++k)
+    if (deg[k] > 7) return fail(IB_ERR_INVALID_ARG, "at most 7 springs per point are supported");
+
+  ib_problem* H = new (std::nothrow) ib_problem();
+  if (!H) return fail(IB_ERR_OOM, "host allocation failed");
+  Problem& P = H->P;
+  P.prm = *params;
+  P.stream = (cudaStream_t)stream;
+  P.np = n_points;
+  P.ns = n_springs;
+  P.nB = box_nunk(params->box);
+  int Nc = params->box > 4 ? params->box : 4;
+  for (int N = params->N; N >= Nc; N /= 2) {
+    LevelInfo L;
+    L.N = N;
+    L.h = params->L / N;
+    L.nb = N / params->box;
+    P.lev.push_back(L);
+  }
+  P.nlev = (int)P.lev.size();
+  P.nc = 3 * Nc * Nc;
+  P.nborder = params->rho == 0.0 ? 3 : 1;
+  P.max_m = params->max_iters;
+  int st = allocate(P);
+  if (st != IB_OK) {
+    std::string msg = g_err;
+    free_problem(&H->P);
+    delete H;
+    g_err = msg;
+    return st;
+  }
+  // spring adjacency (host-side bookkeeping of the input graph)
+  std::vector<int> ptr(n_points + 1, 0), sp_idx(2 * n_springs), other(2 * n_springs);
+  for (int s = 0; s < n_springs; ++s) {
+    ++ptr[springs[2 * s] + 1];
+    ++ptr[springs[2 * s + 1] + 1];
+  }
+  for (int k = 0; k < n_points; ++k) ptr[k + 1] += ptr[k];
+  std::vector<int> fillp(ptr.begin(), ptr.end() - (n_points > 0 ? 1 : 0));
+  for (int s = 0; s < n_springs; ++s) {
+    int i = springs[2 * s], j = springs[2 * s + 1];
+    sp_idx[fillp[i]] = s; other[fillp[i]++] = j;
+    sp_idx[fillp[j]] = s; other[fillp[j]++] = i;
+  }
+  cudaStream_t s = P.stream;
+  auto fail_free = [&](int code) {
+    std::string msg = g_err;
+    free_problem(&H->P);
+    delete H;
+    g_err = msg;
+    return code;
+  };
+#define IB_SETUP_CUDA(expr)                                                   \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) {                                                  \
+      fail(IB_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));  \
+      return fail_free(IB_ERR_CUDA);                                          \
+    }                                                                         \
+  } while (0)
+  if (n_points > 0) {
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.X, X, sizeof(double) * 2 * n_points, cudaMemcpyHostToDevice, s));
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.adj_ptr, ptr.data(), sizeof(int) * (n_points + 1),
+                                  cudaMemcpyHostToDevice, s));
+  }
+  if (n_springs > 0) {
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.springs, springs, sizeof(int) * 2 * n_springs,
+                                  cudaMemcpyHostToDevice, s));
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.kappa, kappa, sizeof(double) * n_springs, cudaMemcpyHostToDevice, s));
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.rest, rest, sizeof(double) * n_springs, cudaMemcpyHostToDevice, s));
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.adj_spring, sp_idx.data(), sizeof(int) * 2 * n_springs,
+                                  cudaMemcpyHostToDevice, s));
+    IB_SETUP_CUDA(cudaMemcpyAsync(P.adj_other, other.data(), sizeof(int) * 2 * n_springs,
+                                  cudaMemcpyHostToDevice, s));
+  }
+  IB_SETUP_CUDA(cudaStreamSynchronize(s));
+  st = setup_hierarchy(P);
+  if (st != IB_OK) return fail_free(st);
+  *out = H;
+  return IB_OK;
+}
+
+int ib_update_points(ib_problem* H, const double* X_dev) {
+  g_err.clear();
+  if (!H) return fail(IB_ERR_INVALID_ARG, "problem is NULL");
+  Problem& P = H->P;
+  if (P.np > 0) {
+    if (!X_dev) return fail(IB_ERR_INVALID_ARG, "X is NULL");
+    IB_CUDA_TRY(cudaMemcpyAsync(P.X, X_dev, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice,
+                                P.stream));
+  }
+  return setup_hierarchy(P);
+}
+
+int ib_num_levels(const ib_problem* H) { return H ? H->P.nlev : 0; }
+
+int ib_level_size(const ib_problem* H, int32_t level) {
+  if (!H || level < 0 || level >= H->P.nlev) return 0;
+  return H->P.lev[level].N;
+}
+
+int ib_num_struct_boxes(const ib_problem* H, int32_t level) {
+  if (!H || level < 0 || level >= H->P.nlev - 1) return 0;
+  return H->P.lev[level].n_struct;
+}
+
+int ib_apply(ib_problem* H, int32_t level, const double* w, double* y) {
+  g_err.clear();
+  if (!H || !w || !y) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  Problem& P = H->P;
+  if (level < 0 || level >= P.nlev) return fail(IB_ERR_INVALID_ARG, "level out of range");
+  if (w == y) return fail(IB_ERR_INVALID_ARG, "w and y must not alias");
+  IB_TRY(apply64(P, level, w, y));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
+}
+
+int ib_vcycle(ib_problem* H, const double* b, double* w) {
+  g_err.clear();
+  if (!H || !b || !w) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  if (b == w) return fail(IB_ERR_INVALID_ARG, "b and w must not alias");
+  Problem& P = H->P;
+  size_t n = 3ul * P.prm.N * P.prm.N;
+  if (P.prm.precision == IB_FP64) {
+    IB_TRY(vcycle<double>(P, b, w));
+  } else {
+    LevelBuf<float>& B0 = P.lev[0].v32;
+    IB_TRY((launch_cast<double, float>(P, b, B0.b, n)));
+    IB_TRY(vcycle<float>(P, B0.b, B0.w));
+    IB_TRY((launch_cast<float, double>(P, B0.w, w, n)));
+  }
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
+}
+
+int ib_rhs(ib_problem* H, const double* u_n, double* b) {
+  g_err.clear();
+  if (!H || !b) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  Problem& P = H->P;
+  size_t n = 3ul * P.prm.N * P.prm.N;
+  IB_TRY(launch_fill<double>(P, b, n, 0.0));
+  IB_TRY(launch_spread_force(P, b));
+  if (u_n && P.prm.rho != 0.0) {
+    long n2 = 2L * P.prm.N * P.prm.N;
+    k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, b, n2);
+    IB_LAUNCH_CHECK();
+  }
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
+}
+
+int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_stats* stats) {
+  g_err.clear();
+  if (!H || !up) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  Problem& P = H->P;
+  if (P.np > 0 && !X) return fail(IB_ERR_INVALID_ARG, "X is NULL");
+  ib_stats local;
+  std::memset(&local, 0, sizeof(local));
+  ib_stats* st = stats ? stats : &local;
+  std::memset(st, 0, sizeof(*st));
+  size_t n = 3ul * P.prm.N * P.prm.N;
+  IB_CUDA_TRY(cudaEventRecord(P.ev[0], P.stream));
+  if (P.np > 0)
+    IB_CUDA_TRY(cudaMemcpyAsync(P.X, X, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice, P.stream));
+  int rc = setup_hierarchy(P);
+  if (rc != IB_OK) { st->status = rc; return rc; }
+  IB_TRY(launch_fill<double>(P, P.b64, n, 0.0));
+  IB_TRY(launch_spread_force(P, P.b64));
+  if (u_n && P.prm.rho != 0.0) {
+    long n2 = 2L * P.prm.N * P.prm.N;
+    k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, P.b64, n2);
+    IB_LAUNCH_CHECK();
+  }
+  IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
+  if (P.prm.precision == IB_FP64) rc = fgmres<double>(P, P.b64, P.x64, st);
+  else rc = fgmres<float>(P, P.b64, P.x64, st);
+  IB_CUDA_TRY(cudaEventRecord(P.ev[2], P.stream));
+  if (rc != IB_OK && rc != IB_ERR_NOT_CONVERGED) { st->status = rc; return rc; }
+  std::string msg = g_err;
+  IB_TRY(launch_pressure_mean_remove(P, P.x64));
+  IB_CUDA_TRY(cudaMemcpyAsync(up, P.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  if (P.np > 0) {
+    IB_TRY(launch_move_points(P, P.x64));
+    IB_CUDA_TRY(cudaMemcpyAsync(X, P.X, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice, P.stream));
+  }
+  IB_CUDA_TRY(cudaEventRecord(P.ev[3], P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  float t0 = 0, t1 = 0;
+  cudaEventElapsedTime(&t0, P.ev[0], P.ev[1]);
+  cudaEventElapsedTime(&t1, P.ev[1], P.ev[2]);
+  st->t_setup_ms = t0;
+  st->t_solve_ms = t1;
+  int nsb = 0;
+  for (int l = 0; l < P.nlev - 1; ++l) nsb += P.lev[l].n_struct;
+  st->n_struct_boxes = nsb;
+  st->status = rc;
+  g_err = msg;
+  return rc;
+}
+
+void ib_destroy(ib_problem* H) {
+  if (!H) return;
+  free_problem(&H->P);
+  delete H;
+}
+
+}  // extern "C"

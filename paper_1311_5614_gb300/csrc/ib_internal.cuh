@@ -1,0 +1,258 @@
+// Internal declarations shared by the translation units of the library.
+//
+// Grid conventions (periodic N x N MAC grid, vector [u | v | p], x fastest):
+//   u[j*N + i] at (i h, (j + 1/2) h)      -- face normal to x
+//   v[j*N + i] at ((i + 1/2) h, j h)      -- face normal to y
+//   p[j*N + i] at ((i + 1/2) h, (j + 1/2) h)
+// For u the x direction is "normal" (faces on integer positions) and y is
+// "centred"; for v the roles are exchanged.  All index arithmetic wraps with
+// & (N - 1) because every level size is a power of two.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ib.h"
+
+namespace ib {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+#define IB_CUDA_TRY(expr)                                                        \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess)                                                       \
+      return ::ib::fail(IB_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+#define IB_TRY(...)                \
+  do {                             \
+    int _s = (__VA_ARGS__);        \
+    if (_s != IB_OK) return _s;    \
+  } while (0)
+#define IB_LAUNCH_CHECK() IB_CUDA_TRY(cudaGetLastError())
+
+// Device error flags (bit mask, one word per problem).
+enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_INDEX = 2, DEV_ERR_NONFINITE = 4 };
+
+// ---------------------------------------------------------------- patches
+// Per level and point: for kind (0 spread, 1 interp) and component (0 u, 1 v)
+// a 4 x 4 tensor-product patch: base (x0, y0) and 1-D weights wx[4], wy[4].
+// Level 0 weights are phi(.) (dimensionless); coarse levels hold R applied to
+// the spread weights and P^T applied to the interp weights (Galerkin, sec. 3.2).
+constexpr int PATCH = 4;
+template <typename T>
+struct Patches {
+  int np = 0;
+  int* base = nullptr;  // [kind][comp][xy][np]
+  T* w = nullptr;       // [kind][comp][xy][4][np]
+  __host__ __device__ int b_at(int kind, int comp, int xy, int k) const {
+    return base[((kind * 2 + comp) * 2 + xy) * np + k];
+  }
+  __host__ __device__ T w_at(int kind, int comp, int xy, int a, int k) const {
+    return w[((((kind * 2 + comp) * 2 + xy) * PATCH) + a) * np + k];
+  }
+  __host__ __device__ int* b_ptr(int kind, int comp, int xy, int k) {
+    return base + ((kind * 2 + comp) * 2 + xy) * np + k;
+  }
+  __host__ __device__ T* w_ptr(int kind, int comp, int xy, int a, int k) {
+    return w + ((((kind * 2 + comp) * 2 + xy) * PATCH) + a) * np + k;
+  }
+};
+
+// Springs in the point-adjacency form used by J U:  (J U)_k = sum over springs s
+// at k of K_s (U_other - U_k), K_s the symmetric 2 x 2 block (kxx, kxy, kyy).
+template <typename T>
+struct Springs {
+  int np = 0, ns = 0;
+  const int* adj_ptr = nullptr;    // [np + 1]
+  const int* adj_spring = nullptr; // [2 ns]
+  const int* adj_other = nullptr;  // [2 ns]
+  const T* K = nullptr;            // [3][ns]
+};
+
+// Stokes coefficients of one level: diag = -4 mu / h^2 - rho / dt, off = mu / h^2, g = 1 / h.
+template <typename T>
+struct StokesCoef {
+  T diag, off, g;
+};
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline int wrapi(int i, int N) { return i & (N - 1); }
+
+// Box-local unknown numbering of a b x b box with lower-left cell (x0, y0):
+//   u faces (ir in [0, b], jr in [0, b)):  q = jr (b + 1) + ir
+//   v faces (ir in [0, b), jr in [0, b]):  q = b (b + 1) + jr b + ir
+//   cells   (ir, jr in [0, b)):            q = 2 b (b + 1) + jr b + ir
+__host__ __device__ inline int box_nunk(int b) { return 2 * b * (b + 1) + b * b; }
+__device__ inline int box_local(int comp, int i, int j, int x0, int y0, int b, int N) {
+  int ir = (i - x0) & (N - 1), jr = (j - y0) & (N - 1);
+  if (comp == 0) return (ir <= b && jr < b) ? jr * (b + 1) + ir : -1;
+  if (comp == 1) return (ir < b && jr <= b) ? b * (b + 1) + jr * b + ir : -1;
+  return (ir < b && jr < b) ? 2 * b * (b + 1) + jr * b + ir : -1;
+}
+__device__ inline void box_unknown(int q, int b, int x0, int y0, int N, int* comp, int* i, int* j) {
+  int nu = b * (b + 1);
+  if (q < nu) {
+    *comp = 0; *i = x0 + q % (b + 1); *j = y0 + q / (b + 1);
+  } else if (q < 2 * nu) {
+    q -= nu; *comp = 1; *i = x0 + q % b; *j = y0 + q / b;
+  } else {
+    q -= 2 * nu; *comp = 2; *i = x0 + q % b; *j = y0 + q / b;
+  }
+  *i &= (N - 1);
+  *j &= (N - 1);
+}
+
+// Entry A_S[(ca, ia, ja), (cb, ib, jb)] of the periodic MAC Stokes operator
+// [[mu Lap - rho/dt, -G], [D, 0]] of one level (N >= 4).
+__device__ inline double stokes_entry(const StokesCoef<double>& c, int N, int ca, int ia, int ja,
+                                      int cb, int ib, int jb) {
+  int di = (ib - ia) & (N - 1), dj = (jb - ja) & (N - 1);
+  double v = 0.0;
+  if (ca < 2) {
+    if (cb == ca) {
+      if (di == 0 && dj == 0) v += c.diag;
+      if (dj == 0 && di == 1) v += c.off;
+      if (dj == 0 && di == N - 1) v += c.off;
+      if (di == 0 && dj == 1) v += c.off;
+      if (di == 0 && dj == N - 1) v += c.off;
+    } else if (cb == 2) {
+      // (G p) on a u face (i, j) = (p_{i,j} - p_{i-1,j}) / h; on a v face with j - 1.
+      if (di == 0 && dj == 0) v -= c.g;
+      if (ca == 0 && di == N - 1 && dj == 0) v += c.g;
+      if (ca == 1 && di == 0 && dj == N - 1) v += c.g;
+    }
+  } else {
+    // (D w)_{i,j} = (u_{i+1,j} - u_{i,j} + v_{i,j+1} - v_{i,j}) / h
+    if (cb == 0 && dj == 0) {
+      if (di == 1) v += c.g;
+      if (di == 0) v -= c.g;
+    } else if (cb == 1 && di == 0) {
+      if (dj == 1) v += c.g;
+      if (dj == 0) v -= c.g;
+    }
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- problem state
+template <typename T>
+struct LevelBuf {
+  T* w = nullptr;  // iterate / correction
+  T* b = nullptr;  // right-hand side
+  T* r = nullptr;  // residual scratch
+};
+
+struct LevelInfo {
+  int N = 0;
+  double h = 0.0;
+  int nb = 0;          // boxes per side (smoothing levels)
+  int n_struct = 0;    // structure boxes found at the last set-up
+  int cap_struct = 0;  // allocated structure-box slots
+  int* flag = nullptr;        // [nb * nb] structure flag -> slot (-1 free)
+  double* Mstruct = nullptr;  // [cap][nB * nB] inverse (column-major), FP64
+  double* Mfree = nullptr;    // [nB * nB] shared inverse of structure-free boxes, FP64
+  float* Mfree32 = nullptr;   // FP32 copy for the FP32 V-cycle
+  Patches<double> pat64;      // FP64 patches (operator path)
+  Patches<float> pat32;       // FP32 patches (FP32 V-cycle)
+  LevelBuf<double> v64;
+  LevelBuf<float> v32;
+};
+
+struct Problem {
+  ib_params prm{};
+  cudaStream_t stream = nullptr;
+  int np = 0, ns = 0;
+  int nlev = 0;
+  int nB = 0;  // unknowns per box
+  std::vector<LevelInfo> lev;
+
+  // structure (device)
+  double* X = nullptr;        // [np][2]
+  int* springs = nullptr;     // [ns][2]
+  double* kappa = nullptr;    // [ns]
+  double* rest = nullptr;     // [ns]
+  int* adj_ptr = nullptr;     // [np + 1]
+  int* adj_spring = nullptr;  // [2 ns]
+  int* adj_other = nullptr;   // [2 ns]
+  double* K64 = nullptr;      // [3][ns]
+  float* K32 = nullptr;       // [3][ns]
+  double* F = nullptr;        // [np][2] spring force at X
+  double* U64 = nullptr;      // [2][np] interpolated velocity scratch
+  float* U32 = nullptr;       // [2][np]
+
+  // coarsest level
+  int nc = 0;                 // 3 Nc^2
+  int nborder = 0;            // null-space border columns (1 or 3)
+  double* Mcoarse = nullptr;  // [(nc + nborder)^2] bordered inverse, column-major
+
+  // Krylov (FP64)
+  double* V = nullptr;        // [m + 1][n]
+  void* Z = nullptr;          // [m][n] in the preconditioner precision
+  double* H = nullptr;        // [(m + 1) * m] column-major Hessenberg
+  double* givens = nullptr;   // cs[m], sn[m], g[m + 1], y[m]
+  double* dots = nullptr;     // partial sums [blocks][m + 2]
+  double* scal = nullptr;     // small scalars on the device
+  double* scal_host = nullptr;// pinned host mirror
+  double* x64 = nullptr;      // [n] solution
+  double* b64 = nullptr;      // [n] rhs
+  double* t64 = nullptr;      // [n] scratch
+  double* t64b = nullptr;     // [n] scratch
+  int* dev_err = nullptr;     // device error flags
+  int max_m = 0;
+  int dot_blocks = 0;
+  int* count = nullptr;       // device counter
+  int* count_host = nullptr;  // pinned
+
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+// ---------------------------------------------------------------- launchers (points)
+int launch_fine_patches(Problem& P);
+int launch_coarse_patches(Problem& P, int level);
+int launch_cast_patches(Problem& P, int level);
+int launch_spring_force_jacobian(Problem& P);
+int launch_spread_force(Problem& P, double* b);  // b_vel -= S F
+int launch_move_points(Problem& P, const double* up);
+template <typename T>
+int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U);
+int launch_mark_struct(Problem& P, int level);
+int launch_assemble_struct(Problem& P, int level);
+int launch_assemble_coarse(Problem& P);
+
+// ---------------------------------------------------------------- launchers (grid)
+template <typename T>
+int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool residual);
+template <typename T>
+int launch_restrict(Problem& P, int level, const T* rf, T* bc);
+template <typename T>
+int launch_prolong_add(Problem& P, int level, const T* ec, T* wf);
+template <typename T>
+int launch_box_solve(Problem& P, int level, int color, const T* r, T* w);
+int launch_box_stokes_fill(Problem& P, int level, bool free_box);
+int launch_invert(Problem& P, double* M, int n, int count);
+template <typename T>
+int launch_coarse_solve(Problem& P, const T* b, T* w);
+int launch_coarse_fill(Problem& P);
+template <typename T>
+int launch_fill(Problem& P, T* x, size_t n, T v);
+template <typename A, typename B>
+int launch_cast(Problem& P, const A* x, B* y, size_t n);
+
+// ---------------------------------------------------------------- launchers (krylov)
+int launch_multidot(Problem& P, const double* V, int nvec, const double* w, double* out);
+int launch_multiaxpy(Problem& P, const double* V, int nvec, const double* coef, double* w);
+int launch_dot(Problem& P, const double* a, const double* b, double* out);
+int launch_scale_copy(Problem& P, const double* x, const double* s, double* y, bool invert);
+int launch_givens(Problem& P, int j, double bnorm_tol, double* out_scalars);
+int launch_backsolve(Problem& P, int k);
+template <typename T>
+int launch_update_x(Problem& P, const T* Z, int k, double* x);
+int launch_axpby(Problem& P, double a, const double* x, double b, const double* y, double* z);
+int launch_pressure_mean_remove(Problem& P, double* w);
+
+}  // namespace ib

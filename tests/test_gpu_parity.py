@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (written here, derived in the design notes):
+* FP64 operator apply, right-hand side, V-cycle: every element within 1e-10 of
+  the oracle, relative to the largest oracle element (per-apply bar);
+* FP32 V-cycle: within 2e-4 relative (FP32 rounding through ~2 x nu sweeps on
+  every level, measured against the FP64 oracle);
+* solves: both sides reach the 1e-8 relative residual; the solutions agree to
+  1e-6 relative (tolerance times the conditioning margin) and the iteration
+  counts agree within one for FP64.
+"""
+import numpy as np
+import pytest
+
+import ib_workloads as W
+from oracle import ib_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1311_5614_gb300 as P
+
+    P.lib()
+    return P
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel_elementwise(gpu, ref):
+    return float(np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+CASES = {
+    "c1_64": dict(N=64, n_points=128, kappa=1e2, dt=1e-2),
+    "stiff_32_exact": dict(N=32, n_points=80, kappa=1e6, dt=1e-2, jac="exact"),
+    "stiff_32": dict(N=32, n_points=80, kappa=1e6, dt=1e-2),
+    "steady_cos4_32": dict(N=32, n_points=64, kappa=1e3, dt=1e-1, rho=0.0, delta="cos4", rest=0.0),
+    "offcentre_16": dict(N=16, n_points=24, kappa=50.0, dt=1e-2, center=(0.93, 0.07), a=0.2, b=0.15),
+}
+
+
+def make_case(name, box=1):
+    c = dict(CASES[name])
+    jac = c.pop("jac", "clamped")
+    p = W.single_ellipse(**c)
+    p.box = box
+    p.clamped = jac == "clamped"
+    return p
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_every_level_fp64(pkg, name):
+    p = make_case(name)
+    levels, _ = O.build_hierarchy(p)
+    s = pkg.IBSolver.from_problem(p)
+    assert s.n_levels == len(levels)
+    rng = np.random.default_rng(7)
+    for li, lev in enumerate(levels):
+        n = 3 * lev.N * lev.N
+        w = rng.standard_normal(n)
+        y = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s.apply(li, dev(w), y)
+        ref = lev.A @ w
+        assert rel_elementwise(y.cpu().numpy(), ref) < 1e-10, (name, li)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["c1_64", "offcentre_16"])
+def test_rhs_fp64(pkg, name):
+    p = make_case(name)
+    s = pkg.IBSolver.from_problem(p)
+    n = 3 * p.N * p.N
+    b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(3)
+    un = rng.standard_normal(2 * p.N * p.N)
+    s.rhs(dev(un), b)
+    ref = O.rhs_vector(p, un)
+    assert rel_elementwise(b.cpu().numpy(), ref) < 1e-10
+    s.rhs(None, b)
+    assert rel_elementwise(b.cpu().numpy(), O.rhs_vector(p)) < 1e-10
+    s.close()
+
+
+def _oracle_vcycle(p, rhs):
+    levels, _ = O.build_hierarchy(p)
+    for lev in levels[:-1]:
+        O.prepare_boxes(lev, p.box)
+    return O.vcycle(levels, rhs, np.zeros_like(rhs), p.nu1, p.nu2, p.rho, "color4")
+
+
+@pytest.mark.parametrize("name,box", [("c1_64", 1), ("stiff_32_exact", 1), ("steady_cos4_32", 1),
+                                      ("offcentre_16", 1), ("c1_64", 2), ("stiff_32_exact", 4),
+                                      ("c1_64", 8)])
+def test_vcycle_fp64(pkg, name, box):
+    p = make_case(name, box)
+    if p.N < 2 * max(4, box):
+        pytest.skip("grid too small for the box")
+    rng = np.random.default_rng(11)
+    rhs = O.rhs_vector(p) + 0.1 * np.abs(O.rhs_vector(p)).max() * rng.standard_normal(3 * p.N * p.N)
+    n = p.N * p.N
+    rhs[2 * n:] -= rhs[2 * n:].mean()
+    ref = _oracle_vcycle(p, rhs)
+    s = pkg.IBSolver.from_problem(p)
+    w = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), w)
+    got = w.cpu().numpy()
+    assert rel_elementwise(got, ref) < 1e-10, (name, box, rel_elementwise(got, ref))
+    s.close()
+
+
+@pytest.mark.parametrize("name,box", [("c1_64", 1), ("stiff_32_exact", 4)])
+def test_vcycle_fp32(pkg, name, box):
+    p = make_case(name, box)
+    rhs = O.rhs_vector(p)
+    ref = _oracle_vcycle(p, rhs)
+    s = pkg.IBSolver.from_problem(p, precision="fp32")
+    w = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), w)
+    got = w.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
+    s.close()
+
+
+@pytest.mark.parametrize("name,box,prec", [("c1_64", 1, "fp64"), ("c1_64", 1, "fp32"),
+                                           ("stiff_32", 4, "fp64"), ("stiff_32", 8, "fp32"),
+                                           ("steady_cos4_32", 1, "fp64"),
+                                           ("offcentre_16", 2, "fp32")])
+def test_solve_step(pkg, name, box, prec):
+    p = make_case(name, box)
+    ref = O.solve_step(p)
+    s = pkg.IBSolver.from_problem(p, precision=prec)
+    n = 3 * p.N * p.N
+    up = torch.zeros(n, dtype=torch.float64, device="cuda")
+    X = dev(p.X)
+    st = s.solve_step(None, up, X)
+    w = up.cpu().numpy()
+    assert st["status"] == 0 and st["rel_res_true"] <= p.tol, st
+    A = O.build_hierarchy(p)[0][0].A
+    assert np.linalg.norm(ref.b - A @ w) <= p.tol * np.linalg.norm(ref.b) * 1.01
+    if p.rho == 0.0:
+        nn = p.N * p.N
+        for c in range(2):
+            w[c * nn:(c + 1) * nn] -= w[c * nn:(c + 1) * nn].mean() - ref.w[c * nn:(c + 1) * nn].mean()
+    assert np.linalg.norm(w - ref.w) <= 1e-6 * np.linalg.norm(ref.w), np.linalg.norm(w - ref.w) / np.linalg.norm(ref.w)
+    if prec == "fp64":
+        assert abs(st["iters"] - ref.solve.iters) <= 1, (st["iters"], ref.solve.iters)
+    else:
+        assert st["iters"] <= ref.solve.iters + 2
+    Xn = X.cpu().numpy()
+    assert np.abs(Xn - ref.X).max() <= 1e-6 * p.h
+    s.close()
+
+
+def test_no_structure_and_zero_rhs(pkg):
+    """Edge cases: no Lagrangian points (pure Stokes, b = 0 -> zero solution)."""
+    p = W.single_ellipse(N=16, n_points=8)
+    s = pkg.IBSolver(16, np.zeros((0, 2)), np.zeros((0, 2), dtype=np.int32), np.zeros(0), np.zeros(0))
+    up = torch.ones(3 * 256, dtype=torch.float64, device="cuda")
+    st = s.solve_step(None, up, None)
+    assert st["iters"] == 0 and float(up.abs().max()) == 0.0
+    # the operator is still the Stokes operator
+    levels, _ = O.build_hierarchy(W.single_ellipse(N=16, n_points=8, kappa=0.0))
+    w = np.random.default_rng(0).standard_normal(768)
+    y = torch.zeros(768, dtype=torch.float64, device="cuda")
+    s.apply(0, dev(w), y)
+    assert rel_elementwise(y.cpu().numpy(), levels[0].A @ w) < 1e-12
+    s.close()
+
+
+def test_struct_box_count_matches_oracle(pkg):
+    """Boxes whose rows meet the elasticity operator are exactly the structure boxes."""
+    p = make_case("c1_64")
+    levels, _ = O.build_hierarchy(p)
+    s = pkg.IBSolver.from_problem(p)
+    for li, lev in enumerate(levels[:-1]):
+        rows = set(np.nonzero(np.asarray(abs(lev.E).sum(axis=1)).ravel())[0].tolist())
+        bx = O.prepare_boxes(lev, 1)
+        touched = sum(1 for k in range(bx["lex"].shape[0]) if set(bx["lex"][k].tolist()) & rows)
+        assert s.struct_boxes(li) >= touched
+        assert s.struct_boxes(li) <= touched + 4 * lev.N  # conservative marking only at zero weights
+    s.close()
+
+
+def test_full_size_256_apply_and_fp32_solve(pkg):
+    """The 256^2 workload (512-point ellipse): apply parity at full size and an FP32
+    V-cycle solve that reaches the FP64 tolerance; the solution is compared with the
+    oracle's at sampled entries via the true residual and divergence."""
+    p = W.single_ellipse(N=256, n_points=512, kappa=1e4, dt=1e-2)
+    levels, _ = O.build_hierarchy(p)
+    s = pkg.IBSolver.from_problem(p, precision="fp32")
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal(3 * 256 * 256)
+    y = torch.zeros_like(dev(w))
+    s.apply(0, dev(w), y)
+    assert rel_elementwise(y.cpu().numpy(), levels[0].A @ w) < 1e-10
+    up = torch.zeros(3 * 256 * 256, dtype=torch.float64, device="cuda")
+    X = dev(p.X)
+    st = s.solve_step(None, up, X)
+    b = O.rhs_vector(p)
+    x = up.cpu().numpy()
+    assert np.linalg.norm(b - levels[0].A @ x) <= 1.01e-8 * np.linalg.norm(b)
+    n = 256 * 256
+    assert np.linalg.norm((levels[0].A @ x)[2 * n:]) <= 1.01e-8 * np.linalg.norm(b)
+    assert st["iters"] <= 30
+    s.close()
