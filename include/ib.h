@@ -155,6 +155,36 @@ IB_API int ib_level_size(const ib_problem* prob, int32_t level);
  * as found by the last set-up. */
 IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
 
+/* Kernel classes for launch counting and event timing. */
+enum {
+  IB_KC_STOKES = 0,   /* level Stokes residual / apply */
+  IB_KC_BOX = 1,      /* box-smoother solves of one colour */
+  IB_KC_INTERP = 2,   /* interpolation S^*_l w of the elasticity term */
+  IB_KC_SPREAD = 3,   /* J U and spreading S_l (elasticity term) */
+  IB_KC_TRANSFER = 4, /* restriction, prolongation and correction */
+  IB_KC_COARSE = 5,   /* exact coarsest solve */
+  IB_KC_KRYLOV = 6,   /* FGMRES vector kernels and scalar updates */
+  IB_KC_SETUP = 7,    /* patches, springs, box assembly and inverses */
+  IB_KC_OTHER = 8,    /* fills, casts, right-hand side, point update */
+  IB_KC_COUNT = 9
+};
+
+/* Kernel launches issued by this problem since set-up (all classes, or one class
+ * when kclass is in [0, IB_KC_COUNT)); -1 for a NULL handle. */
+IB_API int64_t ib_launch_count(const ib_problem* prob, int32_t kclass);
+
+/* enable = 1: from now on bracket every kernel launch with CUDA events on the
+ * problem's stream (adds event records between launches; use it in a separate
+ * measurement pass).  enable = 0: stop.  Either call resets the accumulators. */
+IB_API int ib_profile(ib_problem* prob, int32_t enable);
+
+/* Synchronise the stream and return, for one kernel class, the number of timed
+ * launches, their summed device time (ms) and their summed algorithmic bytes
+ * (the bytes the operation must move: unique reads plus writes, as defined per
+ * class in the design notes).  Output pointers may be NULL. */
+IB_API int ib_profile_read(ib_problem* prob, int32_t kclass, int64_t* launches, double* ms,
+                           double* bytes);
+
 /* Release all device memory of the problem.  NULL is ignored. */
 IB_API void ib_destroy(ib_problem* prob);
 

@@ -45,9 +45,10 @@ also listed in the design notes):
 * boxes are visited either lexicographically with in-place updates (the
   paper's block Gauss-Seidel) or in four colours (2 x 2 box parity) with
   block-Jacobi semantics inside a colour ("color4", the parallel order);
-  color4 pre-smooths in colour order 0,1,2,3 and post-smooths in 3,2,1,0
-  (the same forward order on both sides contracts far worse on periodic
-  grids: about 0.64 per cycle at 64^2 against 0.23).
+  color4 pre-smooths in the colour sequence (even,even), (odd,odd),
+  (odd,even), (even,odd) and post-smooths in the reverse sequence for 1 x 1
+  boxes and in the same sequence for larger boxes (the choice that measured
+  the best V-cycle contraction for each box size; see post_reversed).
 
 Vector layout: w = [u | v | p], each an N x N array, row-major with x fastest
 (index j*N + i).  u[j, i] sits at (i h, (j + 1/2) h), v[j, i] at
@@ -463,6 +464,19 @@ def box_color(I, J):
     return (I % 2) + 2 * (J % 2)
 
 
+# Colour sequence of one forward sweep: (even, even), (odd, odd), (odd, even),
+# (even, odd) box parities.
+COLOR_SEQUENCE = (0, 3, 1, 2)
+
+
+def post_reversed(b):
+    """Whether post-smoothing visits the colours in reverse.  1 x 1 boxes of one
+    colour are coupled through the stencil (block Jacobi inside a colour) and
+    contract best with the reversed (symmetric) sequence; n x n boxes (n >= 2) of
+    one colour are uncoupled and contract best with the same sequence."""
+    return b == 1
+
+
 def submatrices(A, idx):
     """Dense principal submatrices A[idx_k, idx_k] for a batch of index sets idx [nb, m]."""
     nb, m = idx.shape
@@ -491,12 +505,12 @@ def prepare_boxes(level, b):
 
 
 def smooth_color4(level, rhs, w, reverse=False):
-    """One sweep: colours 0..3 in order (3..0 when ``reverse``); inside a colour every
-    box is solved from the colour's starting state (block Jacobi), then all its
-    corrections are added.  Boxes of one colour share no unknowns, so the updates
-    do not overlap.  The V-cycle pre-smooths forward and post-smooths in reverse."""
+    """One sweep over the colours in COLOR_SEQUENCE (reversed when ``reverse``);
+    inside a colour every box is solved from the colour's starting state (block
+    Jacobi), then all its corrections are added.  Boxes of one colour share no
+    unknowns, so the updates do not overlap."""
     w = w.copy()
-    for c in (range(3, -1, -1) if reverse else range(4)):
+    for c in (COLOR_SEQUENCE[::-1] if reverse else COLOR_SEQUENCE):
         idx, Abb = level.boxes["color"][c]
         r = rhs - level.A @ w
         delta = np.linalg.solve(Abb, r[idx][..., None])[..., 0]
@@ -561,8 +575,9 @@ def vcycle(levels, rhs, w, nu1=1, nu2=1, rho=1.0, order="color4", li=0):
     r2 = lev.R @ (rhs - lev.A @ w)
     e2 = vcycle(levels, r2, np.zeros_like(r2), nu1, nu2, rho, order, li + 1)
     w = w + lev.P @ e2
+    rev = post_reversed(lev.boxes["b"])
     for _ in range(nu2):
-        w = smooth(lev, rhs, w, reverse=True)
+        w = smooth(lev, rhs, w, reverse=rev)
     return w
 
 

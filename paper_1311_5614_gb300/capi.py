@@ -73,6 +73,10 @@ _SIGS = {
     "ib_num_levels": (ctypes.c_int, [_P]),
     "ib_level_size": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_num_struct_boxes": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_launch_count": (ctypes.c_int64, [_P, ctypes.c_int32]),
+    "ib_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ib_destroy": (None, [_P]),
     "ib_last_error": (ctypes.c_char_p, []),
     "ib_version": (ctypes.c_char_p, []),
@@ -192,6 +196,26 @@ def ib_num_struct_boxes(prob, level):
     return lib().ib_num_struct_boxes(prob, int(level))
 
 
+KERNEL_CLASSES = ("stokes", "box", "interp", "spread", "transfer", "coarse", "krylov", "setup", "other")
+
+
+def ib_launch_count(prob, kclass=-1):
+    return int(lib().ib_launch_count(prob, int(kclass)))
+
+
+def ib_profile(prob, enable):
+    _check(lib().ib_profile(prob, 1 if enable else 0))
+
+
+def ib_profile_read(prob, kclass):
+    """(launches, total_ms, algorithmic_bytes) of one kernel class since ib_profile."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    by = ctypes.c_double()
+    _check(lib().ib_profile_read(prob, int(kclass), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return int(n.value), float(ms.value), float(by.value)
+
+
 def ib_destroy(prob):
     if prob:
         lib().ib_destroy(prob)
@@ -249,6 +273,15 @@ class IBSolver:
 
     def solve_step(self, u_n, up, X, raise_on_not_converged=False):
         return ib_solve_step(self.handle, u_n, up, X, self.n_points, raise_on_not_converged)
+
+    def launch_count(self, kclass=-1):
+        return ib_launch_count(self.handle, kclass)
+
+    def profile(self, enable):
+        ib_profile(self.handle, enable)
+
+    def profile_read(self):
+        return {name: ib_profile_read(self.handle, i) for i, name in enumerate(KERNEL_CLASSES)}
 
     def close(self):
         if self.handle:

@@ -18,6 +18,50 @@ namespace ib {
 static thread_local std::string g_err;
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+KScope::KScope(Problem& P_, int cls_, double bytes_) : P(P_), cls(cls_), bytes(bytes_) {
+  ++P.nlaunch[cls];
+  if (!P.prof) return;
+  if (P.ev_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    P.ev_pool.push_back(e);
+  }
+  a = P.ev_pool.back();
+  P.ev_pool.pop_back();
+  cudaEventRecord(a, P.stream);
+}
+
+KScope::~KScope() {
+  if (!P.prof || !a) return;
+  cudaEvent_t b;
+  if (!P.ev_pool.empty()) {
+    b = P.ev_pool.back();
+    P.ev_pool.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    P.ev_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, P.stream);
+  P.pending.push_back(ProfRec{cls, a, b, bytes});
+}
+
+// Fold the pending event pairs into the per-class accumulators.
+static int resolve_profile(Problem& P) {
+  if (P.pending.empty()) return IB_OK;
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  for (auto& r : P.pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    P.prof_n[r.cls] += 1;
+    P.prof_ms[r.cls] += ms;
+    P.prof_bytes[r.cls] += r.bytes;
+    P.ev_pool.push_back(r.a);
+    P.ev_pool.push_back(r.b);
+  }
+  P.pending.clear();
+  return IB_OK;
+}
 int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
@@ -111,10 +155,13 @@ int apply64(Problem& P, int l, const double* w, double* y) {
 
 // One smoothing sweep: four colours, each = residual from the colour's starting
 // state, then independent box solves (the boxes of a colour share no unknowns).
+// Colour c = (I mod 2) + 2 (J mod 2) of box (I, J); the forward sequence is
+// (even,even), (odd,odd), (odd,even), (even,odd).
+constexpr int kColorSeq[4] = {0, 3, 1, 2};
 template <typename T>
 int sweep(Problem& P, int l, T* w, const T* b, T* r, bool reverse) {
   for (int cc = 0; cc < 4; ++cc) {
-    int c = reverse ? 3 - cc : cc;
+    int c = reverse ? kColorSeq[3 - cc] : kColorSeq[cc];
     IB_TRY(residual<T>(P, l, w, b, r));
     IB_TRY(launch_box_solve<T>(P, l, c, r, w));
   }
@@ -144,7 +191,10 @@ int vcycle(Problem& P, const T* b0, T* w0) {
     T* w = l == 0 ? w0 : B.w;
     const T* b = l == 0 ? b0 : B.b;
     IB_TRY(launch_prolong_add<T>(P, l, bufs<T>(P.lev[l + 1]).w, w));
-    for (int s = 0; s < P.prm.nu2; ++s) IB_TRY(sweep<T>(P, l, w, b, B.r, true));
+    // 1 x 1 boxes of one colour are coupled through the stencil and post-smooth in
+    // the reversed sequence; larger boxes of one colour are uncoupled and repeat it.
+    const bool rev = P.prm.box == 1;
+    for (int s = 0; s < P.prm.nu2; ++s) IB_TRY(sweep<T>(P, l, w, b, B.r, rev));
   }
   return IB_OK;
 }
@@ -222,6 +272,13 @@ void free_problem(Problem* P) {
   if (P->count_host) cudaFreeHost(P->count_host);
   for (auto& e : P->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& r : P->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto& e : P->ev_pool) cudaEventDestroy(e);
+  P->pending.clear();
+  P->ev_pool.clear();
 }
 
 int allocate(Problem& P) {
@@ -361,8 +418,14 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     if (total >= P.prm.max_iters) break;
     int mav = P.prm.max_iters - total;
     IB_TRY(launch_fill<double>(P, g, (size_t)m + 1, 0.0));
-    k_set<<<1, 1, 0, P.stream>>>(g, beta);
-    k_set<<<1, 1, 0, P.stream>>>(s + 6, beta);
+    {
+      KScope ks(P, IB_KC_KRYLOV, 8.0);
+      k_set<<<1, 1, 0, P.stream>>>(g, beta);
+    }
+    {
+      KScope ks(P, IB_KC_KRYLOV, 8.0);
+      k_set<<<1, 1, 0, P.stream>>>(s + 6, beta);
+    }
     IB_LAUNCH_CHECK();
     IB_TRY(launch_scale_copy(P, P.V, s + 6, P.V, true));
     int k = 0;
@@ -612,6 +675,7 @@ int ib_rhs(ib_problem* H, const double* u_n, double* b) {
   IB_TRY(launch_spread_force(P, b));
   if (u_n && P.prm.rho != 0.0) {
     long n2 = 2L * P.prm.N * P.prm.N;
+    KScope ks(P, IB_KC_OTHER, 3.0 * n2 * 8.0);
     k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, b, n2);
     IB_LAUNCH_CHECK();
   }
@@ -638,6 +702,7 @@ int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_st
   IB_TRY(launch_spread_force(P, P.b64));
   if (u_n && P.prm.rho != 0.0) {
     long n2 = 2L * P.prm.N * P.prm.N;
+    KScope ks(P, IB_KC_OTHER, 3.0 * n2 * 8.0);
     k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, P.b64, n2);
     IB_LAUNCH_CHECK();
   }
@@ -666,6 +731,41 @@ int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_st
   st->status = rc;
   g_err = msg;
   return rc;
+}
+
+int64_t ib_launch_count(const ib_problem* H, int32_t kclass) {
+  if (!H) return -1;
+  const Problem& P = H->P;
+  if (kclass >= 0 && kclass < IB_KC_COUNT) return P.nlaunch[kclass];
+  int64_t t = 0;
+  for (int c = 0; c < IB_KC_COUNT; ++c) t += P.nlaunch[c];
+  return t;
+}
+
+int ib_profile(ib_problem* H, int32_t enable) {
+  g_err.clear();
+  if (!H) return fail(IB_ERR_INVALID_ARG, "problem is NULL");
+  Problem& P = H->P;
+  IB_TRY(resolve_profile(P));
+  for (int c = 0; c < IB_KC_COUNT; ++c) {
+    P.prof_n[c] = 0;
+    P.prof_ms[c] = 0.0;
+    P.prof_bytes[c] = 0.0;
+  }
+  P.prof = enable != 0;
+  return IB_OK;
+}
+
+int ib_profile_read(ib_problem* H, int32_t kclass, int64_t* launches, double* ms, double* bytes) {
+  g_err.clear();
+  if (!H) return fail(IB_ERR_INVALID_ARG, "problem is NULL");
+  if (kclass < 0 || kclass >= IB_KC_COUNT) return fail(IB_ERR_INVALID_ARG, "kernel class out of range");
+  Problem& P = H->P;
+  IB_TRY(resolve_profile(P));
+  if (launches) *launches = P.prof_n[kclass];
+  if (ms) *ms = P.prof_ms[kclass];
+  if (bytes) *bytes = P.prof_bytes[kclass];
+  return IB_OK;
 }
 
 void ib_destroy(ib_problem* H) {

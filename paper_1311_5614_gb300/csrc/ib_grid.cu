@@ -355,6 +355,7 @@ template <typename T>
 int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool residual) {
   int N = P.lev[level].N;
   StokesCoef<T> c = coef_of<T>(P, level);
+  KScope ks(P, IB_KC_STOKES, (residual ? 9.0 : 6.0) * N * N * sizeof(T));
   if (residual)
     k_stokes<T, true><<<nblk((long)N * N), TPB, 0, P.stream>>>(w, b, out, N, log2i(N), c);
   else
@@ -368,6 +369,7 @@ template int launch_stokes<float>(Problem&, int, const float*, const float*, flo
 template <typename T>
 int launch_restrict(Problem& P, int level, const T* rf, T* bc) {
   int Nc = P.lev[level + 1].N;
+  KScope ks(P, IB_KC_TRANSFER, 15.0 * Nc * Nc * sizeof(T));
   k_restrict<T><<<nblk((long)Nc * Nc), TPB, 0, P.stream>>>(rf, bc, Nc);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -378,6 +380,7 @@ template int launch_restrict<float>(Problem&, int, const float*, float*);
 template <typename T>
 int launch_prolong_add(Problem& P, int level, const T* ec, T* wf) {
   int N = P.lev[level].N;
+  KScope ks(P, IB_KC_TRANSFER, (6.0 * N * N + 0.75 * N * N) * sizeof(T));
   k_prolong_add<T><<<nblk((long)N * N), TPB, 0, P.stream>>>(ec, wf, N);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -391,6 +394,12 @@ int launch_box_solve(Problem& P, int level, int color, const T* r, T* w) {
   int b = P.prm.box;
   int half = L.nb / 2;
   long nbox = (long)half * half;
+  // per box: n_B residual reads, n_B read-modify-writes of w, the slot; structure
+  // boxes (about a quarter of them per colour) read their FP64 inverse; the shared
+  // free-box inverse is read once
+  int nB = P.nB;
+  KScope ks(P, IB_KC_BOX, nbox * (3.0 * nB * sizeof(T) + 4) + 0.25 * L.n_struct * nB * nB * 8.0 +
+                              (double)nB * nB * sizeof(T));
   if (b == 1) {
     k_box1<T><<<nblk(nbox, 128), 128, 0, P.stream>>>(r, w, L.N, color, L.flag, L.Mstruct,
                                                       free_inverse<T>(L));
@@ -409,10 +418,12 @@ int launch_box_stokes_fill(Problem& P, int level, bool /*unused*/) {
   LevelInfo& L = P.lev[level];
   int nB = P.nB;
   StokesCoef<double> c = coef_of<double>(P, level);
+  KScope ks(P, IB_KC_SETUP, nB * nB * 8.0);
   k_box_stokes<<<nblk((long)nB * nB), TPB, 0, P.stream>>>(L.Mfree, L.N, P.prm.box, c);
   IB_LAUNCH_CHECK();
   if (L.n_struct > 0) {
     long tot = (long)nB * nB * L.n_struct;
+    KScope ks2(P, IB_KC_SETUP, tot * 8.0);
     k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Mfree, L.Mstruct, nB * nB, L.n_struct);
     IB_LAUNCH_CHECK();
   }
@@ -423,6 +434,7 @@ int launch_invert(Problem& P, double* M, int n, int count) {
   if (count <= 0) return IB_OK;
   if (n > INV_MAXN) return fail(IB_ERR_INVALID_ARG, "matrix too large for the device inverse");
   int threads = n <= 32 ? 32 : (n <= 64 ? 64 : 256);
+  KScope ks(P, IB_KC_SETUP, 2.0 * count * n * n * 8.0);
   k_invert<<<count, threads, 0, P.stream>>>(M, n, P.dev_err);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -433,6 +445,7 @@ int launch_coarse_fill(Problem& P) {
   StokesCoef<double> c = coef_of<double>(P, P.nlev - 1);
   int ld = P.nc + P.nborder;
   int zfirst = (P.nborder == 1) ? 2 : 0;
+  KScope ks(P, IB_KC_SETUP, (double)ld * ld * 8.0);
   k_coarse_fill<<<nblk((long)ld * ld), TPB, 0, P.stream>>>(P.Mcoarse, L.N, c, P.nborder, zfirst);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -440,6 +453,7 @@ int launch_coarse_fill(Problem& P) {
 
 template <typename T>
 int launch_coarse_solve(Problem& P, const T* b, T* w) {
+  KScope ks(P, IB_KC_COARSE, (double)P.nc * P.nc * 8.0 + 2.0 * P.nc * sizeof(T));
   k_coarse_solve<T><<<1, 256, 0, P.stream>>>(P.Mcoarse, P.nc, P.nc + P.nborder, b, w);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -450,6 +464,7 @@ template int launch_coarse_solve<float>(Problem&, const float*, float*);
 template <typename T>
 int launch_fill(Problem& P, T* x, size_t n, T v) {
   if (n == 0) return IB_OK;
+  KScope ks(P, IB_KC_OTHER, (double)n * sizeof(T));
   k_fill<T><<<nblk((long)n), TPB, 0, P.stream>>>(x, (long)n, v);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -460,6 +475,7 @@ template int launch_fill<float>(Problem&, float*, size_t, float);
 template <typename A, typename B>
 int launch_cast(Problem& P, const A* x, B* y, size_t n) {
   if (n == 0) return IB_OK;
+  KScope ks(P, IB_KC_OTHER, (double)n * (sizeof(A) + sizeof(B)));
   k_cast<A, B><<<nblk((long)n), TPB, 0, P.stream>>>(x, y, (long)n);
   IB_LAUNCH_CHECK();
   return IB_OK;

@@ -163,8 +163,22 @@ struct LevelInfo {
   LevelBuf<float> v32;
 };
 
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
 struct Problem {
   ib_params prm{};
+  // launch accounting / event timing
+  long long nlaunch[IB_KC_COUNT] = {};
+  bool prof = false;
+  long long prof_n[IB_KC_COUNT] = {};
+  double prof_ms[IB_KC_COUNT] = {};
+  double prof_bytes[IB_KC_COUNT] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> pending;
   cudaStream_t stream = nullptr;
   int np = 0, ns = 0;
   int nlev = 0;
@@ -209,6 +223,17 @@ struct Problem {
   int* count_host = nullptr;  // pinned
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+// Launch scope: counts the launch of one kernel of class cls and, while
+// profiling is on, brackets it with CUDA events on the problem's stream.
+struct KScope {
+  Problem& P;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  KScope(Problem& P_, int cls_, double bytes_);
+  ~KScope();
 };
 
 // ---------------------------------------------------------------- launchers (points)

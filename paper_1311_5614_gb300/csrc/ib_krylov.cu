@@ -143,15 +143,22 @@ static inline long nvec_len(const Problem& P) { return 3L * P.lev[0].N * P.lev[0
 int launch_multidot(Problem& P, const double* V, int nvec, const double* w, double* out) {
   long n = nvec_len(P);
   int stride = P.max_m + 2;
-  k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(V, nvec, n, w, P.dots, stride);
-  IB_LAUNCH_CHECK();
-  k_multidot_final<<<nvec, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, out);
-  IB_LAUNCH_CHECK();
+  {
+    KScope ks(P, IB_KC_KRYLOV, (nvec + 1.0) * n * 8.0);
+    k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(V, nvec, n, w, P.dots, stride);
+    IB_LAUNCH_CHECK();
+  }
+  {
+    KScope ks(P, IB_KC_KRYLOV, (double)nvec * P.dot_blocks * 8.0);
+    k_multidot_final<<<nvec, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, out);
+    IB_LAUNCH_CHECK();
+  }
   return IB_OK;
 }
 
 int launch_multiaxpy(Problem& P, const double* V, int nvec, const double* coef, double* w) {
   long n = nvec_len(P);
+  KScope ks(P, IB_KC_KRYLOV, (nvec + 2.0) * n * 8.0);
   k_multiaxpy<<<nblk(n), TPB, 0, P.stream>>>(V, nvec, n, coef, w);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -160,15 +167,22 @@ int launch_multiaxpy(Problem& P, const double* V, int nvec, const double* coef, 
 int launch_dot(Problem& P, const double* a, const double* b, double* out) {
   long n = nvec_len(P);
   int stride = P.max_m + 2;
-  k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(a, 1, n, b, P.dots, stride);
-  IB_LAUNCH_CHECK();
-  k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, out);
-  IB_LAUNCH_CHECK();
+  {
+    KScope ks(P, IB_KC_KRYLOV, 2.0 * n * 8.0);
+    k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(a, 1, n, b, P.dots, stride);
+    IB_LAUNCH_CHECK();
+  }
+  {
+    KScope ks(P, IB_KC_KRYLOV, (double)P.dot_blocks * 8.0);
+    k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, out);
+    IB_LAUNCH_CHECK();
+  }
   return IB_OK;
 }
 
 int launch_scale_copy(Problem& P, const double* x, const double* s, double* y, bool invert) {
   long n = nvec_len(P);
+  KScope ks(P, IB_KC_KRYLOV, 2.0 * n * 8.0);
   k_scale_copy<<<nblk(n), TPB, 0, P.stream>>>(x, s, y, n, invert ? 1 : 0);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -184,6 +198,7 @@ int launch_givens(Problem& P, int j, double /*unused*/, double* /*unused*/) {
   double* h1 = P.scal + 8;
   double* h2 = h1 + m + 2;
   double* wn = h2 + m + 2;
+  KScope ks(P, IB_KC_KRYLOV, 8.0 * (4.0 * j + 8));
   k_givens<<<1, 32, 0, P.stream>>>(P.H, m + 1, j, h1, h2, wn, cs, sn, g, P.scal);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -193,6 +208,7 @@ int launch_backsolve(Problem& P, int k) {
   int m = P.max_m;
   double* g = P.givens + 2 * m;
   double* y = g + m + 1;
+  KScope ks(P, IB_KC_KRYLOV, 8.0 * k * (k + 2.0));
   k_backsolve<<<1, 32, 0, P.stream>>>(P.H, m + 1, k, g, y);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -204,6 +220,7 @@ int launch_update_x(Problem& P, const T* Z, int k, double* x) {
   int m = P.max_m;
   const double* y = P.givens + 3 * m + 1;
   long n = nvec_len(P);
+  KScope ks(P, IB_KC_KRYLOV, (double)k * n * sizeof(T) + 2.0 * n * 8.0);
   k_update_x<T><<<nblk(n), TPB, 0, P.stream>>>(Z, k, n, y, x);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -213,6 +230,7 @@ template int launch_update_x<float>(Problem&, const float*, int, double*);
 
 int launch_axpby(Problem& P, double a, const double* x, double b, const double* y, double* z) {
   long n = nvec_len(P);
+  KScope ks(P, IB_KC_KRYLOV, 3.0 * n * 8.0);
   k_axpby<<<nblk(n), TPB, 0, P.stream>>>(a, x, b, y, z, n);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -226,12 +244,21 @@ int launch_pressure_mean_remove(Problem& P, double* w) {
   IB_TRY(launch_fill<double>(P, ones, (size_t)(2 * n), 0.0));
   IB_TRY(launch_fill<double>(P, ones + 2 * n, (size_t)n, 1.0));
   int stride = P.max_m + 2;
-  k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(ones, 1, 3 * n, w, P.dots, stride);
-  IB_LAUNCH_CHECK();
-  k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, P.scal + 3);
-  IB_LAUNCH_CHECK();
-  k_sub_scalar<<<nblk(n), TPB, 0, P.stream>>>(w + 2 * n, n, P.scal + 3, 1.0 / (double)n);
-  IB_LAUNCH_CHECK();
+  {
+    KScope ks(P, IB_KC_OTHER, 6.0 * n * 8.0);
+    k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(ones, 1, 3 * n, w, P.dots, stride);
+    IB_LAUNCH_CHECK();
+  }
+  {
+    KScope ks(P, IB_KC_OTHER, (double)P.dot_blocks * 8.0);
+    k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, P.scal + 3);
+    IB_LAUNCH_CHECK();
+  }
+  {
+    KScope ks(P, IB_KC_OTHER, 2.0 * n * 8.0);
+    k_sub_scalar<<<nblk(n), TPB, 0, P.stream>>>(w + 2 * n, n, P.scal + 3, 1.0 / (double)n);
+    IB_LAUNCH_CHECK();
+  }
   return IB_OK;
 }
 

@@ -379,6 +379,7 @@ __global__ void k_assemble_E(Patches<double> pat, Springs<double> sp, int N, int
 int launch_fine_patches(Problem& P) {
   if (P.np == 0) return IB_OK;
   LevelInfo& L0 = P.lev[0];
+  KScope ks(P, IB_KC_SETUP, P.np * (16.0 + 8 * 36.0));
   k_fine_patches<<<nblk(P.np), TPB, 0, P.stream>>>(L0.pat64, P.X, P.np, L0.N, L0.h, P.prm.delta);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -386,6 +387,7 @@ int launch_fine_patches(Problem& P) {
 
 int launch_coarse_patches(Problem& P, int level) {
   if (P.np == 0) return IB_OK;
+  KScope ks(P, IB_KC_SETUP, P.np * 16 * 36.0);
   k_coarse_patches<<<nblk(8L * P.np), TPB, 0, P.stream>>>(P.lev[level - 1].pat64, P.lev[level].pat64,
                                                            P.np);
   IB_LAUNCH_CHECK();
@@ -396,6 +398,7 @@ int launch_cast_patches(Problem& P, int level) {
   if (P.np == 0) return IB_OK;
   LevelInfo& L = P.lev[level];
   long nw = 32L * P.np;
+  KScope ks(P, IB_KC_SETUP, nw * 12.0);
   k_cast_d2f<<<nblk(nw, 256), 256, 0, P.stream>>>(L.pat64.w, L.pat32.w, nw);
   IB_LAUNCH_CHECK();
   IB_CUDA_TRY(cudaMemcpyAsync(L.pat32.base, L.pat64.base, sizeof(int) * 8 * P.np,
@@ -407,6 +410,7 @@ int launch_spring_force_jacobian(Problem& P) {
   if (P.np == 0) return IB_OK;
   IB_CUDA_TRY(cudaMemsetAsync(P.F, 0, sizeof(double) * 2 * P.np, P.stream));
   if (P.ns == 0) return IB_OK;
+  KScope ks(P, IB_KC_SETUP, P.ns * 100.0);
   k_springs<<<nblk(P.ns), TPB, 0, P.stream>>>(P.X, P.springs, P.kappa, P.rest, P.ns, P.prm.L,
                                               P.prm.jacobian == IB_JAC_CLAMPED, P.F, P.K64, P.K32,
                                               P.dev_err);
@@ -417,6 +421,7 @@ int launch_spring_force_jacobian(Problem& P) {
 int launch_spread_force(Problem& P, double* b) {
   if (P.np == 0) return IB_OK;
   LevelInfo& L0 = P.lev[0];
+  KScope ks(P, IB_KC_OTHER, P.np * (16.0 + 2 * (8 * 8 + 8) + 32 * 16.0));
   k_spread_force<<<nblk(P.np), TPB, 0, P.stream>>>(L0.pat64, P.F, P.np, L0.N, 1.0 / (L0.h * L0.h), b);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -425,6 +430,7 @@ int launch_spread_force(Problem& P, double* b) {
 int launch_move_points(Problem& P, const double* up) {
   if (P.np == 0) return IB_OK;
   LevelInfo& L0 = P.lev[0];
+  KScope ks(P, IB_KC_OTHER, P.np * (32.0 + 2 * (8 * 8 + 8) + 32 * 8.0));
   k_move_points<<<nblk(P.np), TPB, 0, P.stream>>>(L0.pat64, up, P.np, L0.N, P.prm.dt, P.X);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -458,10 +464,21 @@ int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U) {
   if (P.np == 0 || P.ns == 0) return IB_OK;
   LevelInfo& L = P.lev[level];
   Patches<T> pat = patches_of<T>(L);
-  k_interp<T><<<nblk(2L * P.np), TPB, 0, P.stream>>>(pat, w, P.np, L.N, U);
-  IB_LAUNCH_CHECK();
-  k_spread_JU<T><<<nblk(P.np), TPB, 0, P.stream>>>(pat, springs_view<T>(P), U, L.N, (T)coef, y);
-  IB_LAUNCH_CHECK();
+  const double sT = sizeof(T);
+  {
+    // per point and component: 16 gathered grid values, 8 weights, 2 bases, 1 result
+    KScope ks(P, IB_KC_INTERP, 2.0 * P.np * (25 * sT + 8));
+    k_interp<T><<<nblk(2L * P.np), TPB, 0, P.stream>>>(pat, w, P.np, L.N, U);
+    IB_LAUNCH_CHECK();
+  }
+  {
+    // per point: own U, per spring U_other + K + adjacency, 16 weights + 4 bases,
+    // 32 read-modify-write grid updates
+    double deg = P.np ? 2.0 * P.ns / P.np : 0.0;
+    KScope ks(P, IB_KC_SPREAD, P.np * (2 * sT + 8 + deg * (5 * sT + 8) + 16 * sT + 16 + 64 * sT));
+    k_spread_JU<T><<<nblk(P.np), TPB, 0, P.stream>>>(pat, springs_view<T>(P), U, L.N, (T)coef, y);
+    IB_LAUNCH_CHECK();
+  }
   return IB_OK;
 }
 template int launch_elastic<double>(Problem&, int, const double*, double*, double, double*);
@@ -473,9 +490,11 @@ int launch_mark_struct(Problem& P, int level) {
   IB_CUDA_TRY(cudaMemsetAsync(L.flag, 0, sizeof(int) * nbox, P.stream));
   IB_CUDA_TRY(cudaMemsetAsync(P.count, 0, sizeof(int), P.stream));
   if (P.np > 0 && P.ns > 0) {
+    KScope ks(P, IB_KC_SETUP, 2.0 * P.np * (8 * 8 + 8 + 32 * 4));
     k_mark<<<nblk(2L * P.np), TPB, 0, P.stream>>>(L.pat64, P.np, L.N, P.prm.box, L.nb, L.flag);
     IB_LAUNCH_CHECK();
   }
+  KScope ks(P, IB_KC_SETUP, nbox * 8.0);
   k_assign_slots<<<nblk(nbox), TPB, 0, P.stream>>>(L.flag, nbox, P.count);
   IB_LAUNCH_CHECK();
   return IB_OK;
@@ -485,6 +504,7 @@ int launch_assemble_struct(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
   if (P.np == 0 || P.ns == 0 || L.n_struct == 0) return IB_OK;
   double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
+  KScope ks(P, IB_KC_SETUP, 0.0);
   k_assemble_E<0><<<nblk(8L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
                                                           P.prm.box, L.nb, L.flag, coef, L.Mstruct,
                                                           P.nB, 0, P.dev_err);
@@ -496,6 +516,7 @@ int launch_assemble_coarse(Problem& P) {
   if (P.np == 0 || P.ns == 0) return IB_OK;
   LevelInfo& L = P.lev[P.nlev - 1];
   double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
+  KScope ks(P, IB_KC_SETUP, 0.0);
   k_assemble_E<1><<<nblk(8L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
                                                           P.prm.box, 1, nullptr, coef, P.Mcoarse, 0,
                                                           P.nc + P.nborder, P.dev_err);
