@@ -185,6 +185,34 @@ IB_API int ib_profile(ib_problem* prob, int32_t enable);
 IB_API int ib_profile_read(ib_problem* prob, int32_t kclass, int64_t* launches, double* ms,
                            double* bytes);
 
+/* ---- Allocation-free operator apply (the paper has no counterpart) ----
+ *
+ * y = A_0 w on the fine grid, the same operator as ib_apply(prob, 0, w, y),
+ * computed without a problem handle and without allocating any device memory.
+ * It is meant for callers that cannot allocate device memory: code that must not
+ * stall on cudaMalloc's implicit device synchronisation in the middle of a time
+ * step, or a host framework that owns all device memory through its own pool and
+ * does not let libraries allocate.
+ *   params   host; uses N, L, rho, mu, dt, delta and jacobian
+ *   X        device [n_points][2];  springs device int32 [n_springs][2];
+ *   kappa, rest  device [n_springs];  w, y  device 3 N^2 doubles (must not alias)
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ * The one scratch array it needs (the velocity interpolated to the points) is a
+ * fixed static device array of 2 * IB_NOALLOC_MAX_POINTS doubles (1 MiB) that
+ * every GPU which loads the library holds until the process exits; calls with
+ * n_points > IB_NOALLOC_MAX_POINTS return IB_ERR_INVALID_ARG.  All calls on a
+ * device share that array and it keeps the previous call's contents, so calls
+ * that overlap on the GPU (other streams or threads) race and must be serialised
+ * by the caller.  The first call on each device looks up the array's address
+ * with cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  The call waits for its stream to finish (it reads
+ * back a device error word) and returns IB_ERR_INVALID_ARG for out-of-range or
+ * coincident spring end points. */
+#define IB_NOALLOC_MAX_POINTS 65536
+IB_API int ib_apply_noalloc(const ib_params* params, int32_t n_points, const double* X,
+                            int32_t n_springs, const int32_t* springs, const double* kappa,
+                            const double* rest, const double* w, double* y, void* stream);
+
 /* Release all device memory of the problem.  NULL is ignored. */
 IB_API void ib_destroy(ib_problem* prob);
 

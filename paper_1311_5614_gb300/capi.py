@@ -77,6 +77,8 @@ _SIGS = {
     "ib_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ib_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(ib_params), ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                        _P, _P, _P, _P, _P]),
     "ib_destroy": (None, [_P]),
     "ib_last_error": (ctypes.c_char_p, []),
     "ib_version": (ctypes.c_char_p, []),
@@ -194,6 +196,34 @@ def ib_level_size(prob, level):
 
 def ib_num_struct_boxes(prob, level):
     return lib().ib_num_struct_boxes(prob, int(level))
+
+
+IB_NOALLOC_MAX_POINTS = 65536
+
+
+def ib_apply_noalloc(params, X, springs, kappa, rest, w, y, stream=None):
+    """y = A_0 w without a problem handle and without any device allocation.
+
+    For callers that cannot allocate device memory (no cudaMalloc stalls inside a
+    time step, or all memory owned by the caller's own pool).  X, springs (int32),
+    kappa, rest, w and y are CUDA tensors; the scratch is the library's static
+    device array, so concurrent calls on one GPU race and must be serialised.
+    """
+    import torch
+
+    n = int(params.N)
+    npts = 0 if X is None else X.numel() // 2
+    ns = 0 if springs is None else springs.numel() // 2
+    if springs is not None and (springs.dtype != torch.int32 or not springs.is_cuda or
+                                not springs.is_contiguous()):
+        raise TypeError("springs must be a contiguous int32 CUDA tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().ib_apply_noalloc(
+        ctypes.byref(params), npts, _dev_ptr(X, 2 * npts, "X") if npts else None, ns,
+        ctypes.c_void_p(springs.data_ptr()) if ns else None,
+        _dev_ptr(kappa, ns, "kappa") if ns else None, _dev_ptr(rest, ns, "rest") if ns else None,
+        _dev_ptr(w, 3 * n * n, "w"), _dev_ptr(y, 3 * n * n, "y"), ctypes.c_void_p(stream)))
 
 
 KERNEL_CLASSES = ("stokes", "box", "interp", "spread", "transfer", "coarse", "krylov", "setup", "other")
