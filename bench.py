@@ -54,6 +54,7 @@ def config_dict(args):
     return {"workload": "256^2 MAC grid, 512-point ellipse, kappa x dt sweep (8 cases)",
             "N": N_GRID, "n_points": N_POINTS, "cases": [[k, dt] for k, dt in CASES],
             "box": args.box, "precision": args.precision, "nu": [1, 1], "tol": 1e-8,
+            "max_iters": args.max_iters, "escalate": args.precision == "fp32",
             "l2": "flushed (256 MiB write) before every timed step",
             "parallelism": "replicas" if args.world > 1 else "single GPU"}
 
@@ -204,7 +205,7 @@ def run_ours(args):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     probs = workload_problems(args.box)
-    solvers = [pkg.IBSolver.from_problem(p, precision=args.precision) for p in probs]
+    solvers = [pkg.IBSolver.from_problem(p, precision=args.precision, max_iters=args.max_iters) for p in probs]
     nn = 3 * N_GRID * N_GRID
     X0 = [torch.tensor(p.X, dtype=torch.float64, device=dev) for p in probs]
     Xw = [x.clone() for x in X0]
@@ -245,6 +246,7 @@ def run_ours(args):
     per_ib_ms, t_max = aggregate(step_ms, args.steps * len(probs), world)
     iters = [st["iters"] for st in stats]
     status = [st["status"] for st in stats]
+    escal = [st["escalated_at"] for st in stats]
 
     # end-to-end through the C ABI with host buffers: H2D of X^n, D2H of u, v, p and X^{n+1}
     Xh = [torch.tensor(p.X, dtype=torch.float64).pin_memory() for p in probs]
@@ -331,7 +333,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_per, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
-                "clocks": clocks, "iters": iters, "status": status,
+                "clocks": clocks, "iters": iters, "status": status, "escalated_at": escal,
                 "vcycle": {"ms": vcycle_ms, "dof_per_s": vcycle_dofs, "dof": nn,
                            "case": "kappa=1e4, dt=1e-3"},
                 "wall_s_timed": t_wall,
@@ -348,6 +350,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--box", type=int, default=4)
+    ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--rotate", action="store_true", help="reference arm: rotate through the cases")
     ap.add_argument("--traffic", type=float, default=None,

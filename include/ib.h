@@ -81,6 +81,8 @@ typedef struct {
   int32_t jacobian;   /* IB_JAC_CLAMPED (default) or IB_JAC_EXACT spring Jacobian */
   double tol;         /* relative residual target ||b - A x|| / ||b|| (> 0) */
   int32_t max_iters;  /* FGMRES iteration cap, 1..512 (the paper stops at 100) */
+  int32_t escalate;   /* IB_FP32_PRECOND only: 1 = switch the preconditioner to the FP64
+                         V-cycle when FGMRES stagnates (default), 0 = never */
 } ib_params;
 
 /* Statistics of one ib_solve_step call. */
@@ -93,12 +95,13 @@ typedef struct {
   double t_solve_ms;    /* FGMRES time (CUDA events) */
   int32_t n_struct_boxes; /* structure boxes (with elasticity), all levels */
   int32_t status;       /* ib_status of the solve */
+  int32_t escalated_at; /* iteration from which the FP64 V-cycle preconditioned (-1: never) */
 } ib_stats;
 
 typedef struct ib_problem ib_problem;  /* opaque; owned by the library */
 
 /* Fill *p with the defaults: L=1, rho=1, mu=1, dt=1e-2, Peskin4, box 1, V(1,1),
- * FP64, clamped Jacobian, tol 1e-8, max_iters 100.  N is set to 64. */
+ * FP64, clamped Jacobian, tol 1e-8, max_iters 100, escalate 1.  N is set to 64. */
 IB_API void ib_default_params(ib_params* p);
 
 /* Create a problem: validates the parameters, allocates all device workspace

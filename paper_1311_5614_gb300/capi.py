@@ -39,14 +39,15 @@ class ib_params(ctypes.Structure):
                 ("mu", ctypes.c_double), ("dt", ctypes.c_double), ("delta", ctypes.c_int32),
                 ("box", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("jacobian", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int32)]
+                ("max_iters", ctypes.c_int32), ("escalate", ctypes.c_int32)]
 
 
 class ib_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("rel_res_true", ctypes.c_double), ("rel_res_est", ctypes.c_double),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
-                ("n_struct_boxes", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("n_struct_boxes", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("escalated_at", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,7 +127,7 @@ def ib_default_params():
 
 
 def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=1, nu2=1,
-                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100):
+                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100, escalate=True):
     p = ib_default_params()
     p.N, p.L, p.rho, p.mu, p.dt = int(N), float(L), float(rho), float(mu), float(dt)
     p.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
@@ -134,6 +135,7 @@ def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     p.jacobian = JACOBIAN[jacobian] if isinstance(jacobian, str) else int(jacobian)
     p.tol, p.max_iters = float(tol), int(max_iters)
+    p.escalate = 1 if escalate else 0
     return p
 
 

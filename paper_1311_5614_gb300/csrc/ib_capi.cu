@@ -3,6 +3,7 @@
 // step runs in the kernels of the other translation units; this file only
 // orders launches on the problem's stream and reads back the few scalars that
 // decide control flow (structure-box counts, Krylov residual estimates).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "ib_internal.cuh"
+#include "ib_vcycle.cuh"
 
 namespace ib {
 
@@ -112,6 +114,7 @@ int validate(const ib_params* p) {
   if (!(std::isfinite(p->tol) && p->tol > 0)) return fail(IB_ERR_INVALID_ARG, "tol must be > 0");
   if (p->max_iters < 1 || p->max_iters > 512)
     return fail(IB_ERR_INVALID_ARG, "max_iters must be in 1..512");
+  if (p->escalate != 0 && p->escalate != 1) return fail(IB_ERR_INVALID_ARG, "escalate must be 0 or 1");
   return IB_OK;
 }
 
@@ -124,78 +127,10 @@ __global__ void k_axpy_n(double a, const double* __restrict__ x, double* y, long
   if (e < n) y[e] += a * x[e];
 }
 
-template <typename T>
-LevelBuf<T>& bufs(LevelInfo& L);
-template <>
-LevelBuf<double>& bufs<double>(LevelInfo& L) { return L.v64; }
-template <>
-LevelBuf<float>& bufs<float>(LevelInfo& L) { return L.v32; }
-
-template <typename T>
-T* Uscratch(Problem& P);
-template <>
-double* Uscratch<double>(Problem& P) { return P.U64; }
-template <>
-float* Uscratch<float>(Problem& P) { return P.U32; }
-
-// r = b - A_l w on level l (Stokes part + elasticity), precision T.
-template <typename T>
-int residual(Problem& P, int l, const T* w, const T* b, T* r) {
-  IB_TRY(launch_stokes<T>(P, l, w, b, r, true));
-  IB_TRY(launch_elastic<T>(P, l, w, r, -efac(P), Uscratch<T>(P)));
-  return IB_OK;
-}
-
 // y = A_l w in FP64.
 int apply64(Problem& P, int l, const double* w, double* y) {
   IB_TRY(launch_stokes<double>(P, l, w, nullptr, y, false));
   IB_TRY(launch_elastic<double>(P, l, w, y, efac(P), P.U64));
-  return IB_OK;
-}
-
-// One smoothing sweep: four colours, each = residual from the colour's starting
-// state, then independent box solves (the boxes of a colour share no unknowns).
-// Colour c = (I mod 2) + 2 (J mod 2) of box (I, J); the forward sequence is
-// (even,even), (odd,odd), (odd,even), (even,odd).
-constexpr int kColorSeq[4] = {0, 3, 1, 2};
-template <typename T>
-int sweep(Problem& P, int l, T* w, const T* b, T* r, bool reverse) {
-  for (int cc = 0; cc < 4; ++cc) {
-    int c = reverse ? kColorSeq[3 - cc] : kColorSeq[cc];
-    IB_TRY(residual<T>(P, l, w, b, r));
-    IB_TRY(launch_box_solve<T>(P, l, c, r, w));
-  }
-  return IB_OK;
-}
-
-// w0 = MGV(0, b0) (Algorithm 1): pre-smooth, restrict the residual, recurse with
-// zero initial guess, prolong and correct, post-smooth (colours reversed);
-// exact bordered solve on the coarsest grid.
-template <typename T>
-int vcycle(Problem& P, const T* b0, T* w0) {
-  int nl = P.nlev;
-  for (int l = 0; l < nl - 1; ++l) {
-    LevelBuf<T>& B = bufs<T>(P.lev[l]);
-    T* w = l == 0 ? w0 : B.w;
-    const T* b = l == 0 ? b0 : B.b;
-    size_t n = 3ul * P.lev[l].N * P.lev[l].N;
-    IB_TRY(launch_fill<T>(P, w, n, (T)0));
-    for (int s = 0; s < P.prm.nu1; ++s) IB_TRY(sweep<T>(P, l, w, b, B.r, false));
-    IB_TRY(residual<T>(P, l, w, b, B.r));
-    IB_TRY(launch_restrict<T>(P, l, B.r, bufs<T>(P.lev[l + 1]).b));
-  }
-  LevelBuf<T>& C = bufs<T>(P.lev[nl - 1]);
-  IB_TRY(launch_coarse_solve<T>(P, C.b, C.w));
-  for (int l = nl - 2; l >= 0; --l) {
-    LevelBuf<T>& B = bufs<T>(P.lev[l]);
-    T* w = l == 0 ? w0 : B.w;
-    const T* b = l == 0 ? b0 : B.b;
-    IB_TRY(launch_prolong_add<T>(P, l, bufs<T>(P.lev[l + 1]).w, w));
-    // 1 x 1 boxes of one colour are coupled through the stencil and post-smooth in
-    // the reversed sequence; larger boxes of one colour are uncoupled and repeat it.
-    const bool rev = P.prm.box == 1;
-    for (int s = 0; s < P.prm.nu2; ++s) IB_TRY(sweep<T>(P, l, w, b, B.r, rev));
-  }
   return IB_OK;
 }
 
@@ -234,6 +169,7 @@ int setup_hierarchy(Problem& P) {
     LevelInfo& L = P.lev[l];
     int cnt = P.count_host[l];
     if (cnt > L.cap_struct) {
+      P.graph_dirty[0] = P.graph_dirty[1] = true;  // the box kernels take the new pointer
       dfree(L.Mstruct);
       int cap = cnt + cnt / 4 + 16;
       if (cap > L.nb * L.nb) cap = L.nb * L.nb;
@@ -241,31 +177,40 @@ int setup_hierarchy(Problem& P) {
       L.cap_struct = cap;
     }
     L.n_struct = cnt;
-    IB_TRY(launch_box_stokes_fill(P, l, true));
+    if (!P.free_ready) IB_TRY(launch_free_box(P, l));
+    IB_TRY(launch_struct_fill(P, l));
     IB_TRY(launch_assemble_struct(P, l));
     IB_TRY(launch_invert(P, L.Mstruct, nB, cnt));
-    IB_TRY(launch_invert(P, L.Mfree, nB, 1));
-    if (P.prm.precision == IB_FP32_PRECOND)
-      IB_TRY(launch_cast<double, float>(P, L.Mfree, L.Mfree32, (size_t)nB * nB));
   }
+  P.free_ready = true;
   IB_TRY(launch_coarse_fill(P));
   IB_TRY(launch_assemble_coarse(P));
   IB_TRY(launch_invert(P, P.Mcoarse, P.nc + P.nborder, 1));
+  IB_TRY(vcycle_reset_rE(P));
   return check_dev_err(P);
 }
 
 void free_problem(Problem* P) {
   if (!P) return;
   for (auto& L : P->lev) {
-    dfree(L.flag); dfree(L.Mstruct); dfree(L.Mfree); dfree(L.Mfree32);
+    dfree(L.flag); dfree(L.Mstruct); dfree(L.Sfree); dfree(L.Mfree); dfree(L.Mfree32);
     dfree(L.pat64.base); dfree(L.pat64.w); dfree(L.pat32.base); dfree(L.pat32.w);
     dfree(L.v64.w); dfree(L.v64.b); dfree(L.v64.r);
     dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);
+    dfree(L.rE64); dfree(L.rE32);
   }
+  for (auto& g : P->vgraph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+  if (P->gstream) cudaStreamDestroy(P->gstream);
+  P->gstream = nullptr;
+  for (auto& e : P->gev)
+    if (e) cudaEventDestroy(e);
   dfree(P->X); dfree(P->springs); dfree(P->kappa); dfree(P->rest);
   dfree(P->adj_ptr); dfree(P->adj_spring); dfree(P->adj_other);
   dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->U64); dfree(P->U32);
-  dfree(P->Mcoarse); dfree(P->V); dfree(P->Z); dfree(P->H); dfree(P->givens);
+  dfree(P->Mcoarse); dfree(P->V); dfree(P->Z); dfree(P->Z64); dfree(P->H); dfree(P->givens);
   dfree(P->dots); dfree(P->scal); dfree(P->x64); dfree(P->b64); dfree(P->t64); dfree(P->t64b);
   dfree(P->dev_err); dfree(P->count);
   if (P->scal_host) cudaFreeHost(P->scal_host);
@@ -289,6 +234,7 @@ int allocate(Problem& P) {
     size_t n3 = 3ul * L.N * L.N;
     if (l < nl - 1) {
       IB_TRY(dalloc(&L.flag, (size_t)L.nb * L.nb));
+      IB_TRY(dalloc(&L.Sfree, (size_t)P.nB * P.nB));
       IB_TRY(dalloc(&L.Mfree, (size_t)P.nB * P.nB));
       if (fp32) IB_TRY(dalloc(&L.Mfree32, (size_t)P.nB * P.nB));
     }
@@ -304,9 +250,11 @@ int allocate(Problem& P) {
     }
     if (fp32) {
       IB_TRY(dalloc(&L.v32.w, n3)); IB_TRY(dalloc(&L.v32.b, n3)); IB_TRY(dalloc(&L.v32.r, n3));
-    } else {
-      IB_TRY(dalloc(&L.v64.r, n3));
-      if (l > 0) { IB_TRY(dalloc(&L.v64.w, n3)); IB_TRY(dalloc(&L.v64.b, n3)); }
+      IB_TRY(dalloc(&L.rE32, 2ul * L.N * L.N));
+    }
+    if (!fp32 || P.prm.escalate) {
+      IB_TRY(dalloc(&L.v64.w, n3)); IB_TRY(dalloc(&L.v64.b, n3)); IB_TRY(dalloc(&L.v64.r, n3));
+      IB_TRY(dalloc(&L.rE64, 2ul * L.N * L.N));
     }
   }
   int np = P.np, ns = P.ns;
@@ -335,6 +283,7 @@ int allocate(Problem& P) {
     float* z;
     IB_TRY(dalloc(&z, (size_t)m * n));
     P.Z = z;
+    if (P.prm.escalate) IB_TRY(dalloc(&P.Z64, (size_t)m * n));
   } else {
     double* z;
     IB_TRY(dalloc(&z, (size_t)m * n));
@@ -397,6 +346,8 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     return IB_OK;
   }
   int total = 0;
+  std::vector<double> hist;
+  st->escalated_at = -1;
   double* h1 = s + 8;
   double* h2 = h1 + m + 2;
   double* wn = h2 + m + 2;
@@ -417,6 +368,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     }
     if (total >= P.prm.max_iters) break;
     int mav = P.prm.max_iters - total;
+    const int cycle_start = total;
     IB_TRY(launch_fill<double>(P, g, (size_t)m + 1, 0.0));
     {
       KScope ks(P, IB_KC_KRYLOV, 8.0);
@@ -433,14 +385,27 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       double* vj = P.V + (size_t)j * n;
       T* zj = Z + (size_t)j * n;
       if constexpr (std::is_same<T, double>::value) {
-        IB_TRY(vcycle<double>(P, vj, zj));
+        LevelBuf<double>& B0 = P.lev[0].v64;
+        IB_CUDA_TRY(cudaMemcpyAsync(B0.b, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+        IB_TRY(vcycle_run<double>(P));
+        IB_CUDA_TRY(cudaMemcpyAsync(zj, B0.w, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
         IB_TRY(apply64(P, 0, zj, P.t64));
-      } else {
-        LevelBuf<T>& B0 = bufs<T>(P.lev[0]);
-        IB_TRY((launch_cast<double, T>(P, vj, B0.b, n)));
-        IB_TRY(vcycle<T>(P, B0.b, zj));
-        IB_TRY((launch_cast<T, double>(P, zj, P.t64b, n)));
+      } else if (st->escalated_at < 0) {
+        LevelBuf<float>& B0 = P.lev[0].v32;
+        IB_TRY((launch_cast<double, float>(P, vj, B0.b, n)));
+        IB_TRY(vcycle_run<float>(P));
+        IB_CUDA_TRY(cudaMemcpyAsync(zj, B0.w, n * sizeof(float), cudaMemcpyDeviceToDevice, P.stream));
+        IB_TRY((launch_cast<float, double>(P, zj, P.t64b, n)));
         IB_TRY(apply64(P, 0, P.t64b, P.t64));
+      } else {
+        // escalated: the FP64 V-cycle preconditions and its directions are kept in
+        // FP64 (flexible GMRES combines the two bases in the update of x)
+        LevelBuf<double>& B0 = P.lev[0].v64;
+        double* zj64 = P.Z64 + (size_t)j * n;
+        IB_CUDA_TRY(cudaMemcpyAsync(B0.b, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+        IB_TRY(vcycle_run<double>(P));
+        IB_CUDA_TRY(cudaMemcpyAsync(zj64, B0.w, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+        IB_TRY(apply64(P, 0, zj64, P.t64));
       }
       IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h1));
       IB_TRY(launch_multiaxpy(P, P.V, j + 1, h1, P.t64));
@@ -456,10 +421,24 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       st->rel_res_est = est / bnorm;
       if (P.scal_host[2] != 0.0) return fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES");
       if (est <= tol * bnorm) break;
+      hist.push_back(est);
+      // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
+      // the last 8 iterations -> precondition with the FP64 V-cycle from now on
+      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 8 &&
+          est > 0.5 * hist[hist.size() - 9])
+        st->escalated_at = total;
       if (!(P.scal_host[1] > 0.0)) break;  // lucky breakdown: exact solution in the space
     }
     IB_TRY(launch_backsolve(P, k));
-    IB_TRY(launch_update_x<T>(P, Z, k, x));
+    if constexpr (std::is_same<T, double>::value) {
+      IB_TRY(launch_update_x<T>(P, Z, k, x));
+    } else {
+      // directions j < e are FP32 (Z), j >= e FP64 (Z64), e = escalation point in this cycle
+      int e = k;
+      if (st->escalated_at >= 0) e = std::max(0, std::min(k, st->escalated_at - cycle_start));
+      IB_TRY(launch_update_x<float>(P, Z, e, x, 0));
+      if (e < k) IB_TRY(launch_update_x<double>(P, P.Z64, k - e, x, e));
+    }
     IB_TRY(residual64(P, x, b, P.t64));
     IB_TRY(launch_dot(P, P.t64, P.t64, s + 7));
     IB_TRY(read_scalars(P, 8));
@@ -505,6 +484,7 @@ void ib_default_params(ib_params* p) {
   p->jacobian = IB_JAC_CLAMPED;
   p->tol = 1e-8;
   p->max_iters = 100;
+  p->escalate = 1;
 }
 
 int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t n_springs,
@@ -609,6 +589,16 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   IB_SETUP_CUDA(cudaStreamSynchronize(s));
   st = setup_hierarchy(P);
   if (st != IB_OK) return fail_free(st);
+  P.has32 = params->precision == IB_FP32_PRECOND;
+  P.has64 = params->precision == IB_FP64 || params->escalate != 0;
+  if (P.has32) {
+    st = vcycle_prepare<float>(P);
+    if (st != IB_OK) return fail_free(st);
+  }
+  if (P.has64) {
+    st = vcycle_prepare<double>(P);
+    if (st != IB_OK) return fail_free(st);
+  }
   *out = H;
   return IB_OK;
 }
@@ -655,11 +645,14 @@ int ib_vcycle(ib_problem* H, const double* b, double* w) {
   Problem& P = H->P;
   size_t n = 3ul * P.prm.N * P.prm.N;
   if (P.prm.precision == IB_FP64) {
-    IB_TRY(vcycle<double>(P, b, w));
+    LevelBuf<double>& B0 = P.lev[0].v64;
+    IB_CUDA_TRY(cudaMemcpyAsync(B0.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+    IB_TRY(vcycle_run<double>(P));
+    IB_CUDA_TRY(cudaMemcpyAsync(w, B0.w, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
   } else {
     LevelBuf<float>& B0 = P.lev[0].v32;
     IB_TRY((launch_cast<double, float>(P, b, B0.b, n)));
-    IB_TRY(vcycle<float>(P, B0.b, B0.w));
+    IB_TRY(vcycle_run<float>(P));
     IB_TRY((launch_cast<float, double>(P, B0.w, w, n)));
   }
   IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
@@ -692,6 +685,7 @@ int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_st
   std::memset(&local, 0, sizeof(local));
   ib_stats* st = stats ? stats : &local;
   std::memset(st, 0, sizeof(*st));
+  st->escalated_at = -1;
   size_t n = 3ul * P.prm.N * P.prm.N;
   IB_CUDA_TRY(cudaEventRecord(P.ev[0], P.stream));
   if (P.np > 0)

@@ -44,141 +44,6 @@ __global__ void k_stokes(const T* __restrict__ w, const T* __restrict__ b, T* __
   }
 }
 
-// Restriction (sec. 3.1) from an N grid to N/2, one thread per coarse cell.
-template <typename T>
-__global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ bc, int Nc) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int nc = Nc * Nc;
-  if (idx >= nc) return;
-  int N = 2 * Nc, n = N * N;
-  int I = idx % Nc, J = idx / Nc;
-  const T* u = rf;
-  const T* v = rf + n;
-  const T* p = rf + 2 * n;
-  int xm = (2 * I - 1) & (N - 1), x0 = 2 * I, x1 = 2 * I + 1;
-  int ym = (2 * J - 1) & (N - 1), y0 = 2 * J, y1 = 2 * J + 1;
-  // u: (1/8)[1 2 1; 1 2 1] -- faces 2I-1, 2I, 2I+1 in x, rows 2J, 2J+1 in y
-  T su = (T)0.125 * (u[y0 * N + xm] + u[y1 * N + xm] + u[y0 * N + x1] + u[y1 * N + x1]) +
-         (T)0.25 * (u[y0 * N + x0] + u[y1 * N + x0]);
-  // v: transposed stencil
-  T sv = (T)0.125 * (v[ym * N + x0] + v[ym * N + x1] + v[y1 * N + x0] + v[y1 * N + x1]) +
-         (T)0.25 * (v[y0 * N + x0] + v[y0 * N + x1]);
-  T sp = (T)0.25 * (p[y0 * N + x0] + p[y0 * N + x1] + p[y1 * N + x0] + p[y1 * N + x1]);
-  bc[idx] = su;
-  bc[nc + idx] = sv;
-  bc[2 * nc + idx] = sp;
-}
-
-// w_f += P e_c (sec. 3.1): velocity linear along its normal direction and
-// 3/4-1/4 between cell-centred rows, pressure constant.  One thread per fine cell.
-template <typename T>
-__global__ void k_prolong_add(const T* __restrict__ ec, T* __restrict__ wf, int N) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int n = N * N;
-  if (idx >= n) return;
-  int Nc = N / 2, nc = Nc * Nc;
-  int i = idx & (N - 1), j = idx / N;
-  int I = i >> 1, J = j >> 1;
-  const T* u = ec;
-  const T* v = ec + nc;
-  const T* p = ec + 2 * nc;
-  // centred-direction neighbour row/column: J-1 for even fine index, J+1 for odd
-  int Jn = ((j & 1) ? J + 1 : J - 1) & (Nc - 1);
-  int In = ((i & 1) ? I + 1 : I - 1) & (Nc - 1);
-  int I1 = (I + 1) & (Nc - 1), J1 = (J + 1) & (Nc - 1);
-  T cu, cv;
-  if ((i & 1) == 0) {
-    cu = (T)0.75 * u[J * Nc + I] + (T)0.25 * u[Jn * Nc + I];
-  } else {
-    cu = (T)0.375 * (u[J * Nc + I] + u[J * Nc + I1]) + (T)0.125 * (u[Jn * Nc + I] + u[Jn * Nc + I1]);
-  }
-  if ((j & 1) == 0) {
-    cv = (T)0.75 * v[J * Nc + I] + (T)0.25 * v[J * Nc + In];
-  } else {
-    cv = (T)0.375 * (v[J * Nc + I] + v[J1 * Nc + I]) + (T)0.125 * (v[J * Nc + In] + v[J1 * Nc + In]);
-  }
-  wf[idx] += cu;
-  wf[n + idx] += cv;
-  wf[2 * n + idx] += p[J * Nc + I];
-}
-
-// Box solve for one colour, 1 x 1 boxes: one thread per box.  delta = A_BB^{-1} r_B,
-// w_B += delta.  Structure boxes use their own FP64 inverse, the others the
-// shared inverse of the structure-free box.
-template <typename T>
-__global__ void k_box1(const T* __restrict__ r, T* __restrict__ w, int N, int color,
-                       const int* __restrict__ slot, const double* __restrict__ Ms,
-                       const T* __restrict__ Mf) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int half = N >> 1;
-  if (t >= half * half) return;
-  int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
-  int n = N * N;
-  int I1 = (I + 1) & (N - 1), J1 = (J + 1) & (N - 1);
-  int g[5] = {J * N + I, J * N + I1, n + J * N + I, n + J1 * N + I, 2 * n + J * N + I};
-  int sl = slot[J * N + I];
-  if (sl >= 0) {
-    const double* M = Ms + (size_t)sl * 25;
-    double rb[5];
-    for (int q = 0; q < 5; ++q) rb[q] = (double)r[g[q]];
-    for (int q = 0; q < 5; ++q) {
-      double d = 0.0;
-      for (int s = 0; s < 5; ++s) d += M[s * 5 + q] * rb[s];
-      w[g[q]] += (T)d;
-    }
-  } else {
-    T rb[5];
-    for (int q = 0; q < 5; ++q) rb[q] = r[g[q]];
-    for (int q = 0; q < 5; ++q) {
-      T d = 0;
-      for (int s = 0; s < 5; ++s) d += Mf[s * 5 + q] * rb[s];
-      w[g[q]] += d;
-    }
-  }
-}
-
-// Box solve for one colour, b x b boxes (b >= 2): one warp per box; the box
-// residual is staged in shared memory, lanes own rows of delta.
-constexpr int BOX_WARPS = 4;
-constexpr int MAX_NB = 208;  // 2 b (b + 1) + b^2 for b = 8
-template <typename T>
-__global__ void k_boxb(const T* __restrict__ r, T* __restrict__ w, int N, int b, int color,
-                       const int* __restrict__ slot, const double* __restrict__ Ms,
-                       const T* __restrict__ Mf) {
-  __shared__ double rs[BOX_WARPS][MAX_NB];
-  __shared__ int gs[BOX_WARPS][MAX_NB];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int nb = N / b, half = nb >> 1;
-  int t = blockIdx.x * BOX_WARPS + warp;
-  if (t >= half * half) return;
-  int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
-  int x0 = I * b, y0 = J * b, n = N * N;
-  int nB = box_nunk(b);
-  for (int q = lane; q < nB; q += 32) {
-    int c, i, j;
-    box_unknown(q, b, x0, y0, N, &c, &i, &j);
-    int gq = c * n + j * N + i;
-    gs[warp][q] = gq;
-    rs[warp][q] = (double)r[gq];
-  }
-  __syncwarp();
-  int sl = slot[J * nb + I];
-  if (sl >= 0) {
-    const double* M = Ms + (size_t)sl * nB * nB;
-    for (int q = lane; q < nB; q += 32) {
-      double d = 0.0;
-      for (int s = 0; s < nB; ++s) d += M[(size_t)s * nB + q] * rs[warp][s];
-      w[gs[warp][q]] += (T)d;
-    }
-  } else {
-    for (int q = lane; q < nB; q += 32) {
-      T d = 0;
-      for (int s = 0; s < nB; ++s) d += Mf[(size_t)s * nB + q] * (T)rs[warp][s];
-      w[gs[warp][q]] += d;
-    }
-  }
-}
-
 // Stokes block of a box at the origin of a level (identical for every box by
 // translation invariance), column-major n_B x n_B.
 __global__ void k_box_stokes(double* M, int N, int b, StokesCoef<double> c) {
@@ -218,20 +83,19 @@ __global__ void k_coarse_fill(double* M, int N, StokesCoef<double> c, int nz, in
   M[e] = v;
 }
 
-// In-place Gauss-Jordan inversion with partial pivoting, one CTA per matrix
-// (row-major n x n storage; applied to a column-major A it returns A^{-1} in
-// column-major order).  Row interchanges are undone by the reverse sequence of
-// column interchanges at the end.
+// In-place Gauss-Jordan inversion with partial pivoting by one CTA (row-major
+// n x n storage; applied to a column-major A it returns A^{-1} in column-major
+// order).  Row interchanges are undone by the reverse sequence of column
+// interchanges at the end.  M may live in global or shared memory.
 constexpr int INV_MAXN = 256;
-__global__ void k_invert(double* Ms, int n, int* err) {
+__device__ void gj_invert(double* M, int n, int* err) {
   __shared__ double f[INV_MAXN];
   __shared__ int perm[INV_MAXN];
   __shared__ double rv[32];
   __shared__ int ri[32];
   __shared__ int prow;
-  double* M = Ms + (size_t)blockIdx.x * n * n;
-  int tid = threadIdx.x, bd = blockDim.x;
-  int lane = tid & 31, wid = tid >> 5, nw = (bd + 31) >> 5;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = (bd + 31) >> 5;
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
     int bi = n;
@@ -256,7 +120,7 @@ __global__ void k_invert(double* Ms, int n, int* err) {
       perm[k] = i0;
     }
     __syncthreads();
-    int p = prow;
+    const int p = prow;
     if (p != k) {
       for (int j = tid; j < n; j += bd) {
         double t = M[(size_t)k * n + j];
@@ -271,9 +135,10 @@ __global__ void k_invert(double* Ms, int n, int* err) {
       piv = 1.0;
     }
     __syncthreads();
+    const double inv = 1.0 / piv;
     for (int j = tid; j < n; j += bd) {
       double v = (j == k) ? 1.0 : M[(size_t)k * n + j];
-      M[(size_t)k * n + j] = v / piv;
+      M[(size_t)k * n + j] = v * inv;
     }
     for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[(size_t)i * n + k];
     __syncthreads();
@@ -299,18 +164,76 @@ __global__ void k_invert(double* Ms, int n, int* err) {
   }
 }
 
-// w = (M^{-1})[0:nc, 0:nc] b for the bordered coarsest system, one CTA.
-template <typename T>
-__global__ void k_coarse_solve(const double* __restrict__ M, int nc, int ld, const T* __restrict__ b,
-                               T* __restrict__ w) {
-  __shared__ double bs[3 * 64 + 8];
-  for (int s = threadIdx.x; s < nc; s += blockDim.x) bs[s] = (double)b[s];
+// One matrix per CTA, worked on in global memory (large n).
+__global__ void k_invert(double* Ms, int n, int* err) { gj_invert(Ms + (size_t)blockIdx.x * n * n, n, err); }
+
+// One matrix per CTA, staged in shared memory (n^2 doubles of dynamic shared memory).
+__global__ void k_invert_sm(double* Ms, int n, int* err) {
+  extern __shared__ double sm[];
+  double* M = Ms + (size_t)blockIdx.x * n * n;
+  const int nn = n * n;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) sm[e] = M[e];
   __syncthreads();
-  for (int r = threadIdx.x; r < nc; r += blockDim.x) {
-    double acc = 0.0;
-    for (int s = 0; s < nc; ++s) acc += M[(size_t)s * ld + r] * bs[s];
-    w[r] = (T)acc;
+  gj_invert(sm, n, err);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = sm[e];
+}
+
+// 5 x 5 matrices (1 x 1 boxes), one per thread in registers: the same
+// Gauss-Jordan steps with partial pivoting.
+__global__ void k_invert5(double* Ms, int count, int* err) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  double* Mg = Ms + (size_t)t * 25;
+  double M[25];
+  int perm[5];
+#pragma unroll
+  for (int e = 0; e < 25; ++e) M[e] = Mg[e];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    int p = k;
+    double best = fabs(M[k * 5 + k]);
+#pragma unroll
+    for (int i = k + 1; i < 5; ++i) {
+      double a = fabs(M[i * 5 + k]);
+      if (a > best) { best = a; p = i; }
+    }
+    perm[k] = p;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double a = M[k * 5 + j], b = M[p * 5 + j];
+      M[k * 5 + j] = (p == k) ? a : b;
+      M[p * 5 + j] = (p == k) ? b : a;
+    }
+    double piv = M[k * 5 + k];
+    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+      atomicOr(err, DEV_ERR_SINGULAR);
+      piv = 1.0;
+    }
+    double inv = 1.0 / piv;
+    M[k * 5 + k] = 1.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) M[k * 5 + j] *= inv;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (i == k) continue;
+      double fi = M[i * 5 + k];
+      M[i * 5 + k] = 0.0;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) M[i * 5 + j] -= fi * M[k * 5 + j];
+    }
   }
+#pragma unroll
+  for (int k = 4; k >= 0; --k) {
+    int p = perm[k];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      double a = M[i * 5 + k], b = M[i * 5 + p];
+      M[i * 5 + k] = (p == k) ? a : b;
+      M[i * 5 + p] = (p == k) ? b : a;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 25; ++e) Mg[e] = M[e];
 }
 
 template <typename T>
@@ -342,13 +265,6 @@ StokesCoef<T> coef_of(const Problem& P, int level) {
   return c;
 }
 
-template <typename T>
-const T* free_inverse(const LevelInfo& L);
-template <>
-const double* free_inverse<double>(const LevelInfo& L) { return L.Mfree; }
-template <>
-const float* free_inverse<float>(const LevelInfo& L) { return L.Mfree32; }
-
 }  // namespace
 
 template <typename T>
@@ -366,76 +282,58 @@ int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool re
 template int launch_stokes<double>(Problem&, int, const double*, const double*, double*, bool);
 template int launch_stokes<float>(Problem&, int, const float*, const float*, float*, bool);
 
-template <typename T>
-int launch_restrict(Problem& P, int level, const T* rf, T* bc) {
-  int Nc = P.lev[level + 1].N;
-  KScope ks(P, IB_KC_TRANSFER, 15.0 * Nc * Nc * sizeof(T));
-  k_restrict<T><<<nblk((long)Nc * Nc), TPB, 0, P.stream>>>(rf, bc, Nc);
-  IB_LAUNCH_CHECK();
-  return IB_OK;
-}
-template int launch_restrict<double>(Problem&, int, const double*, double*);
-template int launch_restrict<float>(Problem&, int, const float*, float*);
-
-template <typename T>
-int launch_prolong_add(Problem& P, int level, const T* ec, T* wf) {
-  int N = P.lev[level].N;
-  KScope ks(P, IB_KC_TRANSFER, (6.0 * N * N + 0.75 * N * N) * sizeof(T));
-  k_prolong_add<T><<<nblk((long)N * N), TPB, 0, P.stream>>>(ec, wf, N);
-  IB_LAUNCH_CHECK();
-  return IB_OK;
-}
-template int launch_prolong_add<double>(Problem&, int, const double*, double*);
-template int launch_prolong_add<float>(Problem&, int, const float*, float*);
-
-template <typename T>
-int launch_box_solve(Problem& P, int level, int color, const T* r, T* w) {
-  LevelInfo& L = P.lev[level];
-  int b = P.prm.box;
-  int half = L.nb / 2;
-  long nbox = (long)half * half;
-  // per box: n_B residual reads, n_B read-modify-writes of w, the slot; structure
-  // boxes (about a quarter of them per colour) read their FP64 inverse; the shared
-  // free-box inverse is read once
-  int nB = P.nB;
-  KScope ks(P, IB_KC_BOX, nbox * (3.0 * nB * sizeof(T) + 4) + 0.25 * L.n_struct * nB * nB * 8.0 +
-                              (double)nB * nB * sizeof(T));
-  if (b == 1) {
-    k_box1<T><<<nblk(nbox, 128), 128, 0, P.stream>>>(r, w, L.N, color, L.flag, L.Mstruct,
-                                                      free_inverse<T>(L));
-  } else {
-    k_boxb<T><<<nblk(nbox, BOX_WARPS), 32 * BOX_WARPS, 0, P.stream>>>(r, w, L.N, b, color, L.flag,
-                                                                       L.Mstruct, free_inverse<T>(L));
-  }
-  IB_LAUNCH_CHECK();
-  return IB_OK;
-}
-template int launch_box_solve<double>(Problem&, int, int, const double*, double*);
-template int launch_box_solve<float>(Problem&, int, int, const float*, float*);
-
-// Free-box Stokes block into L.Mfree, copied into every structure slot.
-int launch_box_stokes_fill(Problem& P, int level, bool /*unused*/) {
+// Stokes block of the structure-free box of a level into L.Sfree and its inverse
+// into L.Mfree (and L.Mfree32): it depends only on the grid and fluid
+// parameters, so it is computed once per problem.
+int launch_free_box(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
   int nB = P.nB;
   StokesCoef<double> c = coef_of<double>(P, level);
-  KScope ks(P, IB_KC_SETUP, nB * nB * 8.0);
-  k_box_stokes<<<nblk((long)nB * nB), TPB, 0, P.stream>>>(L.Mfree, L.N, P.prm.box, c);
-  IB_LAUNCH_CHECK();
+  {
+    KScope ks(P, IB_KC_SETUP, nB * nB * 8.0);
+    k_box_stokes<<<nblk((long)nB * nB), TPB, 0, P.stream>>>(L.Sfree, L.N, P.prm.box, c);
+    IB_LAUNCH_CHECK();
+  }
+  IB_CUDA_TRY(cudaMemcpyAsync(L.Mfree, L.Sfree, sizeof(double) * nB * nB, cudaMemcpyDeviceToDevice, P.stream));
+  IB_TRY(launch_invert(P, L.Mfree, nB, 1));
+  if (L.Mfree32) IB_TRY((launch_cast<double, float>(P, L.Mfree, L.Mfree32, (size_t)nB * nB)));
+  return IB_OK;
+}
+
+// Every structure slot starts from the Stokes block of the free box.
+int launch_struct_fill(Problem& P, int level) {
+  LevelInfo& L = P.lev[level];
+  int nB = P.nB;
   if (L.n_struct > 0) {
     long tot = (long)nB * nB * L.n_struct;
-    KScope ks2(P, IB_KC_SETUP, tot * 8.0);
-    k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Mfree, L.Mstruct, nB * nB, L.n_struct);
+    KScope ks(P, IB_KC_SETUP, tot * 16.0);
+    k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Sfree, L.Mstruct, nB * nB, L.n_struct);
     IB_LAUNCH_CHECK();
   }
   return IB_OK;
 }
 
+// Invert count n x n matrices stored back to back: 5 x 5 in registers (one per
+// thread), n^2 doubles that fit in shared memory staged there (one CTA each),
+// larger ones in global memory.
 int launch_invert(Problem& P, double* M, int n, int count) {
   if (count <= 0) return IB_OK;
   if (n > INV_MAXN) return fail(IB_ERR_INVALID_ARG, "matrix too large for the device inverse");
-  int threads = n <= 32 ? 32 : (n <= 64 ? 64 : 256);
   KScope ks(P, IB_KC_SETUP, 2.0 * count * n * n * 8.0);
-  k_invert<<<count, threads, 0, P.stream>>>(M, n, P.dev_err);
+  size_t smem = (size_t)n * n * sizeof(double);
+  if (n == 5) {
+    k_invert5<<<nblk(count, 128), 128, 0, P.stream>>>(M, count, P.dev_err);
+  } else if (smem <= 160u * 1024u) {
+    static bool attr = false;
+    if (!attr) {
+      IB_CUDA_TRY(cudaFuncSetAttribute(k_invert_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+      attr = true;
+    }
+    int threads = n <= 32 ? 64 : (n <= 64 ? 128 : 256);
+    k_invert_sm<<<count, threads, smem, P.stream>>>(M, n, P.dev_err);
+  } else {
+    k_invert<<<count, 1024, 0, P.stream>>>(M, n, P.dev_err);
+  }
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
@@ -450,16 +348,6 @@ int launch_coarse_fill(Problem& P) {
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
-
-template <typename T>
-int launch_coarse_solve(Problem& P, const T* b, T* w) {
-  KScope ks(P, IB_KC_COARSE, (double)P.nc * P.nc * 8.0 + 2.0 * P.nc * sizeof(T));
-  k_coarse_solve<T><<<1, 256, 0, P.stream>>>(P.Mcoarse, P.nc, P.nc + P.nborder, b, w);
-  IB_LAUNCH_CHECK();
-  return IB_OK;
-}
-template int launch_coarse_solve<double>(Problem&, const double*, double*);
-template int launch_coarse_solve<float>(Problem&, const float*, float*);
 
 template <typename T>
 int launch_fill(Problem& P, T* x, size_t n, T v) {

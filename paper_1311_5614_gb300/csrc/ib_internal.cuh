@@ -155,8 +155,11 @@ struct LevelInfo {
   int cap_struct = 0;  // allocated structure-box slots
   int* flag = nullptr;        // [nb * nb] structure flag -> slot (-1 free)
   double* Mstruct = nullptr;  // [cap][nB * nB] inverse (column-major), FP64
+  double* Sfree = nullptr;    // [nB * nB] Stokes block of a box (column-major), FP64
   double* Mfree = nullptr;    // [nB * nB] shared inverse of structure-free boxes, FP64
   float* Mfree32 = nullptr;   // FP32 copy for the FP32 V-cycle
+  double* rE64 = nullptr;     // [2 N^2] elasticity residual part -dt E w (patch rows only)
+  float* rE32 = nullptr;
   Patches<double> pat64;      // FP64 patches (operator path)
   Patches<float> pat32;       // FP32 patches (FP32 V-cycle)
   LevelBuf<double> v64;
@@ -179,10 +182,21 @@ struct Problem {
   double prof_bytes[IB_KC_COUNT] = {};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<ProfRec> pending;
+  // V-cycle engine
+  // index [0] = FP32 V-cycle, [1] = FP64 V-cycle
+  int tail_level[2] = {0, 0};    // first level handled by the single-CTA kernel
+  bool use_graph = true;
+  bool graph_dirty[2] = {true, true};
+  cudaGraphExec_t vgraph[2] = {nullptr, nullptr};
+  bool has64 = false, has32 = false;  // hierarchies available for the V-cycle
+  cudaStream_t gstream = nullptr;                 // private stream the graph is captured on and replayed on
+  cudaEvent_t gev[2] = {nullptr, nullptr};        // joins between the caller's stream and gstream
+  long long graph_launches[2][IB_KC_COUNT] = {};
   cudaStream_t stream = nullptr;
   int np = 0, ns = 0;
   int nlev = 0;
   int nB = 0;  // unknowns per box
+  bool free_ready = false;  // free-box inverses computed (they do not depend on the points)
   std::vector<LevelInfo> lev;
 
   // structure (device)
@@ -207,6 +221,7 @@ struct Problem {
   // Krylov (FP64)
   double* V = nullptr;        // [m + 1][n]
   void* Z = nullptr;          // [m][n] in the preconditioner precision
+  double* Z64 = nullptr;      // [m][n] FP64 directions after an FP32 -> FP64 escalation
   double* H = nullptr;        // [(m + 1) * m] column-major Hessenberg
   double* givens = nullptr;   // cs[m], sn[m], g[m + 1], y[m]
   double* dots = nullptr;     // partial sums [blocks][m + 2]
@@ -252,16 +267,9 @@ int launch_assemble_coarse(Problem& P);
 // ---------------------------------------------------------------- launchers (grid)
 template <typename T>
 int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool residual);
-template <typename T>
-int launch_restrict(Problem& P, int level, const T* rf, T* bc);
-template <typename T>
-int launch_prolong_add(Problem& P, int level, const T* ec, T* wf);
-template <typename T>
-int launch_box_solve(Problem& P, int level, int color, const T* r, T* w);
-int launch_box_stokes_fill(Problem& P, int level, bool free_box);
+int launch_free_box(Problem& P, int level);
+int launch_struct_fill(Problem& P, int level);
 int launch_invert(Problem& P, double* M, int n, int count);
-template <typename T>
-int launch_coarse_solve(Problem& P, const T* b, T* w);
 int launch_coarse_fill(Problem& P);
 template <typename T>
 int launch_fill(Problem& P, T* x, size_t n, T v);
@@ -276,7 +284,7 @@ int launch_scale_copy(Problem& P, const double* x, const double* s, double* y, b
 int launch_givens(Problem& P, int j, double bnorm_tol, double* out_scalars);
 int launch_backsolve(Problem& P, int k);
 template <typename T>
-int launch_update_x(Problem& P, const T* Z, int k, double* x);
+int launch_update_x(Problem& P, const T* Z, int k, double* x, int first = 0);
 int launch_axpby(Problem& P, double a, const double* x, double b, const double* y, double* z);
 int launch_pressure_mean_remove(Problem& P, double* w);
 

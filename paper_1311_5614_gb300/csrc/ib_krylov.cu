@@ -215,18 +215,19 @@ int launch_backsolve(Problem& P, int k) {
 }
 
 template <typename T>
-int launch_update_x(Problem& P, const T* Z, int k, double* x) {
+int launch_update_x(Problem& P, const T* Z, int k, double* x, int first) {
   if (k <= 0) return IB_OK;
   int m = P.max_m;
-  const double* y = P.givens + 3 * m + 1;
+  const double* y = P.givens + 3 * m + 1 + first;
+  Z += (size_t)first * 3 * P.lev[0].N * P.lev[0].N;
   long n = nvec_len(P);
   KScope ks(P, IB_KC_KRYLOV, (double)k * n * sizeof(T) + 2.0 * n * 8.0);
   k_update_x<T><<<nblk(n), TPB, 0, P.stream>>>(Z, k, n, y, x);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
-template int launch_update_x<double>(Problem&, const double*, int, double*);
-template int launch_update_x<float>(Problem&, const float*, int, double*);
+template int launch_update_x<double>(Problem&, const double*, int, double*, int);
+template int launch_update_x<float>(Problem&, const float*, int, double*, int);
 
 int launch_axpby(Problem& P, double a, const double* x, double b, const double* y, double* z) {
   long n = nvec_len(P);

@@ -1,0 +1,174 @@
+// Element-level device functions of the V-cycle, shared by the grid-wide
+// kernels of the fine levels and the single-CTA kernel of the coarse levels.
+// Pointers may address global or shared memory.
+#pragma once
+
+#include "ib_internal.cuh"
+
+namespace ib {
+
+// (A_S w) at the unknown (comp, i, j) of a periodic N x N level (sec. 2.2
+// stencils: mu Lap - rho/dt on velocities, -G p on faces, D w on cells).
+template <typename T>
+__device__ __forceinline__ T stokes_row(const T* __restrict__ w, int N, const StokesCoef<T>& c, int comp,
+                                        int i, int j) {
+  const int n = N * N, m = N - 1;
+  const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+  const T* u = w;
+  const T* v = w + n;
+  const T* p = w + 2 * n;
+  if (comp == 0) {
+    return c.diag * u[j * N + i] + c.off * (u[j * N + ip] + u[j * N + im] + u[jp * N + i] + u[jm * N + i]) -
+           c.g * (p[j * N + i] - p[j * N + im]);
+  }
+  if (comp == 1) {
+    return c.diag * v[j * N + i] + c.off * (v[j * N + ip] + v[j * N + im] + v[jp * N + i] + v[jm * N + i]) -
+           c.g * (p[j * N + i] - p[jm * N + i]);
+  }
+  return c.g * (u[j * N + ip] - u[j * N + i] + v[jp * N + i] - v[j * N + i]);
+}
+
+// Residual r = b - A_S w + rE at (comp, i, j); rE (-dt E w, velocity rows only)
+// may be NULL.
+template <typename T>
+__device__ __forceinline__ T resid_at(const T* w, const T* b, const T* rE, int N, const StokesCoef<T>& c,
+                                      int comp, int i, int j) {
+  int g = comp * N * N + j * N + i;
+  T r = b[g] - stokes_row(w, N, c, comp, i, j);
+  if (rE && comp < 2) r += rE[g];
+  return r;
+}
+
+// Restriction of the full residual (b - A_S w + rE) to coarse cell (I, J) of an
+// Nc grid: u by (1/8)[1 2 1; 1 2 1], v transposed, p by the four-cell average.
+template <typename T>
+__device__ __forceinline__ void restrict_resid_cell(const T* w, const T* b, const T* rE, int N,
+                                                    const StokesCoef<T>& c, int I, int J, T* ru, T* rv, T* rp) {
+  const int m = N - 1;
+  const int xm = (2 * I - 1) & m, x0 = 2 * I, x1 = 2 * I + 1;
+  const int ym = (2 * J - 1) & m, y0 = 2 * J, y1 = 2 * J + 1;
+  *ru = (T)0.125 * (resid_at(w, b, rE, N, c, 0, xm, y0) + resid_at(w, b, rE, N, c, 0, xm, y1) +
+                    resid_at(w, b, rE, N, c, 0, x1, y0) + resid_at(w, b, rE, N, c, 0, x1, y1)) +
+        (T)0.25 * (resid_at(w, b, rE, N, c, 0, x0, y0) + resid_at(w, b, rE, N, c, 0, x0, y1));
+  *rv = (T)0.125 * (resid_at(w, b, rE, N, c, 1, x0, ym) + resid_at(w, b, rE, N, c, 1, x1, ym) +
+                    resid_at(w, b, rE, N, c, 1, x0, y1) + resid_at(w, b, rE, N, c, 1, x1, y1)) +
+        (T)0.25 * (resid_at(w, b, rE, N, c, 1, x0, y0) + resid_at(w, b, rE, N, c, 1, x1, y0));
+  *rp = (T)0.25 * (resid_at(w, b, rE, N, c, 2, x0, y0) + resid_at(w, b, rE, N, c, 2, x1, y0) +
+                   resid_at(w, b, rE, N, c, 2, x0, y1) + resid_at(w, b, rE, N, c, 2, x1, y1));
+}
+
+// Same restriction applied to a stored residual vector r.
+template <typename T>
+__device__ __forceinline__ void restrict_cell(const T* r, int N, int I, int J, T* ru, T* rv, T* rp) {
+  const int n = N * N, m = N - 1;
+  const T* u = r;
+  const T* v = r + n;
+  const T* p = r + 2 * n;
+  const int xm = (2 * I - 1) & m, x0 = 2 * I, x1 = 2 * I + 1;
+  const int ym = (2 * J - 1) & m, y0 = 2 * J, y1 = 2 * J + 1;
+  *ru = (T)0.125 * (u[y0 * N + xm] + u[y1 * N + xm] + u[y0 * N + x1] + u[y1 * N + x1]) +
+        (T)0.25 * (u[y0 * N + x0] + u[y1 * N + x0]);
+  *rv = (T)0.125 * (v[ym * N + x0] + v[ym * N + x1] + v[y1 * N + x0] + v[y1 * N + x1]) +
+        (T)0.25 * (v[y0 * N + x0] + v[y0 * N + x1]);
+  *rp = (T)0.25 * (p[y0 * N + x0] + p[y0 * N + x1] + p[y1 * N + x0] + p[y1 * N + x1]);
+}
+
+// Prolongation (sec. 3.1) of the coarse correction e (Nc = N/2) to fine cell
+// (i, j): returns the three fine corrections.
+template <typename T>
+__device__ __forceinline__ void prolong_cell(const T* e, int N, int i, int j, T* cu, T* cv, T* cp) {
+  const int Nc = N / 2, nc = Nc * Nc, mc = Nc - 1;
+  const int I = i >> 1, J = j >> 1;
+  const T* u = e;
+  const T* v = e + nc;
+  const T* p = e + 2 * nc;
+  const int Jn = ((j & 1) ? J + 1 : J - 1) & mc;
+  const int In = ((i & 1) ? I + 1 : I - 1) & mc;
+  const int I1 = (I + 1) & mc, J1 = (J + 1) & mc;
+  if ((i & 1) == 0) *cu = (T)0.75 * u[J * Nc + I] + (T)0.25 * u[Jn * Nc + I];
+  else *cu = (T)0.375 * (u[J * Nc + I] + u[J * Nc + I1]) + (T)0.125 * (u[Jn * Nc + I] + u[Jn * Nc + I1]);
+  if ((j & 1) == 0) *cv = (T)0.75 * v[J * Nc + I] + (T)0.25 * v[J * Nc + In];
+  else *cv = (T)0.375 * (v[J * Nc + I] + v[J1 * Nc + I]) + (T)0.125 * (v[J * Nc + In] + v[J1 * Nc + In]);
+  *cp = p[J * Nc + I];
+}
+
+// Interpolated velocity component of point k on level grid N: sum over its
+// interp patch of w_c * wx * wy.
+template <typename T>
+__device__ __forceinline__ T interp_point(const Patches<T>& pat, const T* w, int N, int comp, int k) {
+  const T* wc = w + (size_t)comp * N * N;
+  const int x0 = pat.b_at(1, comp, 0, k), y0 = pat.b_at(1, comp, 1, k), m = N - 1;
+  T wx[PATCH];
+  int ix[PATCH];
+#pragma unroll
+  for (int a = 0; a < PATCH; ++a) {
+    wx[a] = pat.w_at(1, comp, 0, a, k);
+    ix[a] = (x0 + a) & m;
+  }
+  T s = 0;
+#pragma unroll
+  for (int bb = 0; bb < PATCH; ++bb) {
+    const T* row = wc + ((y0 + bb) & m) * N;
+    T sx = 0;
+#pragma unroll
+    for (int a = 0; a < PATCH; ++a) sx += wx[a] * row[ix[a]];
+    s += pat.w_at(1, comp, 1, bb, k) * sx;
+  }
+  return s;
+}
+
+// (J U)_k = sum over the springs at k of K_s (U_other - U_k).
+template <typename T>
+__device__ __forceinline__ void JU_point(const Springs<T>& sp, const T* U, int k, T* gx, T* gy) {
+  const int np = sp.np, ns = sp.ns;
+  const T ux = U[k], uy = U[np + k];
+  T ax = 0, ay = 0;
+  for (int q = sp.adj_ptr[k]; q < sp.adj_ptr[k + 1]; ++q) {
+    const int s = sp.adj_spring[q], o = sp.adj_other[q];
+    const T dx = U[o] - ux, dy = U[np + o] - uy;
+    const T kxx = sp.K[s], kxy = sp.K[ns + s], kyy = sp.K[2 * ns + s];
+    ax += kxx * dx + kxy * dy;
+    ay += kxy * dx + kyy * dy;
+  }
+  *gx = ax;
+  *gy = ay;
+}
+
+// y_c += g * (row bb of the spread patch of point k): 4 atomic additions.
+template <typename T>
+__device__ __forceinline__ void spread_row(const Patches<T>& pat, int N, int comp, int k, int bb, T g, T* y) {
+  const T wy = pat.w_at(0, comp, 1, bb, k) * g;
+  if (wy == (T)0) return;
+  const int m = N - 1;
+  const int x0 = pat.b_at(0, comp, 0, k), y0 = pat.b_at(0, comp, 1, k);
+  T* row = y + comp * N * N + ((y0 + bb) & m) * N;
+#pragma unroll
+  for (int a = 0; a < PATCH; ++a) {
+    const T wx = pat.w_at(0, comp, 0, a, k);
+    if (wx != (T)0) atomicAdd(&row[(x0 + a) & m], wx * wy);
+  }
+}
+
+// Zero row bb of the spread patch of point k in y (a velocity-row vector).
+template <typename T>
+__device__ __forceinline__ void zero_row(const Patches<T>& pat, int N, int comp, int k, int bb, T* y) {
+  const int m = N - 1;
+  const int x0 = pat.b_at(0, comp, 0, k), y0 = pat.b_at(0, comp, 1, k);
+  T* row = y + comp * N * N + ((y0 + bb) & m) * N;
+#pragma unroll
+  for (int a = 0; a < PATCH; ++a) row[(x0 + a) & m] = (T)0;
+}
+
+// delta = M r for a box of nB unknowns, M column-major (M[s * nB + q]); rows q
+// from q0 in steps of dq.
+template <typename TM, typename TR, typename TW>
+__device__ __forceinline__ void box_apply_rows(const TM* __restrict__ M, int nB, const TR* rs, int q0, int dq,
+                                               TW* w, const int* gs) {
+  for (int q = q0; q < nB; q += dq) {
+    TM d = 0;
+    for (int s = 0; s < nB; ++s) d += M[(size_t)s * nB + q] * (TM)rs[s];
+    w[gs[q]] += (TW)d;
+  }
+}
+
+}  // namespace ib

@@ -281,27 +281,31 @@ __global__ void k_assign_slots(int* flag, int nbox, int* count) {
 }
 
 // Add coef * (S_l J S^*_l) restricted to box rows/cols to the dense box blocks.
-// Thread = (point k, coupling q): q = 0 is the diagonal block J_kk = -sum K_s,
-// q >= 1 the off-diagonal block J_kl = K_s of the q-th spring at k.
+// Thread = (point k, coupling q, row component c, row node of k's spread patch):
+// q = 0 is the diagonal block J_kk = -sum K_s, q >= 1 the off-diagonal block
+// J_kl = K_s of the q-th spring at k (at most 7 springs per point).
 // mode 0: structure boxes (column-major n_B x n_B blocks indexed by slot);
 // mode 1: the whole coarsest grid (one dense matrix, leading dimension ldm).
 template <int MODE>
 __global__ void k_assemble_E(Patches<double> pat, Springs<double> sp, int N, int b, int nb,
                              const int* __restrict__ slot, double coef, double* M, int nB, int ldm,
                              int* err) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int np = sp.np, ns = sp.ns;
-  // one thread per (point, coupling): couplings = 1 + degree
-  int k = t / 8, q = t % 8;
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int np = sp.np, ns = sp.ns;
+  const int k = (int)(t >> 8), rem = (int)(t & 255);
+  const int q = rem >> 5, c = (rem >> 4) & 1, node = rem & 15;
   if (k >= np) return;
-  int deg = sp.adj_ptr[k + 1] - sp.adj_ptr[k];
+  const int deg = sp.adj_ptr[k + 1] - sp.adj_ptr[k];
   if (q > deg) return;
-  if (deg > 7 && q == 0) atomicOr(err, DEV_ERR_INDEX);  // more than 7 springs per point unsupported
+  if (deg > 7 && rem == 0) atomicOr(err, DEV_ERR_INDEX);
+  const int ra = node & 3, rb = node >> 2;
+  const double ws = pat.w_at(0, c, 0, ra, k) * pat.w_at(0, c, 1, rb, k);
+  if (ws == 0.0) return;
   int l;
   double J[2][2];
   if (q == 0) {
     l = k;
-    J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.0;
+    J[0][0] = J[0][1] = J[1][1] = 0.0;
     for (int a = sp.adj_ptr[k]; a < sp.adj_ptr[k + 1]; ++a) {
       int s = sp.adj_spring[a];
       J[0][0] -= sp.K[s];
@@ -317,55 +321,43 @@ __global__ void k_assemble_E(Patches<double> pat, Springs<double> sp, int N, int
     J[1][1] = sp.K[2 * ns + s];
   }
   J[1][0] = J[0][1];
-  int n = N * N;
-  for (int c = 0; c < 2; ++c) {  // row component (spread patch of k)
-    int sx0 = pat.b_at(0, c, 0, k), sy0 = pat.b_at(0, c, 1, k);
-    for (int rb = 0; rb < PATCH; ++rb) {
-      double wsy = pat.w_at(0, c, 1, rb, k);
-      if (wsy == 0.0) continue;
-      int rj = wrapi(sy0 + rb, N);
-      for (int ra = 0; ra < PATCH; ++ra) {
-        double ws = pat.w_at(0, c, 0, ra, k) * wsy;
-        if (ws == 0.0) continue;
-        int ri = wrapi(sx0 + ra, N);
-        // boxes containing the row unknown (c, ri, rj)
-        int nbx = (MODE == 0) ? 2 : 1;
-        for (int bx = 0; bx < nbx; ++bx) {
-          int x0 = 0, y0 = 0, sl = 0;
-          if (MODE == 0) {
-            int I = ri / b, Jb = rj / b;
-            if (bx == 1) {
-              if (c == 0 && ri % b == 0) I = (I - 1 + nb) % nb;
-              else if (c == 1 && rj % b == 0) Jb = (Jb - 1 + nb) % nb;
-              else continue;
-            }
-            sl = slot[Jb * nb + I];
-            if (sl < 0) { atomicOr(err, DEV_ERR_INDEX); continue; }
-            x0 = I * b;
-            y0 = Jb * b;
-          }
-          int rq = (MODE == 0) ? box_local(c, ri, rj, x0, y0, b, N) : c * n + rj * N + ri;
-          if (rq < 0) { atomicOr(err, DEV_ERR_INDEX); continue; }
-          double* Mb = (MODE == 0) ? M + (size_t)sl * nB * nB : M;
-          int ld = (MODE == 0) ? nB : ldm;
-          for (int cc = 0; cc < 2; ++cc) {  // column component (interp patch of l)
-            double jv = coef * ws * J[c][cc];
-            if (jv == 0.0) continue;
-            int ix0 = pat.b_at(1, cc, 0, l), iy0 = pat.b_at(1, cc, 1, l);
-            for (int cb = 0; cb < PATCH; ++cb) {
-              double wiy = pat.w_at(1, cc, 1, cb, l);
-              if (wiy == 0.0) continue;
-              int cj = wrapi(iy0 + cb, N);
-              for (int ca = 0; ca < PATCH; ++ca) {
-                double wi = pat.w_at(1, cc, 0, ca, l) * wiy;
-                if (wi == 0.0) continue;
-                int ci = wrapi(ix0 + ca, N);
-                int cq = (MODE == 0) ? box_local(cc, ci, cj, x0, y0, b, N) : cc * n + cj * N + ci;
-                if (cq < 0) continue;
-                atomicAdd(&Mb[(size_t)cq * ld + rq], jv * wi);
-              }
-            }
-          }
+  const int n = N * N;
+  const int ri = wrapi(pat.b_at(0, c, 0, k) + ra, N), rj = wrapi(pat.b_at(0, c, 1, k) + rb, N);
+  const int nbx = (MODE == 0) ? 2 : 1;
+  for (int bx = 0; bx < nbx; ++bx) {
+    int x0 = 0, y0 = 0, sl = 0;
+    if (MODE == 0) {
+      int I = ri / b, Jb = rj / b;
+      if (bx == 1) {
+        // a face on a box edge belongs to the two boxes on either side
+        if (c == 0 && ri % b == 0) I = (I - 1 + nb) % nb;
+        else if (c == 1 && rj % b == 0) Jb = (Jb - 1 + nb) % nb;
+        else continue;
+      }
+      sl = slot[Jb * nb + I];
+      if (sl < 0) { atomicOr(err, DEV_ERR_INDEX); continue; }
+      x0 = I * b;
+      y0 = Jb * b;
+    }
+    const int rq = (MODE == 0) ? box_local(c, ri, rj, x0, y0, b, N) : c * n + rj * N + ri;
+    if (rq < 0) { atomicOr(err, DEV_ERR_INDEX); continue; }
+    double* Mb = (MODE == 0) ? M + (size_t)sl * nB * nB : M;
+    const int ld = (MODE == 0) ? nB : ldm;
+    for (int cc = 0; cc < 2; ++cc) {  // column component (interp patch of l)
+      const double jv = coef * ws * J[c][cc];
+      if (jv == 0.0) continue;
+      const int ix0 = pat.b_at(1, cc, 0, l), iy0 = pat.b_at(1, cc, 1, l);
+      for (int cb = 0; cb < PATCH; ++cb) {
+        const double wiy = pat.w_at(1, cc, 1, cb, l);
+        if (wiy == 0.0) continue;
+        const int cj = wrapi(iy0 + cb, N);
+        for (int ca = 0; ca < PATCH; ++ca) {
+          const double wi = pat.w_at(1, cc, 0, ca, l) * wiy;
+          if (wi == 0.0) continue;
+          const int ci = wrapi(ix0 + ca, N);
+          const int cq = (MODE == 0) ? box_local(cc, ci, cj, x0, y0, b, N) : cc * n + cj * N + ci;
+          if (cq < 0) continue;
+          atomicAdd(&Mb[(size_t)cq * ld + rq], jv * wi);
         }
       }
     }
@@ -505,7 +497,7 @@ int launch_assemble_struct(Problem& P, int level) {
   if (P.np == 0 || P.ns == 0 || L.n_struct == 0) return IB_OK;
   double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
   KScope ks(P, IB_KC_SETUP, 0.0);
-  k_assemble_E<0><<<nblk(8L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
+  k_assemble_E<0><<<nblk(256L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
                                                           P.prm.box, L.nb, L.flag, coef, L.Mstruct,
                                                           P.nB, 0, P.dev_err);
   IB_LAUNCH_CHECK();
@@ -517,7 +509,7 @@ int launch_assemble_coarse(Problem& P) {
   LevelInfo& L = P.lev[P.nlev - 1];
   double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
   KScope ks(P, IB_KC_SETUP, 0.0);
-  k_assemble_E<1><<<nblk(8L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
+  k_assemble_E<1><<<nblk(256L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
                                                           P.prm.box, 1, nullptr, coef, P.Mcoarse, 0,
                                                           P.nc + P.nborder, P.dev_err);
   IB_LAUNCH_CHECK();

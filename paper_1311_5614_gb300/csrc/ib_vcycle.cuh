@@ -1,0 +1,42 @@
+// Launch arguments of the single-CTA coarse-level ("tail") kernel and the
+// host entry points of the V-cycle engine.
+#pragma once
+
+#include "ib_internal.cuh"
+
+namespace ib {
+
+constexpr int MAX_LEVELS = 16;
+
+template <typename T>
+struct TailLevel {
+  int N;
+  StokesCoef<T> c;
+  Patches<T> pat;
+  const int* slot;
+  const double* Ms;
+  const T* Mf;
+};
+
+template <typename T>
+struct TailArgs {
+  int nlev;  // levels in the tail: lev[0] is the finest of them, lev[nlev-1] the coarsest grid
+  TailLevel<T> lev[MAX_LEVELS];
+  const T* b_in;  // right-hand side of lev[0] (global)
+  T* w_out;       // correction of lev[0] (global)
+  T* U;           // point velocities (global scratch)
+  Springs<T> sp;
+  T coefE;        // -dt / h_0^2: residual sign of the elasticity term
+  const double* Mc;
+  int nc, ldc;
+  int nu1, nu2, box, nB, post_rev, stage_warps;
+  int off_w[MAX_LEVELS], off_b[MAX_LEVELS], off_r, off_sr, off_sg;  // shared-memory offsets (bytes)
+};
+
+template <typename T>
+int vcycle_prepare(Problem& P);
+template <typename T>
+int vcycle_run(Problem& P);
+int vcycle_reset_rE(Problem& P);
+
+}  // namespace ib
