@@ -5,9 +5,11 @@ Workload (default): the 256^2 periodic MAC grid with the 512-point elastic
 ellipse (semi-axes 0.28/0.22 at (0.5, 0.5), rest length 2*pi*0.25/512), rho =
 mu = 1, swept over kappa in {1, 1e2, 1e4, 1e6} x dt in {1e-3, 1e-2}: one bench
 step = one backward-Euler IB step (set-up + MG-preconditioned FGMRES to 1e-8
-+ point update) for each of the 8 cases, inputs resident on the device.
-value = mean wall time per implicit IB step (ms), CUDA events, L2 flushed
-between timed steps.
++ point update) for each of the 8 cases, solved together as one batch
+(ib_solve_step_batch, FP32 V-cycle in FP64 FGMRES), inputs resident on the
+device.  value = device time of the step / 8 (ms per implicit IB step), CUDA
+events, L2 flushed between timed steps.  The line also carries the same sweep
+solved case by case in FP64 and in FP32 ("forms").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|fp64] [--box B]
@@ -56,6 +58,7 @@ def config_dict(args):
             "box": args.box, "precision": args.precision, "nu": [1, 1], "tol": 1e-8,
             "max_iters": args.max_iters, "escalate": args.precision == "fp32",
             "l2": "flushed (256 MiB write) before every timed step",
+            "form": "batched (one stream per case)",
             "parallelism": "replicas" if args.world > 1 else "single GPU"}
 
 
@@ -196,81 +199,117 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def _timed_steps(torch, step_fn, flush, stream, warmup, steps, profile_range=False):
+    """W untimed steps, then K steps each bracketed by CUDA events, L2 flushed before each.
+    With profile_range the first timed step is also bracketed by cudaProfilerStart/Stop
+    (for an ncu launch list of exactly one step with --profile-from-start off)."""
+    for _ in range(warmup):
+        step_fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        if profile_range and k == 0:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+        ev[k][0].record(stream)
+        step_fn()
+        ev[k][1].record(stream)
+        if profile_range and k == 0:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
 def run_ours(args):
     import torch
 
     import paper_1311_5614_gb300 as pkg
+    from paper_1311_5614_gb300 import capi as C
 
     rank, world, local_rank = args.rank, args.world, args.local_rank
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     probs = workload_problems(args.box)
-    solvers = [pkg.IBSolver.from_problem(p, precision=args.precision, max_iters=args.max_iters) for p in probs]
+    nc = len(probs)
     nn = 3 * N_GRID * N_GRID
-    X0 = [torch.tensor(p.X, dtype=torch.float64, device=dev) for p in probs]
-    Xw = [x.clone() for x in X0]
-    up = [torch.zeros(nn, dtype=torch.float64, device=dev) for _ in probs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    stats = [None] * len(probs)
+    X0 = torch.tensor(np.concatenate([p.X for p in probs]), dtype=torch.float64, device=dev)
+    Xw = X0.clone()
+    up = torch.zeros(nc * nn, dtype=torch.float64, device=dev)
+    npts = [p.n_points for p in probs]
+    xoff = np.concatenate([[0], np.cumsum(npts)])  # row offsets of each case in X
 
-    def one_step():
+    # --- sequential forms: one IBSolver per case, solved one after another
+    def make_seq(prec):
+        return [pkg.IBSolver.from_problem(p, precision=prec, max_iters=args.max_iters) for p in probs]
+
+    def seq_step(solvers, stats):
+        Xw.copy_(X0)
         for i, s in enumerate(solvers):
-            Xw[i].copy_(X0[i])
-            stats[i] = s.solve_step(None, up[i], Xw[i])
+            stats[i] = s.solve_step(None, up[i * nn:(i + 1) * nn], Xw[xoff[i]:xoff[i + 1]])
 
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
+    forms = {}
+    seq_stats = {}
+    for prec in (["fp64", "fp32"] if args.forms else [args.precision]):
+        solvers = make_seq(prec)
+        st = [None] * nc
+        ms = _timed_steps(torch, lambda: seq_step(solvers, st), flush, stream, args.warmup, args.steps)
+        forms["sequential_" + prec] = {"ms_per_ib_step": sum(ms) / (args.steps * nc),
+                                       "iters": [x["iters"] for x in st], "status": [x["status"] for x in st],
+                                       "escalated_at": [x["escalated_at"] for x in st]}
+        seq_stats[prec] = (solvers, st)
 
-    # timed region
+    # --- batched form (headline): all cases in one ib_solve_step_batch call
+    batch = pkg.IBBatch(probs, precision=args.precision, max_iters=args.max_iters)
+    bstats = [None]
+
+    def batch_step():
+        Xw.copy_(X0)
+        bstats[0] = batch.solve_step(None, up, Xw)
+
+    launches0 = sum(C.ib_launch_count(batch.problem(k)) for k in range(nc))
     clk = ClockSampler(local_rank)
-    launches0 = sum(s.launch_count() for s in solvers)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    # warm-up of the batched form, then the timed region
+    for _ in range(args.warmup):
+        batch_step()
+    torch.cuda.synchronize()
+    launches0 = sum(C.ib_launch_count(batch.problem(k)) for k in range(nc))
     barrier(world)
     torch.cuda.synchronize()
     clk.start()
     t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        one_step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = _timed_steps(torch, batch_step, flush, stream, 0, args.steps, args.profile_range)
     t_wall = time.perf_counter() - t_wall
     barrier(world)
     clocks = clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    gpu_launches = sum(s.launch_count() for s in solvers) - launches0
-    per_ib_ms, t_max = aggregate(step_ms, args.steps * len(probs), world)
-    iters = [st["iters"] for st in stats]
-    status = [st["status"] for st in stats]
-    escal = [st["escalated_at"] for st in stats]
+    gpu_launches = sum(C.ib_launch_count(batch.problem(k)) for k in range(nc)) - launches0
+    per_ib_ms, t_max = aggregate(step_ms, args.steps * nc, world)
+    stats = bstats[0]
+    forms["batched_" + args.precision] = {"ms_per_ib_step": per_ib_ms, "iters": [x["iters"] for x in stats],
+                                          "status": [x["status"] for x in stats],
+                                          "escalated_at": [x["escalated_at"] for x in stats]}
 
     # end-to-end through the C ABI with host buffers: H2D of X^n, D2H of u, v, p and X^{n+1}
-    Xh = [torch.tensor(p.X, dtype=torch.float64).pin_memory() for p in probs]
-    uph = [torch.empty(nn, dtype=torch.float64).pin_memory() for _ in probs]
-    Xoh = [torch.empty_like(x) .pin_memory() for x in Xh]
-    e2e_ms = []
-    for k in range(args.warmup + args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for i, s in enumerate(solvers):
-            Xw[i].copy_(Xh[i], non_blocking=True)
-            s.solve_step(None, up[i], Xw[i])
-            uph[i].copy_(up[i], non_blocking=True)
-            Xoh[i].copy_(Xw[i], non_blocking=True)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
-    e2e_per, _ = aggregate(e2e_ms, args.steps * len(probs), world)
-    h2d = sum(x.numel() * 8 for x in Xh)
-    d2h = sum(u.numel() * 8 for u in uph) + sum(x.numel() * 8 for x in Xoh)
+    Xh = torch.tensor(np.concatenate([p.X for p in probs]), dtype=torch.float64).pin_memory()
+    uph = torch.empty(nc * nn, dtype=torch.float64).pin_memory()
+    Xoh = torch.empty_like(Xh).pin_memory()
+
+    def e2e_step():
+        Xw.copy_(Xh, non_blocking=True)
+        batch.solve_step(None, up, Xw)
+        uph.copy_(up, non_blocking=True)
+        Xoh.copy_(Xw, non_blocking=True)
+
+    e2e_ms = _timed_steps(torch, e2e_step, flush, stream, args.warmup, args.steps)
+    e2e_per, _ = aggregate(e2e_ms, args.steps * nc, world)
+    h2d = Xh.numel() * 8
+    d2h = uph.numel() * 8 + Xoh.numel() * 8
 
     # V-cycle throughput on the kappa = 1e4, dt = 1e-3 case (the preconditioner alone)
+    solvers, _ = seq_stats[args.precision] if args.precision in seq_stats else (make_seq(args.precision), None)
     vs = solvers[2]
     bv = torch.randn(nn, dtype=torch.float64, device=dev)
     wv = torch.zeros_like(bv)
@@ -286,10 +325,12 @@ def run_ours(args):
     vcycle_ms = a.elapsed_time(b) / nv
     vcycle_dofs = nn / (vcycle_ms * 1e-3)
 
-    # profiled pass (separate from the timed region): per-class device time and bytes
+    # profiled pass (separate from the timed region, sequential so launches do not
+    # overlap): per-class device time and algorithmic bytes
     for s in solvers:
         s.profile(True)
-    one_step()
+    st = [None] * nc
+    seq_step(solvers, st)
     torch.cuda.synchronize()
     prof = {}
     for s in solvers:
@@ -299,7 +340,7 @@ def run_ours(args):
             q[1] += ms_
             q[2] += by_
         s.profile(False)
-    hot = [c for c in ("stokes", "box", "interp", "spread", "transfer")]
+    hot = ("stokes", "box", "interp", "spread", "transfer")
     dom = max(hot, key=lambda c: prof[c][1])
     n_, ms_, by_ = prof[dom]
     peaks = {}
@@ -322,8 +363,10 @@ def run_ours(args):
         cpu = {"value": ms_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one implicit step of the kappa=1e4, dt=1e-3 case (%d FGMRES iterations)" % its_cpu}
 
-    for s in solvers:
-        s.close()
+    for pr in seq_stats.values():
+        for s in pr[0]:
+            s.close()
+    batch.close()
     if rank == 0:
         line = {"metric": METRIC, "value": per_ib_ms, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -333,9 +376,9 @@ def run_ours(args):
                 "e2e": {"value": e2e_per, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
-                "clocks": clocks, "iters": iters, "status": status, "escalated_at": escal,
+                "clocks": clocks, "forms": forms,
                 "vcycle": {"ms": vcycle_ms, "dof_per_s": vcycle_dofs, "dof": nn,
-                           "case": "kappa=1e4, dt=1e-3"},
+                           "case": "kappa=1e4, dt=1e-3", "precision": args.precision},
                 "wall_s_timed": t_wall,
                 "profile": {k: {"launches": v[0], "ms": v[1], "bytes": v[2]} for k, v in prof.items()}}
         print(json.dumps(line), flush=True)
@@ -352,6 +395,10 @@ def main(argv=None):
     ap.add_argument("--box", type=int, default=4)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the first timed step with cudaProfilerStart/Stop")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the sequential FP64 / FP32 comparison forms")
     ap.add_argument("--rotate", action="store_true", help="reference arm: rotate through the cases")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel (from a capture)")

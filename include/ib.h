@@ -158,6 +158,36 @@ IB_API int ib_level_size(const ib_problem* prob, int32_t level);
  * as found by the last set-up. */
 IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
 
+/* ---- Batches of independent problems (SURVEY batching row; not in the paper) ----
+ *
+ * A batch holds nprob independent problems of any grid sizes and parameters.
+ * Each problem gets its own CUDA stream and its own captured V-cycle graph, and
+ * a pool of host threads (up to 16; the environment variable IB_BATCH_THREADS
+ * overrides the count) drives the problems' FGMRES iterations at the same time,
+ * so the small, latency-bound launches of different problems overlap on the GPU.
+ *   params   host [nprob]
+ *   pt_off   host [nprob + 1] point offsets (pt_off[0] = 0); sp_off likewise for springs
+ *   X, springs, kappa, rest   host, concatenated per problem; spring indices are
+ *            local to their problem
+ *   stream   the caller's stream: ib_solve_step_batch starts after the work already
+ *            queued on it and the caller's stream waits for the whole batch
+ * Storage of the batched vectors: problem k's block of up_all starts at
+ * sum_{i<k} 3 N_i^2 doubles, of u_n_all at sum_{i<k} 2 N_i^2, of X_all at
+ * 2 pt_off[k]. */
+typedef struct ib_batch ib_batch;
+IB_API int ib_setup_batch(int32_t nprob, const ib_params* params, const int32_t* pt_off, const double* X,
+                          const int32_t* sp_off, const int32_t* springs, const double* kappa,
+                          const double* rest, void* stream, ib_batch** out);
+/* One implicit step of every problem (see ib_solve_step).  u_n_all device or NULL;
+ * up_all, X_all device; stats host [nprob] or NULL.  Returns the worst status over
+ * the problems (IB_ERR_NOT_CONVERGED only if every other problem succeeded). */
+IB_API int ib_solve_step_batch(ib_batch* batch, const double* u_n_all, double* up_all, double* X_all,
+                               ib_stats* stats);
+IB_API int ib_batch_size(const ib_batch* batch);
+/* The k-th problem of the batch (owned by the batch; do not destroy it). */
+IB_API ib_problem* ib_batch_problem(ib_batch* batch, int32_t k);
+IB_API void ib_destroy_batch(ib_batch* batch);
+
 /* Kernel classes for launch counting and event timing. */
 enum {
   IB_KC_STOKES = 0,   /* level Stokes residual / apply */

@@ -80,6 +80,11 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ib_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(ib_params), ctypes.c_int32, _P, ctypes.c_int32, _P,
                                         _P, _P, _P, _P, _P]),
+    "ib_setup_batch": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "ib_solve_step_batch": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ib_batch_size": (ctypes.c_int, [_P]),
+    "ib_batch_problem": (_P, [_P, ctypes.c_int32]),
+    "ib_destroy_batch": (None, [_P]),
     "ib_destroy": (None, [_P]),
     "ib_last_error": (ctypes.c_char_p, []),
     "ib_version": (ctypes.c_char_p, []),
@@ -259,6 +264,79 @@ def ib_last_error():
 
 def ib_version():
     return lib().ib_version().decode()
+
+
+def ib_setup_batch(params_list, X_list, springs_list, kappa_list, rest_list, stream=None):
+    """Create a batch of independent problems from per-problem host arrays."""
+    import torch
+
+    n = len(params_list)
+    P = (ib_params * n)(*params_list)
+    pt = np.zeros(n + 1, dtype=np.int32)
+    sp = np.zeros(n + 1, dtype=np.int32)
+    for k in range(n):
+        pt[k + 1] = pt[k] + np.asarray(X_list[k]).reshape(-1, 2).shape[0]
+        sp[k + 1] = sp[k] + np.asarray(springs_list[k]).reshape(-1, 2).shape[0]
+    X = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 2) for x in X_list]))
+    S = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32).reshape(-1, 2) for x in springs_list]))
+    K = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).ravel() for x in kappa_list]))
+    R = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).ravel() for x in rest_list]))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    _check(lib().ib_setup_batch(n, P, pt.ctypes.data_as(_P), X.ctypes.data_as(_P), sp.ctypes.data_as(_P),
+                                S.ctypes.data_as(_P), K.ctypes.data_as(_P), R.ctypes.data_as(_P),
+                                ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out, pt, sp
+
+
+def ib_solve_step_batch(batch, u_n_all, up_all, X_all, nprob, raise_on_not_converged=False):
+    """One implicit step of every problem; returns the per-problem stats dicts."""
+    st = (ib_stats * nprob)()
+
+    def ptr(t):
+        return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+    code = lib().ib_solve_step_batch(batch, ptr(u_n_all), ptr(up_all), ptr(X_all), st)
+    if code != IB_OK and (code != IB_ERR_NOT_CONVERGED or raise_on_not_converged):
+        _check(code)
+    return [s.as_dict() for s in st]
+
+
+class IBBatch:
+    """Independent problems solved together (each on its own stream)."""
+
+    def __init__(self, problems, **kw):
+        plist = []
+        for p in problems:
+            d = dict(L=p.L, rho=p.rho, mu=p.mu, dt=p.dt, delta=p.delta, box=p.box, nu1=p.nu1, nu2=p.nu2,
+                     tol=p.tol, max_iters=p.max_iters, jacobian="clamped" if p.clamped else "exact")
+            d.update(kw)
+            plist.append(make_params(p.N, **d))
+        self.params = plist
+        self.sizes = [p.N for p in problems]
+        self.handle, self.pt_off, self.sp_off = ib_setup_batch(
+            plist, [p.X for p in problems], [p.springs for p in problems], [p.kappa for p in problems],
+            [p.rest for p in problems])
+        self.up_off = np.concatenate([[0], np.cumsum([3 * n * n for n in self.sizes])]).astype(np.int64)
+        self.nprob = len(problems)
+
+    def solve_step(self, u_n_all, up_all, X_all, raise_on_not_converged=False):
+        return ib_solve_step_batch(self.handle, u_n_all, up_all, X_all, self.nprob, raise_on_not_converged)
+
+    def problem(self, k):
+        return lib().ib_batch_problem(self.handle, int(k))
+
+    def close(self):
+        if self.handle:
+            lib().ib_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class IBSolver:

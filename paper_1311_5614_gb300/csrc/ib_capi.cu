@@ -4,8 +4,11 @@
 // orders launches on the problem's stream and reads back the few scalars that
 // decide control flow (structure-box counts, Krylov residual estimates).
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -453,6 +456,55 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
   return fail(IB_ERR_NOT_CONVERGED, "FGMRES reached max_iters above tol");
 }
 
+// One implicit IB step on the problem's stream (the body of ib_solve_step).
+int solve_step_impl(Problem& P, const double* u_n, double* up, double* X, ib_stats* stats) {
+  if (P.np > 0 && !X) return fail(IB_ERR_INVALID_ARG, "X is NULL");
+  ib_stats local;
+  std::memset(&local, 0, sizeof(local));
+  ib_stats* st = stats ? stats : &local;
+  std::memset(st, 0, sizeof(*st));
+  st->escalated_at = -1;
+  size_t n = 3ul * P.prm.N * P.prm.N;
+  IB_CUDA_TRY(cudaEventRecord(P.ev[0], P.stream));
+  if (P.np > 0)
+    IB_CUDA_TRY(cudaMemcpyAsync(P.X, X, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice, P.stream));
+  int rc = setup_hierarchy(P);
+  if (rc != IB_OK) { st->status = rc; return rc; }
+  IB_TRY(launch_fill<double>(P, P.b64, n, 0.0));
+  IB_TRY(launch_spread_force(P, P.b64));
+  if (u_n && P.prm.rho != 0.0) {
+    long n2 = 2L * P.prm.N * P.prm.N;
+    KScope ks(P, IB_KC_OTHER, 3.0 * n2 * 8.0);
+    k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, P.b64, n2);
+    IB_LAUNCH_CHECK();
+  }
+  IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
+  if (P.prm.precision == IB_FP64) rc = fgmres<double>(P, P.b64, P.x64, st);
+  else rc = fgmres<float>(P, P.b64, P.x64, st);
+  IB_CUDA_TRY(cudaEventRecord(P.ev[2], P.stream));
+  if (rc != IB_OK && rc != IB_ERR_NOT_CONVERGED) { st->status = rc; return rc; }
+  std::string msg = g_err;
+  IB_TRY(launch_pressure_mean_remove(P, P.x64));
+  IB_CUDA_TRY(cudaMemcpyAsync(up, P.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  if (P.np > 0) {
+    IB_TRY(launch_move_points(P, P.x64));
+    IB_CUDA_TRY(cudaMemcpyAsync(X, P.X, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice, P.stream));
+  }
+  IB_CUDA_TRY(cudaEventRecord(P.ev[3], P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  float t0 = 0, t1 = 0;
+  cudaEventElapsedTime(&t0, P.ev[0], P.ev[1]);
+  cudaEventElapsedTime(&t1, P.ev[1], P.ev[2]);
+  st->t_setup_ms = t0;
+  st->t_solve_ms = t1;
+  int nsb = 0;
+  for (int l = 0; l < P.nlev - 1; ++l) nsb += P.lev[l].n_struct;
+  st->n_struct_boxes = nsb;
+  st->status = rc;
+  g_err = msg;
+  return rc;
+}
+
 }  // namespace
 }  // namespace ib
 
@@ -679,52 +731,7 @@ int ib_rhs(ib_problem* H, const double* u_n, double* b) {
 int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_stats* stats) {
   g_err.clear();
   if (!H || !up) return fail(IB_ERR_INVALID_ARG, "NULL argument");
-  Problem& P = H->P;
-  if (P.np > 0 && !X) return fail(IB_ERR_INVALID_ARG, "X is NULL");
-  ib_stats local;
-  std::memset(&local, 0, sizeof(local));
-  ib_stats* st = stats ? stats : &local;
-  std::memset(st, 0, sizeof(*st));
-  st->escalated_at = -1;
-  size_t n = 3ul * P.prm.N * P.prm.N;
-  IB_CUDA_TRY(cudaEventRecord(P.ev[0], P.stream));
-  if (P.np > 0)
-    IB_CUDA_TRY(cudaMemcpyAsync(P.X, X, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice, P.stream));
-  int rc = setup_hierarchy(P);
-  if (rc != IB_OK) { st->status = rc; return rc; }
-  IB_TRY(launch_fill<double>(P, P.b64, n, 0.0));
-  IB_TRY(launch_spread_force(P, P.b64));
-  if (u_n && P.prm.rho != 0.0) {
-    long n2 = 2L * P.prm.N * P.prm.N;
-    KScope ks(P, IB_KC_OTHER, 3.0 * n2 * 8.0);
-    k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, P.b64, n2);
-    IB_LAUNCH_CHECK();
-  }
-  IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
-  if (P.prm.precision == IB_FP64) rc = fgmres<double>(P, P.b64, P.x64, st);
-  else rc = fgmres<float>(P, P.b64, P.x64, st);
-  IB_CUDA_TRY(cudaEventRecord(P.ev[2], P.stream));
-  if (rc != IB_OK && rc != IB_ERR_NOT_CONVERGED) { st->status = rc; return rc; }
-  std::string msg = g_err;
-  IB_TRY(launch_pressure_mean_remove(P, P.x64));
-  IB_CUDA_TRY(cudaMemcpyAsync(up, P.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
-  if (P.np > 0) {
-    IB_TRY(launch_move_points(P, P.x64));
-    IB_CUDA_TRY(cudaMemcpyAsync(X, P.X, sizeof(double) * 2 * P.np, cudaMemcpyDeviceToDevice, P.stream));
-  }
-  IB_CUDA_TRY(cudaEventRecord(P.ev[3], P.stream));
-  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
-  float t0 = 0, t1 = 0;
-  cudaEventElapsedTime(&t0, P.ev[0], P.ev[1]);
-  cudaEventElapsedTime(&t1, P.ev[1], P.ev[2]);
-  st->t_setup_ms = t0;
-  st->t_solve_ms = t1;
-  int nsb = 0;
-  for (int l = 0; l < P.nlev - 1; ++l) nsb += P.lev[l].n_struct;
-  st->n_struct_boxes = nsb;
-  st->status = rc;
-  g_err = msg;
-  return rc;
+  return solve_step_impl(H->P, u_n, up, X, stats);
 }
 
 int64_t ib_launch_count(const ib_problem* H, int32_t kclass) {
@@ -767,5 +774,153 @@ void ib_destroy(ib_problem* H) {
   free_problem(&H->P);
   delete H;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches of independent problems
+
+struct ib_batch {
+  std::vector<ib_problem*> probs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  std::vector<size_t> up_off, x_off;
+  cudaStream_t caller = nullptr;
+  cudaEvent_t start = nullptr;
+  int threads = 1;
+};
+
+namespace {
+
+// Run f(k) for k in [0, n) on up to `threads` host threads; returns the first
+// failing status (IB_ERR_NOT_CONVERGED only if nothing worse happened) and its message.
+template <typename F>
+int parallel_for(int n, int threads, F f, std::string* msg) {
+  std::atomic<int> next(0);
+  std::vector<int> codes(n, IB_OK);
+  std::vector<std::string> msgs(n);
+  auto work = [&]() {
+    for (;;) {
+      int k = next.fetch_add(1);
+      if (k >= n) break;
+      codes[k] = f(k);
+      if (codes[k] != IB_OK) msgs[k] = "problem " + std::to_string(k) + ": " + g_err;
+    }
+  };
+  int nt = std::max(1, std::min(threads, n));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  int worst = IB_OK;
+  for (int k = 0; k < n; ++k) {
+    if (codes[k] == IB_OK) continue;
+    if (worst == IB_OK || (worst == IB_ERR_NOT_CONVERGED && codes[k] != IB_ERR_NOT_CONVERGED)) {
+      worst = codes[k];
+      *msg = msgs[k];
+    }
+  }
+  return worst;
+}
+
+void free_batch(ib_batch* B) {
+  if (!B) return;
+  for (auto* p : B->probs)
+    if (p) ib_destroy(p);
+  for (auto s : B->streams)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : B->done)
+    if (e) cudaEventDestroy(e);
+  if (B->start) cudaEventDestroy(B->start);
+  delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ib_setup_batch(int32_t nprob, const ib_params* params, const int32_t* pt_off, const double* X,
+                   const int32_t* sp_off, const int32_t* springs, const double* kappa, const double* rest,
+                   void* stream, ib_batch** out) {
+  g_err.clear();
+  if (!out) return fail(IB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !params || !pt_off || !sp_off) return fail(IB_ERR_INVALID_ARG, "bad batch description");
+  for (int k = 0; k < nprob; ++k) {
+    if (pt_off[k + 1] < pt_off[k] || sp_off[k + 1] < sp_off[k])
+      return fail(IB_ERR_INVALID_ARG, "batch offsets must be non-decreasing");
+    IB_TRY(validate(&params[k]));
+  }
+  if (pt_off[0] != 0 || sp_off[0] != 0) return fail(IB_ERR_INVALID_ARG, "batch offsets must start at 0");
+  ib_batch* B = new (std::nothrow) ib_batch();
+  if (!B) return fail(IB_ERR_OOM, "host allocation failed");
+  B->caller = (cudaStream_t)stream;
+  B->probs.assign(nprob, nullptr);
+  B->streams.assign(nprob, nullptr);
+  B->done.assign(nprob, nullptr);
+  unsigned hw = std::thread::hardware_concurrency();
+  B->threads = (int)std::max(1u, std::min(hw ? hw : 4u, 16u));
+  if (const char* e = std::getenv("IB_BATCH_THREADS")) {  // host worker threads (>= 1)
+    int t = std::atoi(e);
+    if (t >= 1) B->threads = std::min(t, 64);
+  }
+  size_t uo = 0, xo = 0;
+  for (int k = 0; k < nprob; ++k) {
+    B->up_off.push_back(uo);
+    B->x_off.push_back(xo);
+    uo += 3ul * params[k].N * params[k].N;
+    xo += 2ul * (pt_off[k + 1] - pt_off[k]);
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&B->start, cudaEventDisableTiming);
+  for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    free_batch(B);
+    return fail(IB_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+  }
+  std::string msg;
+  int rc = parallel_for(nprob, B->threads, [&](int k) {
+    const int p0 = pt_off[k], s0 = sp_off[k];
+    return ib_setup(&params[k], pt_off[k + 1] - p0, X ? X + 2 * p0 : nullptr, sp_off[k + 1] - s0,
+                    springs ? springs + 2 * s0 : nullptr, kappa ? kappa + s0 : nullptr,
+                    rest ? rest + s0 : nullptr, B->streams[k], &B->probs[k]);
+  }, &msg);
+  if (rc != IB_OK) {
+    free_batch(B);
+    return fail(rc, msg);
+  }
+  *out = B;
+  return IB_OK;
+}
+
+int ib_batch_size(const ib_batch* B) { return B ? (int)B->probs.size() : 0; }
+
+ib_problem* ib_batch_problem(ib_batch* B, int32_t k) {
+  if (!B || k < 0 || k >= (int)B->probs.size()) return nullptr;
+  return B->probs[k];
+}
+
+int ib_solve_step_batch(ib_batch* B, const double* u_n_all, double* up_all, double* X_all, ib_stats* stats) {
+  g_err.clear();
+  if (!B || !up_all) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  const int nprob = (int)B->probs.size();
+  IB_CUDA_TRY(cudaEventRecord(B->start, B->caller));
+  for (int k = 0; k < nprob; ++k) IB_CUDA_TRY(cudaStreamWaitEvent(B->streams[k], B->start, 0));
+  std::string msg;
+  int rc = parallel_for(nprob, B->threads, [&](int k) {
+    Problem& P = B->probs[k]->P;
+    const double* un = u_n_all ? u_n_all + (B->up_off[k] / 3) * 2 : nullptr;
+    double* Xk = (X_all && P.np > 0) ? X_all + B->x_off[k] : nullptr;
+    int c = solve_step_impl(P, un, up_all + B->up_off[k], Xk, stats ? &stats[k] : nullptr);
+    cudaEventRecord(B->done[k], B->streams[k]);
+    return c;
+  }, &msg);
+  for (int k = 0; k < nprob; ++k) IB_CUDA_TRY(cudaStreamWaitEvent(B->caller, B->done[k], 0));
+  if (rc != IB_OK) return fail(rc, msg);
+  return IB_OK;
+}
+
+void ib_destroy_batch(ib_batch* B) { free_batch(B); }
 
 }  // extern "C"

@@ -3,6 +3,7 @@
 // big-box smoother solves (secs. 5-6), dense box / coarsest-level matrices and
 // their Gauss-Jordan inverses, and the exact coarsest solve (Algorithm 1).
 #include <cmath>
+#include <mutex>
 
 #include "ib_internal.cuh"
 
@@ -324,11 +325,12 @@ int launch_invert(Problem& P, double* M, int n, int count) {
   if (n == 5) {
     k_invert5<<<nblk(count, 128), 128, 0, P.stream>>>(M, count, P.dev_err);
   } else if (smem <= 160u * 1024u) {
-    static bool attr = false;
-    if (!attr) {
-      IB_CUDA_TRY(cudaFuncSetAttribute(k_invert_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-      attr = true;
-    }
+    static std::once_flag once;
+    cudaError_t ae = cudaSuccess;
+    std::call_once(once, [&] {
+      ae = cudaFuncSetAttribute(k_invert_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
+    IB_CUDA_TRY(ae);
     int threads = n <= 32 ? 64 : (n <= 64 ? 128 : 256);
     k_invert_sm<<<count, threads, smem, P.stream>>>(M, n, P.dev_err);
   } else {

@@ -17,6 +17,7 @@
 // The whole sequence is captured once into a CUDA graph and replayed for every
 // V-cycle; the graph is re-captured when a kernel argument changes.
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ib_ops.cuh"
@@ -612,7 +613,17 @@ int vcycle_prepare(Problem& P) {
     cand.push_back(P.nlev - 1);
     if (s > smem_max) smem_max = s;
   }
-  IB_CUDA_TRY(cudaFuncSetAttribute(kv_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+  // the limit is a per-function setting shared by every problem in the process:
+  // only ever raise it (problems of a batch are prepared on several threads)
+  {
+    static std::mutex mu;
+    static size_t granted = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem_max > granted) {
+      IB_CUDA_TRY(cudaFuncSetAttribute(kv_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+      granted = smem_max;
+    }
+  }
   constexpr int ix = pix<T>();
   if (cand.size() == 1 || P.prof || !P.use_graph) {
     P.tail_level[ix] = cand.front();
