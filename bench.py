@@ -255,12 +255,17 @@ def run_ours(args):
     seq_stats = {}
     for prec in (["fp64", "fp32"] if args.forms else [args.precision]):
         solvers = make_seq(prec)
+        forms.setdefault("tail_grid", {})[prec] = [s.tail_grid(prec) for s in solvers]
         st = [None] * nc
-        ms = _timed_steps(torch, lambda: seq_step(solvers, st), flush, stream, args.warmup, args.steps)
+        ms = _timed_steps(torch, lambda: seq_step(solvers, st), flush, stream, args.warmup, args.steps,
+                          args.profile_range and prec == args.precision)
         forms["sequential_" + prec] = {"ms_per_ib_step": sum(ms) / (args.steps * nc),
                                        "iters": [x["iters"] for x in st], "status": [x["status"] for x in st],
                                        "escalated_at": [x["escalated_at"] for x in st]}
         seq_stats[prec] = (solvers, st)
+
+    if args.no_batch:
+        return _report_sequential(args, forms, seq_stats, torch)
 
     # --- batched form (headline): all cases in one ib_solve_step_batch call
     batch = pkg.IBBatch(probs, precision=args.precision, max_iters=args.max_iters)
@@ -281,7 +286,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk.start()
     t_wall = time.perf_counter()
-    step_ms = _timed_steps(torch, batch_step, flush, stream, 0, args.steps, args.profile_range)
+    step_ms = _timed_steps(torch, batch_step, flush, stream, 0, args.steps)
     t_wall = time.perf_counter() - t_wall
     barrier(world)
     clocks = clk.stop()
@@ -385,6 +390,154 @@ def run_ours(args):
     return 0
 
 
+def _report_sequential(args, forms, seq_stats, torch):
+    """Line for --no-batch runs (used for single-stream profiler captures)."""
+    for pr in seq_stats.values():
+        for s in pr[0]:
+            s.close()
+    f = forms["sequential_" + args.precision]
+    if args.rank == 0:
+        print(json.dumps({"metric": METRIC, "value": f["ms_per_ib_step"], "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                          "data": "synthetic", "config": dict(config_dict(args), form="sequential"),
+                          "forms": forms}), flush=True)
+    return 0
+
+
+def run_vcycle(args):
+    """V-cycle throughput alone on an N x N grid (default 2048) with the 0.28/0.22 ellipse of
+    2N points, kappa = 1e4, dt = 1e-3: W warm-up and K timed cycles, L2 flushed before each.
+    Roofline: the V(1,1) algorithmic traffic of 56 B/DOF (FP32) or 112 B/DOF (FP64) against
+    the measured HBM copy bandwidth."""
+    import torch
+
+    import paper_1311_5614_gb300 as pkg
+
+    torch.cuda.set_device(args.local_rank)
+    N = args.grid
+    prob = W.single_ellipse(N=N, n_points=2 * N, kappa=1e4, dt=1e-3)
+    prob.box = args.box
+    s = pkg.IBSolver.from_problem(prob, precision=args.precision)
+    n = 3 * N * N
+    b = torch.randn(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ms = _timed_steps(torch, lambda: s.vcycle(b, w), flush, torch.cuda.current_stream(), args.warmup,
+                      args.steps)
+    per = sum(ms) / len(ms)
+    # ib_vcycle converts the FP64 input and output around the cycle: time that part separately
+    bpd = 56.0 if args.precision == "fp32" else 112.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bpd * n / (per * 1e-3) / 1e9
+    line = {"metric": "V-cycle DOF/s", "value": n / (per * 1e-3), "unit": "DOF/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per, "higher_is_better": True,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "V(1,1) on %d^2, ellipse of %d points, kappa=1e4, dt=1e-3" % (N, 2 * N),
+                       "box": args.box, "precision": args.precision, "tail_grid": s.tail_grid(args.precision),
+                       "note": "ib_vcycle includes the FP64<->FP32 conversion of b and w"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "alg_bytes_per_dof": bpd,
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}}
+    s.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_multi1024(args):
+    """1024^2 grid, 16 random ellipses of 2048 points, kappa = 1e4, dt = 1e-3: consecutive
+    implicit steps (u^n and X carried from step to step); value = ms per step."""
+    import torch
+
+    import paper_1311_5614_gb300 as pkg
+
+    torch.cuda.set_device(args.local_rank)
+    prob = W.many_ellipses(N=1024, count=16, n_per=2048, kappa=1e4, dt=1e-3, seed=1311)
+    prob.box = args.box
+    s = pkg.IBSolver.from_problem(prob, precision=args.precision, max_iters=args.max_iters, restart=50)
+    n = 3 * prob.N * prob.N
+    up = torch.zeros(n, dtype=torch.float64, device="cuda")
+    un = torch.zeros(2 * prob.N * prob.N, dtype=torch.float64, device="cuda")
+    X = torch.tensor(prob.X, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    stats = []
+
+    def step():
+        st = s.solve_step(un, up, X)
+        un.copy_(up[: 2 * prob.N * prob.N])
+        stats.append(st)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clk = ClockSampler(args.local_rank)
+    clk.start()
+    ms = _timed_steps(torch, step, flush, stream, args.warmup, args.steps)
+    clocks = clk.stop()
+    s.close()
+    line = {"metric": METRIC, "value": sum(ms) / len(ms), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": "f32 V-cycle + f64 Krylov",
+            "data": "synthetic",
+            "config": {"workload": "1024^2, 16 ellipses x 2048 points (seed 1311), kappa=1e4, dt=1e-3, "
+                                   "consecutive steps", "box": args.box, "precision": args.precision,
+                       "restart": 50, "max_iters": args.max_iters},
+            "iters": [x["iters"] for x in stats], "status": [x["status"] for x in stats],
+            "rel_res_true": [x["rel_res_true"] for x in stats], "setup_ms": [x["t_setup_ms"] for x in stats],
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch256(args):
+    """256 independent problems, grids drawn from {64, 128, 256, 512} (seed 5614), one
+    ellipse each with 4 points per cell of perimeter, kappa log-uniform in [1, 1e6]:
+    one bench step = one ib_solve_step_batch over all of them."""
+    import torch
+
+    import paper_1311_5614_gb300 as pkg
+
+    torch.cuda.set_device(args.local_rank)
+    probs = W.batch(count=256, seed=5614)
+    for p in probs:
+        p.box = args.box
+    B = pkg.IBBatch(probs, precision=args.precision, max_iters=args.max_iters, restart=30)
+    n = sum(3 * p.N * p.N for p in probs)
+    up = torch.zeros(n, dtype=torch.float64, device="cuda")
+    X0 = torch.tensor(np.concatenate([p.X for p in probs]), dtype=torch.float64, device="cuda")
+    X = X0.clone()
+    stats = [None]
+
+    def step():
+        X.copy_(X0)
+        stats[0] = B.solve_step(None, up, X)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clk = ClockSampler(args.local_rank)
+    clk.start()
+    ms = _timed_steps(torch, step, flush, torch.cuda.current_stream(), args.warmup, args.steps)
+    clocks = clk.stop()
+    st = stats[0]
+    B.close()
+    dof = sum(3 * p.N * p.N for p in probs)
+    its = [x["iters"] for x in st]
+    line = {"metric": METRIC, "value": sum(ms) / (len(ms) * len(probs)), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms),
+            "higher_is_better": False, "dtype": "f32 V-cycle + f64 Krylov", "data": "synthetic",
+            "config": {"workload": "256 problems, N in {64,128,256,512} (seed 5614), kappa 10^U[0,6], dt=1e-2",
+                       "box": args.box, "precision": args.precision, "restart": 30,
+                       "max_iters": args.max_iters, "total_dof": dof},
+            "iters_total": int(sum(its)), "iters_max": int(max(its)),
+            "not_converged": int(sum(1 for x in st if x["status"] != 0)),
+            "escalated": int(sum(1 for x in st if x["escalated_at"] >= 0)),
+            "dof_vcycles_per_s": float(sum(3 * p.N * p.N * x["iters"] for p, x in zip(probs, st)) /
+                                       (sum(ms) / len(ms) * 1e-3)),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,9 +547,16 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--box", type=int, default=4)
     ap.add_argument("--max-iters", type=int, default=200)
+    ap.add_argument("--grid", type=int, default=2048, help="grid size of the vcycle workload")
+    ap.add_argument("--workload", default="sweep256", choices=["sweep256", "multi1024", "batch256", "vcycle"],
+                    help="sweep256 (default): the 256^2 kappa x dt sweep; multi1024 / batch256: the "
+                         "1024^2 multi-structure run and the 256-problem batch (extra lines)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--profile-range", action="store_true",
-                    help="bracket the first timed step with cudaProfilerStart/Stop")
+                    help="bracket the first timed step of the sequential form in the bench precision "
+                         "with cudaProfilerStart/Stop (for an ncu launch list of one sweep)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="time only the sequential form (single stream; for profiler captures)")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the sequential FP64 / FP32 comparison forms")
     ap.add_argument("--rotate", action="store_true", help="reference arm: rotate through the cases")
@@ -418,6 +578,12 @@ def main(argv=None):
     try:
         if args.impl == "reference":
             return run_reference(args)
+        if args.workload == "multi1024":
+            return run_multi1024(args)
+        if args.workload == "batch256":
+            return run_batch256(args)
+        if args.workload == "vcycle":
+            return run_vcycle(args)
         return run_ours(args)
     finally:
         if args.world > 1:

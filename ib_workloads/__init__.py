@@ -176,3 +176,40 @@ def random_points_field(n, seed):
     """Standard-normal Lagrangian vector [n, 2], float64."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((n, 2))
+
+
+# ----------------------------------------------------------------------------- learned stage inputs
+
+# Parameter shapes of the learned stage's U-Net (c_in, c_out, kernel), in the
+# parameter order [W_0 b_0 W_1 b_1 ...]; only used to draw initial values.
+UNET_SHAPES = [(4, 16, 3), (16, 16, 3), (16, 32, 3), (32, 32, 3), (32, 64, 3), (64, 64, 3),
+               (96, 32, 3), (32, 32, 3), (48, 16, 3), (16, 16, 3), (16, 3, 1)]
+
+
+def unet_init_params(seed, scale=1.0):
+    """Seeded He-normal weights (std scale*sqrt(2/fan_in)) and zero biases, float32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co, k in UNET_SHAPES:
+        out.append(rng.standard_normal(co * ci * k * k) * (scale * math.sqrt(2.0 / (ci * k * k))))
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32)
+
+
+def random_smooth_field(N, seed, count=3, kmax=12, noise=0.05):
+    """[count, N, N] periodic field: random Fourier modes with |k| <= kmax and
+    amplitudes falling off as 1/(1+|k|^2), plus white noise of relative size
+    ``noise``; unit RMS per component."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((count, N, N))
+    ky = np.fft.fftfreq(N) * N
+    kx = np.fft.rfftfreq(N) * N
+    KY, KX = np.meshgrid(ky, kx, indexing="ij")
+    kk = np.hypot(KX, KY)
+    mask = kk <= kmax
+    for c in range(count):
+        coef = (rng.standard_normal(KX.shape) + 1j * rng.standard_normal(KX.shape)) * mask / (1.0 + kk ** 2)
+        f = np.fft.irfft2(coef, s=(N, N))
+        f /= max(np.sqrt((f ** 2).mean()), 1e-300)
+        out[c] = f + noise * rng.standard_normal((N, N))
+    return out

@@ -83,6 +83,8 @@ typedef struct {
   int32_t max_iters;  /* FGMRES iteration cap, 1..512 (the paper stops at 100) */
   int32_t escalate;   /* IB_FP32_PRECOND only: 1 = switch the preconditioner to the FP64
                          V-cycle when FGMRES stagnates (default), 0 = never */
+  int32_t restart;    /* FGMRES restart length m (Krylov vectors kept), 0 = max_iters;
+                         workspace grows with m: (m + 1) FP64 + m preconditioner vectors */
 } ib_params;
 
 /* Statistics of one ib_solve_step call. */
@@ -96,12 +98,14 @@ typedef struct {
   int32_t n_struct_boxes; /* structure boxes (with elasticity), all levels */
   int32_t status;       /* ib_status of the solve */
   int32_t escalated_at; /* iteration from which the FP64 V-cycle preconditioned (-1: never) */
+  int32_t learned_used; /* iterations whose direction the learned stage improved (kept) */
 } ib_stats;
 
 typedef struct ib_problem ib_problem;  /* opaque; owned by the library */
 
 /* Fill *p with the defaults: L=1, rho=1, mu=1, dt=1e-2, Peskin4, box 1, V(1,1),
- * FP64, clamped Jacobian, tol 1e-8, max_iters 100, escalate 1.  N is set to 64. */
+ * FP64, clamped Jacobian, tol 1e-8, max_iters 100, escalate 1, restart 0 (no restart
+ * before max_iters).  N is set to 64. */
 IB_API void ib_default_params(ib_params* p);
 
 /* Create a problem: validates the parameters, allocates all device workspace
@@ -154,6 +158,12 @@ IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double
 IB_API int ib_num_levels(const ib_problem* prob);
 IB_API int ib_level_size(const ib_problem* prob, int32_t level);
 
+/* Grid size of the finest level run by the single-CTA coarse-level kernel in the
+ * V-cycle of the given precision (IB_FP64 or IB_FP32_PRECOND), 0 if that V-cycle
+ * does not exist.  The split is timed at set-up unless the environment variable
+ * IB_TAIL_NMAX (the largest grid size for that kernel) pins it. */
+IB_API int ib_tail_grid(const ib_problem* prob, int32_t precision);
+
 /* Number of structure boxes (boxes whose block includes elasticity) on a level,
  * as found by the last set-up. */
 IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
@@ -187,6 +197,41 @@ IB_API int ib_batch_size(const ib_batch* batch);
 /* The k-th problem of the batch (owned by the batch; do not destroy it). */
 IB_API ib_problem* ib_batch_problem(ib_batch* batch, int32_t k);
 IB_API void ib_destroy_batch(ib_batch* batch);
+
+/* ---- Learned preconditioner stage (SURVEY learned-stage row; not in the paper) ----
+ *
+ * A 3-level convolutional U-Net (16/32/64 channels, 3x3 circular convolutions,
+ * GELU, 2x2 average pooling, nearest upsampling with skip concatenation, a 1x1
+ * head; BF16 weights with FP32 master copies, FP32 accumulation) that maps the
+ * residual left by a V-cycle to an estimate of the remaining error.  Input
+ * channels: r_u, r_v, r_p divided by ||r||, and a structure channel
+ * log(1 + dt/(mu h^2) sum_k Kbar_k phi phi) (Kbar_k = summed stiffness of the
+ * springs at point k).  Output: the error estimate divided by ||r||.
+ * Parameters are one FP32 vector of ib_unet_num_params() values in layer order
+ * [W_0 b_0 W_1 b_1 ...], W_l in [c_out][c_in][k][k].  All arrays device FP32
+ * [C][N][N] unless stated; N a power of two in 64..4096. */
+typedef struct ib_unet ib_unet;
+IB_API int64_t ib_unet_num_params(void);
+/* params: host FP32 initial parameters (NULL = zeros); stream as for ib_setup. */
+IB_API int ib_unet_create(int32_t N, const float* params, void* stream, ib_unet** out);
+IB_API int ib_unet_set_params(ib_unet* net, const float* params /* host */);
+IB_API int ib_unet_get_params(ib_unet* net, float* params /* host */);
+/* y [3][N][N] = net(x [4][N][N]) */
+IB_API int ib_unet_forward(ib_unet* net, const float* x, float* y);
+/* loss = ||net(x) - t||^2 / ||t||^2 and its gradient (host, num_params values; may be NULL) */
+IB_API int ib_unet_loss_grad(ib_unet* net, const float* x, const float* t, double* loss, float* grad);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on that loss */
+IB_API int ib_unet_train_step(ib_unet* net, const float* x, const float* t, float lr, double* loss);
+IB_API void ib_unet_destroy(ib_unet* net);
+/* Attach (net != NULL) or detach the learned stage of a problem (same N; the problem
+ * does not own the network).  With a stage attached each FGMRES direction z = MG(v)
+ * is replaced by z + ||r|| net(features(r)), r = v - A z, when that lowers
+ * ||v - A z|| and is finite; otherwise the V-cycle direction is kept. */
+IB_API int ib_set_learned_stage(ib_problem* prob, ib_unet* net);
+/* A training pair from the method itself: b = A x, z = MG(b) (one V-cycle of the
+ * problem's precision), r = b - A z, e = x - z; writes features(r) to in4 [4][N][N]
+ * and e / ||r|| to target [3][N][N].  x: device 3N^2 doubles. */
+IB_API int ib_learned_pair(ib_problem* prob, const double* x, float* in4, float* target);
 
 /* Kernel classes for launch counting and event timing. */
 enum {

@@ -39,7 +39,7 @@ class ib_params(ctypes.Structure):
                 ("mu", ctypes.c_double), ("dt", ctypes.c_double), ("delta", ctypes.c_int32),
                 ("box", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("jacobian", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int32), ("escalate", ctypes.c_int32)]
+                ("max_iters", ctypes.c_int32), ("escalate", ctypes.c_int32), ("restart", ctypes.c_int32)]
 
 
 class ib_stats(ctypes.Structure):
@@ -47,7 +47,7 @@ class ib_stats(ctypes.Structure):
                 ("rel_res_true", ctypes.c_double), ("rel_res_est", ctypes.c_double),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("n_struct_boxes", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("escalated_at", ctypes.c_int32)]
+                ("escalated_at", ctypes.c_int32), ("learned_used", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +74,7 @@ _SIGS = {
     "ib_num_levels": (ctypes.c_int, [_P]),
     "ib_level_size": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_num_struct_boxes": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_tail_grid": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_launch_count": (ctypes.c_int64, [_P, ctypes.c_int32]),
     "ib_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -85,6 +86,16 @@ _SIGS = {
     "ib_batch_size": (ctypes.c_int, [_P]),
     "ib_batch_problem": (_P, [_P, ctypes.c_int32]),
     "ib_destroy_batch": (None, [_P]),
+    "ib_unet_num_params": (ctypes.c_int64, []),
+    "ib_unet_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(_P)]),
+    "ib_unet_set_params": (ctypes.c_int, [_P, _P]),
+    "ib_unet_get_params": (ctypes.c_int, [_P, _P]),
+    "ib_unet_forward": (ctypes.c_int, [_P, _P, _P]),
+    "ib_unet_loss_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "ib_unet_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
+    "ib_unet_destroy": (None, [_P]),
+    "ib_set_learned_stage": (ctypes.c_int, [_P, _P]),
+    "ib_learned_pair": (ctypes.c_int, [_P, _P, _P, _P]),
     "ib_destroy": (None, [_P]),
     "ib_last_error": (ctypes.c_char_p, []),
     "ib_version": (ctypes.c_char_p, []),
@@ -132,7 +143,7 @@ def ib_default_params():
 
 
 def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=1, nu2=1,
-                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100, escalate=True):
+                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100, escalate=True, restart=0):
     p = ib_default_params()
     p.N, p.L, p.rho, p.mu, p.dt = int(N), float(L), float(rho), float(mu), float(dt)
     p.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
@@ -141,6 +152,7 @@ def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=
     p.jacobian = JACOBIAN[jacobian] if isinstance(jacobian, str) else int(jacobian)
     p.tol, p.max_iters = float(tol), int(max_iters)
     p.escalate = 1 if escalate else 0
+    p.restart = int(restart)
     return p
 
 
@@ -339,6 +351,81 @@ class IBBatch:
             pass
 
 
+def _f32_ptr(t, numel, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ib_unet_num_params():
+    return int(lib().ib_unet_num_params())
+
+
+class UNet:
+    """The learned stage's network (parameters on the device; FP32 master, BF16 copy)."""
+
+    def __init__(self, N, params=None, stream=None):
+        import torch
+
+        self.N = int(N)
+        self.n_params = ib_unet_num_params()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        host = None
+        if params is not None:
+            host = np.ascontiguousarray(params, dtype=np.float32)
+            if host.size != self.n_params:
+                raise ValueError("expected %d parameters" % self.n_params)
+        out = ctypes.c_void_p()
+        _check(lib().ib_unet_create(self.N, host.ctypes.data_as(_P) if host is not None else None,
+                                    ctypes.c_void_p(stream), ctypes.byref(out)))
+        self.handle = out
+
+    def set_params(self, params):
+        host = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().ib_unet_set_params(self.handle, host.ctypes.data_as(_P)))
+
+    def get_params(self):
+        host = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().ib_unet_get_params(self.handle, host.ctypes.data_as(_P)))
+        return host
+
+    def forward(self, x, y):
+        n = self.N * self.N
+        _check(lib().ib_unet_forward(self.handle, _f32_ptr(x, 4 * n, "x"), _f32_ptr(y, 3 * n, "y")))
+        return y
+
+    def loss_grad(self, x, t):
+        n = self.N * self.N
+        L = ctypes.c_double()
+        g = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().ib_unet_loss_grad(self.handle, _f32_ptr(x, 4 * n, "x"), _f32_ptr(t, 3 * n, "t"),
+                                       ctypes.byref(L), g.ctypes.data_as(_P)))
+        return float(L.value), g
+
+    def train_step(self, x, t, lr):
+        n = self.N * self.N
+        L = ctypes.c_double()
+        _check(lib().ib_unet_train_step(self.handle, _f32_ptr(x, 4 * n, "x"), _f32_ptr(t, 3 * n, "t"),
+                                        ctypes.c_float(lr), ctypes.byref(L)))
+        return float(L.value)
+
+    def close(self):
+        if self.handle:
+            lib().ib_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class IBSolver:
     """Owns one problem handle; methods forward to the functions above."""
 
@@ -366,6 +453,9 @@ class IBSolver:
     def struct_boxes(self, level):
         return ib_num_struct_boxes(self.handle, level)
 
+    def tail_grid(self, precision="fp32"):
+        return lib().ib_tail_grid(self.handle, PRECISION[precision])
+
     def apply(self, level, w, y):
         ib_apply(self.handle, level, w, y)
         return y
@@ -383,6 +473,14 @@ class IBSolver:
 
     def solve_step(self, u_n, up, X, raise_on_not_converged=False):
         return ib_solve_step(self.handle, u_n, up, X, self.n_points, raise_on_not_converged)
+
+    def set_learned_stage(self, net):
+        _check(lib().ib_set_learned_stage(self.handle, net.handle if net is not None else None))
+
+    def learned_pair(self, x, in4, target):
+        n = self.N * self.N
+        _check(lib().ib_learned_pair(self.handle, _dev_ptr(x, 3 * n, "x"), _f32_ptr(in4, 4 * n, "in4"),
+                                     _f32_ptr(target, 3 * n, "target")))
 
     def launch_count(self, kclass=-1):
         return ib_launch_count(self.handle, kclass)

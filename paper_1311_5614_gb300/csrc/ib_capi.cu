@@ -118,6 +118,7 @@ int validate(const ib_params* p) {
   if (p->max_iters < 1 || p->max_iters > 512)
     return fail(IB_ERR_INVALID_ARG, "max_iters must be in 1..512");
   if (p->escalate != 0 && p->escalate != 1) return fail(IB_ERR_INVALID_ARG, "escalate must be 0 or 1");
+  if (p->restart < 0 || p->restart > 512) return fail(IB_ERR_INVALID_ARG, "restart must be in 0..512");
   return IB_OK;
 }
 
@@ -190,6 +191,7 @@ int setup_hierarchy(Problem& P) {
   IB_TRY(launch_assemble_coarse(P));
   IB_TRY(launch_invert(P, P.Mcoarse, P.nc + P.nborder, 1));
   IB_TRY(vcycle_reset_rE(P));
+  if (P.nn_sch) IB_TRY(learned_struct_channel(P));
   return check_dev_err(P);
 }
 
@@ -216,6 +218,7 @@ void free_problem(Problem* P) {
   dfree(P->Mcoarse); dfree(P->V); dfree(P->Z); dfree(P->Z64); dfree(P->H); dfree(P->givens);
   dfree(P->dots); dfree(P->scal); dfree(P->x64); dfree(P->b64); dfree(P->t64); dfree(P->t64b);
   dfree(P->dev_err); dfree(P->count);
+  dfree(P->nn_sch); dfree(P->nn_x); dfree(P->nn_y); dfree(P->nn_r); dfree(P->nn_dz); dfree(P->nn_adz);
   if (P->scal_host) cudaFreeHost(P->scal_host);
   if (P->count_host) cudaFreeHost(P->count_host);
   for (auto& e : P->ev)
@@ -325,6 +328,58 @@ int residual64(Problem& P, const double* x, const double* b, double* r) {
   return IB_OK;
 }
 
+__global__ void k_add_d2t_f(float* z, const double* __restrict__ dz, long n) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) z[i] += (float)dz[i];
+}
+__global__ void k_add_d2t_d(double* z, const double* __restrict__ dz, long n) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) z[i] += dz[i];
+}
+
+// Learned stage of one FGMRES iteration: with P.t64 = A z_j, propose
+// z_j + ||r|| net(features(r)), r = v_j - A z_j, and keep it only if it is finite and
+// lowers ||v_j - A z||; then P.t64 = A (stored z_j).  z64 (if not NULL) is the FP64
+// copy of z_j used after an FP32 -> FP64 escalation.
+template <typename T>
+int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st) {
+  const size_t n = 3ul * P.prm.N * P.prm.N;
+  double* sc = P.scal + 8 + 2 * (P.max_m + 2) + 1;  // two free scalars after ||w||^2
+  IB_TRY(launch_axpby(P, 1.0, vj, -1.0, P.t64, P.nn_r));
+  IB_TRY(learned_features(P, P.nn_r, sc, P.nn_x));
+  {
+    KScope ks(P, IB_KC_OTHER, 0.0);  // the network's own launches are not counted per class
+    IB_TRY(learned_forward(P.net, P.stream, P.nn_x, P.nn_y));
+  }
+  IB_TRY(learned_scale_out(P, P.nn_y, sc, P.nn_dz));
+  IB_TRY(apply64(P, 0, P.nn_dz, P.nn_adz));
+  IB_TRY(launch_axpby(P, 1.0, P.nn_r, -1.0, P.nn_adz, P.nn_adz));
+  IB_TRY(launch_dot(P, P.nn_adz, P.nn_adz, sc + 1));
+  IB_CUDA_TRY(cudaMemcpyAsync(P.scal_host + 16, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  const double r0 = P.scal_host[16], r1 = P.scal_host[17];
+  if (!(std::isfinite(r1) && r1 < r0)) return IB_OK;  // keep the V-cycle direction
+  st->learned_used += 1;
+  const int tpb = 256;
+  const int nbk = (int)((n + tpb - 1) / tpb);
+  KScope ks(P, IB_KC_OTHER, n * 20.0);
+  if (z64) {
+    k_add_d2t_d<<<nbk, tpb, 0, P.stream>>>(z64, P.nn_dz, (long)n);
+    IB_LAUNCH_CHECK();
+    return apply64(P, 0, z64, P.t64);
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    k_add_d2t_d<<<nbk, tpb, 0, P.stream>>>(zj, P.nn_dz, (long)n);
+    IB_LAUNCH_CHECK();
+    return apply64(P, 0, zj, P.t64);
+  } else {
+    k_add_d2t_f<<<nbk, tpb, 0, P.stream>>>(zj, P.nn_dz, (long)n);
+    IB_LAUNCH_CHECK();
+    IB_TRY((launch_cast<float, double>(P, zj, P.t64b, n)));
+    return apply64(P, 0, P.t64b, P.t64);
+  }
+}
+
 // Flexible GMRES with the V-cycle as right preconditioner (sec. 3.3), zero
 // initial guess, classical Gram-Schmidt applied twice, Givens rotations; stop
 // when the estimate reaches tol ||b||, confirm with the true FP64 residual and
@@ -370,7 +425,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       return IB_OK;
     }
     if (total >= P.prm.max_iters) break;
-    int mav = P.prm.max_iters - total;
+    int mav = std::min(P.max_m, P.prm.max_iters - total);
     const int cycle_start = total;
     IB_TRY(launch_fill<double>(P, g, (size_t)m + 1, 0.0));
     {
@@ -409,6 +464,10 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
         IB_TRY(vcycle_run<double>(P));
         IB_CUDA_TRY(cudaMemcpyAsync(zj64, B0.w, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
         IB_TRY(apply64(P, 0, zj64, P.t64));
+      }
+      if (P.net) {
+        bool esc = !std::is_same<T, double>::value && st->escalated_at >= 0;
+        IB_TRY(learned_step<T>(P, vj, zj, esc ? P.Z64 + (size_t)j * n : nullptr, st));
       }
       IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h1));
       IB_TRY(launch_multiaxpy(P, P.V, j + 1, h1, P.t64));
@@ -537,6 +596,7 @@ void ib_default_params(ib_params* p) {
   p->tol = 1e-8;
   p->max_iters = 100;
   p->escalate = 1;
+  p->restart = 0;
 }
 
 int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t n_springs,
@@ -585,7 +645,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   P.nlev = (int)P.lev.size();
   P.nc = 3 * Nc * Nc;
   P.nborder = params->rho == 0.0 ? 3 : 1;
-  P.max_m = params->max_iters;
+  P.max_m = (params->restart > 0 && params->restart < params->max_iters) ? params->restart : params->max_iters;
   int st = allocate(P);
   if (st != IB_OK) {
     std::string msg = g_err;
@@ -674,6 +734,14 @@ int ib_level_size(const ib_problem* H, int32_t level) {
   return H->P.lev[level].N;
 }
 
+int ib_tail_grid(const ib_problem* H, int32_t precision) {
+  if (!H || (precision != IB_FP64 && precision != IB_FP32_PRECOND)) return 0;
+  const Problem& P = H->P;
+  const int ix = precision == IB_FP64 ? 1 : 0;
+  if ((ix == 1 && !P.has64) || (ix == 0 && !P.has32)) return 0;
+  return P.lev[P.tail_level[ix]].N;
+}
+
 int ib_num_struct_boxes(const ib_problem* H, int32_t level) {
   if (!H || level < 0 || level >= H->P.nlev - 1) return 0;
   return H->P.lev[level].n_struct;
@@ -732,6 +800,60 @@ int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_st
   g_err.clear();
   if (!H || !up) return fail(IB_ERR_INVALID_ARG, "NULL argument");
   return solve_step_impl(H->P, u_n, up, X, stats);
+}
+
+static int learned_buffers(Problem& P) {
+  const size_t n1 = (size_t)P.prm.N * P.prm.N;
+  if (!P.nn_x) {
+    IB_TRY(dalloc(&P.nn_x, 4 * n1));
+    IB_TRY(dalloc(&P.nn_y, 3 * n1));
+    IB_TRY(dalloc(&P.nn_r, 3 * n1));
+    IB_TRY(dalloc(&P.nn_dz, 3 * n1));
+    IB_TRY(dalloc(&P.nn_adz, 3 * n1));
+  }
+  if (!P.nn_sch) IB_TRY(learned_struct_channel(P));
+  return IB_OK;
+}
+
+int ib_set_learned_stage(ib_problem* H, ib_unet* net) {
+  g_err.clear();
+  if (!H) return fail(IB_ERR_INVALID_ARG, "problem is NULL");
+  Problem& P = H->P;
+  if (net && learned_unet_size(net) != P.prm.N)
+    return fail(IB_ERR_INVALID_ARG, "the network's grid size differs from the problem's");
+  if (net) IB_TRY(learned_buffers(P));
+  P.net = net;
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
+}
+
+int ib_learned_pair(ib_problem* H, const double* x, float* in4, float* target) {
+  g_err.clear();
+  if (!H || !x || !in4 || !target) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  Problem& P = H->P;
+  IB_TRY(learned_buffers(P));
+  const size_t n = 3ul * P.prm.N * P.prm.N;
+  double* sc = P.scal + 8 + 2 * (P.max_m + 2) + 1;
+  // b = A x into nn_r; z = MG(b) into nn_dz; r = b - A z into nn_r; e = x - z into nn_dz
+  IB_TRY(apply64(P, 0, x, P.nn_r));
+  if (P.prm.precision == IB_FP64) {
+    LevelBuf<double>& B0 = P.lev[0].v64;
+    IB_CUDA_TRY(cudaMemcpyAsync(B0.b, P.nn_r, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+    IB_TRY(vcycle_run<double>(P));
+    IB_CUDA_TRY(cudaMemcpyAsync(P.nn_dz, B0.w, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  } else {
+    LevelBuf<float>& B0 = P.lev[0].v32;
+    IB_TRY((launch_cast<double, float>(P, P.nn_r, B0.b, n)));
+    IB_TRY(vcycle_run<float>(P));
+    IB_TRY((launch_cast<float, double>(P, B0.w, P.nn_dz, n)));
+  }
+  IB_TRY(apply64(P, 0, P.nn_dz, P.nn_adz));
+  IB_TRY(launch_axpby(P, 1.0, P.nn_r, -1.0, P.nn_adz, P.nn_r));
+  IB_TRY(launch_axpby(P, 1.0, x, -1.0, P.nn_dz, P.nn_dz));
+  IB_TRY(learned_features(P, P.nn_r, sc, in4));
+  IB_TRY(learned_target(P, P.nn_dz, sc, target));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
 }
 
 int64_t ib_launch_count(const ib_problem* H, int32_t kclass) {

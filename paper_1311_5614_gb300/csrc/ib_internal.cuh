@@ -232,6 +232,14 @@ struct Problem {
   double* t64 = nullptr;      // [n] scratch
   double* t64b = nullptr;     // [n] scratch
   int* dev_err = nullptr;     // device error flags
+  // learned stage
+  ib_unet* net = nullptr;     // attached network (not owned)
+  float* nn_sch = nullptr;    // [N^2] structure channel
+  float* nn_x = nullptr;      // [4 N^2] network input
+  float* nn_y = nullptr;      // [3 N^2] network output
+  double* nn_r = nullptr;     // [3 N^2] residual v - A z
+  double* nn_dz = nullptr;    // [3 N^2] proposed correction
+  double* nn_adz = nullptr;   // [3 N^2] A dz
   int max_m = 0;
   int dot_blocks = 0;
   int* count = nullptr;       // device counter
@@ -275,6 +283,14 @@ template <typename T>
 int launch_fill(Problem& P, T* x, size_t n, T v);
 template <typename A, typename B>
 int launch_cast(Problem& P, const A* x, B* y, size_t n);
+
+// ---------------------------------------------------------------- learned stage
+int learned_struct_channel(Problem& P);
+int learned_features(Problem& P, const double* r, double* nrm2, float* x);
+int learned_scale_out(Problem& P, const float* y, const double* nrm2, double* dz);
+int learned_target(Problem& P, const double* e, const double* nrm2, float* t);
+int learned_forward(ib_unet* U, cudaStream_t s, const float* x, float* y);
+int learned_unet_size(const ib_unet* U);
 
 // ---------------------------------------------------------------- launchers (krylov)
 int launch_multidot(Problem& P, const double* V, int nvec, const double* w, double* out);

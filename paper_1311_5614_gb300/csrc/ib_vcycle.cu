@@ -16,6 +16,7 @@
 //
 // The whole sequence is captured once into a CUDA graph and replayed for every
 // V-cycle; the graph is re-captured when a kernel argument changes.
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -625,6 +626,20 @@ int vcycle_prepare(Problem& P) {
     }
   }
   constexpr int ix = pix<T>();
+  // IB_TAIL_NMAX pins the split instead of timing it (profiler runs distort the
+  // timings): the tail starts at the first candidate level with N_l <= value
+  if (const char* e = std::getenv("IB_TAIL_NMAX")) {
+    int nt = std::atoi(e);
+    int pick = cand.back();
+    for (int l : cand)
+      if (P.lev[l].N <= nt) {
+        pick = l;
+        break;
+      }
+    P.tail_level[ix] = pick;
+    P.graph_dirty[ix] = true;
+    return IB_OK;
+  }
   if (cand.size() == 1 || P.prof || !P.use_graph) {
     P.tail_level[ix] = cand.front();
     P.graph_dirty[ix] = true;

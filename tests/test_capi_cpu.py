@@ -48,12 +48,14 @@ def test_version_and_defaults(capi):
     p = capi.ib_default_params()
     assert (p.N, p.box, p.nu1, p.nu2, p.max_iters) == (64, 1, 1, 1, 100)
     assert p.tol == 1e-8 and p.rho == 1.0 and p.mu == 1.0 and p.dt == 1e-2
-    assert ctypes.sizeof(capi.ib_params) == 80
+    assert ctypes.sizeof(capi.ib_params) == 88
+    assert p.escalate == 1 and p.restart == 0
 
 
 @pytest.mark.parametrize("field,value", [
     ("N", 48), ("N", 4), ("box", 3), ("mu", 0.0), ("dt", -1.0), ("rho", -1.0), ("tol", 0.0),
-    ("max_iters", 0), ("max_iters", 1000), ("nu1", 9), ("delta", 5), ("precision", 7), ("L", 0.0)])
+    ("max_iters", 0), ("max_iters", 1000), ("nu1", 9), ("delta", 5), ("precision", 7), ("L", 0.0),
+    ("restart", -1), ("escalate", 2)])
 def test_setup_rejects_bad_params(capi, field, value):
     prob = W.single_ellipse(N=32, n_points=16)
     p = capi.make_params(32)

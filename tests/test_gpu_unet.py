@@ -1,0 +1,118 @@
+"""The learned stage on the GPU against its FP64 oracle, and inside FGMRES."""
+import numpy as np
+import pytest
+
+import ib_workloads as W
+from oracle import ib_oracle as O
+from oracle import unet_oracle as UO
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N = 64
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1311_5614_gb300 as P
+
+    P.lib()
+    return P
+
+
+def _data(seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((4, N, N)).astype(np.float32)
+    t = rng.standard_normal((3, N, N)).astype(np.float32)
+    th = W.unet_init_params(seed + 10)
+    th[UO.param_count() - 3:] = [0.1, -0.2, 0.3]
+    return th, x, t
+
+
+def f32(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def test_param_count(pkg):
+    assert pkg.ib_unet_num_params() == UO.param_count()
+
+
+def test_forward_matches_oracle(pkg):
+    th, x, _ = _data()
+    net = pkg.UNet(N, th)
+    y = torch.zeros(3 * N * N, dtype=torch.float32, device="cuda")
+    net.forward(f32(x).reshape(-1), y)
+    ref = UO.forward(th, x, bf16=True)
+    got = y.cpu().numpy().reshape(3, N, N)
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max() + 1e-6
+    assert np.allclose(net.get_params(), th)
+    net.close()
+
+
+def test_loss_and_gradient_match_oracle(pkg):
+    th, x, t = _data(1)
+    net = pkg.UNet(N, th)
+    L, g = net.loss_grad(f32(x).reshape(-1), f32(t).reshape(-1))
+    Lr, gr = UO.loss_and_grad(th, x, t, bf16=True)
+    assert abs(L - Lr) <= 1e-5 * abs(Lr)
+    assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr)
+    net.close()
+
+
+def test_training_lowers_the_loss(pkg):
+    th, x, t = _data(2)
+    net = pkg.UNet(N, th)
+    xs, ts = f32(x).reshape(-1), f32(t).reshape(-1)
+    l0 = net.train_step(xs, ts, 1e-3)
+    for _ in range(20):
+        l1 = net.train_step(xs, ts, 1e-3)
+    assert l1 < 0.9 * l0
+    net.close()
+
+
+def test_learned_pair_matches_oracle_definition(pkg):
+    p = W.single_ellipse(N=N, n_points=128, kappa=1e3, dt=1e-2)
+    s = pkg.IBSolver.from_problem(p)
+    x = W.random_smooth_field(N, 5).ravel()
+    in4 = torch.zeros(4 * N * N, dtype=torch.float32, device="cuda")
+    tg = torch.zeros(3 * N * N, dtype=torch.float32, device="cuda")
+    s.learned_pair(torch.tensor(x, device="cuda"), in4, tg)
+    levels, ops = O.build_hierarchy(p)
+    for lev in levels[:-1]:
+        O.prepare_boxes(lev, 1)
+    A = levels[0].A
+    b = A @ x
+    z = O.vcycle(levels, b, np.zeros_like(b), 1, 1, p.rho, "color4")
+    r = b - A @ z
+    e = x - z
+    nr = np.linalg.norm(r)
+    got = in4.cpu().numpy()
+    assert np.abs(got[:3 * N * N] - r / nr).max() <= 1e-6 * np.abs(r / nr).max()
+    assert np.abs(tg.cpu().numpy() - e / nr).max() <= 1e-6 * np.abs(e / nr).max()
+    # structure channel: log(1 + dt/mu * (S_u Kbar)) with S_u the u-block of spreading
+    kbar = np.zeros(p.n_points)
+    np.add.at(kbar, p.springs[:, 0], p.kappa)
+    np.add.at(kbar, p.springs[:, 1], p.kappa)
+    Su = ops["S"][: N * N, : p.n_points]
+    sch = np.log1p(p.dt / p.mu * (Su @ kbar))
+    assert np.abs(got[3 * N * N:] - sch).max() <= 1e-5 * max(1.0, np.abs(sch).max())
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_with_learned_stage_converges(pkg, prec):
+    p = W.single_ellipse(N=N, n_points=128, kappa=1e4, dt=1e-2)
+    s = pkg.IBSolver.from_problem(p, precision=prec)
+    net = pkg.UNet(N, W.unet_init_params(3, scale=0.1))
+    s.set_learned_stage(net)
+    up = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
+    X = torch.tensor(p.X, device="cuda")
+    st = s.solve_step(None, up, X)
+    assert st["status"] == 0 and st["rel_res_true"] <= p.tol
+    ref = O.solve_step(p)
+    assert np.linalg.norm(up.cpu().numpy() - ref.w) <= 1e-6 * np.linalg.norm(ref.w)
+    s.set_learned_stage(None)
+    s.close()
+    net.close()
