@@ -448,6 +448,36 @@ def run_vcycle(args):
     return 0
 
 
+def run_learned512(args):
+    """Learned stage at 512^2 (1024-point ellipse): pairs harvested from the method's own
+    V-cycles on problems with kappa = 10^U[2,6], U-Net trained on the GPU with the
+    library's kernels, then plain vs learned MG-FGMRES on held-out kappa in {1e2, 1e4, 1e6}."""
+    import torch
+
+    from paper_1311_5614_gb300 import learned
+
+    torch.cuda.set_device(args.local_rank)
+    res = learned.run(N=512, n_problems=args.learn_problems, pairs_per_problem=args.learn_pairs,
+                      epochs=args.learn_epochs, lr=1e-3, seed=0, log=lambda m: print(m, file=sys.stderr))
+    params = res.pop("params")
+    try:
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        np.save(os.path.join(ROOT, "gpurun_out", "unet512_params.npy"), params)
+    except Exception:
+        pass
+    ev = res["eval"]
+    plain = sum(r["plain"]["ms"] for r in ev) / len(ev)
+    lrn = sum(r["learned"]["ms"] for r in ev) / len(ev)
+    line = {"metric": METRIC, "value": lrn, "unit": UNIT, "n_gpus": 1, "steps": len(ev), "warmup": 1,
+            "higher_is_better": False, "dtype": "f32 V-cycle + f64 Krylov + f32/bf16 U-Net",
+            "data": "synthetic",
+            "config": {"workload": "512^2, 1024-point ellipse, dt=1e-2; learned stage vs plain",
+                       "pairs": res["pairs"], "epochs": res["epochs"], "box": 4, "precision": "fp32"},
+            "forms": {"plain_ms_per_ib_step": plain, "learned_ms_per_ib_step": lrn}, "learned": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_multi1024(args):
     """1024^2 grid, 16 random ellipses of 2048 points, kappa = 1e4, dt = 1e-3: consecutive
     implicit steps (u^n and X carried from step to step); value = ms per step."""
@@ -548,7 +578,10 @@ def main(argv=None):
     ap.add_argument("--box", type=int, default=4)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--grid", type=int, default=2048, help="grid size of the vcycle workload")
-    ap.add_argument("--workload", default="sweep256", choices=["sweep256", "multi1024", "batch256", "vcycle"],
+    ap.add_argument("--learn-problems", type=int, default=16)
+    ap.add_argument("--learn-pairs", type=int, default=64, help="pairs per training problem")
+    ap.add_argument("--learn-epochs", type=int, default=2)
+    ap.add_argument("--workload", default="sweep256", choices=["sweep256", "multi1024", "batch256", "vcycle", "learned512"],
                     help="sweep256 (default): the 256^2 kappa x dt sweep; multi1024 / batch256: the "
                          "1024^2 multi-structure run and the 256-problem batch (extra lines)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
@@ -584,6 +617,8 @@ def main(argv=None):
             return run_batch256(args)
         if args.workload == "vcycle":
             return run_vcycle(args)
+        if args.workload == "learned512":
+            return run_learned512(args)
         return run_ours(args)
     finally:
         if args.world > 1:

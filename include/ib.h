@@ -164,6 +164,11 @@ IB_API int ib_level_size(const ib_problem* prob, int32_t level);
  * IB_TAIL_NMAX (the largest grid size for that kernel) pins it. */
 IB_API int ib_tail_grid(const ib_problem* prob, int32_t precision);
 
+/* Levels with at least IB_BOX_GEMM_MIN boxes per colour (environment variable,
+ * default 2048) solve their n x n boxes (n = 2, 4) with a register-blocked kernel
+ * that treats the free boxes of a CTA as one small matrix product; smaller levels
+ * use one thread per box row.  Read at ib_setup. */
+
 /* Number of structure boxes (boxes whose block includes elasticity) on a level,
  * as found by the last set-up. */
 IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
@@ -203,10 +208,12 @@ IB_API void ib_destroy_batch(ib_batch* batch);
  * A 3-level convolutional U-Net (16/32/64 channels, 3x3 circular convolutions,
  * GELU, 2x2 average pooling, nearest upsampling with skip concatenation, a 1x1
  * head; BF16 weights with FP32 master copies, FP32 accumulation) that maps the
- * residual left by a V-cycle to an estimate of the remaining error.  Input
- * channels: r_u, r_v, r_p divided by ||r||, and a structure channel
+ * residual left by a V-cycle to an estimate of the remaining error.  The residual
+ * is first brought to velocity-error units, rs = (h^2/mu r_u, h^2/mu r_v, h r_p).
+ * Input channels: rs / ||rs||, and a structure channel
  * log(1 + dt/(mu h^2) sum_k Kbar_k phi phi) (Kbar_k = summed stiffness of the
- * springs at point k).  Output: the error estimate divided by ||r||.
+ * springs at point k).  Output: the error estimate divided by ||rs|| (the pressure
+ * channel further divided by mu/h).
  * Parameters are one FP32 vector of ib_unet_num_params() values in layer order
  * [W_0 b_0 W_1 b_1 ...], W_l in [c_out][c_in][k][k].  All arrays device FP32
  * [C][N][N] unless stated; N a power of two in 64..4096. */
@@ -225,12 +232,14 @@ IB_API int ib_unet_train_step(ib_unet* net, const float* x, const float* t, floa
 IB_API void ib_unet_destroy(ib_unet* net);
 /* Attach (net != NULL) or detach the learned stage of a problem (same N; the problem
  * does not own the network).  With a stage attached each FGMRES direction z = MG(v)
- * is replaced by z + ||r|| net(features(r)), r = v - A z, when that lowers
- * ||v - A z|| and is finite; otherwise the V-cycle direction is kept. */
+ * becomes z + alpha d, d the network's correction for r = v - A z and alpha the
+ * exact minimiser of ||r - alpha A d||, when alpha > 0 and the residual drops by at
+ * least 0.1 %; otherwise the V-cycle direction is kept. */
 IB_API int ib_set_learned_stage(ib_problem* prob, ib_unet* net);
 /* A training pair from the method itself: b = A x, z = MG(b) (one V-cycle of the
- * problem's precision), r = b - A z, e = x - z; writes features(r) to in4 [4][N][N]
- * and e / ||r|| to target [3][N][N].  x: device 3N^2 doubles. */
+ * problem's precision), r = b - A z, e = x - z; writes the network input for r to
+ * in4 [4][N][N] and the scaled error (as the network's output is defined) to target
+ * [3][N][N].  x: device 3N^2 doubles. */
 IB_API int ib_learned_pair(ib_problem* prob, const double* x, float* in4, float* target);
 
 /* Kernel classes for launch counting and event timing. */

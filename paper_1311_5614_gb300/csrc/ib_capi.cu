@@ -328,52 +328,62 @@ int residual64(Problem& P, const double* x, const double* b, double* r) {
   return IB_OK;
 }
 
-__global__ void k_add_d2t_f(float* z, const double* __restrict__ dz, long n) {
+__global__ void k_add_d2t_f(float* z, const double* __restrict__ dz, const double* __restrict__ alpha, long n) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i < n) z[i] += (float)dz[i];
+  if (i < n) z[i] += (float)((*alpha) * dz[i]);
 }
-__global__ void k_add_d2t_d(double* z, const double* __restrict__ dz, long n) {
+__global__ void k_add_d2t_d(double* z, const double* __restrict__ dz, const double* __restrict__ alpha, long n) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i < n) z[i] += dz[i];
+  if (i < n) z[i] += (*alpha) * dz[i];
 }
 
-// Learned stage of one FGMRES iteration: with P.t64 = A z_j, propose
-// z_j + ||r|| net(features(r)), r = v_j - A z_j, and keep it only if it is finite and
-// lowers ||v_j - A z||; then P.t64 = A (stored z_j).  z64 (if not NULL) is the FP64
-// copy of z_j used after an FP32 -> FP64 escalation.
+// Learned stage of one FGMRES iteration: with P.t64 = A z_j and r = v_j - A z_j,
+// d = the network's correction for r, alpha = <r, A d> / <A d, A d> (exact line
+// search along d); z_j + alpha d is kept when alpha > 0 and it lowers ||r||^2 by at
+// least 0.1%, then P.t64 = A (stored z_j).  z64 (if not NULL) is the FP64 copy of z_j
+// used after an FP32 -> FP64 escalation.
 template <typename T>
 int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st) {
   const size_t n = 3ul * P.prm.N * P.prm.N;
-  double* sc = P.scal + 8 + 2 * (P.max_m + 2) + 1;  // two free scalars after ||w||^2
+  double* sc = P.scal + 8 + 2 * (P.max_m + 2) + 1;  // free scalars after ||w||^2
   IB_TRY(launch_axpby(P, 1.0, vj, -1.0, P.t64, P.nn_r));
-  IB_TRY(learned_features(P, P.nn_r, sc, P.nn_x));
+  IB_TRY(learned_features(P, P.nn_r, P.nn_dz, sc, P.nn_x));
   {
     KScope ks(P, IB_KC_OTHER, 0.0);  // the network's own launches are not counted per class
     IB_TRY(learned_forward(P.net, P.stream, P.nn_x, P.nn_y));
   }
   IB_TRY(learned_scale_out(P, P.nn_y, sc, P.nn_dz));
   IB_TRY(apply64(P, 0, P.nn_dz, P.nn_adz));
-  IB_TRY(launch_axpby(P, 1.0, P.nn_r, -1.0, P.nn_adz, P.nn_adz));
-  IB_TRY(launch_dot(P, P.nn_adz, P.nn_adz, sc + 1));
-  IB_CUDA_TRY(cudaMemcpyAsync(P.scal_host + 16, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+  IB_TRY(launch_dot(P, P.nn_r, P.nn_adz, sc + 1));
+  IB_TRY(launch_dot(P, P.nn_adz, P.nn_adz, sc + 2));
+  IB_TRY(launch_dot(P, P.nn_r, P.nn_r, sc + 3));
+  IB_CUDA_TRY(cudaMemcpyAsync(P.scal_host + 16, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
   IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
-  const double r0 = P.scal_host[16], r1 = P.scal_host[17];
-  if (!(std::isfinite(r1) && r1 < r0)) return IB_OK;  // keep the V-cycle direction
+  const double ra = P.scal_host[17], aa = P.scal_host[18], rr = P.scal_host[19];
+  if (!(std::isfinite(ra) && std::isfinite(aa) && aa > 0.0 && ra > 0.0)) return IB_OK;
+  const double gain = ra * ra / aa;  // ||r||^2 - ||r - alpha A d||^2
+  if (!(gain >= 1e-3 * rr)) return IB_OK;  // keep the V-cycle direction
+  const double alpha = ra / aa;
+  {
+    KScope ks(P, IB_KC_OTHER, 8.0);
+    k_set<<<1, 1, 0, P.stream>>>(sc + 4, alpha);
+    IB_LAUNCH_CHECK();
+  }
   st->learned_used += 1;
   const int tpb = 256;
   const int nbk = (int)((n + tpb - 1) / tpb);
   KScope ks(P, IB_KC_OTHER, n * 20.0);
   if (z64) {
-    k_add_d2t_d<<<nbk, tpb, 0, P.stream>>>(z64, P.nn_dz, (long)n);
+    k_add_d2t_d<<<nbk, tpb, 0, P.stream>>>(z64, P.nn_dz, sc + 4, (long)n);
     IB_LAUNCH_CHECK();
     return apply64(P, 0, z64, P.t64);
   }
   if constexpr (std::is_same<T, double>::value) {
-    k_add_d2t_d<<<nbk, tpb, 0, P.stream>>>(zj, P.nn_dz, (long)n);
+    k_add_d2t_d<<<nbk, tpb, 0, P.stream>>>(zj, P.nn_dz, sc + 4, (long)n);
     IB_LAUNCH_CHECK();
     return apply64(P, 0, zj, P.t64);
   } else {
-    k_add_d2t_f<<<nbk, tpb, 0, P.stream>>>(zj, P.nn_dz, (long)n);
+    k_add_d2t_f<<<nbk, tpb, 0, P.stream>>>(zj, P.nn_dz, sc + 4, (long)n);
     IB_LAUNCH_CHECK();
     IB_TRY((launch_cast<float, double>(P, zj, P.t64b, n)));
     return apply64(P, 0, P.t64b, P.t64);
@@ -701,6 +711,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   IB_SETUP_CUDA(cudaStreamSynchronize(s));
   st = setup_hierarchy(P);
   if (st != IB_OK) return fail_free(st);
+  if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
   P.has32 = params->precision == IB_FP32_PRECOND;
   P.has64 = params->precision == IB_FP64 || params->escalate != 0;
   if (P.has32) {
@@ -850,7 +861,7 @@ int ib_learned_pair(ib_problem* H, const double* x, float* in4, float* target) {
   IB_TRY(apply64(P, 0, P.nn_dz, P.nn_adz));
   IB_TRY(launch_axpby(P, 1.0, P.nn_r, -1.0, P.nn_adz, P.nn_r));
   IB_TRY(launch_axpby(P, 1.0, x, -1.0, P.nn_dz, P.nn_dz));
-  IB_TRY(learned_features(P, P.nn_r, sc, in4));
+  IB_TRY(learned_features(P, P.nn_r, P.t64, sc, in4));
   IB_TRY(learned_target(P, P.nn_dz, sc, target));
   IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
   return IB_OK;

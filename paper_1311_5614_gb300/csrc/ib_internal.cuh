@@ -189,6 +189,7 @@ struct Problem {
   bool graph_dirty[2] = {true, true};
   cudaGraphExec_t vgraph[2] = {nullptr, nullptr};
   bool has64 = false, has32 = false;  // hierarchies available for the V-cycle
+  long box_gemm_min = 2048;           // boxes per colour from which n x n boxes use the GEMM kernel
   cudaStream_t gstream = nullptr;                 // private stream the graph is captured on and replayed on
   cudaEvent_t gev[2] = {nullptr, nullptr};        // joins between the caller's stream and gstream
   long long graph_launches[2][IB_KC_COUNT] = {};
@@ -286,7 +287,7 @@ int launch_cast(Problem& P, const A* x, B* y, size_t n);
 
 // ---------------------------------------------------------------- learned stage
 int learned_struct_channel(Problem& P);
-int learned_features(Problem& P, const double* r, double* nrm2, float* x);
+int learned_features(Problem& P, const double* r, double* scratch, double* nrm2, float* x);
 int learned_scale_out(Problem& P, const float* y, const double* nrm2, double* dz);
 int learned_target(Problem& P, const double* e, const double* nrm2, float* t);
 int learned_forward(ib_unet* U, cudaStream_t s, const float* x, float* y);

@@ -342,33 +342,43 @@ __global__ void k_log1p_scale(const double* __restrict__ s, float* out, long n, 
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)log1p(scale * s[i]);
 }
-// x[0..2] = r / ||r|| (FP32), x[3] = the structure channel
-__global__ void k_features(const double* __restrict__ r, const double* __restrict__ nrm2,
+// Physical scaling of the stage: the residual is brought to velocity-error units
+// (u, v rows times h^2/mu, p rows times h) before normalisation, and the pressure
+// output is scaled by mu/h.  rs = sigma_in r.
+__global__ void k_scaled_copy(const double* __restrict__ r, double* rs, long n1, double su, double sp) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < 3 * n1) rs[i] = r[i] * (i < 2 * n1 ? su : sp);
+}
+// x[0..2] = rs / ||rs|| (FP32), x[3] = the structure channel
+__global__ void k_features(const double* __restrict__ rs, const double* __restrict__ nrm2,
                            const float* __restrict__ sch, float* x, long n1) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= 4 * n1) return;
   if (i < 3 * n1) {
     const double nr = sqrt(*nrm2);
-    x[i] = nr > 0.0 ? (float)(r[i] / nr) : 0.f;
+    x[i] = nr > 0.0 ? (float)(rs[i] / nr) : 0.f;
   } else {
     x[i] = sch[i - 3 * n1];
   }
 }
-// dz = ||r|| y (FP64)
-__global__ void k_scale_out(const float* __restrict__ y, const double* __restrict__ nrm2, double* dz, long n) {
+// dz = ||rs|| y, pressure rows also times mu/h (FP64)
+__global__ void k_scale_out(const float* __restrict__ y, const double* __restrict__ nrm2, double* dz, long n1,
+                            double po) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i < n) dz[i] = sqrt(*nrm2) * (double)y[i];
+  if (i < 3 * n1) dz[i] = sqrt(*nrm2) * (i < 2 * n1 ? 1.0 : po) * (double)y[i];
 }
-// target = e / ||r||
-__global__ void k_target(const double* __restrict__ e, const double* __restrict__ nrm2, float* t, long n) {
+// target = e / ||rs||, pressure rows also divided by mu/h
+__global__ void k_target(const double* __restrict__ e, const double* __restrict__ nrm2, float* t, long n1,
+                         double po) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= 3 * n1) return;
   const double nr = sqrt(*nrm2);
-  t[i] = nr > 0.0 ? (float)(e[i] / nr) : 0.f;
+  t[i] = nr > 0.0 ? (float)(e[i] / (nr * (i < 2 * n1 ? 1.0 : po))) : 0.f;
 }
 
+}  // namespace
 
-
+namespace {
 int ualloc(ib_unet* U, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -542,28 +552,35 @@ int learned_struct_channel(Problem& P) {
   return IB_OK;
 }
 
-// NN input from a residual r (FP64, 3N^2): ||r||^2 into nrm2 (device), x = [r/||r||; s].
-int learned_features(Problem& P, const double* r, double* nrm2, float* x) {
+// NN input from a residual r (FP64, 3N^2): rs = sigma_in r in scratch, ||rs||^2 into
+// nrm2 (device), x = [rs / ||rs||; structure channel].
+int learned_features(Problem& P, const double* r, double* scratch, double* nrm2, float* x) {
   const long n1 = (long)P.lev[0].N * P.lev[0].N;
-  IB_TRY(launch_dot(P, r, r, nrm2));
+  const double h = P.lev[0].h;
+  {
+    KScope ks(P, IB_KC_OTHER, n1 * 48.0);
+    k_scaled_copy<<<nb(3 * n1), 256, 0, P.stream>>>(r, scratch, n1, h * h / P.prm.mu, h);
+    IB_LAUNCH_CHECK();
+  }
+  IB_TRY(launch_dot(P, scratch, scratch, nrm2));
   KScope ks(P, IB_KC_OTHER, n1 * 32.0);
-  k_features<<<nb(4 * n1), 256, 0, P.stream>>>(r, nrm2, P.nn_sch, x, n1);
+  k_features<<<nb(4 * n1), 256, 0, P.stream>>>(scratch, nrm2, P.nn_sch, x, n1);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
 
 int learned_scale_out(Problem& P, const float* y, const double* nrm2, double* dz) {
-  const long n = 3L * P.lev[0].N * P.lev[0].N;
-  KScope ks(P, IB_KC_OTHER, n * 12.0);
-  k_scale_out<<<nb(n), 256, 0, P.stream>>>(y, nrm2, dz, n);
+  const long n1 = (long)P.lev[0].N * P.lev[0].N;
+  KScope ks(P, IB_KC_OTHER, n1 * 36.0);
+  k_scale_out<<<nb(3 * n1), 256, 0, P.stream>>>(y, nrm2, dz, n1, P.prm.mu / P.lev[0].h);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
 
 int learned_target(Problem& P, const double* e, const double* nrm2, float* t) {
-  const long n = 3L * P.lev[0].N * P.lev[0].N;
-  KScope ks(P, IB_KC_OTHER, n * 12.0);
-  k_target<<<nb(n), 256, 0, P.stream>>>(e, nrm2, t, n);
+  const long n1 = (long)P.lev[0].N * P.lev[0].N;
+  KScope ks(P, IB_KC_OTHER, n1 * 36.0);
+  k_target<<<nb(3 * n1), 256, 0, P.stream>>>(e, nrm2, t, n1, P.prm.mu / P.lev[0].h);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }

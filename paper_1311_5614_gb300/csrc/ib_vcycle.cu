@@ -178,20 +178,157 @@ __global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* 
   }
 }
 
+// Register-blocked variant for n = 2, 4: the free-box solves of the CTA's boxes are
+// one small GEMM (shared inverse x the block of box residuals), each thread owning
+// an RB x CB tile (rows x boxes) and reading RB inverse entries with one vector
+// load; structure boxes are then solved with their own FP64 inverse.
+template <typename T, int BS>
+struct BoxGemm {
+  static constexpr int NB = 2 * BS * (BS + 1) + BS * BS;
+  static constexpr int THREADS = 128;
+  static constexpr int BPC = BS == 2 ? 32 : 16;   // boxes per CTA
+  static constexpr int RB = sizeof(T) == 4 ? 4 : 2;  // rows per thread (one vector load)
+  static constexpr int RG = NB / RB;                 // row groups
+  // box groups: the largest power-of-two divisor of BPC with RG * BG <= THREADS
+  static constexpr int bg_of(int g) { return RG * g <= THREADS ? g : bg_of(g / 2); }
+  static constexpr int BG = bg_of(BPC);
+  static constexpr int CB = BPC / BG;                // boxes per thread
+  static_assert(NB % RB == 0, "rows");
+  static_assert(BG * CB == BPC && RG * BG <= THREADS, "tiling");
+};
+
+template <typename T, int RB>
+struct VecOf;
+template <>
+struct VecOf<float, 4> {
+  using type = float4;
+};
+template <>
+struct VecOf<double, 2> {
+  using type = double2;
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, const T* __restrict__ rE, int N,
+                                               StokesCoef<T> c, int color, const int* __restrict__ slot,
+                                               const double* __restrict__ Ms, const T* __restrict__ Mf) {
+  using G = BoxGemm<T, BS>;
+  using V = typename VecOf<T, G::RB>::type;
+  constexpr int NB = G::NB;
+  __shared__ __align__(16) T sMf[NB * NB];
+  __shared__ T rs[G::BPC][NB];
+  __shared__ int sslot[G::BPC];
+  const int tid = threadIdx.x;
+  const int nb = N / BS, half = nb >> 1, nbox = half * half;
+  const int box0 = blockIdx.x * G::BPC;
+  for (int e = tid; e < NB * NB; e += G::THREADS) sMf[e] = Mf[e];
+  if (tid < G::BPC) {
+    const int t = box0 + tid;
+    int sl = -2;  // -2: no box
+    if (t < nbox) {
+      const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+      sl = slot[J * nb + I];
+    }
+    sslot[tid] = sl;
+  }
+  for (int e = tid; e < G::BPC * NB; e += G::THREADS) {
+    const int lb = e / NB, q = e - lb * NB, t = box0 + lb;
+    T r = 0;
+    if (t < nbox) {
+      const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+      int cc, i, j;
+      box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
+      r = resid_at(w, b, rE, N, c, cc, i, j);
+    }
+    rs[lb][q] = r;
+  }
+  __syncthreads();
+  // free boxes: delta[q][box] = sum_s Mf[s][q] r[box][s]
+  const int rg = tid % G::RG, bg = tid / G::RG;
+  if (bg < G::BG) {
+    T acc[G::RB][G::CB];
+#pragma unroll
+    for (int a = 0; a < G::RB; ++a)
+#pragma unroll
+      for (int k = 0; k < G::CB; ++k) acc[a][k] = 0;
+#pragma unroll 4
+    for (int s2 = 0; s2 < NB; ++s2) {
+      const V m = *reinterpret_cast<const V*>(&sMf[s2 * NB + rg * G::RB]);
+      const T* mv = reinterpret_cast<const T*>(&m);
+#pragma unroll
+      for (int k = 0; k < G::CB; ++k) {
+        const T rv = rs[bg * G::CB + k][s2];
+#pragma unroll
+        for (int a = 0; a < G::RB; ++a) acc[a][k] += mv[a] * rv;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < G::CB; ++k) {
+      const int lb = bg * G::CB + k;
+      if (sslot[lb] != -1) continue;  // structure box or no box
+      const int t = box0 + lb;
+      const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+#pragma unroll
+      for (int a = 0; a < G::RB; ++a) {
+        int cc, i, j;
+        box_unknown(rg * G::RB + a, BS, I * BS, J * BS, N, &cc, &i, &j);
+        w[cc * N * N + j * N + i] += acc[a][k];
+      }
+    }
+  }
+  // structure boxes: their own FP64 inverse; all threads share the (box, row) pairs
+  __shared__ int slist[G::BPC];
+  __shared__ int ns;
+  if (tid == 0) {
+    int k = 0;
+    for (int lb = 0; lb < G::BPC; ++lb)
+      if (sslot[lb] >= 0) slist[k++] = lb;
+    ns = k;
+  }
+  __syncthreads();
+  for (int e = tid; e < ns * NB; e += G::THREADS) {
+    const int lb = slist[e / NB], q = e % NB;
+    const int t = box0 + lb;
+    const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+    const double* M = Ms + (size_t)sslot[lb] * NB * NB + q;
+    double d0 = 0.0, d1 = 0.0;
+#pragma unroll 4
+    for (int s2 = 0; s2 < NB; s2 += 2) {
+      d0 += M[(size_t)s2 * NB] * (double)rs[lb][s2];
+      d1 += M[(size_t)(s2 + 1) * NB] * (double)rs[lb][s2 + 1];
+    }
+    int cc, i, j;
+    box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
+    w[cc * N * N + j * N + i] += (T)(d0 + d1);
+  }
+}
+
 template <typename T>
 int launch_boxn(Problem& P, int l, T* w, const T* b, const T* rE, int color) {
   LevelInfo& L = P.lev[l];
   const StokesCoef<T> c = coefs<T>(P, l);
   const int half = L.nb / 2;
   const long nbox = (long)half * half;
+  // the GEMM form pays off on large levels; small levels keep one box per CTA slot
+  const bool gemm = nbox >= P.box_gemm_min;
   switch (P.prm.box) {
     case 2:
-      kv_boxn<T, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(
-          w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
+      if (!gemm) {
+        kv_boxn<T, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(
+            w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
+        break;
+      }
+      kv_boxg<T, 2><<<nblk(nbox, BoxGemm<T, 2>::BPC), 128, 0, P.stream>>>(w, b, rE, L.N, c, color, L.flag,
+                                                                       L.Mstruct, Mfree_of<T>(L));
       break;
     case 4:
-      kv_boxn<T, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(
-          w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
+      if (!gemm) {
+        kv_boxn<T, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(
+            w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
+        break;
+      }
+      kv_boxg<T, 4><<<nblk(nbox, BoxGemm<T, 4>::BPC), 128, 0, P.stream>>>(w, b, rE, L.N, c, color, L.flag,
+                                                                       L.Mstruct, Mfree_of<T>(L));
       break;
     default:
       kv_boxn<T, 8><<<nblk(nbox, BoxShape<8>::BPC), BoxShape<8>::THREADS, 0, P.stream>>>(

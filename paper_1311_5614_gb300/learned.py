@@ -1,0 +1,128 @@
+"""Training and evaluation of the learned FGMRES stage (orchestration only).
+
+Every numerical step runs in libibmg.so: pairs come from ib_learned_pair (the
+problem's own operator and V-cycle), training from ib_unet_train_step (the
+library's forward, backward and Adam kernels).  This module only draws the
+seeded inputs, orders the calls and keeps the pairs in device memory.
+
+Pair recipe (not in the paper): for a problem with a random stiffness and a
+random smooth field x (ib_workloads.random_smooth_field), b = A x, z = MG(b)
+(one V-cycle), r = b - A z, e = x - z; the network learns r/|r| (+ the
+structure channel) -> e/|r|, the correction FGMRES needs after the V-cycle.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+import ib_workloads as W
+
+from . import capi as C
+
+
+def harvest(N=512, n_points=1024, n_problems=16, pairs_per_problem=64, seed=0, log_kappa=(2.0, 6.0),
+            dt=1e-2, box=4, precision="fp32"):
+    """Return device tensors X [P, 4 N^2], T [P, 3 N^2] (float32) and the problems' kappas."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    P = n_problems * pairs_per_problem
+    X = torch.empty((P, 4 * N * N), dtype=torch.float32, device="cuda")
+    T = torch.empty((P, 3 * N * N), dtype=torch.float32, device="cuda")
+    kappas = []
+    k = 0
+    for i in range(n_problems):
+        kap = float(10.0 ** rng.uniform(*log_kappa))
+        cx, cy = 0.5 + 0.02 * rng.standard_normal(2)
+        prob = W.single_ellipse(N=N, n_points=n_points, kappa=kap, dt=dt, center=(cx, cy))
+        prob.box = box
+        s = C.IBSolver.from_problem(prob, precision=precision)
+        for j in range(pairs_per_problem):
+            x = torch.tensor(W.random_smooth_field(N, int(rng.integers(1 << 31))).ravel(), device="cuda")
+            s.learned_pair(x, X[k], T[k])
+            k += 1
+        s.close()
+        kappas.append(kap)
+    torch.cuda.synchronize()
+    return X, T, kappas
+
+
+def train(net, X, T, epochs=2, lr=1e-3, seed=0, log=None):
+    """Adam over the pairs in a seeded random order; returns the per-epoch mean losses."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    P = X.shape[0]
+    losses = []
+    total = epochs * P
+    step = 0
+    for ep in range(epochs):
+        order = rng.permutation(P)
+        acc = 0.0
+        for idx in order:
+            # cosine decay of the learning rate over the whole run
+            a = lr * 0.5 * (1.0 + np.cos(np.pi * step / max(total, 1)))
+            acc += net.train_step(X[int(idx)], T[int(idx)], float(max(a, 1e-5)))
+            step += 1
+        losses.append(acc / P)
+        if log:
+            log("epoch %d loss %.4f" % (ep, losses[-1]))
+    torch.cuda.synchronize()
+    return losses
+
+
+def evaluate(net, N=512, n_points=1024, kappas=(1e2, 1e4, 1e6), dt=1e-2, box=4, precision="fp32",
+             seed=1000003, repeats=3):
+    """Plain MG-FGMRES vs MG-FGMRES with the learned stage on held-out problems:
+    iterations and device time of one implicit step each."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for kap in kappas:
+        cx, cy = 0.5 + 0.02 * rng.standard_normal(2)
+        prob = W.single_ellipse(N=N, n_points=n_points, kappa=kap, dt=dt, center=(cx, cy))
+        prob.box = box
+        row = {"kappa": kap}
+        for mode in ("plain", "learned"):
+            s = C.IBSolver.from_problem(prob, precision=precision, max_iters=200)
+            if mode == "learned":
+                s.set_learned_stage(net)
+            up = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
+            X0 = torch.tensor(prob.X, device="cuda")
+            times, st = [], None
+            for r in range(repeats + 1):
+                X = X0.clone()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                st = s.solve_step(None, up, X)
+                b.record()
+                torch.cuda.synchronize()
+                if r > 0:
+                    times.append(a.elapsed_time(b))
+            row[mode] = {"iters": st["iters"], "ms": float(np.median(times)), "status": st["status"],
+                         "rel_res_true": st["rel_res_true"], "learned_used": st["learned_used"],
+                         "escalated_at": st["escalated_at"]}
+            if mode == "learned":
+                s.set_learned_stage(None)
+            s.close()
+        out.append(row)
+    return out
+
+
+def run(N=512, n_problems=16, pairs_per_problem=64, epochs=2, lr=1e-3, seed=0, log=print):
+    """Harvest, train from a seeded initialisation, evaluate; returns a summary dict."""
+    t0 = time.perf_counter()
+    X, T, kap = harvest(N=N, n_problems=n_problems, pairs_per_problem=pairs_per_problem, seed=seed)
+    t1 = time.perf_counter()
+    net = C.UNet(N, W.unet_init_params(seed + 7))
+    losses = train(net, X, T, epochs=epochs, lr=lr, seed=seed, log=log)
+    t2 = time.perf_counter()
+    del X, T
+    ev = evaluate(net, N=N)
+    t3 = time.perf_counter()
+    params = net.get_params()
+    net.close()
+    return {"pairs": n_problems * pairs_per_problem, "train_kappas": kap, "epochs": epochs, "losses": losses,
+            "harvest_s": t1 - t0, "train_s": t2 - t1, "eval_s": t3 - t2, "eval": ev, "params": params}

@@ -116,6 +116,13 @@ def test_vcycle_fp64(pkg, name, box):
     s.close()
 
 
+@pytest.mark.parametrize("name,box", [("c1_64", 2), ("c1_64", 4), ("stiff_32_exact", 4)])
+def test_vcycle_fp64_gemm_box_kernel(pkg, name, box, monkeypatch):
+    """The register-blocked box kernel (used on large levels) forced on every level."""
+    monkeypatch.setenv("IB_BOX_GEMM_MIN", "0")
+    test_vcycle_fp64(pkg, name, box)
+
+
 @pytest.mark.parametrize("name,box", [("c1_64", 1), ("stiff_32_exact", 4)])
 def test_vcycle_fp32(pkg, name, box):
     p = make_case(name, box)

@@ -87,10 +87,15 @@ def test_learned_pair_matches_oracle_definition(pkg):
     z = O.vcycle(levels, b, np.zeros_like(b), 1, 1, p.rho, "color4")
     r = b - A @ z
     e = x - z
-    nr = np.linalg.norm(r)
+    n1 = N * N
+    h = p.h
+    sig_in = np.concatenate([np.full(2 * n1, h * h / p.mu), np.full(n1, h)])
+    sig_out = np.concatenate([np.ones(2 * n1), np.full(n1, p.mu / h)])
+    rs = sig_in * r
+    nr = np.linalg.norm(rs)
     got = in4.cpu().numpy()
-    assert np.abs(got[:3 * N * N] - r / nr).max() <= 1e-6 * np.abs(r / nr).max()
-    assert np.abs(tg.cpu().numpy() - e / nr).max() <= 1e-6 * np.abs(e / nr).max()
+    assert np.abs(got[:3 * n1] - rs / nr).max() <= 1e-6 * np.abs(rs / nr).max()
+    assert np.abs(tg.cpu().numpy() - e / (nr * sig_out)).max() <= 1e-6 * np.abs(e / (nr * sig_out)).max()
     # structure channel: log(1 + dt/mu * (S_u Kbar)) with S_u the u-block of spreading
     kbar = np.zeros(p.n_points)
     np.add.at(kbar, p.springs[:, 0], p.kappa)
