@@ -3,9 +3,9 @@
  *
  * Method: Guy, Philip & Griffith, "Geometric multigrid for an implicit-time
  * immersed boundary method".  One backward-Euler IB step with lagged
- * spreading/interpolation (sec. 2.3, Eqs. 11-14) is reduced to a Stokes-type
+ * spreading/interpolation (sec. 2.3.2, Eqs. 17-20) is reduced to a Stokes-type
  * saddle-point system on a 2-D staggered (MAC) grid by eliminating the
- * Lagrangian unknowns (Eqs. 15-16, the block system of sec. 3):
+ * Lagrangian unknowns (Eqs. 21-22; the block system, Eq. 23, sec. 3):
  *
  *     [ mu*Lap_h - (rho/dt) I + dt * S J S^*   -grad_h ] [u]   [ -(rho/dt) u^n - S F(X^n) ]
  *     [ div_h                                   0      ] [p] = [ 0                        ]
@@ -18,7 +18,7 @@
  * with the box / big-box smoother (secs. 5-6), re-discretised Stokes and
  * Galerkin-coarsened elasticity on coarse levels (sec. 3.2), staggered
  * transfers (sec. 3.1) and an exact solve on the N_c = max(4, box) grid
- * (sec. 6.1).  Then X^{n+1} = X^n + dt S^* u^{n+1} (Eq. 14).
+ * (sec. 6.1).  Then X^{n+1} = X^n + dt S^* u^{n+1} (Eq. 20).
  *
  * Conventions for every entry point:
  *  - Domain: periodic square of side L, N x N cells, h = L / N.
@@ -173,7 +173,7 @@ IB_API int ib_tail_grid(const ib_problem* prob, int32_t precision);
  * as found by the last set-up. */
 IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
 
-/* ---- Batches of independent problems (SURVEY batching row; not in the paper) ----
+/* ---- Batches of independent problems (not in the paper) ----
  *
  * A batch holds nprob independent problems of any grid sizes and parameters.
  * Each problem gets its own CUDA stream and its own captured V-cycle graph, and
@@ -203,7 +203,7 @@ IB_API int ib_batch_size(const ib_batch* batch);
 IB_API ib_problem* ib_batch_problem(ib_batch* batch, int32_t k);
 IB_API void ib_destroy_batch(ib_batch* batch);
 
-/* ---- Learned preconditioner stage (SURVEY learned-stage row; not in the paper) ----
+/* ---- Learned preconditioner stage (not in the paper) ----
  *
  * A 3-level convolutional U-Net (16/32/64 channels, 3x3 circular convolutions,
  * GELU, 2x2 average pooling, nearest upsampling with skip concatenation, a 1x1

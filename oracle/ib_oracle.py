@@ -13,14 +13,14 @@ implicit-time immersed boundary method"):
 * the regularised delta function, spreading S_h and interpolation S_h^*,
   sec. 2.2 (delta and spreading/interpolation equations);
 * the backward-Euler step with lagged S, and the elimination of the
-  Lagrangian unknowns onto the grid, sec. 2.3 (Eqs. 11-16 and the block
+  Lagrangian unknowns onto the grid, sec. 2.3.2 (Eqs. 17-22 and the block
   system "matrixeq");
 * the staggered restriction / prolongation of sec. 3.1, the hybrid coarse
   operator of sec. 3.2 (re-discretised Stokes + Galerkin elasticity);
 * the V-cycle of Algorithm 1 with the box (Vanka) smoother of sec. 5 and the
   n x n "big boxes" of sec. 6, exact coarsest solve on N_c = max(4, n);
 * flexible GMRES with the V-cycle as right preconditioner, sec. 3.3;
-* the position update X^{n+1} = X^n + dt S^* u^{n+1}, Eq. 14.
+* the position update X^{n+1} = X^n + dt S^* u^{n+1}, Eq. 20.
 
 Everything is assembled as explicit sparse matrices (scipy CSR) and applied
 with plain matrix-vector products; box matrices are principal submatrices of
@@ -37,7 +37,7 @@ also listed in the design notes):
   (sec. 7 allows semi-implicit linearisation of nonlinear laws); the default
   Jacobian is clamped to be negative semidefinite; with zero rest length both
   variants equal kappa * A_f exactly;
-* the right-hand side is -S F(X^n) - (rho/dt) u^n (the paper's Eq. 15 omits the
+* the right-hand side is -S F(X^n) - (rho/dt) u^n (the paper's Eq. 21 omits the
   stiffness factor gamma in front of S A_f X^n; the force F = gamma A_f X is
   what the elimination produces);
 * the 1-D cosine kernel is read as (1 + cos(pi r / (2h))) / (4h) for |r| < 2h;

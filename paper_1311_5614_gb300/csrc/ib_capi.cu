@@ -74,25 +74,6 @@ int fail(int code, const std::string& msg) {
 
 namespace {
 
-template <typename T>
-int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) return IB_OK;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    return fail(IB_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
-  }
-  return IB_OK;
-}
-
-template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
-  p = nullptr;
-}
-
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 int validate(const ib_params* p) {
@@ -175,9 +156,11 @@ int setup_hierarchy(Problem& P) {
     if (cnt > L.cap_struct) {
       P.graph_dirty[0] = P.graph_dirty[1] = true;  // the box kernels take the new pointer
       dfree(L.Mstruct);
+      dfree(L.Mstruct32);
       int cap = cnt + cnt / 4 + 16;
       if (cap > L.nb * L.nb) cap = L.nb * L.nb;
       IB_TRY(dalloc(&L.Mstruct, (size_t)cap * nB * nB));
+      if (P.prm.precision == IB_FP32_PRECOND) IB_TRY(dalloc(&L.Mstruct32, (size_t)cap * nB * nB));
       L.cap_struct = cap;
     }
     L.n_struct = cnt;
@@ -185,6 +168,8 @@ int setup_hierarchy(Problem& P) {
     IB_TRY(launch_struct_fill(P, l));
     IB_TRY(launch_assemble_struct(P, l));
     IB_TRY(launch_invert(P, L.Mstruct, nB, cnt));
+    if (P.prm.precision == IB_FP32_PRECOND && cnt > 0)
+      IB_TRY(launch_cast<double, float>(P, L.Mstruct, L.Mstruct32, (size_t)cnt * nB * nB));
   }
   P.free_ready = true;
   IB_TRY(launch_coarse_fill(P));
@@ -198,7 +183,7 @@ int setup_hierarchy(Problem& P) {
 void free_problem(Problem* P) {
   if (!P) return;
   for (auto& L : P->lev) {
-    dfree(L.flag); dfree(L.Mstruct); dfree(L.Sfree); dfree(L.Mfree); dfree(L.Mfree32);
+    dfree(L.flag); dfree(L.Mstruct); dfree(L.Mstruct32); dfree(L.Sfree); dfree(L.Mfree); dfree(L.Mfree32);
     dfree(L.pat64.base); dfree(L.pat64.w); dfree(L.pat32.base); dfree(L.pat32.w);
     dfree(L.v64.w); dfree(L.v64.b); dfree(L.v64.r);
     dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);

@@ -155,10 +155,14 @@ struct LevelInfo {
   int cap_struct = 0;  // allocated structure-box slots
   int* flag = nullptr;        // [nb * nb] structure flag -> slot (-1 free)
   double* Mstruct = nullptr;  // [cap][nB * nB] inverse (column-major), FP64
+  float* Mstruct32 = nullptr; // FP32 copy for the FP32 V-cycle
   double* Sfree = nullptr;    // [nB * nB] Stokes block of a box (column-major), FP64
   double* Mfree = nullptr;    // [nB * nB] shared inverse of structure-free boxes, FP64
   float* Mfree32 = nullptr;   // FP32 copy for the FP32 V-cycle
-  double* rE64 = nullptr;     // [2 N^2] elasticity residual part -dt E w (patch rows only)
+  // elasticity residual part -dt E_l w of the V-cycle, [2 N^2]: zero between
+  // uses (each colour phase adds to its own rows and the box solves take the
+  // values back out; prolongation clears what the restriction used)
+  double* rE64 = nullptr;
   float* rE32 = nullptr;
   Patches<double> pat64;      // FP64 patches (operator path)
   Patches<float> pat32;       // FP32 patches (FP32 V-cycle)
@@ -260,6 +264,26 @@ struct KScope {
   ~KScope();
 };
 
+// Device allocation with the library's error reporting (count 0: NULL).
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return IB_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(IB_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  return IB_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
 // ---------------------------------------------------------------- launchers (points)
 int launch_fine_patches(Problem& P);
 int launch_coarse_patches(Problem& P, int level);
@@ -270,6 +294,7 @@ int launch_move_points(Problem& P, const double* up);
 template <typename T>
 int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U);
 int launch_mark_struct(Problem& P, int level);
+
 int launch_assemble_struct(Problem& P, int level);
 int launch_assemble_coarse(Problem& P);
 

@@ -33,28 +33,28 @@ __device__ __forceinline__ T stokes_row(const T* __restrict__ w, int N, const St
 template <typename T>
 __device__ __forceinline__ T resid_at(const T* w, const T* b, const T* rE, int N, const StokesCoef<T>& c,
                                       int comp, int i, int j) {
-  int g = comp * N * N + j * N + i;
+  const int g = comp * N * N + j * N + i;
   T r = b[g] - stokes_row(w, N, c, comp, i, j);
   if (rE && comp < 2) r += rE[g];
   return r;
 }
 
-// Restriction of the full residual (b - A_S w + rE) to coarse cell (I, J) of an
-// Nc grid: u by (1/8)[1 2 1; 1 2 1], v transposed, p by the four-cell average.
+// Restriction of the full residual to coarse cell (I, J) of an Nc grid (sec. 3.1,
+// Eqs. 25-26): u by (1/8)[1 2 1; 1 2 1], v transposed, p by the four-cell average.
 template <typename T>
-__device__ __forceinline__ void restrict_resid_cell(const T* w, const T* b, const T* rE, int N,
+__device__ __forceinline__ void restrict_resid_cell(const T* w, const T* b, const T* E, int N,
                                                     const StokesCoef<T>& c, int I, int J, T* ru, T* rv, T* rp) {
   const int m = N - 1;
   const int xm = (2 * I - 1) & m, x0 = 2 * I, x1 = 2 * I + 1;
   const int ym = (2 * J - 1) & m, y0 = 2 * J, y1 = 2 * J + 1;
-  *ru = (T)0.125 * (resid_at(w, b, rE, N, c, 0, xm, y0) + resid_at(w, b, rE, N, c, 0, xm, y1) +
-                    resid_at(w, b, rE, N, c, 0, x1, y0) + resid_at(w, b, rE, N, c, 0, x1, y1)) +
-        (T)0.25 * (resid_at(w, b, rE, N, c, 0, x0, y0) + resid_at(w, b, rE, N, c, 0, x0, y1));
-  *rv = (T)0.125 * (resid_at(w, b, rE, N, c, 1, x0, ym) + resid_at(w, b, rE, N, c, 1, x1, ym) +
-                    resid_at(w, b, rE, N, c, 1, x0, y1) + resid_at(w, b, rE, N, c, 1, x1, y1)) +
-        (T)0.25 * (resid_at(w, b, rE, N, c, 1, x0, y0) + resid_at(w, b, rE, N, c, 1, x1, y0));
-  *rp = (T)0.25 * (resid_at(w, b, rE, N, c, 2, x0, y0) + resid_at(w, b, rE, N, c, 2, x1, y0) +
-                   resid_at(w, b, rE, N, c, 2, x0, y1) + resid_at(w, b, rE, N, c, 2, x1, y1));
+  *ru = (T)0.125 * (resid_at(w, b, E, N, c, 0, xm, y0) + resid_at(w, b, E, N, c, 0, xm, y1) +
+                    resid_at(w, b, E, N, c, 0, x1, y0) + resid_at(w, b, E, N, c, 0, x1, y1)) +
+        (T)0.25 * (resid_at(w, b, E, N, c, 0, x0, y0) + resid_at(w, b, E, N, c, 0, x0, y1));
+  *rv = (T)0.125 * (resid_at(w, b, E, N, c, 1, x0, ym) + resid_at(w, b, E, N, c, 1, x1, ym) +
+                    resid_at(w, b, E, N, c, 1, x0, y1) + resid_at(w, b, E, N, c, 1, x1, y1)) +
+        (T)0.25 * (resid_at(w, b, E, N, c, 1, x0, y0) + resid_at(w, b, E, N, c, 1, x1, y0));
+  *rp = (T)0.25 * (resid_at(w, b, E, N, c, 2, x0, y0) + resid_at(w, b, E, N, c, 2, x1, y0) +
+                   resid_at(w, b, E, N, c, 2, x0, y1) + resid_at(w, b, E, N, c, 2, x1, y1));
 }
 
 // Same restriction applied to a stored residual vector r.
@@ -132,6 +132,96 @@ __device__ __forceinline__ void JU_point(const Springs<T>& sp, const T* U, int k
   }
   *gx = ax;
   *gy = ay;
+}
+
+// Force term of point k, coef * (J S*_l w)_k, by an aligned quad of lanes (j =
+// lane & 3, qmask the quad's lanes).  Lane 0 interpolates the point's own
+// velocity, lanes 1..3 those of its first three spring neighbours (further ones
+// round robin), all at the same time; the spring terms K_s (U_other - U_k) are
+// then summed over the quad.  Every lane of the quad must call this; the result
+// is valid in lane j == 0.
+template <typename T>
+__device__ __forceinline__ void force_quad(const Patches<T>& pat, const Springs<T>& sp, const T* w, int N, T coef,
+                                           int k, int j, unsigned qmask, int qlane0, T* gx, T* gy) {
+  const int p0 = sp.adj_ptr[k], deg = sp.adj_ptr[k + 1] - p0, ns = sp.ns;
+  T ux = 0, uy = 0;
+  int o = -1, s = -1;
+  if (j == 0) {
+    ux = interp_point(pat, w, N, 0, k);
+    uy = interp_point(pat, w, N, 1, k);
+  } else if (j - 1 < deg) {
+    o = sp.adj_other[p0 + j - 1];
+    s = sp.adj_spring[p0 + j - 1];
+    ux = interp_point(pat, w, N, 0, o);
+    uy = interp_point(pat, w, N, 1, o);
+  }
+  const T ux0 = __shfl_sync(qmask, ux, qlane0);
+  const T uy0 = __shfl_sync(qmask, uy, qlane0);
+  T ax = 0, ay = 0;
+  if (s >= 0) {
+    const T dx = ux - ux0, dy = uy - uy0;
+    const T kxx = sp.K[s], kxy = sp.K[ns + s], kyy = sp.K[2 * ns + s];
+    ax = kxx * dx + kxy * dy;
+    ay = kxy * dx + kyy * dy;
+    for (int m = j + 2; m < deg; m += 3) {
+      const int o2 = sp.adj_other[p0 + m], s2 = sp.adj_spring[p0 + m];
+      const T ex = interp_point(pat, w, N, 0, o2) - ux0, ey = interp_point(pat, w, N, 1, o2) - uy0;
+      const T k2xx = sp.K[s2], k2xy = sp.K[ns + s2], k2yy = sp.K[2 * ns + s2];
+      ax += k2xx * ex + k2xy * ey;
+      ay += k2xy * ex + k2yy * ey;
+    }
+  }
+  ax += __shfl_xor_sync(qmask, ax, 1);
+  ay += __shfl_xor_sync(qmask, ay, 1);
+  ax += __shfl_xor_sync(qmask, ax, 2);
+  ay += __shfl_xor_sync(qmask, ay, 2);
+  *gx = coef * ax;
+  *gy = coef * ay;
+}
+
+// Whether velocity row (comp, i, j) of a level with b x b boxes is an unknown of
+// a box of colour `color` (-1: any).  A face on the low edge of its box is also
+// the far-edge unknown of the neighbouring box, whose colour parity differs.
+__device__ __forceinline__ bool row_in_color(int comp, int i, int j, int b, int color) {
+  if (color < 0) return true;
+  const int cx = (i / b) & 1, cy = ((j / b) & 1) << 1;
+  if ((cx | cy) == color) return true;
+  if (comp == 0 && i % b == 0) return ((cx ^ 1) | cy) == color;
+  if (comp == 1 && j % b == 0) return (cx | (cy ^ 2)) == color;
+  return false;
+}
+
+// rE += coef * S_l J S*_l w restricted to the rows of boxes of one colour (-1:
+// all rows), for point k by an aligned quad of lanes: the force (force_quad),
+// then lane j spreads component j & 1 over patch rows 2 (j >> 1) and
+// 2 (j >> 1) + 1 with atomic additions.  Every lane of the quad must call this.
+template <typename T>
+__device__ __forceinline__ void force_spread_quad(const Patches<T>& pat, const Springs<T>& sp, const T* w, int N,
+                                                  T coef, int k, int j, unsigned qmask, int qlane0, int b, int color,
+                                                  T* rE) {
+  T gx, gy;
+  force_quad(pat, sp, w, N, coef, k, j, qmask, qlane0, &gx, &gy);
+  gx = __shfl_sync(qmask, gx, qlane0);
+  gy = __shfl_sync(qmask, gy, qlane0);
+  const int comp = j & 1;
+  const T g = comp ? gy : gx;
+  if (g == (T)0) return;
+  const int m = N - 1;
+  const int x0 = pat.b_at(0, comp, 0, k), y0 = pat.b_at(0, comp, 1, k);
+  T* yc = rE + (size_t)comp * N * N;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int bb = 2 * (j >> 1) + r;
+    const T wy = pat.w_at(0, comp, 1, bb, k) * g;
+    if (wy == (T)0) continue;
+    const int jj = (y0 + bb) & m;
+#pragma unroll
+    for (int a = 0; a < PATCH; ++a) {
+      const T wx = pat.w_at(0, comp, 0, a, k);
+      const int ii = (x0 + a) & m;
+      if (wx != (T)0 && row_in_color(comp, ii, jj, b, color)) atomicAdd(&yc[jj * N + ii], wx * wy);
+    }
+  }
 }
 
 // y_c += g * (row bb of the spread patch of point k): 4 atomic additions.

@@ -174,7 +174,7 @@ __global__ void k_spread_force(Patches<double> pat, const double* __restrict__ F
   }
 }
 
-// X += dt * S^* u with the level-0 interpolation weights (Eq. 14).
+// X += dt * S^* u with the level-0 interpolation weights (Eq. 20).
 __global__ void k_move_points(Patches<double> pat, const double* __restrict__ up, int np, int N,
                               double dt, double* X) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,9 +1,10 @@
 // The V-cycle of Algorithm 1 as GB300 kernels.
 //
 // Fine levels (N_l above the tail size) run grid-wide kernels, one phase per
-// launch: per colour the elasticity residual term rE = -dt E_l w (interp, then
-// J U spread with atomics into the patch rows), then the box solves of that
-// colour.  For n x n boxes (n >= 2) the Stokes residual of a box is evaluated
+// launch: per colour one kernel forms the point forces -dt/h_0^2 J S*_l w (a
+// quad of lanes per point) and spreads them with atomic additions into rE, on
+// the rows of that colour's boxes only; then the box solves of the colour, which
+// take rE back out of their structure rows (leaving rE zero).  For n x n boxes (n >= 2) the Stokes residual of a box is evaluated
 // inside the box kernel: boxes of one colour are at least n >= 2 cells apart,
 // farther than the 5-point stencil reaches, so no box reads an unknown another
 // box of its colour writes.  1 x 1 boxes of one colour are one cell apart, so
@@ -59,6 +60,13 @@ template <>
 LevelBuf<float>& lbuf<float>(LevelInfo& L) { return L.v32; }
 
 template <typename T>
+const T* Mstruct_of(const LevelInfo& L);
+template <>
+const double* Mstruct_of<double>(const LevelInfo& L) { return L.Mstruct; }
+template <>
+const float* Mstruct_of<float>(const LevelInfo& L) { return L.Mstruct32; }
+
+template <typename T>
 T* rEbuf(LevelInfo& L);
 template <>
 double* rEbuf<double>(LevelInfo& L) { return L.rE64; }
@@ -93,38 +101,24 @@ T* Ubuf(Problem& P) {
 
 // ------------------------------------------------------------------ fine-level kernels
 
-// U = S^*_l w at every point, and zero the spread-patch rows of rE.
-// Thread (row bb, component, point): bb == 0 also computes U.
+// rE += coef * S_l J S*_l w on the rows of colour `color` (-1: all rows): one
+// quad of lanes per point.
 template <typename T>
-__global__ void kv_interp_zero(Patches<T> pat, const T* __restrict__ w, int np, int N, T* __restrict__ U,
-                               T* __restrict__ rE) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 8 * np) return;
-  int bb = t / (2 * np), rem = t - bb * 2 * np;
-  int comp = rem / np, k = rem - comp * np;
-  if (bb == 0) U[comp * np + k] = interp_point(pat, w, N, comp, k);
-  zero_row(pat, N, comp, k, bb, rE);
+__global__ void kv_force_spread(Patches<T> pat, Springs<T> sp, const T* __restrict__ w, int N, T coef, int b,
+                                int color, T* __restrict__ rE) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int k = (int)(t >> 2), j = (int)(t & 3);
+  if (k >= sp.np) return;  // whole quads: blockDim is a multiple of 4
+  const int lane = threadIdx.x & 31;
+  force_spread_quad(pat, sp, w, N, coef, k, j, 0xFu << (lane & ~3), lane & ~3, b, color, rE);
 }
 
-// rE += coef * S_l (J U), thread (row bb, component, point).
-template <typename T>
-__global__ void kv_spread(Patches<T> pat, Springs<T> sp, const T* __restrict__ U, int N, T coef, T* rE) {
-  int np = sp.np;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 8 * np) return;
-  int bb = t / (2 * np), rem = t - bb * 2 * np;
-  int comp = rem / np, k = rem - comp * np;
-  T gx, gy;
-  JU_point(sp, U, k, &gx, &gy);
-  T g = coef * (comp == 0 ? gx : gy);
-  if (g != (T)0) spread_row(pat, N, comp, k, bb, g, rE);
-}
-
-// n x n boxes (n >= 2) of one colour, Stokes residual inline.  One thread per
-// box unknown (row of the box inverse), several boxes per CTA; the shared
-// inverse of the structure-free box is staged in shared memory (n <= 4), the
-// FP64 inverses of structure boxes are read column by column (coalesced over
-// the box's threads).
+// n x n boxes (n >= 2) of one colour, residual inline (Stokes stencil plus rE on
+// structure rows, which the kernel then clears: each such row belongs to exactly
+// one box of the colour).  One thread per box unknown (row
+// of the box inverse), several boxes per CTA; the shared inverse of the
+// structure-free box is staged in shared memory (n <= 4), the inverses of
+// structure boxes are read column by column (coalesced over the box's threads).
 template <int BS>
 struct BoxShape {
   static constexpr int NB = 2 * BS * (BS + 1) + BS * BS;
@@ -135,15 +129,15 @@ struct BoxShape {
 };
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* __restrict__ b,
-                                                                 const T* __restrict__ rE, int N, StokesCoef<T> c,
-                                                                 int color, const int* __restrict__ slot,
-                                                                 const double* __restrict__ Ms,
+__global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* __restrict__ b, T* rE, int N,
+                                                                 StokesCoef<T> c, int color,
+                                                                 const int* __restrict__ slot,
+                                                                 const T* __restrict__ Ms,
                                                                  const T* __restrict__ Mf) {
   using S = BoxShape<BS>;
-  constexpr int NB = S::NB;
+  constexpr int NB = S::NB, NV = 2 * BS * (BS + 1);
   __shared__ T sMf[S::SMEM_MF ? NB * NB : 1];
-  __shared__ double rs[S::BPC][NB];
+  __shared__ T rs[S::BPC][NB];
   const int tid = threadIdx.x;
   if (S::SMEM_MF)
     for (int e = tid; e < NB * NB; e += S::THREADS) sMf[e] = Mf[e];
@@ -151,29 +145,34 @@ __global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* 
   const int nb = N / BS, half = nb >> 1;
   const int t = blockIdx.x * S::BPC + lb;
   const bool valid = t < half * half && q < NB;
-  int I = 0, J = 0, gq = 0;
+  int gq = 0, sl = -1;
   if (valid) {
-    I = 2 * (t % half) + (color & 1);
-    J = 2 * (t / half) + (color >> 1);
+    const int I = 2 * (t % half) + (color & 1);
+    const int J = 2 * (t / half) + (color >> 1);
+    sl = slot[J * nb + I];
     int cc, i, j;
     box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
     gq = cc * N * N + j * N + i;
-    rs[lb][q] = (double)resid_at(w, b, rE, N, c, cc, i, j);
+    T r = b[gq] - stokes_row(w, N, c, cc, i, j);
+    if (rE && sl >= 0 && q < NV) {
+      r += rE[gq];
+      rE[gq] = (T)0;
+    }
+    rs[lb][q] = r;
   }
   __syncthreads();
   if (!valid) return;
-  const int sl = slot[J * nb + I];
   if (sl >= 0) {
-    const double* M = Ms + (size_t)sl * NB * NB + q;
-    double d = 0.0;
+    const T* M = Ms + (size_t)sl * NB * NB + q;
+    T d = 0;
 #pragma unroll 8
     for (int s = 0; s < NB; ++s) d += M[(size_t)s * NB] * rs[lb][s];
-    w[gq] += (T)d;
+    w[gq] += d;
   } else {
     const T* M = S::SMEM_MF ? sMf + q : Mf + q;
     T d = 0;
 #pragma unroll 8
-    for (int s = 0; s < NB; ++s) d += M[s * NB] * (T)rs[lb][s];
+    for (int s = 0; s < NB; ++s) d += M[s * NB] * rs[lb][s];
     w[gq] += d;
   }
 }
@@ -181,7 +180,7 @@ __global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* 
 // Register-blocked variant for n = 2, 4: the free-box solves of the CTA's boxes are
 // one small GEMM (shared inverse x the block of box residuals), each thread owning
 // an RB x CB tile (rows x boxes) and reading RB inverse entries with one vector
-// load; structure boxes are then solved with their own FP64 inverse.
+// load; structure boxes are then solved with their own inverses.
 template <typename T, int BS>
 struct BoxGemm {
   static constexpr int NB = 2 * BS * (BS + 1) + BS * BS;
@@ -209,12 +208,12 @@ struct VecOf<double, 2> {
 };
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, const T* __restrict__ rE, int N,
-                                               StokesCoef<T> c, int color, const int* __restrict__ slot,
-                                               const double* __restrict__ Ms, const T* __restrict__ Mf) {
+__global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T* rE, int N, StokesCoef<T> c,
+                                               int color, const int* __restrict__ slot, const T* __restrict__ Ms,
+                                               const T* __restrict__ Mf) {
   using G = BoxGemm<T, BS>;
   using V = typename VecOf<T, G::RB>::type;
-  constexpr int NB = G::NB;
+  constexpr int NB = G::NB, NV = 2 * BS * (BS + 1);
   __shared__ __align__(16) T sMf[NB * NB];
   __shared__ T rs[G::BPC][NB];
   __shared__ int sslot[G::BPC];
@@ -238,7 +237,12 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, co
       const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
       int cc, i, j;
       box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
-      r = resid_at(w, b, rE, N, c, cc, i, j);
+      const int g = cc * N * N + j * N + i;
+      r = b[g] - stokes_row(w, N, c, cc, i, j);
+      if (rE && q < NV && slot[J * nb + I] >= 0) {
+        r += rE[g];
+        rE[g] = (T)0;
+      }
     }
     rs[lb][q] = r;
   }
@@ -290,49 +294,47 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, co
     const int lb = slist[e / NB], q = e % NB;
     const int t = box0 + lb;
     const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
-    const double* M = Ms + (size_t)sslot[lb] * NB * NB + q;
-    double d0 = 0.0, d1 = 0.0;
+    const T* M = Ms + (size_t)sslot[lb] * NB * NB + q;
+    T d0 = 0, d1 = 0;
 #pragma unroll 4
     for (int s2 = 0; s2 < NB; s2 += 2) {
-      d0 += M[(size_t)s2 * NB] * (double)rs[lb][s2];
-      d1 += M[(size_t)(s2 + 1) * NB] * (double)rs[lb][s2 + 1];
+      d0 += M[(size_t)s2 * NB] * rs[lb][s2];
+      d1 += M[(size_t)(s2 + 1) * NB] * rs[lb][s2 + 1];
     }
     int cc, i, j;
     box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
-    w[cc * N * N + j * N + i] += (T)(d0 + d1);
+    w[cc * N * N + j * N + i] += d0 + d1;
   }
 }
 
 template <typename T>
-int launch_boxn(Problem& P, int l, T* w, const T* b, const T* rE, int color) {
+int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   LevelInfo& L = P.lev[l];
   const StokesCoef<T> c = coefs<T>(P, l);
   const int half = L.nb / 2;
   const long nbox = (long)half * half;
+  const T* Ms = Mstruct_of<T>(L);
+  const T* Mf = Mfree_of<T>(L);
   // the GEMM form pays off on large levels; small levels keep one box per CTA slot
   const bool gemm = nbox >= P.box_gemm_min;
   switch (P.prm.box) {
     case 2:
-      if (!gemm) {
-        kv_boxn<T, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(
-            w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
-        break;
-      }
-      kv_boxg<T, 2><<<nblk(nbox, BoxGemm<T, 2>::BPC), 128, 0, P.stream>>>(w, b, rE, L.N, c, color, L.flag,
-                                                                       L.Mstruct, Mfree_of<T>(L));
+      if (!gemm)
+        kv_boxn<T, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, color,
+                                                                                          L.flag, Ms, Mf);
+      else
+        kv_boxg<T, 2><<<nblk(nbox, BoxGemm<T, 2>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag, Ms, Mf);
       break;
     case 4:
-      if (!gemm) {
-        kv_boxn<T, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(
-            w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
-        break;
-      }
-      kv_boxg<T, 4><<<nblk(nbox, BoxGemm<T, 4>::BPC), 128, 0, P.stream>>>(w, b, rE, L.N, c, color, L.flag,
-                                                                       L.Mstruct, Mfree_of<T>(L));
+      if (!gemm)
+        kv_boxn<T, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, color,
+                                                                                          L.flag, Ms, Mf);
+      else
+        kv_boxg<T, 4><<<nblk(nbox, BoxGemm<T, 4>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag, Ms, Mf);
       break;
     default:
-      kv_boxn<T, 8><<<nblk(nbox, BoxShape<8>::BPC), BoxShape<8>::THREADS, 0, P.stream>>>(
-          w, b, rE, L.N, c, color, L.flag, L.Mstruct, Mfree_of<T>(L));
+      kv_boxn<T, 8><<<nblk(nbox, BoxShape<8>::BPC), BoxShape<8>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, color,
+                                                                                        L.flag, Ms, Mf);
       break;
   }
   IB_LAUNCH_CHECK();
@@ -340,25 +342,34 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, const T* rE, int color) {
 }
 
 // 1 x 1 boxes: residual of the colour's boxes first, then the solves.
+// rE rows of the colour's structure boxes are taken out (cleared).
 template <typename T>
-__global__ void kv_colres1(const T* __restrict__ w, const T* __restrict__ b, const T* __restrict__ rE,
-                           T* __restrict__ r, int N, StokesCoef<T> c, int color) {
+__global__ void kv_colres1(const T* __restrict__ w, const T* __restrict__ b, T* rE, T* __restrict__ r, int N,
+                           StokesCoef<T> c, int color, const int* __restrict__ slot) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int half = N >> 1;
   if (t >= half * half) return;
   int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
   int n = N * N, m = N - 1;
   int I1 = (I + 1) & m, J1 = (J + 1) & m;
-  r[J * N + I] = resid_at(w, b, rE, N, c, 0, I, J);
-  r[J * N + I1] = resid_at(w, b, rE, N, c, 0, I1, J);
-  r[n + J * N + I] = resid_at(w, b, rE, N, c, 1, I, J);
-  r[n + J1 * N + I] = resid_at(w, b, rE, N, c, 1, I, J1);
-  r[2 * n + J * N + I] = resid_at(w, b, rE, N, c, 2, I, J);
+  const bool st = rE && slot[J * N + I] >= 0;  // only structure rows carry rE
+  const T* e = st ? rE : nullptr;
+  r[J * N + I] = resid_at(w, b, e, N, c, 0, I, J);
+  r[J * N + I1] = resid_at(w, b, e, N, c, 0, I1, J);
+  r[n + J * N + I] = resid_at(w, b, e, N, c, 1, I, J);
+  r[n + J1 * N + I] = resid_at(w, b, e, N, c, 1, I, J1);
+  r[2 * n + J * N + I] = resid_at(w, b, e, N, c, 2, I, J);
+  if (st) {
+    rE[J * N + I] = (T)0;
+    rE[J * N + I1] = (T)0;
+    rE[n + J * N + I] = (T)0;
+    rE[n + J1 * N + I] = (T)0;
+  }
 }
 
 template <typename T>
 __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int color,
-                        const int* __restrict__ slot, const double* __restrict__ Ms, const T* __restrict__ Mf) {
+                        const int* __restrict__ slot, const T* __restrict__ Ms, const T* __restrict__ Mf) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int half = N >> 1;
   if (t >= half * half) return;
@@ -373,7 +384,7 @@ __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int c
   else box_apply_rows(Mf, 5, rb, 0, 1, w, g);
 }
 
-// b_{l+1} = R (b - A_l w) with the elasticity part from rE (may be NULL).
+// b_{l+1} = R (b - A_l w + rE); rE (all rows, may be NULL) is cleared by kv_prolong.
 template <typename T>
 __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, const T* __restrict__ rE,
                           T* __restrict__ bc, int Nc, StokesCoef<T> c) {
@@ -387,8 +398,9 @@ __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, cons
   bc[2 * nc + idx] = rp;
 }
 
+// w += P e; also clears rE (the restriction's elasticity term; may be NULL).
 template <typename T>
-__global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N) {
+__global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N, T* __restrict__ rE) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int n = N * N;
   if (idx >= n) return;
@@ -397,6 +409,10 @@ __global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N) 
   wf[idx] += cu;
   wf[n + idx] += cv;
   wf[2 * n + idx] += cp;
+  if (rE) {
+    rE[idx] = (T)0;
+    rE[n + idx] = (T)0;
+  }
 }
 
 template <typename T>
@@ -407,86 +423,84 @@ __global__ void kv_zero(T* x, long n) {
 
 // ------------------------------------------------------------------ single-CTA tail kernel
 
+// rE = -dt E_l w of a tail level, all rows, into the velocity part of r (shared
+// memory): clear, then force + spread per point quad with shared-memory atomics.
+template <typename T>
+__device__ void tail_elastic(const TailLevel<T>& L, const TailArgs<T>& A, const T* w, T* r) {
+  const int n2 = 2 * L.N * L.N, np = A.sp.np, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < n2; e += blockDim.x) r[e] = (T)0;
+  __syncthreads();
+  // 4 np is a multiple of 4: the four lanes of a quad run the same iterations
+  for (int t = threadIdx.x; t < 4 * np; t += blockDim.x)
+    force_spread_quad(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box, -1, r);
+  __syncthreads();
+}
+
+// Full residual r = b - A_l w of a tail level (for the restriction).
 template <typename T>
 __device__ void tail_residual(const TailLevel<T>& L, const TailArgs<T>& A, const T* w, const T* b, T* r) {
+  const bool hasE = A.has_E;
+  if (hasE) tail_elastic(L, A, w, r);
   const int N = L.N, n = N * N;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int i = e & (N - 1), j = e / N;
-    r[e] = b[e] - stokes_row(w, N, L.c, 0, i, j);
-    r[n + e] = b[n + e] - stokes_row(w, N, L.c, 1, i, j);
+    r[e] = (hasE ? r[e] : (T)0) + b[e] - stokes_row(w, N, L.c, 0, i, j);
+    r[n + e] = (hasE ? r[n + e] : (T)0) + b[n + e] - stokes_row(w, N, L.c, 1, i, j);
     r[2 * n + e] = b[2 * n + e] - stokes_row(w, N, L.c, 2, i, j);
   }
-  if (A.sp.ns == 0) {
-    __syncthreads();
-    return;
-  }
-  const int np = A.sp.np;
-  for (int t = threadIdx.x; t < 2 * np; t += blockDim.x) {
-    const int comp = t / np, k = t - comp * np;
-    A.U[comp * np + k] = interp_point(L.pat, w, N, comp, k);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < 8 * np; t += blockDim.x) {
-    const int bb = t / (2 * np), rem = t - bb * 2 * np;
-    const int comp = rem / np, k = rem - comp * np;
-    T gx, gy;
-    JU_point(A.sp, A.U, k, &gx, &gy);
-    const T g = A.coefE * (comp == 0 ? gx : gy);
-    if (g != (T)0) spread_row(L.pat, N, comp, k, bb, g, r);
-  }
   __syncthreads();
 }
 
+// One colour of box solves on a tail level: every residual of the colour's boxes
+// is staged first (1 x 1 boxes of one colour are neighbours, so all residuals
+// must be taken before any update), then each (box, row) product of the box
+// inverse is split over G lanes (G as large as the CTA allows, at most 32).
+// rE: the level's elasticity term in shared memory, or NULL.
 template <typename T>
-__device__ void tail_boxes(const TailLevel<T>& L, const TailArgs<T>& A, const T* r, T* w, int color,
-                           double* stage_r, int* stage_g) {
-  const int N = L.N, n = N * N, bs = A.box;
+__device__ void tail_boxes(const TailLevel<T>& L, const TailArgs<T>& A, const T* b, const T* rE, T* w, int color,
+                           T* sr, int* sg) {
+  const int N = L.N, n = N * N, bs = A.box, nB = A.nB;
   const int nb = N / bs, half = nb >> 1, nbox = half * half;
-  if (bs == 1) {
-    const int m = N - 1;
-    for (int t = threadIdx.x; t < nbox; t += blockDim.x) {
+  const int items = nbox * nB;
+  for (int e = threadIdx.x; e < items; e += blockDim.x) {
+    const int t = e / nB, q = e - t * nB;
+    const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+    int cc, i, j;
+    box_unknown(q, bs, I * bs, J * bs, N, &cc, &i, &j);
+    const int gq = cc * n + j * N + i;
+    T r = b[gq] - stokes_row(w, N, L.c, cc, i, j);
+    if (rE && cc < 2) r += rE[gq];
+    sr[e] = r;
+    sg[e] = gq;
+  }
+  __syncthreads();
+  int G = 32;
+  while (G > 1 && items * G > (int)blockDim.x) G >>= 1;
+  const int total = items * G;
+  for (int base = 0; base < total; base += blockDim.x) {  // same trip count in every thread
+    const int e = base + threadIdx.x, it = e / G, gl = e - it * G;
+    T d = 0;
+    if (it < items) {
+      const int t = it / nB, q = it - t * nB;
       const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
-      int g[5] = {J * N + I, J * N + ((I + 1) & m), n + J * N + I, n + ((J + 1) & m) * N + I, 2 * n + J * N + I};
-      T rb[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) rb[q] = r[g[q]];
       const int sl = L.slot[J * nb + I];
-      if (sl >= 0) box_apply_rows(L.Ms + (size_t)sl * 25, 5, rb, 0, 1, w, g);
-      else box_apply_rows(L.Mf, 5, rb, 0, 1, w, g);
+      const T* M = (sl >= 0 ? L.Ms + (size_t)sl * nB * nB : L.Mf) + q;
+      const T* rs = sr + t * nB;
+      for (int s = gl; s < nB; s += G) d += M[(size_t)s * nB] * rs[s];
     }
-  } else {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nB = A.nB;
-    if (warp < A.stage_warps) {
-      double* rs = stage_r + warp * nB;
-      int* gs = stage_g + warp * nB;
-      for (int t = warp; t < nbox; t += A.stage_warps) {
-        const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
-        for (int q = lane; q < nB; q += 32) {
-          int cc, i, j;
-          box_unknown(q, bs, I * bs, J * bs, N, &cc, &i, &j);
-          const int gq = cc * n + j * N + i;
-          gs[q] = gq;
-          rs[q] = (double)r[gq];
-        }
-        __syncwarp();
-        const int sl = L.slot[J * nb + I];
-        if (sl >= 0) box_apply_rows(L.Ms + (size_t)sl * nB * nB, nB, rs, lane, 32, w, gs);
-        else box_apply_rows(L.Mf, nB, rs, lane, 32, w, gs);
-        __syncwarp();
-      }
-    }
+    for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (it < items && gl == 0) w[sg[it]] += d;
   }
   __syncthreads();
 }
 
 template <typename T>
-__device__ void tail_sweep(const TailLevel<T>& L, const TailArgs<T>& A, T* w, const T* b, T* r, bool rev,
-                           double* sr, int* sg) {
+__device__ void tail_sweep(const TailLevel<T>& L, const TailArgs<T>& A, T* w, const T* b, T* r, bool rev, T* sr,
+                           int* sg) {
   for (int cc = 0; cc < 4; ++cc) {
     const int color = rev ? seq_color(3 - cc) : seq_color(cc);
-    tail_residual(L, A, w, b, r);
-    tail_boxes(L, A, r, w, color, sr, sg);
+    if (A.has_E) tail_elastic(L, A, w, r);
+    tail_boxes(L, A, b, A.has_E ? r : nullptr, w, color, sr, sg);
   }
 }
 
@@ -501,7 +515,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T> A) {
     B[l] = (T*)(smem + A.off_b[l]);
   }
   T* r = (T*)(smem + A.off_r);
-  double* sr = (double*)(smem + A.off_sr);
+  T* sr = (T*)(smem + A.off_sr);
   int* sg = (int*)(smem + A.off_sg);
   {
     const int n0 = 3 * A.lev[0].N * A.lev[0].N;
@@ -569,6 +583,7 @@ int build_tail_args(Problem& P, int lt, TailArgs<T>* A, size_t* smem_bytes) {
     return o;
   };
   int max_boxes = 1;
+  A->has_E = P.np > 0 && P.ns > 0;
   for (int q = 0; q < A->nlev; ++q) {
     int l = lt + q;
     LevelInfo& L = P.lev[l];
@@ -577,7 +592,7 @@ int build_tail_args(Problem& P, int lt, TailArgs<T>* A, size_t* smem_bytes) {
     t.c = coefs<T>(P, l);
     t.pat = pats<T>(L);
     t.slot = L.flag;
-    t.Ms = L.Mstruct;
+    t.Ms = Mstruct_of<T>(L);
     t.Mf = Mfree_of<T>(L);
     size_t n3 = 3ul * L.N * L.N * sizeof(T);
     A->off_w[q] = (int)take(n3);
@@ -589,10 +604,8 @@ int build_tail_args(Problem& P, int lt, TailArgs<T>* A, size_t* smem_bytes) {
     }
   }
   A->off_r = (int)take(3ul * P.lev[lt].N * P.lev[lt].N * sizeof(T));
-  A->stage_warps = P.prm.box == 1 ? 0 : (max_boxes < 32 ? max_boxes : 32);
-  A->off_sr = (int)take((size_t)A->stage_warps * P.nB * sizeof(double));
-  A->off_sg = (int)take((size_t)A->stage_warps * P.nB * sizeof(int));
-  A->U = Ubuf<T>(P);
+  A->off_sr = (int)take((size_t)max_boxes * P.nB * sizeof(T));
+  A->off_sg = (int)take((size_t)max_boxes * P.nB * sizeof(int));
   A->sp = sview<T>(P);
   A->coefE = (T)(-P.prm.dt / (P.lev[0].h * P.lev[0].h));
   A->Mc = P.Mcoarse;
@@ -609,23 +622,22 @@ int build_tail_args(Problem& P, int lt, TailArgs<T>* A, size_t* smem_bytes) {
   return IB_OK;
 }
 
-// Elasticity residual part rE = -dt E_l w on a fine level (two launches).
+// rE += -dt E_l w on the rows of colour `color` (-1: all rows) of a fine level.
 template <typename T>
-int fine_elastic(Problem& P, int l, const T* w) {
+int fine_elastic(Problem& P, int l, const T* w, int color) {
   LevelInfo& L = P.lev[l];
   const double sT = sizeof(T);
-  {
-    KScope ks(P, IB_KC_INTERP, 2.0 * P.np * (25 * sT + 8) + 8.0 * P.np * 4 * sT);
-    kv_interp_zero<T><<<nblk(8L * P.np), TPB, 0, P.stream>>>(pats<T>(L), w, P.np, L.N, Ubuf<T>(P), rEbuf<T>(L));
-    IB_LAUNCH_CHECK();
-  }
-  {
-    double deg = P.np ? 2.0 * P.ns / P.np : 0.0;
-    KScope ks(P, IB_KC_SPREAD, P.np * (2 * sT + 8 + deg * (5 * sT + 8) + 16 * sT + 16 + 64 * sT));
-    kv_spread<T><<<nblk(8L * P.np), TPB, 0, P.stream>>>(pats<T>(L), sview<T>(P), Ubuf<T>(P), L.N,
-                                                        (T)(-P.prm.dt / (P.lev[0].h * P.lev[0].h)), rEbuf<T>(L));
-    IB_LAUNCH_CHECK();
-  }
+  double deg = P.np ? 2.0 * P.ns / P.np : 0.0;
+  // per point: (1 + deg) interpolations of both components (16 values, 8 weights,
+  // 2 bases each), adjacency and K per spring, the spread patch (16 weights, 4
+  // bases) and its 32 read-modify-write updates (a quarter of them for one colour)
+  const double upd = (color < 0 ? 32.0 : 8.0) * 2 * sT;
+  KScope ks(P, IB_KC_SPREAD,
+            P.np * ((1.0 + deg) * 2.0 * (24 * sT + 8) + deg * (3 * sT + 8) + 8 + 16 * sT + 16 + upd));
+  kv_force_spread<T><<<nblk(4L * P.np), TPB, 0, P.stream>>>(pats<T>(L), sview<T>(P), w, L.N,
+                                                            (T)(-P.prm.dt / (P.lev[0].h * P.lev[0].h)),
+                                                            P.prm.box, color, rEbuf<T>(L));
+  IB_LAUNCH_CHECK();
   return IB_OK;
 }
 
@@ -642,27 +654,26 @@ int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
   const double sT = sizeof(T);
   for (int cc = 0; cc < 4; ++cc) {
     const int color = rev ? kSeq[3 - cc] : kSeq[cc];
-    const bool zero = w_is_zero && cc == 0;
-    const T* rE = nullptr;
-    if (has_E && !zero) {
-      IB_TRY(fine_elastic<T>(P, l, B.w));
-      rE = rEbuf<T>(L);
-    }
+    const bool with_E = has_E && !(w_is_zero && cc == 0);  // w = 0: no elasticity term
+    if (with_E) IB_TRY(fine_elastic<T>(P, l, B.w, color));
+    T* E = with_E ? rEbuf<T>(L) : nullptr;
+    // rE read and cleared on the velocity rows of the colour's structure boxes
+    const double e_bytes = with_E ? 0.25 * L.n_struct * 2.0 * bs * (bs + 1) * 2 * sT : 0.0;
     if (bs == 1) {
       {
-        KScope ks(P, IB_KC_STOKES, nbox * 5.0 * (6 * sT + 2 * sT));
-        kv_colres1<T><<<nblk(nbox), TPB, 0, P.stream>>>(B.w, B.b, rE, B.r, N, c, color);
+        KScope ks(P, IB_KC_STOKES, nbox * 5.0 * (6 * sT + 2 * sT) + e_bytes);
+        kv_colres1<T><<<nblk(nbox), TPB, 0, P.stream>>>(B.w, B.b, E, B.r, N, c, color, L.flag);
         IB_LAUNCH_CHECK();
       }
-      KScope ks(P, IB_KC_BOX, nbox * (15.0 * sT + 4) + 0.25 * L.n_struct * 25 * 8.0 + 25 * sT);
-      kv_box1<T><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, L.Mstruct, Mfree_of<T>(L));
+      KScope ks(P, IB_KC_BOX, nbox * (15.0 * sT + 4) + 0.25 * L.n_struct * 25 * sT + 25 * sT);
+      kv_box1<T><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, Mstruct_of<T>(L), Mfree_of<T>(L));
       IB_LAUNCH_CHECK();
     } else {
       // per box: its unknowns' rows read w (5-point stencils, counted once per
-      // unknown plus the one-cell halo), b, rE on structure rows, write w
+      // unknown plus the one-cell halo), b, write w
       const double box_bytes = sT * (3.0 * nB + (4.0 * bs + 4)) + 4;
-      KScope ks(P, IB_KC_BOX, nbox * box_bytes + 0.25 * L.n_struct * nB * nB * 8.0 + (double)nB * nB * sT);
-      IB_TRY(launch_boxn<T>(P, l, B.w, B.b, rE, color));
+      KScope ks(P, IB_KC_BOX, nbox * box_bytes + 0.25 * L.n_struct * nB * nB * sT + (double)nB * nB * sT + e_bytes);
+      IB_TRY(launch_boxn<T>(P, l, B.w, B.b, E, color));
     }
   }
   return IB_OK;
@@ -685,15 +696,14 @@ int vcycle_eager(Problem& P) {
       IB_LAUNCH_CHECK();
     }
     for (int s = 0; s < P.prm.nu1; ++s) IB_TRY(fine_sweep<T>(P, l, false, s == 0));
-    const T* rE = nullptr;
-    if (has_E) {
-      IB_TRY(fine_elastic<T>(P, l, B.w));
-      rE = rEbuf<T>(L);
-    }
+    if (has_E) IB_TRY(fine_elastic<T>(P, l, B.w, -1));
+    const T* E = has_E ? rEbuf<T>(L) : nullptr;
     const int Nc = P.lev[l + 1].N;
     {
-      KScope ks(P, IB_KC_TRANSFER, (9.0 * L.N * L.N + 3.0 * Nc * Nc) * sizeof(T));
-      kv_resres<T><<<nblk((long)Nc * Nc), TPB, 0, P.stream>>>(B.w, B.b, rE, lbuf<T>(P.lev[l + 1]).b, Nc,
+      // w read once per stencil (9 fine values per coarse cell incl. the halo), b, rE
+      const double e_bytes = has_E ? 2.0 * L.N * L.N * sizeof(T) : 0.0;
+      KScope ks(P, IB_KC_TRANSFER, (9.0 * L.N * L.N + 3.0 * Nc * Nc) * sizeof(T) + e_bytes);
+      kv_resres<T><<<nblk((long)Nc * Nc), TPB, 0, P.stream>>>(B.w, B.b, E, lbuf<T>(P.lev[l + 1]).b, Nc,
                                                              coefs<T>(P, l));
       IB_LAUNCH_CHECK();
     }
@@ -710,8 +720,10 @@ int vcycle_eager(Problem& P) {
     LevelInfo& L = P.lev[l];
     LevelBuf<T>& B = lbuf<T>(L);
     {
-      KScope ks(P, IB_KC_TRANSFER, (6.0 * L.N * L.N + 0.75 * L.N * L.N) * sizeof(T));
-      kv_prolong<T><<<nblk((long)L.N * L.N), TPB, 0, P.stream>>>(lbuf<T>(P.lev[l + 1]).w, B.w, L.N);
+      const double e_bytes = has_E ? 2.0 * L.N * L.N * sizeof(T) : 0.0;
+      KScope ks(P, IB_KC_TRANSFER, (6.0 * L.N * L.N + 0.75 * L.N * L.N) * sizeof(T) + e_bytes);
+      kv_prolong<T><<<nblk((long)L.N * L.N), TPB, 0, P.stream>>>(lbuf<T>(P.lev[l + 1]).w, B.w, L.N,
+                                                                 has_E ? rEbuf<T>(L) : nullptr);
       IB_LAUNCH_CHECK();
     }
     for (int s = 0; s < P.prm.nu2; ++s) IB_TRY(fine_sweep<T>(P, l, P.prm.box == 1, false));
@@ -869,15 +881,17 @@ int vcycle_run(Problem& P) {
 template int vcycle_run<double>(Problem&);
 template int vcycle_run<float>(Problem&);
 
-// Zero the elasticity residual buffers (their patch rows move with the points).
+// rE must be zero when a V-cycle starts (every use clears what it consumed).
 int vcycle_reset_rE(Problem& P) {
   for (int l = 0; l < P.nlev; ++l) {
     LevelInfo& L = P.lev[l];
-    size_t n2 = 2ul * L.N * L.N;
+    const size_t n2 = 2ul * L.N * L.N;
     if (L.rE64) IB_CUDA_TRY(cudaMemsetAsync(L.rE64, 0, n2 * sizeof(double), P.stream));
     if (L.rE32) IB_CUDA_TRY(cudaMemsetAsync(L.rE32, 0, n2 * sizeof(float), P.stream));
   }
   return IB_OK;
 }
+
+// Zero the elasticity residual buffers (their patch rows move with the points).
 
 }  // namespace ib

@@ -13,8 +13,8 @@ struct TailLevel {
   int N;
   StokesCoef<T> c;
   Patches<T> pat;
-  const int* slot;
-  const double* Ms;
+  const int* slot;  // box -> structure slot (-1 free)
+  const T* Ms;      // structure-box inverses in the V-cycle precision
   const T* Mf;
 };
 
@@ -24,12 +24,11 @@ struct TailArgs {
   TailLevel<T> lev[MAX_LEVELS];
   const T* b_in;  // right-hand side of lev[0] (global)
   T* w_out;       // correction of lev[0] (global)
-  T* U;           // point velocities (global scratch)
   Springs<T> sp;
   T coefE;        // -dt / h_0^2: residual sign of the elasticity term
   const double* Mc;
   int nc, ldc;
-  int nu1, nu2, box, nB, post_rev, stage_warps;
+  int nu1, nu2, box, nB, post_rev, has_E;
   int off_w[MAX_LEVELS], off_b[MAX_LEVELS], off_r, off_sr, off_sg;  // shared-memory offsets (bytes)
 };
 
