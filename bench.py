@@ -12,7 +12,7 @@ events, L2 flushed between timed steps.  The line also carries the same sweep
 solved case by case in FP64 and in FP32 ("forms").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|fp64] [--box B]
+                  [--precision fp32|fp64|mixed] [--box B]
 
 Under torchrun each rank solves the whole sweep on its own GPU (independent
 replicas, no collective on the data path); rank 0 prints one JSON line.
@@ -39,6 +39,9 @@ import ib_workloads as W  # noqa: E402
 METRIC = "implicit IB step time to 1e-8 residual; V-cycle DOF/s; mixed/learned vs FP64"
 UNIT = "ms per implicit IB step"
 CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
+# arithmetic of the V-cycle per precision mode (FGMRES and the operator are FP64 in all)
+DTYPE = {"fp32": "f32 V-cycle + f64 Krylov", "fp64": "f64",
+         "mixed": "f64 V-cycle vectors, f32 box solves + f64 Krylov"}
 N_GRID = 256
 N_POINTS = 512
 
@@ -253,7 +256,7 @@ def run_ours(args):
 
     forms = {}
     seq_stats = {}
-    for prec in (["fp64", "fp32"] if args.forms else [args.precision]):
+    for prec in (["fp64", "mixed", "fp32"] if args.forms else [args.precision]):
         solvers = make_seq(prec)
         forms.setdefault("tail_grid", {})[prec] = [s.tail_grid(prec) for s in solvers]
         st = [None] * nc
@@ -376,7 +379,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": per_ib_ms, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 V-cycle + f64 Krylov" if args.precision == "fp32" else "f64",
+                "dtype": DTYPE[args.precision],
                 "data": "synthetic", "config": config_dict(args),
                 "e2e": {"value": e2e_per, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -426,7 +429,7 @@ def run_vcycle(args):
                       args.steps)
     per = sum(ms) / len(ms)
     # ib_vcycle converts the FP64 input and output around the cycle: time that part separately
-    bpd = 56.0 if args.precision == "fp32" else 112.0
+    bpd = 56.0 if args.precision == "fp32" else 112.0  # vectors in FP64 for fp64 and mixed
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -436,7 +439,7 @@ def run_vcycle(args):
     achieved = bpd * n / (per * 1e-3) / 1e9
     line = {"metric": "V-cycle DOF/s", "value": n / (per * 1e-3), "unit": "DOF/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per, "higher_is_better": True,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "V(1,1) on %d^2, ellipse of %d points, kappa=1e4, dt=1e-3" % (N, 2 * N),
                        "box": args.box, "precision": args.precision, "tail_grid": s.tail_grid(args.precision),
                        "note": "ib_vcycle includes the FP64<->FP32 conversion of b and w"},
@@ -574,7 +577,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--box", type=int, default=4)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--grid", type=int, default=2048, help="grid size of the vcycle workload")

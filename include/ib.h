@@ -64,7 +64,15 @@ typedef enum {
 } ib_status;
 
 enum { IB_DELTA_PESKIN4 = 0, IB_DELTA_COS4 = 1 };
-enum { IB_FP64 = 0, IB_FP32_PRECOND = 1 };
+/* Precision of the V-cycle (FGMRES, the operator and the true residual are FP64
+ * in every mode; not in the paper):
+ *   IB_FP64            everything FP64.
+ *   IB_FP32_PRECOND    V-cycle in FP32 (vectors, stencils, elasticity, box inverses).
+ *   IB_MIXED_PRECOND   V-cycle in FP64 except the structure-free boxes, whose shared
+ *                      inverse is applied in FP32 (the FP64 pipe is the GB300's
+ *                      slowest unit and those box products are most of the
+ *                      V-cycle's FLOPs; stiff structure boxes need FP64). */
+enum { IB_FP64 = 0, IB_FP32_PRECOND = 1, IB_MIXED_PRECOND = 2 };
 enum { IB_JAC_CLAMPED = 0, IB_JAC_EXACT = 1 };
 
 /* Problem parameters (sec. 2: grid, fluid, time step; secs. 5-6: smoother). */
@@ -77,12 +85,12 @@ typedef struct {
   int32_t delta;      /* IB_DELTA_PESKIN4 or IB_DELTA_COS4 (sec. 2.2) */
   int32_t box;        /* box size b in {1, 2, 4, 8} (sec. 6) */
   int32_t nu1, nu2;   /* pre/post smoothing sweeps, 0..8 (Algorithm 1) */
-  int32_t precision;  /* IB_FP64 or IB_FP32_PRECOND (V-cycle in FP32, Krylov in FP64) */
+  int32_t precision;  /* IB_FP64, IB_FP32_PRECOND or IB_MIXED_PRECOND (see above) */
   int32_t jacobian;   /* IB_JAC_CLAMPED (default) or IB_JAC_EXACT spring Jacobian */
   double tol;         /* relative residual target ||b - A x|| / ||b|| (> 0) */
   int32_t max_iters;  /* FGMRES iteration cap, 1..512 (the paper stops at 100) */
-  int32_t escalate;   /* IB_FP32_PRECOND only: 1 = switch the preconditioner to the FP64
-                         V-cycle when FGMRES stagnates (default), 0 = never */
+  int32_t escalate;   /* IB_FP32_PRECOND only: 1 = switch the preconditioner to the
+                         mixed-precision V-cycle when FGMRES stagnates (default), 0 = never */
   int32_t restart;    /* FGMRES restart length m (Krylov vectors kept), 0 = max_iters;
                          workspace grows with m: (m + 1) FP64 + m preconditioner vectors */
 } ib_params;
@@ -135,8 +143,8 @@ IB_API int ib_apply(ib_problem* prob, int32_t level, const double* w, double* y)
 
 /* One V-cycle (Algorithm 1, nu1/nu2 sweeps, zero initial guess) on the fine
  * level: w = MGV(0, b).  device b, w: 3N^2 doubles (may not alias).  With
- * IB_FP32_PRECOND the cycle runs in FP32 (structure boxes in FP64) and b, w are
- * converted at entry and exit. */
+ * IB_FP32_PRECOND the cycle runs in FP32 and b, w are converted at entry and
+ * exit; with IB_MIXED_PRECOND the free-box solves apply an FP32 inverse. */
 IB_API int ib_vcycle(ib_problem* prob, const double* b, double* w);
 
 /* b = [-(rho/dt) u^n - S F(X); 0] for the current points (device, 3N^2
@@ -159,8 +167,8 @@ IB_API int ib_num_levels(const ib_problem* prob);
 IB_API int ib_level_size(const ib_problem* prob, int32_t level);
 
 /* Grid size of the finest level run by the single-CTA coarse-level kernel in the
- * V-cycle of the given precision (IB_FP64 or IB_FP32_PRECOND), 0 if that V-cycle
- * does not exist.  The split is timed at set-up unless the environment variable
+ * V-cycle of the given precision (IB_FP32_PRECOND for the FP32 V-cycle, IB_FP64 or
+ * IB_MIXED_PRECOND for the one on FP64 vectors), 0 if that V-cycle does not exist.  The split is timed at set-up unless the environment variable
  * IB_TAIL_NMAX (the largest grid size for that kernel) pins it. */
 IB_API int ib_tail_grid(const ib_problem* prob, int32_t precision);
 

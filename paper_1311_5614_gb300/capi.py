@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "IB_OK", 1: "IB_ERR_INVALID_ARG", 2: "IB_ERR_CUDA", 3: "IB_ER
                 7: "IB_ERR_TIMEOUT"}
 
 DELTA = {"peskin4": 0, "cos4": 1}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 JACOBIAN = {"clamped": 0, "exact": 1}
 
 

@@ -89,7 +89,7 @@ int validate(const ib_params* p) {
   if (!(std::isfinite(p->rho) && p->rho >= 0)) return fail(IB_ERR_INVALID_ARG, "rho must be >= 0");
   if (p->delta != IB_DELTA_PESKIN4 && p->delta != IB_DELTA_COS4)
     return fail(IB_ERR_INVALID_ARG, "unknown delta kernel");
-  if (p->precision != IB_FP64 && p->precision != IB_FP32_PRECOND)
+  if (p->precision != IB_FP64 && p->precision != IB_FP32_PRECOND && p->precision != IB_MIXED_PRECOND)
     return fail(IB_ERR_INVALID_ARG, "unknown precision");
   if (p->jacobian != IB_JAC_CLAMPED && p->jacobian != IB_JAC_EXACT)
     return fail(IB_ERR_INVALID_ARG, "unknown jacobian variant");
@@ -227,7 +227,7 @@ int allocate(Problem& P) {
       IB_TRY(dalloc(&L.flag, (size_t)L.nb * L.nb));
       IB_TRY(dalloc(&L.Sfree, (size_t)P.nB * P.nB));
       IB_TRY(dalloc(&L.Mfree, (size_t)P.nB * P.nB));
-      if (fp32) IB_TRY(dalloc(&L.Mfree32, (size_t)P.nB * P.nB));
+      if (P.prm.precision != IB_FP64) IB_TRY(dalloc(&L.Mfree32, (size_t)P.nB * P.nB));
     }
     if (P.np > 0) {
       L.pat64.np = P.np;
@@ -451,7 +451,8 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
         IB_TRY((launch_cast<float, double>(P, zj, P.t64b, n)));
         IB_TRY(apply64(P, 0, P.t64b, P.t64));
       } else {
-        // escalated: the FP64 V-cycle preconditions and its directions are kept in
+        // escalated: the mixed-precision V-cycle (FP64 vectors and residuals, FP32
+        // box solves) preconditions and its directions are kept in
         // FP64 (flexible GMRES combines the two bases in the update of x)
         LevelBuf<double>& B0 = P.lev[0].v64;
         double* zj64 = P.Z64 + (size_t)j * n;
@@ -480,7 +481,8 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       if (est <= tol * bnorm) break;
       hist.push_back(est);
       // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
-      // the last 8 iterations -> precondition with the FP64 V-cycle from now on
+      // the last 8 iterations -> precondition with the mixed-precision V-cycle
+      // (FP64 residuals, which the stiff cancellation needs) from now on
       if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 8 &&
           est > 0.5 * hist[hist.size() - 9])
         st->escalated_at = total;
@@ -533,7 +535,7 @@ int solve_step_impl(Problem& P, const double* u_n, double* up, double* X, ib_sta
     IB_LAUNCH_CHECK();
   }
   IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
-  if (P.prm.precision == IB_FP64) rc = fgmres<double>(P, P.b64, P.x64, st);
+  if (P.prm.precision != IB_FP32_PRECOND) rc = fgmres<double>(P, P.b64, P.x64, st);
   else rc = fgmres<float>(P, P.b64, P.x64, st);
   IB_CUDA_TRY(cudaEventRecord(P.ev[2], P.stream));
   if (rc != IB_OK && rc != IB_ERR_NOT_CONVERGED) { st->status = rc; return rc; }
@@ -698,7 +700,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   if (st != IB_OK) return fail_free(st);
   if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
   P.has32 = params->precision == IB_FP32_PRECOND;
-  P.has64 = params->precision == IB_FP64 || params->escalate != 0;
+  P.has64 = params->precision != IB_FP32_PRECOND || params->escalate != 0;
   if (P.has32) {
     st = vcycle_prepare<float>(P);
     if (st != IB_OK) return fail_free(st);
@@ -731,9 +733,9 @@ int ib_level_size(const ib_problem* H, int32_t level) {
 }
 
 int ib_tail_grid(const ib_problem* H, int32_t precision) {
-  if (!H || (precision != IB_FP64 && precision != IB_FP32_PRECOND)) return 0;
+  if (!H || (precision != IB_FP64 && precision != IB_FP32_PRECOND && precision != IB_MIXED_PRECOND)) return 0;
   const Problem& P = H->P;
-  const int ix = precision == IB_FP64 ? 1 : 0;
+  const int ix = precision == IB_FP32_PRECOND ? 0 : 1;
   if ((ix == 1 && !P.has64) || (ix == 0 && !P.has32)) return 0;
   return P.lev[P.tail_level[ix]].N;
 }
@@ -760,7 +762,7 @@ int ib_vcycle(ib_problem* H, const double* b, double* w) {
   if (b == w) return fail(IB_ERR_INVALID_ARG, "b and w must not alias");
   Problem& P = H->P;
   size_t n = 3ul * P.prm.N * P.prm.N;
-  if (P.prm.precision == IB_FP64) {
+  if (P.prm.precision != IB_FP32_PRECOND) {
     LevelBuf<double>& B0 = P.lev[0].v64;
     IB_CUDA_TRY(cudaMemcpyAsync(B0.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
     IB_TRY(vcycle_run<double>(P));
@@ -832,7 +834,7 @@ int ib_learned_pair(ib_problem* H, const double* x, float* in4, float* target) {
   double* sc = P.scal + 8 + 2 * (P.max_m + 2) + 1;
   // b = A x into nn_r; z = MG(b) into nn_dz; r = b - A z into nn_r; e = x - z into nn_dz
   IB_TRY(apply64(P, 0, x, P.nn_r));
-  if (P.prm.precision == IB_FP64) {
+  if (P.prm.precision != IB_FP32_PRECOND) {
     LevelBuf<double>& B0 = P.lev[0].v64;
     IB_CUDA_TRY(cudaMemcpyAsync(B0.b, P.nn_r, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
     IB_TRY(vcycle_run<double>(P));

@@ -128,15 +128,18 @@ struct BoxShape {
   static constexpr bool SMEM_MF = BS <= 4;
 };
 
-template <typename T, int BS>
+// T: vectors, residuals and structure-box inverses; TM: the shared inverse of the
+// structure-free boxes and its products (TM = float with T = double is the
+// mixed-precision V-cycle).
+template <typename T, typename TM, int BS>
 __global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* __restrict__ b, T* rE, int N,
                                                                  StokesCoef<T> c, int color,
                                                                  const int* __restrict__ slot,
                                                                  const T* __restrict__ Ms,
-                                                                 const T* __restrict__ Mf) {
+                                                                 const TM* __restrict__ Mf) {
   using S = BoxShape<BS>;
   constexpr int NB = S::NB, NV = 2 * BS * (BS + 1);
-  __shared__ T sMf[S::SMEM_MF ? NB * NB : 1];
+  __shared__ TM sMf[S::SMEM_MF ? NB * NB : 1];
   __shared__ T rs[S::BPC][NB];
   const int tid = threadIdx.x;
   if (S::SMEM_MF)
@@ -169,11 +172,11 @@ __global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* 
     for (int s = 0; s < NB; ++s) d += M[(size_t)s * NB] * rs[lb][s];
     w[gq] += d;
   } else {
-    const T* M = S::SMEM_MF ? sMf + q : Mf + q;
-    T d = 0;
+    const TM* M = S::SMEM_MF ? sMf + q : Mf + q;
+    TM d = 0;
 #pragma unroll 8
-    for (int s = 0; s < NB; ++s) d += M[s * NB] * rs[lb][s];
-    w[gq] += d;
+    for (int s = 0; s < NB; ++s) d += M[s * NB] * (TM)rs[lb][s];
+    w[gq] += (T)d;
   }
 }
 
@@ -207,14 +210,14 @@ struct VecOf<double, 2> {
   using type = double2;
 };
 
-template <typename T, int BS>
+template <typename T, typename TM, int BS>
 __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T* rE, int N, StokesCoef<T> c,
                                                int color, const int* __restrict__ slot, const T* __restrict__ Ms,
-                                               const T* __restrict__ Mf) {
-  using G = BoxGemm<T, BS>;
-  using V = typename VecOf<T, G::RB>::type;
+                                               const TM* __restrict__ Mf) {
+  using G = BoxGemm<TM, BS>;
+  using V = typename VecOf<TM, G::RB>::type;
   constexpr int NB = G::NB, NV = 2 * BS * (BS + 1);
-  __shared__ __align__(16) T sMf[NB * NB];
+  __shared__ __align__(16) TM sMf[NB * NB];
   __shared__ T rs[G::BPC][NB];
   __shared__ int sslot[G::BPC];
   const int tid = threadIdx.x;
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
   // free boxes: delta[q][box] = sum_s Mf[s][q] r[box][s]
   const int rg = tid % G::RG, bg = tid / G::RG;
   if (bg < G::BG) {
-    T acc[G::RB][G::CB];
+    TM acc[G::RB][G::CB];
 #pragma unroll
     for (int a = 0; a < G::RB; ++a)
 #pragma unroll
@@ -258,10 +261,10 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
 #pragma unroll 4
     for (int s2 = 0; s2 < NB; ++s2) {
       const V m = *reinterpret_cast<const V*>(&sMf[s2 * NB + rg * G::RB]);
-      const T* mv = reinterpret_cast<const T*>(&m);
+      const TM* mv = reinterpret_cast<const TM*>(&m);
 #pragma unroll
       for (int k = 0; k < G::CB; ++k) {
-        const T rv = rs[bg * G::CB + k][s2];
+        const TM rv = (TM)rs[bg * G::CB + k][s2];
 #pragma unroll
         for (int a = 0; a < G::RB; ++a) acc[a][k] += mv[a] * rv;
       }
@@ -276,11 +279,11 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
       for (int a = 0; a < G::RB; ++a) {
         int cc, i, j;
         box_unknown(rg * G::RB + a, BS, I * BS, J * BS, N, &cc, &i, &j);
-        w[cc * N * N + j * N + i] += acc[a][k];
+        w[cc * N * N + j * N + i] += (T)acc[a][k];
       }
     }
   }
-  // structure boxes: their own FP64 inverse; all threads share the (box, row) pairs
+  // structure boxes: their own inverses; all threads share the (box, row) pairs
   __shared__ int slist[G::BPC];
   __shared__ int ns;
   if (tid == 0) {
@@ -307,34 +310,36 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
   }
 }
 
-template <typename T>
+template <typename T, typename TM>
 int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   LevelInfo& L = P.lev[l];
   const StokesCoef<T> c = coefs<T>(P, l);
   const int half = L.nb / 2;
   const long nbox = (long)half * half;
   const T* Ms = Mstruct_of<T>(L);
-  const T* Mf = Mfree_of<T>(L);
+  const TM* Mf = Mfree_of<TM>(L);
   // the GEMM form pays off on large levels; small levels keep one box per CTA slot
   const bool gemm = nbox >= P.box_gemm_min;
   switch (P.prm.box) {
     case 2:
       if (!gemm)
-        kv_boxn<T, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, color,
-                                                                                          L.flag, Ms, Mf);
+        kv_boxn<T, TM, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(
+            w, b, E, L.N, c, color, L.flag, Ms, Mf);
       else
-        kv_boxg<T, 2><<<nblk(nbox, BoxGemm<T, 2>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag, Ms, Mf);
+        kv_boxg<T, TM, 2><<<nblk(nbox, BoxGemm<TM, 2>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag,
+                                                                               Ms, Mf);
       break;
     case 4:
       if (!gemm)
-        kv_boxn<T, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, color,
-                                                                                          L.flag, Ms, Mf);
+        kv_boxn<T, TM, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(
+            w, b, E, L.N, c, color, L.flag, Ms, Mf);
       else
-        kv_boxg<T, 4><<<nblk(nbox, BoxGemm<T, 4>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag, Ms, Mf);
+        kv_boxg<T, TM, 4><<<nblk(nbox, BoxGemm<TM, 4>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag,
+                                                                               Ms, Mf);
       break;
     default:
-      kv_boxn<T, 8><<<nblk(nbox, BoxShape<8>::BPC), BoxShape<8>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, color,
-                                                                                        L.flag, Ms, Mf);
+      kv_boxn<T, TM, 8><<<nblk(nbox, BoxShape<8>::BPC), BoxShape<8>::THREADS, 0, P.stream>>>(
+          w, b, E, L.N, c, color, L.flag, Ms, Mf);
       break;
   }
   IB_LAUNCH_CHECK();
@@ -367,9 +372,9 @@ __global__ void kv_colres1(const T* __restrict__ w, const T* __restrict__ b, T* 
   }
 }
 
-template <typename T>
+template <typename T, typename TM>
 __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int color,
-                        const int* __restrict__ slot, const T* __restrict__ Ms, const T* __restrict__ Mf) {
+                        const int* __restrict__ slot, const T* __restrict__ Ms, const TM* __restrict__ Mf) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int half = N >> 1;
   if (t >= half * half) return;
@@ -425,8 +430,8 @@ __global__ void kv_zero(T* x, long n) {
 
 // rE = -dt E_l w of a tail level, all rows, into the velocity part of r (shared
 // memory): clear, then force + spread per point quad with shared-memory atomics.
-template <typename T>
-__device__ void tail_elastic(const TailLevel<T>& L, const TailArgs<T>& A, const T* w, T* r) {
+template <typename T, typename TM>
+__device__ void tail_elastic(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, T* r) {
   const int n2 = 2 * L.N * L.N, np = A.sp.np, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < n2; e += blockDim.x) r[e] = (T)0;
   __syncthreads();
@@ -437,8 +442,8 @@ __device__ void tail_elastic(const TailLevel<T>& L, const TailArgs<T>& A, const 
 }
 
 // Full residual r = b - A_l w of a tail level (for the restriction).
-template <typename T>
-__device__ void tail_residual(const TailLevel<T>& L, const TailArgs<T>& A, const T* w, const T* b, T* r) {
+template <typename T, typename TM>
+__device__ void tail_residual(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, const T* b, T* r) {
   const bool hasE = A.has_E;
   if (hasE) tail_elastic(L, A, w, r);
   const int N = L.N, n = N * N;
@@ -456,9 +461,9 @@ __device__ void tail_residual(const TailLevel<T>& L, const TailArgs<T>& A, const
 // must be taken before any update), then each (box, row) product of the box
 // inverse is split over G lanes (G as large as the CTA allows, at most 32).
 // rE: the level's elasticity term in shared memory, or NULL.
-template <typename T>
-__device__ void tail_boxes(const TailLevel<T>& L, const TailArgs<T>& A, const T* b, const T* rE, T* w, int color,
-                           T* sr, int* sg) {
+template <typename T, typename TM>
+__device__ void tail_boxes(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* b, const T* rE, T* w,
+                           int color, T* sr, int* sg) {
   const int N = L.N, n = N * N, bs = A.box, nB = A.nB;
   const int nb = N / bs, half = nb >> 1, nbox = half * half;
   const int items = nbox * nB;
@@ -484,9 +489,16 @@ __device__ void tail_boxes(const TailLevel<T>& L, const TailArgs<T>& A, const T*
       const int t = it / nB, q = it - t * nB;
       const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
       const int sl = L.slot[J * nb + I];
-      const T* M = (sl >= 0 ? L.Ms + (size_t)sl * nB * nB : L.Mf) + q;
       const T* rs = sr + t * nB;
-      for (int s = gl; s < nB; s += G) d += M[(size_t)s * nB] * rs[s];
+      if (sl >= 0) {
+        const T* M = L.Ms + (size_t)sl * nB * nB + q;
+        for (int s = gl; s < nB; s += G) d += M[(size_t)s * nB] * rs[s];
+      } else {
+        const TM* M = L.Mf + q;
+        TM dm = 0;
+        for (int s = gl; s < nB; s += G) dm += M[(size_t)s * nB] * (TM)rs[s];
+        d = (T)dm;
+      }
     }
     for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if (it < items && gl == 0) w[sg[it]] += d;
@@ -494,9 +506,9 @@ __device__ void tail_boxes(const TailLevel<T>& L, const TailArgs<T>& A, const T*
   __syncthreads();
 }
 
-template <typename T>
-__device__ void tail_sweep(const TailLevel<T>& L, const TailArgs<T>& A, T* w, const T* b, T* r, bool rev, T* sr,
-                           int* sg) {
+template <typename T, typename TM>
+__device__ void tail_sweep(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, T* w, const T* b, T* r, bool rev,
+                           T* sr, int* sg) {
   for (int cc = 0; cc < 4; ++cc) {
     const int color = rev ? seq_color(3 - cc) : seq_color(cc);
     if (A.has_E) tail_elastic(L, A, w, r);
@@ -504,8 +516,8 @@ __device__ void tail_sweep(const TailLevel<T>& L, const TailArgs<T>& A, T* w, co
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T> A) {
+template <typename T, typename TM>
+__global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T, TM> A) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* W[MAX_LEVELS];
   T* B[MAX_LEVELS];
@@ -523,7 +535,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T> A) {
   }
   __syncthreads();
   for (int l = 0; l < nl - 1; ++l) {
-    const TailLevel<T>& L = A.lev[l];
+    const TailLevel<T, TM>& L = A.lev[l];
     const int n3 = 3 * L.N * L.N;
     for (int e = threadIdx.x; e < n3; e += blockDim.x) W[l][e] = (T)0;
     __syncthreads();
@@ -551,7 +563,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T> A) {
     __syncthreads();
   }
   for (int l = nl - 2; l >= 0; --l) {
-    const TailLevel<T>& L = A.lev[l];
+    const TailLevel<T, TM>& L = A.lev[l];
     const int N = L.N, n = N * N;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
       T cu, cv, cp;
@@ -571,8 +583,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T> A) {
 
 // ------------------------------------------------------------------ host side
 
-template <typename T>
-int build_tail_args(Problem& P, int lt, TailArgs<T>* A, size_t* smem_bytes) {
+template <typename T, typename TM>
+int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes) {
   std::memset((void*)A, 0, sizeof(*A));
   A->nlev = P.nlev - lt;
   if (A->nlev > MAX_LEVELS) return fail(IB_ERR_INVALID_ARG, "too many tail levels");
@@ -587,13 +599,13 @@ int build_tail_args(Problem& P, int lt, TailArgs<T>* A, size_t* smem_bytes) {
   for (int q = 0; q < A->nlev; ++q) {
     int l = lt + q;
     LevelInfo& L = P.lev[l];
-    TailLevel<T>& t = A->lev[q];
+    TailLevel<T, TM>& t = A->lev[q];
     t.N = L.N;
     t.c = coefs<T>(P, l);
     t.pat = pats<T>(L);
     t.slot = L.flag;
     t.Ms = Mstruct_of<T>(L);
-    t.Mf = Mfree_of<T>(L);
+    t.Mf = Mfree_of<TM>(L);
     size_t n3 = 3ul * L.N * L.N * sizeof(T);
     A->off_w[q] = (int)take(n3);
     A->off_b[q] = (int)take(n3);
@@ -634,14 +646,17 @@ int fine_elastic(Problem& P, int l, const T* w, int color) {
   const double upd = (color < 0 ? 32.0 : 8.0) * 2 * sT;
   KScope ks(P, IB_KC_SPREAD,
             P.np * ((1.0 + deg) * 2.0 * (24 * sT + 8) + deg * (3 * sT + 8) + 8 + 16 * sT + 16 + upd));
-  kv_force_spread<T><<<nblk(4L * P.np), TPB, 0, P.stream>>>(pats<T>(L), sview<T>(P), w, L.N,
+  // FP64: small CTAs so that the interpolation FMAs spread over many SMs (the FP64
+  // pipe is narrow); FP32: the usual block size (a multiple of 4 either way)
+  const int tpb = sizeof(T) == 8 ? 64 : TPB;
+  kv_force_spread<T><<<nblk(4L * P.np, tpb), tpb, 0, P.stream>>>(pats<T>(L), sview<T>(P), w, L.N,
                                                             (T)(-P.prm.dt / (P.lev[0].h * P.lev[0].h)),
                                                             P.prm.box, color, rEbuf<T>(L));
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
 
-template <typename T>
+template <typename T, typename TM>
 int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
   LevelInfo& L = P.lev[l];
   LevelBuf<T>& B = lbuf<T>(L);
@@ -666,14 +681,15 @@ int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
         IB_LAUNCH_CHECK();
       }
       KScope ks(P, IB_KC_BOX, nbox * (15.0 * sT + 4) + 0.25 * L.n_struct * 25 * sT + 25 * sT);
-      kv_box1<T><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, Mstruct_of<T>(L), Mfree_of<T>(L));
+      kv_box1<T, TM><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, Mstruct_of<T>(L),
+                                                        Mfree_of<TM>(L));
       IB_LAUNCH_CHECK();
     } else {
       // per box: its unknowns' rows read w (5-point stencils, counted once per
       // unknown plus the one-cell halo), b, write w
       const double box_bytes = sT * (3.0 * nB + (4.0 * bs + 4)) + 4;
       KScope ks(P, IB_KC_BOX, nbox * box_bytes + 0.25 * L.n_struct * nB * nB * sT + (double)nB * nB * sT + e_bytes);
-      IB_TRY(launch_boxn<T>(P, l, B.w, B.b, E, color));
+      IB_TRY((launch_boxn<T, TM>(P, l, B.w, B.b, E, color)));
     }
   }
   return IB_OK;
@@ -682,8 +698,8 @@ int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
 template <typename T>
 constexpr int pix() { return sizeof(T) == 8 ? 1 : 0; }
 
-template <typename T>
-int vcycle_eager(Problem& P) {
+template <typename T, typename TM>
+int vcycle_eager_t(Problem& P) {
   const int lt = P.tail_level[pix<T>()];
   const bool has_E = P.np > 0 && P.ns > 0;
   for (int l = 0; l < lt; ++l) {
@@ -695,7 +711,7 @@ int vcycle_eager(Problem& P) {
       kv_zero<T><<<nblk(n3), TPB, 0, P.stream>>>(B.w, n3);
       IB_LAUNCH_CHECK();
     }
-    for (int s = 0; s < P.prm.nu1; ++s) IB_TRY(fine_sweep<T>(P, l, false, s == 0));
+    for (int s = 0; s < P.prm.nu1; ++s) IB_TRY((fine_sweep<T, TM>(P, l, false, s == 0)));
     if (has_E) IB_TRY(fine_elastic<T>(P, l, B.w, -1));
     const T* E = has_E ? rEbuf<T>(L) : nullptr;
     const int Nc = P.lev[l + 1].N;
@@ -709,11 +725,11 @@ int vcycle_eager(Problem& P) {
     }
   }
   {
-    TailArgs<T> A;
+    TailArgs<T, TM> A;
     size_t smem = 0;
-    IB_TRY(build_tail_args<T>(P, lt, &A, &smem));
+    IB_TRY((build_tail_args<T, TM>(P, lt, &A, &smem)));
     KScope ks(P, IB_KC_COARSE, 0.0);
-    kv_tail<T><<<1, TAIL_THREADS, smem, P.stream>>>(A);
+    kv_tail<T, TM><<<1, TAIL_THREADS, smem, P.stream>>>(A);
     IB_LAUNCH_CHECK();
   }
   for (int l = lt - 1; l >= 0; --l) {
@@ -726,9 +742,64 @@ int vcycle_eager(Problem& P) {
                                                                  has_E ? rEbuf<T>(L) : nullptr);
       IB_LAUNCH_CHECK();
     }
-    for (int s = 0; s < P.prm.nu2; ++s) IB_TRY(fine_sweep<T>(P, l, P.prm.box == 1, false));
+    for (int s = 0; s < P.prm.nu2; ++s) IB_TRY((fine_sweep<T, TM>(P, l, P.prm.box == 1, false)));
   }
   return IB_OK;
+}
+
+// The FP64 V-cycle applies the FP32 free-box inverse unless the problem asked for
+// FP64 throughout (the mixed-precision V-cycle: FP64 vectors, residuals,
+// transfers, elasticity and structure-box solves; FP32 free-box solves).
+template <typename T>
+int vcycle_eager(Problem& P) {
+  if constexpr (sizeof(T) == 8) {
+    if (P.prm.precision != IB_FP64) return vcycle_eager_t<double, float>(P);
+    return vcycle_eager_t<double, double>(P);
+  } else {
+    return vcycle_eager_t<float, float>(P);
+  }
+}
+
+// Shared-memory bytes of the tail kernel starting at level lt, and raising the
+// kernel's dynamic shared-memory limit to smem_max.
+template <typename T, typename TM>
+int tail_smem_t(Problem& P, int lt, size_t* bytes) {
+  TailArgs<T, TM> A;
+  return build_tail_args<T, TM>(P, lt, &A, bytes);
+}
+
+template <typename T, typename TM>
+int tail_raise_smem_t(size_t smem_max) {
+  // the limit is a per-function setting shared by every problem in the process:
+  // only ever raise it (problems of a batch are prepared on several threads)
+  static std::mutex mu;
+  static size_t granted = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem_max > granted) {
+    IB_CUDA_TRY(cudaFuncSetAttribute(kv_tail<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    granted = smem_max;
+  }
+  return IB_OK;
+}
+
+template <typename T>
+int tail_smem(Problem& P, int lt, size_t* bytes) {
+  if constexpr (sizeof(T) == 8) {
+    if (P.prm.precision != IB_FP64) return tail_smem_t<double, float>(P, lt, bytes);
+    return tail_smem_t<double, double>(P, lt, bytes);
+  } else {
+    return tail_smem_t<float, float>(P, lt, bytes);
+  }
+}
+
+template <typename T>
+int tail_raise_smem(Problem& P, size_t smem_max) {
+  if constexpr (sizeof(T) == 8) {
+    if (P.prm.precision != IB_FP64) return tail_raise_smem_t<double, float>(smem_max);
+    return tail_raise_smem_t<double, double>(smem_max);
+  } else {
+    return tail_raise_smem_t<float, float>(smem_max);
+  }
 }
 
 }  // namespace
@@ -748,32 +819,20 @@ int vcycle_prepare(Problem& P) {
   size_t smem_max = 0;
   for (int l = 0; l < P.nlev; ++l) {
     if (P.lev[l].N > nmax) continue;
-    TailArgs<T> A;
     size_t s = 0;
-    IB_TRY(build_tail_args<T>(P, l, &A, &s));
+    IB_TRY(tail_smem<T>(P, l, &s));
     if (s <= 227u * 1024u) {
       cand.push_back(l);
       if (s > smem_max) smem_max = s;
     }
   }
   if (cand.empty() || cand.back() != P.nlev - 1) {
-    TailArgs<T> A;
     size_t s = 0;
-    IB_TRY(build_tail_args<T>(P, P.nlev - 1, &A, &s));
+    IB_TRY(tail_smem<T>(P, P.nlev - 1, &s));
     cand.push_back(P.nlev - 1);
     if (s > smem_max) smem_max = s;
   }
-  // the limit is a per-function setting shared by every problem in the process:
-  // only ever raise it (problems of a batch are prepared on several threads)
-  {
-    static std::mutex mu;
-    static size_t granted = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    if (smem_max > granted) {
-      IB_CUDA_TRY(cudaFuncSetAttribute(kv_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-      granted = smem_max;
-    }
-  }
+  IB_TRY(tail_raise_smem<T>(P, smem_max));
   constexpr int ix = pix<T>();
   // IB_TAIL_NMAX pins the split instead of timing it (profiler runs distort the
   // timings): the tail starts at the first candidate level with N_l <= value

@@ -8,20 +8,22 @@ namespace ib {
 
 constexpr int MAX_LEVELS = 16;
 
-template <typename T>
+// T: vectors of the V-cycle and structure-box inverses; TM: the free-box inverse
+// (float with T = double in the mixed-precision V-cycle).
+template <typename T, typename TM = T>
 struct TailLevel {
   int N;
   StokesCoef<T> c;
   Patches<T> pat;
   const int* slot;  // box -> structure slot (-1 free)
-  const T* Ms;      // structure-box inverses in the V-cycle precision
-  const T* Mf;
+  const T* Ms;      // structure-box inverses
+  const TM* Mf;     // shared inverse of the structure-free boxes
 };
 
-template <typename T>
+template <typename T, typename TM = T>
 struct TailArgs {
   int nlev;  // levels in the tail: lev[0] is the finest of them, lev[nlev-1] the coarsest grid
-  TailLevel<T> lev[MAX_LEVELS];
+  TailLevel<T, TM> lev[MAX_LEVELS];
   const T* b_in;  // right-hand side of lev[0] (global)
   T* w_out;       // correction of lev[0] (global)
   Springs<T> sp;

@@ -136,8 +136,24 @@ def test_vcycle_fp32(pkg, name, box):
     s.close()
 
 
+@pytest.mark.parametrize("name,box", [("c1_64", 1), ("c1_64", 4), ("stiff_32_exact", 4), ("stiff_32", 8)])
+def test_vcycle_mixed(pkg, name, box):
+    """FP64 vectors and residuals, FP32 box inverses: within FP32 rounding of the
+    oracle's FP64 V-cycle."""
+    p = make_case(name, box)
+    rhs = O.rhs_vector(p)
+    ref = _oracle_vcycle(p, rhs)
+    s = pkg.IBSolver.from_problem(p, precision="mixed")
+    w = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), w)
+    got = w.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
+    s.close()
+
+
 @pytest.mark.parametrize("name,box,prec", [("c1_64", 1, "fp64"), ("c1_64", 1, "fp32"),
                                            ("stiff_32", 4, "fp64"), ("stiff_32", 8, "fp32"),
+                                           ("stiff_32", 4, "mixed"), ("c1_64", 2, "mixed"),
                                            ("steady_cos4_32", 1, "fp64"),
                                            ("offcentre_16", 2, "fp32")])
 def test_solve_step(pkg, name, box, prec):
