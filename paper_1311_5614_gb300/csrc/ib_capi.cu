@@ -481,10 +481,10 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       if (est <= tol * bnorm) break;
       hist.push_back(est);
       // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
-      // the last 8 iterations -> precondition with the mixed-precision V-cycle
+      // the last 4 iterations -> precondition with the mixed-precision V-cycle
       // (FP64 residuals, which the stiff cancellation needs) from now on
-      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 8 &&
-          est > 0.5 * hist[hist.size() - 9])
+      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 4 &&
+          est > 0.5 * hist[hist.size() - 5])
         st->escalated_at = total;
       if (!(P.scal_host[1] > 0.0)) break;  // lucky breakdown: exact solution in the space
     }

@@ -119,25 +119,28 @@ __global__ void kv_force_spread(Patches<T> pat, Springs<T> sp, const T* __restri
 // of the box inverse), several boxes per CTA; the shared inverse of the
 // structure-free box is staged in shared memory (n <= 4), the inverses of
 // structure boxes are read column by column (coalesced over the box's threads).
-template <int BS>
+// BPC boxes per CTA; with one box per CTA (small levels: more CTAs, so that the
+// FP64 products of structure boxes spread over more SMs) the free-box inverse is
+// read through the cache instead of being staged.
+template <int BS, int BPC_ = (BS == 2 ? 8 : (BS == 4 ? 4 : 1))>
 struct BoxShape {
   static constexpr int NB = 2 * BS * (BS + 1) + BS * BS;
   static constexpr int TPBOX = (NB + 31) / 32 * 32;
-  static constexpr int BPC = BS == 2 ? 8 : (BS == 4 ? 4 : 1);
+  static constexpr int BPC = BPC_;
   static constexpr int THREADS = TPBOX * BPC;
-  static constexpr bool SMEM_MF = BS <= 4;
+  static constexpr bool SMEM_MF = BS <= 4 && BPC > 1;
 };
 
 // T: vectors, residuals and structure-box inverses; TM: the shared inverse of the
 // structure-free boxes and its products (TM = float with T = double is the
 // mixed-precision V-cycle).
-template <typename T, typename TM, int BS>
-__global__ void __launch_bounds__(BoxShape<BS>::THREADS) kv_boxn(T* w, const T* __restrict__ b, T* rE, int N,
+template <typename T, typename TM, int BS, int BPC>
+__global__ void __launch_bounds__(BoxShape<BS, BPC>::THREADS) kv_boxn(T* w, const T* __restrict__ b, T* rE, int N,
                                                                  StokesCoef<T> c, int color,
                                                                  const int* __restrict__ slot,
                                                                  const T* __restrict__ Ms,
                                                                  const TM* __restrict__ Mf) {
-  using S = BoxShape<BS>;
+  using S = BoxShape<BS, BPC>;
   constexpr int NB = S::NB, NV = 2 * BS * (BS + 1);
   __shared__ TM sMf[S::SMEM_MF ? NB * NB : 1];
   __shared__ T rs[S::BPC][NB];
@@ -318,30 +321,36 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const long nbox = (long)half * half;
   const T* Ms = Mstruct_of<T>(L);
   const TM* Mf = Mfree_of<TM>(L);
-  // the GEMM form pays off on large levels; small levels keep one box per CTA slot
+  // the GEMM form pays off on large levels, one box per CTA on small ones
   const bool gemm = nbox >= P.box_gemm_min;
+  const bool one = nbox <= 512;
+#define IB_BOXN(BS_, BPC_)                                                                              \
+  kv_boxn<T, TM, BS_, BPC_><<<nblk(nbox, BPC_), BoxShape<BS_, BPC_>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, \
+                                                                                           color, L.flag, Ms, Mf)
   switch (P.prm.box) {
     case 2:
-      if (!gemm)
-        kv_boxn<T, TM, 2><<<nblk(nbox, BoxShape<2>::BPC), BoxShape<2>::THREADS, 0, P.stream>>>(
-            w, b, E, L.N, c, color, L.flag, Ms, Mf);
-      else
+      if (gemm)
         kv_boxg<T, TM, 2><<<nblk(nbox, BoxGemm<TM, 2>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag,
                                                                                Ms, Mf);
+      else if (one)
+        IB_BOXN(2, 1);
+      else
+        IB_BOXN(2, 8);
       break;
     case 4:
-      if (!gemm)
-        kv_boxn<T, TM, 4><<<nblk(nbox, BoxShape<4>::BPC), BoxShape<4>::THREADS, 0, P.stream>>>(
-            w, b, E, L.N, c, color, L.flag, Ms, Mf);
-      else
+      if (gemm)
         kv_boxg<T, TM, 4><<<nblk(nbox, BoxGemm<TM, 4>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag,
                                                                                Ms, Mf);
+      else if (one)
+        IB_BOXN(4, 1);
+      else
+        IB_BOXN(4, 4);
       break;
     default:
-      kv_boxn<T, TM, 8><<<nblk(nbox, BoxShape<8>::BPC), BoxShape<8>::THREADS, 0, P.stream>>>(
-          w, b, E, L.N, c, color, L.flag, Ms, Mf);
+      IB_BOXN(8, 1);
       break;
   }
+#undef IB_BOXN
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
