@@ -649,12 +649,14 @@ int fine_elastic(Problem& P, int l, const T* w, int color) {
   LevelInfo& L = P.lev[l];
   const double sT = sizeof(T);
   double deg = P.np ? 2.0 * P.ns / P.np : 0.0;
-  // per point: (1 + deg) interpolations of both components (16 values, 8 weights,
-  // 2 bases each), adjacency and K per spring, the spread patch (16 weights, 4
-  // bases) and its 32 read-modify-write updates (a quarter of them for one colour)
+  // algorithmic bytes per point (the re-interpolation of neighbours is redundant
+  // work, not data): its interpolation patch for both components (16 values, 8
+  // weights, 2 bases each), half of its springs' K and adjacency, its spread
+  // patch (8 weights, 2 bases per component) and the read-modify-write of the
+  // spread entries (32 for all rows, about 8 on the rows of one colour)
   const double upd = (color < 0 ? 32.0 : 8.0) * 2 * sT;
   KScope ks(P, IB_KC_SPREAD,
-            P.np * ((1.0 + deg) * 2.0 * (24 * sT + 8) + deg * (3 * sT + 8) + 8 + 16 * sT + 16 + upd));
+            P.np * (2.0 * (24 * sT + 8) + 0.5 * deg * (3 * sT + 8) + 8 + 2.0 * (8 * sT + 8) + upd));
   // FP64: small CTAs so that the interpolation FMAs spread over many SMs (the FP64
   // pipe is narrow); FP32: the usual block size (a multiple of 4 either way)
   const int tpb = sizeof(T) == 8 ? 64 : TPB;
