@@ -489,11 +489,8 @@ def run_learned512(args):
     res = learned.run(N=512, n_problems=args.learn_problems, pairs_per_problem=args.learn_pairs,
                       epochs=args.learn_epochs, lr=1e-3, seed=0, log=lambda m: print(m, file=sys.stderr))
     params = res.pop("params")
-    try:
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        np.save(os.path.join(ROOT, "gpurun_out", "unet512_params.npy"), params)
-    except Exception:
-        pass
+    if args.save_params:
+        np.save(args.save_params, params)
     ev = res["eval"]
     plain = sum(r["plain"]["ms"] for r in ev) / len(ev)
     lrn = sum(r["learned"]["ms"] for r in ev) / len(ev)
@@ -607,8 +604,10 @@ def main(argv=None):
     ap.add_argument("--box", type=int, default=4)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--grid", type=int, default=2048, help="grid size of the vcycle workload")
-    ap.add_argument("--learn-problems", type=int, default=16)
-    ap.add_argument("--learn-pairs", type=int, default=64, help="pairs per training problem")
+    ap.add_argument("--learn-problems", type=int, default=40)
+    ap.add_argument("--learn-pairs", type=int, default=256,
+                    help="pairs per training problem (40 x 256 = 10240 pairs by default)")
+    ap.add_argument("--save-params", default=None, help="learned512: write the trained U-Net parameters (.npy)")
     ap.add_argument("--learn-epochs", type=int, default=2)
     ap.add_argument("--workload", default="sweep256", choices=["sweep256", "multi1024", "batch256", "vcycle", "learned512"],
                     help="sweep256 (default): the 256^2 kappa x dt sweep; multi1024 / batch256: the "

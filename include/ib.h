@@ -67,11 +67,13 @@ enum { IB_DELTA_PESKIN4 = 0, IB_DELTA_COS4 = 1 };
 /* Precision of the V-cycle (FGMRES, the operator and the true residual are FP64
  * in every mode; not in the paper):
  *   IB_FP64            everything FP64.
- *   IB_FP32_PRECOND    V-cycle in FP32 (vectors, stencils, elasticity, box inverses).
+ *   IB_FP32_PRECOND    V-cycle in FP32 (vectors, stencils, elasticity, free-box
+ *                      solves); the solves of structure boxes (whose condition
+ *                      number grows with the stiffness) in FP64, cast at the box.
  *   IB_MIXED_PRECOND   V-cycle in FP64 except the structure-free boxes, whose shared
  *                      inverse is applied in FP32 (the FP64 pipe is the GB300's
  *                      slowest unit and those box products are most of the
- *                      V-cycle's FLOPs; stiff structure boxes need FP64). */
+ *                      V-cycle's FLOPs). */
 enum { IB_FP64 = 0, IB_FP32_PRECOND = 1, IB_MIXED_PRECOND = 2 };
 enum { IB_JAC_CLAMPED = 0, IB_JAC_EXACT = 1 };
 
@@ -242,7 +244,8 @@ IB_API void ib_unet_destroy(ib_unet* net);
  * does not own the network).  With a stage attached each FGMRES direction z = MG(v)
  * becomes z + alpha d, d the network's correction for r = v - A z and alpha the
  * exact minimiser of ||r - alpha A d||, when alpha > 0 and the residual drops by at
- * least 0.1 %; otherwise the V-cycle direction is kept. */
+ * least 0.1 %; otherwise the V-cycle direction is kept.  After 3 consecutive
+ * rejections the stage is not evaluated again in that solve. */
 IB_API int ib_set_learned_stage(ib_problem* prob, ib_unet* net);
 /* A training pair from the method itself: b = A x, z = MG(b) (one V-cycle of the
  * problem's precision), r = b - A z, e = x - z; writes the network input for r to

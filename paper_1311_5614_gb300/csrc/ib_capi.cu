@@ -156,11 +156,9 @@ int setup_hierarchy(Problem& P) {
     if (cnt > L.cap_struct) {
       P.graph_dirty[0] = P.graph_dirty[1] = true;  // the box kernels take the new pointer
       dfree(L.Mstruct);
-      dfree(L.Mstruct32);
       int cap = cnt + cnt / 4 + 16;
       if (cap > L.nb * L.nb) cap = L.nb * L.nb;
       IB_TRY(dalloc(&L.Mstruct, (size_t)cap * nB * nB));
-      if (P.prm.precision == IB_FP32_PRECOND) IB_TRY(dalloc(&L.Mstruct32, (size_t)cap * nB * nB));
       L.cap_struct = cap;
     }
     L.n_struct = cnt;
@@ -168,8 +166,6 @@ int setup_hierarchy(Problem& P) {
     IB_TRY(launch_struct_fill(P, l));
     IB_TRY(launch_assemble_struct(P, l));
     IB_TRY(launch_invert(P, L.Mstruct, nB, cnt));
-    if (P.prm.precision == IB_FP32_PRECOND && cnt > 0)
-      IB_TRY(launch_cast<double, float>(P, L.Mstruct, L.Mstruct32, (size_t)cnt * nB * nB));
   }
   P.free_ready = true;
   IB_TRY(launch_coarse_fill(P));
@@ -183,7 +179,7 @@ int setup_hierarchy(Problem& P) {
 void free_problem(Problem* P) {
   if (!P) return;
   for (auto& L : P->lev) {
-    dfree(L.flag); dfree(L.Mstruct); dfree(L.Mstruct32); dfree(L.Sfree); dfree(L.Mfree); dfree(L.Mfree32);
+    dfree(L.flag); dfree(L.Mstruct); dfree(L.Sfree); dfree(L.Mfree); dfree(L.Mfree32);
     dfree(L.pat64.base); dfree(L.pat64.w); dfree(L.pat32.base); dfree(L.pat32.w);
     dfree(L.v64.w); dfree(L.v64.b); dfree(L.v64.r);
     dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);
@@ -328,7 +324,8 @@ __global__ void k_add_d2t_d(double* z, const double* __restrict__ dz, const doub
 // least 0.1%, then P.t64 = A (stored z_j).  z64 (if not NULL) is the FP64 copy of z_j
 // used after an FP32 -> FP64 escalation.
 template <typename T>
-int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st) {
+int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st, bool* accepted) {
+  *accepted = false;
   const size_t n = 3ul * P.prm.N * P.prm.N;
   double* sc = P.scal + 8 + 2 * (P.max_m + 2) + 1;  // free scalars after ||w||^2
   IB_TRY(launch_axpby(P, 1.0, vj, -1.0, P.t64, P.nn_r));
@@ -355,6 +352,7 @@ int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st)
     IB_LAUNCH_CHECK();
   }
   st->learned_used += 1;
+  *accepted = true;
   const int tpb = 256;
   const int nbk = (int)((n + tpb - 1) / tpb);
   KScope ks(P, IB_KC_OTHER, n * 20.0);
@@ -400,6 +398,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
   }
   int total = 0;
   std::vector<double> hist;
+  int nn_rejected = 0;  // consecutive rejections of the learned stage
   st->escalated_at = -1;
   double* h1 = s + 8;
   double* h2 = h1 + m + 2;
@@ -463,7 +462,11 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       }
       if (P.net) {
         bool esc = !std::is_same<T, double>::value && st->escalated_at >= 0;
-        IB_TRY(learned_step<T>(P, vj, zj, esc ? P.Z64 + (size_t)j * n : nullptr, st));
+        if (nn_rejected < 3) {
+          bool acc = false;
+          IB_TRY(learned_step<T>(P, vj, zj, esc ? P.Z64 + (size_t)j * n : nullptr, st, &acc));
+          nn_rejected = acc ? 0 : nn_rejected + 1;
+        }
       }
       IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h1));
       IB_TRY(launch_multiaxpy(P, P.V, j + 1, h1, P.t64));

@@ -155,7 +155,6 @@ struct LevelInfo {
   int cap_struct = 0;  // allocated structure-box slots
   int* flag = nullptr;        // [nb * nb] structure flag -> slot (-1 free)
   double* Mstruct = nullptr;  // [cap][nB * nB] inverse (column-major), FP64
-  float* Mstruct32 = nullptr; // FP32 copy for the FP32 V-cycle
   double* Sfree = nullptr;    // [nB * nB] Stokes block of a box (column-major), FP64
   double* Mfree = nullptr;    // [nB * nB] shared inverse of structure-free boxes, FP64
   float* Mfree32 = nullptr;   // FP32 copy for the FP32 V-cycle

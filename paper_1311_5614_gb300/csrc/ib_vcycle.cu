@@ -59,12 +59,6 @@ LevelBuf<double>& lbuf<double>(LevelInfo& L) { return L.v64; }
 template <>
 LevelBuf<float>& lbuf<float>(LevelInfo& L) { return L.v32; }
 
-template <typename T>
-const T* Mstruct_of(const LevelInfo& L);
-template <>
-const double* Mstruct_of<double>(const LevelInfo& L) { return L.Mstruct; }
-template <>
-const float* Mstruct_of<float>(const LevelInfo& L) { return L.Mstruct32; }
 
 template <typename T>
 T* rEbuf(LevelInfo& L);
@@ -131,14 +125,16 @@ struct BoxShape {
   static constexpr bool SMEM_MF = BS <= 4 && BPC > 1;
 };
 
-// T: vectors, residuals and structure-box inverses; TM: the shared inverse of the
-// structure-free boxes and its products (TM = float with T = double is the
-// mixed-precision V-cycle).
+// T: vectors and residuals; TM: the shared inverse of the structure-free boxes
+// and its products (TM = float with T = double is the mixed-precision V-cycle).
+// Structure boxes (stiff: their condition number grows with the stiffness) are
+// always solved in FP64, the residual cast up and the correction cast back at the
+// box boundary.
 template <typename T, typename TM, int BS, int BPC>
 __global__ void __launch_bounds__(BoxShape<BS, BPC>::THREADS) kv_boxn(T* w, const T* __restrict__ b, T* rE, int N,
                                                                  StokesCoef<T> c, int color,
                                                                  const int* __restrict__ slot,
-                                                                 const T* __restrict__ Ms,
+                                                                 const double* __restrict__ Ms,
                                                                  const TM* __restrict__ Mf) {
   using S = BoxShape<BS, BPC>;
   constexpr int NB = S::NB, NV = 2 * BS * (BS + 1);
@@ -169,11 +165,11 @@ __global__ void __launch_bounds__(BoxShape<BS, BPC>::THREADS) kv_boxn(T* w, cons
   __syncthreads();
   if (!valid) return;
   if (sl >= 0) {
-    const T* M = Ms + (size_t)sl * NB * NB + q;
-    T d = 0;
+    const double* M = Ms + (size_t)sl * NB * NB + q;
+    double d = 0.0;
 #pragma unroll 8
-    for (int s = 0; s < NB; ++s) d += M[(size_t)s * NB] * rs[lb][s];
-    w[gq] += d;
+    for (int s = 0; s < NB; ++s) d += M[(size_t)s * NB] * (double)rs[lb][s];
+    w[gq] += (T)d;
   } else {
     const TM* M = S::SMEM_MF ? sMf + q : Mf + q;
     TM d = 0;
@@ -215,8 +211,8 @@ struct VecOf<double, 2> {
 
 template <typename T, typename TM, int BS>
 __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T* rE, int N, StokesCoef<T> c,
-                                               int color, const int* __restrict__ slot, const T* __restrict__ Ms,
-                                               const TM* __restrict__ Mf) {
+                                               int color, const int* __restrict__ slot,
+                                               const double* __restrict__ Ms, const TM* __restrict__ Mf) {
   using G = BoxGemm<TM, BS>;
   using V = typename VecOf<TM, G::RB>::type;
   constexpr int NB = G::NB, NV = 2 * BS * (BS + 1);
@@ -286,7 +282,7 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
       }
     }
   }
-  // structure boxes: their own inverses; all threads share the (box, row) pairs
+  // structure boxes: their own FP64 inverses; all threads share the (box, row) pairs
   __shared__ int slist[G::BPC];
   __shared__ int ns;
   if (tid == 0) {
@@ -300,16 +296,16 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
     const int lb = slist[e / NB], q = e % NB;
     const int t = box0 + lb;
     const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
-    const T* M = Ms + (size_t)sslot[lb] * NB * NB + q;
-    T d0 = 0, d1 = 0;
+    const double* M = Ms + (size_t)sslot[lb] * NB * NB + q;
+    double d0 = 0.0, d1 = 0.0;
 #pragma unroll 4
     for (int s2 = 0; s2 < NB; s2 += 2) {
-      d0 += M[(size_t)s2 * NB] * rs[lb][s2];
-      d1 += M[(size_t)(s2 + 1) * NB] * rs[lb][s2 + 1];
+      d0 += M[(size_t)s2 * NB] * (double)rs[lb][s2];
+      d1 += M[(size_t)(s2 + 1) * NB] * (double)rs[lb][s2 + 1];
     }
     int cc, i, j;
     box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
-    w[cc * N * N + j * N + i] += d0 + d1;
+    w[cc * N * N + j * N + i] += (T)(d0 + d1);
   }
 }
 
@@ -319,7 +315,7 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const StokesCoef<T> c = coefs<T>(P, l);
   const int half = L.nb / 2;
   const long nbox = (long)half * half;
-  const T* Ms = Mstruct_of<T>(L);
+  const double* Ms = L.Mstruct;
   const TM* Mf = Mfree_of<TM>(L);
   // the GEMM form pays off on large levels, one box per CTA on small ones
   const bool gemm = nbox >= P.box_gemm_min;
@@ -383,7 +379,8 @@ __global__ void kv_colres1(const T* __restrict__ w, const T* __restrict__ b, T* 
 
 template <typename T, typename TM>
 __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int color,
-                        const int* __restrict__ slot, const T* __restrict__ Ms, const TM* __restrict__ Mf) {
+                        const int* __restrict__ slot, const double* __restrict__ Ms,
+                        const TM* __restrict__ Mf) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int half = N >> 1;
   if (t >= half * half) return;
@@ -500,8 +497,10 @@ __device__ void tail_boxes(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, 
       const int sl = L.slot[J * nb + I];
       const T* rs = sr + t * nB;
       if (sl >= 0) {
-        const T* M = L.Ms + (size_t)sl * nB * nB + q;
-        for (int s = gl; s < nB; s += G) d += M[(size_t)s * nB] * rs[s];
+        const double* M = L.Ms + (size_t)sl * nB * nB + q;
+        double dd = 0.0;
+        for (int s = gl; s < nB; s += G) dd += M[(size_t)s * nB] * (double)rs[s];
+        d = (T)dd;
       } else {
         const TM* M = L.Mf + q;
         TM dm = 0;
@@ -613,7 +612,7 @@ int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes) 
     t.c = coefs<T>(P, l);
     t.pat = pats<T>(L);
     t.slot = L.flag;
-    t.Ms = Mstruct_of<T>(L);
+    t.Ms = L.Mstruct;
     t.Mf = Mfree_of<TM>(L);
     size_t n3 = 3ul * L.N * L.N * sizeof(T);
     A->off_w[q] = (int)take(n3);
@@ -692,8 +691,7 @@ int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
         IB_LAUNCH_CHECK();
       }
       KScope ks(P, IB_KC_BOX, nbox * (15.0 * sT + 4) + 0.25 * L.n_struct * 25 * sT + 25 * sT);
-      kv_box1<T, TM><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, Mstruct_of<T>(L),
-                                                        Mfree_of<TM>(L));
+      kv_box1<T, TM><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, L.Mstruct, Mfree_of<TM>(L));
       IB_LAUNCH_CHECK();
     } else {
       // per box: its unknowns' rows read w (5-point stencils, counted once per

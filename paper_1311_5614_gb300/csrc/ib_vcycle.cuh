@@ -8,15 +8,15 @@ namespace ib {
 
 constexpr int MAX_LEVELS = 16;
 
-// T: vectors of the V-cycle and structure-box inverses; TM: the free-box inverse
-// (float with T = double in the mixed-precision V-cycle).
+// T: vectors of the V-cycle; TM: the free-box inverse (float with T = double in
+// the mixed-precision V-cycle).  Structure-box inverses are FP64 in every mode.
 template <typename T, typename TM = T>
 struct TailLevel {
   int N;
   StokesCoef<T> c;
   Patches<T> pat;
   const int* slot;  // box -> structure slot (-1 free)
-  const T* Ms;      // structure-box inverses
+  const double* Ms; // structure-box inverses (FP64)
   const TM* Mf;     // shared inverse of the structure-free boxes
 };
 

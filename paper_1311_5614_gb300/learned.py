@@ -21,29 +21,38 @@ import ib_workloads as W
 from . import capi as C
 
 
-def harvest(N=512, n_points=1024, n_problems=16, pairs_per_problem=64, seed=0, log_kappa=(2.0, 6.0),
+def harvest(N=512, n_points=1024, n_problems=40, pairs_per_problem=256, seed=0, log_kappa=(2.0, 6.0),
             dt=1e-2, box=4, precision="fp32"):
     """Return device tensors X [P, 4 N^2], T [P, 3 N^2] (float32) and the problems' kappas."""
     import torch
+
+    from concurrent.futures import ThreadPoolExecutor
 
     rng = np.random.default_rng(seed)
     P = n_problems * pairs_per_problem
     X = torch.empty((P, 4 * N * N), dtype=torch.float32, device="cuda")
     T = torch.empty((P, 3 * N * N), dtype=torch.float32, device="cuda")
-    kappas = []
-    k = 0
+    # draw every seed in the fixed order first, then generate the fields on host
+    # threads ahead of the device work (the FFTs release the GIL)
+    plan = []
     for i in range(n_problems):
         kap = float(10.0 ** rng.uniform(*log_kappa))
         cx, cy = 0.5 + 0.02 * rng.standard_normal(2)
-        prob = W.single_ellipse(N=N, n_points=n_points, kappa=kap, dt=dt, center=(cx, cy))
-        prob.box = box
-        s = C.IBSolver.from_problem(prob, precision=precision)
-        for j in range(pairs_per_problem):
-            x = torch.tensor(W.random_smooth_field(N, int(rng.integers(1 << 31))).ravel(), device="cuda")
-            s.learned_pair(x, X[k], T[k])
-            k += 1
-        s.close()
-        kappas.append(kap)
+        seeds = [int(rng.integers(1 << 31)) for _ in range(pairs_per_problem)]
+        plan.append((kap, (cx, cy), seeds))
+    kappas = []
+    k = 0
+    with ThreadPoolExecutor(max_workers=8) as pool:
+        for kap, centre, seeds in plan:
+            fields = pool.map(lambda sd: W.random_smooth_field(N, sd).ravel(), seeds)
+            prob = W.single_ellipse(N=N, n_points=n_points, kappa=kap, dt=dt, center=centre)
+            prob.box = box
+            s = C.IBSolver.from_problem(prob, precision=precision)
+            for f in fields:
+                s.learned_pair(torch.tensor(f, device="cuda"), X[k], T[k])
+                k += 1
+            s.close()
+            kappas.append(kap)
     torch.cuda.synchronize()
     return X, T, kappas
 
@@ -111,7 +120,7 @@ def evaluate(net, N=512, n_points=1024, kappas=(1e2, 1e4, 1e6), dt=1e-2, box=4, 
     return out
 
 
-def run(N=512, n_problems=16, pairs_per_problem=64, epochs=2, lr=1e-3, seed=0, log=print):
+def run(N=512, n_problems=40, pairs_per_problem=256, epochs=2, lr=1e-3, seed=0, log=print):
     """Harvest, train from a seeded initialisation, evaluate; returns a summary dict."""
     t0 = time.perf_counter()
     X, T, kap = harvest(N=N, n_problems=n_problems, pairs_per_problem=pairs_per_problem, seed=seed)
