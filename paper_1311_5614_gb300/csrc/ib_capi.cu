@@ -204,6 +204,8 @@ void free_problem(Problem* P) {
   if (P->count_host) cudaFreeHost(P->count_host);
   for (auto& e : P->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : P->pev)
+    if (e) cudaEventDestroy(e);
   for (auto& r : P->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -292,6 +294,7 @@ int allocate(Problem& P) {
   IB_CUDA_TRY(cudaMallocHost((void**)&P.scal_host, 64 * sizeof(double)));
   IB_CUDA_TRY(cudaMallocHost((void**)&P.count_host, 128 * sizeof(int)));
   for (auto& e : P.ev) IB_CUDA_TRY(cudaEventCreate(&e));
+  for (auto& e : P.pev) IB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return IB_OK;
 }
 
@@ -377,6 +380,13 @@ int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st,
 // initial guess, classical Gram-Schmidt applied twice, Givens rotations; stop
 // when the estimate reaches tol ||b||, confirm with the true FP64 residual and
 // restart from the iterate if needed.
+//
+// The iterations are pipelined on the host: iteration j is launched before the
+// residual estimate of iteration j - 1 is read, so the device never waits for
+// the host between iterations.  When j - 1 turns out to be the last one, the
+// work of iteration j is discarded: it only touched column j of H, g[j], g[j+1],
+// V[j+1] and Z[j], none of which the update with k = j directions reads.
+// Decisions taken from iteration j - 1 (escalation) apply from iteration j + 1.
 template <typename T>
 int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
   const size_t n = 3ul * P.prm.N * P.prm.N;
@@ -433,6 +443,27 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     IB_LAUNCH_CHECK();
     IB_TRY(launch_scale_copy(P, P.V, s + 6, P.V, true));
     int k = 0;
+    bool stopped = false;
+    // Reads the scalars of iteration jj (waiting for them): 1 = stop after jj
+    // (converged or lucky breakdown), 0 = continue, -1 = non-finite or CUDA error.
+    auto check = [&](int jj) -> int {
+      if (cudaEventSynchronize(P.pev[jj & 1]) != cudaSuccess) return -1;
+      const double* h = P.scal_host + 24 + 4 * (jj & 1);
+      const double est = h[0];
+      st->rel_res_est = est / bnorm;
+      if (h[2] != 0.0) return -1;
+      if (est <= tol * bnorm) return 1;
+      hist.push_back(est);
+      // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
+      // the last 4 iterations -> precondition with the mixed-precision V-cycle
+      // (FP64 residuals, which the stiff cancellation needs) from the next
+      // iteration not yet launched (jj + 2) on
+      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 4 &&
+          est > 0.5 * hist[hist.size() - 5])
+        st->escalated_at = cycle_start + jj + 2;
+      if (!(h[1] > 0.0)) return 1;  // lucky breakdown: exact solution in the space
+      return 0;
+    };
     for (int j = 0; j < mav; ++j) {
       double* vj = P.V + (size_t)j * n;
       T* zj = Z + (size_t)j * n;
@@ -475,21 +506,29 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       IB_TRY(launch_dot(P, P.t64, P.t64, wn));
       IB_TRY(launch_givens(P, j, 0.0, nullptr));
       IB_TRY(launch_scale_copy(P, P.t64, s + 1, P.V + (size_t)(j + 1) * n, true));
-      IB_TRY(read_scalars(P, 3));
+      IB_CUDA_TRY(cudaMemcpyAsync(P.scal_host + 24 + 4 * (j & 1), P.scal, 3 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, P.stream));
+      IB_CUDA_TRY(cudaEventRecord(P.pev[j & 1], P.stream));
       ++total;
       k = j + 1;
-      double est = P.scal_host[0];
-      st->rel_res_est = est / bnorm;
-      if (P.scal_host[2] != 0.0) return fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES");
-      if (est <= tol * bnorm) break;
-      hist.push_back(est);
-      // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
-      // the last 4 iterations -> precondition with the mixed-precision V-cycle
-      // (FP64 residuals, which the stiff cancellation needs) from now on
-      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 4 &&
-          est > 0.5 * hist[hist.size() - 5])
-        st->escalated_at = total;
-      if (!(P.scal_host[1] > 0.0)) break;  // lucky breakdown: exact solution in the space
+      if (j > 0) {
+        int rc = check(j - 1);
+        if (rc < 0) return P.scal_host[24 + 4 * ((j - 1) & 1) + 2] != 0.0
+                               ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
+                               : fail(IB_ERR_CUDA, "FGMRES pipeline");
+        if (rc == 1) {  // iteration j - 1 was the last: drop iteration j
+          k = j;
+          --total;
+          stopped = true;
+          break;
+        }
+      }
+    }
+    if (!stopped && k > 0) {
+      int rc = check(k - 1);
+      if (rc < 0) return P.scal_host[24 + 4 * ((k - 1) & 1) + 2] != 0.0
+                             ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
+                             : fail(IB_ERR_CUDA, "FGMRES pipeline");
     }
     IB_TRY(launch_backsolve(P, k));
     if constexpr (std::is_same<T, double>::value) {

@@ -250,6 +250,7 @@ struct Problem {
   int* count_host = nullptr;  // pinned
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t pev[2] = {nullptr, nullptr};  // FGMRES pipeline: scalars of iterations j, j - 1
 };
 
 // Launch scope: counts the launch of one kernel of class cls and, while

@@ -1,6 +1,9 @@
 // Flexible GMRES building blocks (sec. 3.3: GMRES right-preconditioned by the
 // V-cycle; flexible form so that an FP32 preconditioner is admissible).  All
-// vectors are FP64; reductions are two-stage and deterministic.
+// vectors are FP64; reductions are two-stage and deterministic.  The Krylov
+// bases (V, Z) are read with the streaming cache hint (evict first): at a few
+// hundred MB they would otherwise push the V-cycle's working set out of L2
+// between preconditioner applications.
 #include <cmath>
 
 #include "ib_internal.cuh"
@@ -25,18 +28,41 @@ __device__ inline double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// partial[blk * stride + i] = sum over the block's range of V_i . w
+// partial[blk * stride + i] = sum over the block's range of V_i . w.  The basis
+// vectors are taken MDG at a time: per element w is read once and MDG independent
+// loads are in flight, and one block reduction serves the whole group.
+constexpr int MDG = 8;
 __global__ void k_multidot_partial(const double* __restrict__ V, int nvec, long n,
                                    const double* __restrict__ w, double* partial, int stride) {
-  __shared__ double sh[32];
-  long per = (n + gridDim.x - 1) / gridDim.x;
-  long lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
-  for (int i = 0; i < nvec; ++i) {
-    const double* v = V + (size_t)i * n;
-    double s = 0.0;
-    for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) s += v[e] * w[e];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * stride + i] = s;
+  __shared__ double sh[32][MDG];  // [warp][vector of the group]
+  const long per = (n + gridDim.x - 1) / gridDim.x;
+  const long lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < nvec; i0 += MDG) {
+    const int nv = nvec - i0 < MDG ? nvec - i0 : MDG;
+    const double* v0 = V + (size_t)i0 * n;
+    double acc[MDG];
+#pragma unroll
+    for (int q = 0; q < MDG; ++q) acc[q] = 0.0;
+    for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+      const double we = w[e];
+#pragma unroll
+      for (int q = 0; q < MDG; ++q)
+        if (q < nv) acc[q] += __ldcs(v0 + (size_t)q * n + e) * we;
+    }
+#pragma unroll
+    for (int q = 0; q < MDG; ++q)
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < MDG; ++q) sh[wid][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < nv) {
+      double s = 0.0;
+      for (int q = 0; q < nw; ++q) s += sh[q][threadIdx.x];
+      partial[(size_t)blockIdx.x * stride + i0 + threadIdx.x] = s;
+    }
+    __syncthreads();
   }
 }
 
@@ -59,7 +85,8 @@ __global__ void k_multiaxpy(const double* __restrict__ V, int nvec, long n,
   long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
   double s = w[e];
-  for (int i = 0; i < nvec; ++i) s -= c[i] * V[(size_t)i * n + e];
+#pragma unroll 8
+  for (int i = 0; i < nvec; ++i) s -= c[i] * __ldcs(V + (size_t)i * n + e);
   w[e] = s;
 }
 
@@ -121,7 +148,8 @@ __global__ void k_update_x(const T* __restrict__ Z, int k, long n, const double*
   long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
   double s = x[e];
-  for (int i = 0; i < k; ++i) s += c[i] * (double)Z[(size_t)i * n + e];
+#pragma unroll 8
+  for (int i = 0; i < k; ++i) s += c[i] * (double)__ldcs(Z + (size_t)i * n + e);
   x[e] = s;
 }
 
