@@ -176,8 +176,10 @@ IB_API int ib_tail_grid(const ib_problem* prob, int32_t precision);
 
 /* Levels with at least IB_BOX_GEMM_MIN boxes per colour (environment variable,
  * default 2048) solve their n x n boxes (n = 2, 4) with a register-blocked kernel
- * that treats the free boxes of a CTA as one small matrix product; smaller levels
- * use one thread per box row.  Read at ib_setup. */
+ * that treats the free boxes of a CTA as one small matrix product; levels with at
+ * most IB_BOX_ONE_MAX (default 512) give each box its own CTA with its inverse in
+ * shared memory; the levels between use one thread per box row, several boxes per
+ * CTA.  Both read at ib_setup. */
 
 /* Number of structure boxes (boxes whose block includes elasticity) on a level,
  * as found by the last set-up. */

@@ -741,6 +741,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   st = setup_hierarchy(P);
   if (st != IB_OK) return fail_free(st);
   if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
+  if (const char* e = std::getenv("IB_BOX_ONE_MAX")) P.box_one_max = std::atol(e);
   P.has32 = params->precision == IB_FP32_PRECOND;
   P.has64 = params->precision != IB_FP32_PRECOND || params->escalate != 0;
   if (P.has32) {

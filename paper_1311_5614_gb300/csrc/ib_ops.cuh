@@ -134,33 +134,113 @@ __device__ __forceinline__ void JU_point(const Springs<T>& sp, const T* U, int k
   *gy = ay;
 }
 
-// Force term of point k, coef * (J S*_l w)_k, by an aligned quad of lanes (j =
-// lane & 3, qmask the quad's lanes).  Lane 0 interpolates the point's own
+// Whether velocity row (comp, i, j) of a level with b x b boxes is an unknown of
+// a box of colour `color` (-1: any).  A face on the low edge of its box is also
+// the far-edge unknown of the neighbouring box, whose colour parity differs.
+__device__ __forceinline__ bool row_in_color(int comp, int i, int j, int b, int color) {
+  if (color < 0) return true;
+  const int cx = (i / b) & 1, cy = ((j / b) & 1) << 1;
+  if ((cx | cy) == color) return true;
+  if (comp == 0 && i % b == 0) return ((cx ^ 1) | cy) == color;
+  if (comp == 1 && j % b == 0) return (cx | (cy ^ 2)) == color;
+  return false;
+}
+
+// Programmatic dependent launch entry: wait until the grids this kernel depends
+// on have completed (their results visible), then let the next kernel of the
+// stream begin launching.  Only set-up data may be read before it.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Interpolation patch (kind 1) of one component of one point: bases and weights.
+template <typename T>
+struct IPatch {
+  int x0, y0;
+  T wx[PATCH], wy[PATCH];
+};
+
+template <typename T>
+__device__ __forceinline__ IPatch<T> load_ipatch(const Patches<T>& pat, int comp, int k) {
+  IPatch<T> p;
+  p.x0 = pat.b_at(1, comp, 0, k);
+  p.y0 = pat.b_at(1, comp, 1, k);
+#pragma unroll
+  for (int a = 0; a < PATCH; ++a) {
+    p.wx[a] = pat.w_at(1, comp, 0, a, k);
+    p.wy[a] = pat.w_at(1, comp, 1, a, k);
+  }
+  return p;
+}
+
+// sum over the patch of wc * wx * wy (wc: one component of a level vector)
+template <typename T>
+__device__ __forceinline__ T interp_ip(const IPatch<T>& p, const T* wc, int N) {
+  const int m = N - 1;
+  T s = 0;
+#pragma unroll
+  for (int bb = 0; bb < PATCH; ++bb) {
+    const T* row = wc + ((p.y0 + bb) & m) * N;
+    T sx = 0;
+#pragma unroll
+    for (int a = 0; a < PATCH; ++a) sx += p.wx[a] * row[(p.x0 + a) & m];
+    s += p.wy[bb] * sx;
+  }
+  return s;
+}
+
+// rE += coef * S_l J S*_l w restricted to the rows of boxes of one colour (-1:
+// all rows), for point k by an aligned quad of lanes (j = lane & 3, qmask the
+// quad's lanes, qlane0 its first lane).  Lane 0 interpolates the point's own
 // velocity, lanes 1..3 those of its first three spring neighbours (further ones
 // round robin), all at the same time; the spring terms K_s (U_other - U_k) are
-// then summed over the quad.  Every lane of the quad must call this; the result
-// is valid in lane j == 0.
-template <typename T>
-__device__ __forceinline__ void force_quad(const Patches<T>& pat, const Springs<T>& sp, const T* w, int N, T coef,
-                                           int k, int j, unsigned qmask, int qlane0, T* gx, T* gy) {
+// summed over the quad; then lane j spreads component j & 1 over patch rows
+// 2 (j >> 1) and 2 (j >> 1) + 1 with atomic additions.  Adjacency, spring
+// blocks and both patches are loaded first; with WAIT the kernel's
+// programmatic-launch wait comes after them, so that only the loads of w depend
+// on the previous kernel.  Every lane of the quad must call this.
+template <typename T, bool WAIT>
+__device__ __forceinline__ void force_spread_quad(const Patches<T>& pat, const Springs<T>& sp, const T* w, int N,
+                                                  T coef, int k, int j, unsigned qmask, int qlane0, int b, int color,
+                                                  T* rE) {
   const int p0 = sp.adj_ptr[k], deg = sp.adj_ptr[k + 1] - p0, ns = sp.ns;
-  T ux = 0, uy = 0;
-  int o = -1, s = -1;
+  int pid = -1, s = -1;
   if (j == 0) {
-    ux = interp_point(pat, w, N, 0, k);
-    uy = interp_point(pat, w, N, 1, k);
+    pid = k;
   } else if (j - 1 < deg) {
-    o = sp.adj_other[p0 + j - 1];
+    pid = sp.adj_other[p0 + j - 1];
     s = sp.adj_spring[p0 + j - 1];
-    ux = interp_point(pat, w, N, 0, o);
-    uy = interp_point(pat, w, N, 1, o);
+  }
+  IPatch<T> pu, pv;
+  if (pid >= 0) {
+    pu = load_ipatch(pat, 0, pid);
+    pv = load_ipatch(pat, 1, pid);
+  }
+  T kxx = 0, kxy = 0, kyy = 0;
+  if (s >= 0) {
+    kxx = sp.K[s];
+    kxy = sp.K[ns + s];
+    kyy = sp.K[2 * ns + s];
+  }
+  const int comp = j & 1, r0 = 2 * (j >> 1);
+  const int sx0 = pat.b_at(0, comp, 0, k), sy0 = pat.b_at(0, comp, 1, k);
+  T swx[PATCH], swy[2];
+#pragma unroll
+  for (int a = 0; a < PATCH; ++a) swx[a] = pat.w_at(0, comp, 0, a, k);
+  swy[0] = pat.w_at(0, comp, 1, r0, k);
+  swy[1] = pat.w_at(0, comp, 1, r0 + 1, k);
+  if (WAIT) pdl_enter();
+  T ux = 0, uy = 0;
+  if (pid >= 0) {
+    ux = interp_ip(pu, w, N);
+    uy = interp_ip(pv, w + (size_t)N * N, N);
   }
   const T ux0 = __shfl_sync(qmask, ux, qlane0);
   const T uy0 = __shfl_sync(qmask, uy, qlane0);
   T ax = 0, ay = 0;
   if (s >= 0) {
     const T dx = ux - ux0, dy = uy - uy0;
-    const T kxx = sp.K[s], kxy = sp.K[ns + s], kyy = sp.K[2 * ns + s];
     ax = kxx * dx + kxy * dy;
     ay = kxy * dx + kyy * dy;
     for (int m = j + 2; m < deg; m += 3) {
@@ -175,51 +255,19 @@ __device__ __forceinline__ void force_quad(const Patches<T>& pat, const Springs<
   ay += __shfl_xor_sync(qmask, ay, 1);
   ax += __shfl_xor_sync(qmask, ax, 2);
   ay += __shfl_xor_sync(qmask, ay, 2);
-  *gx = coef * ax;
-  *gy = coef * ay;
-}
-
-// Whether velocity row (comp, i, j) of a level with b x b boxes is an unknown of
-// a box of colour `color` (-1: any).  A face on the low edge of its box is also
-// the far-edge unknown of the neighbouring box, whose colour parity differs.
-__device__ __forceinline__ bool row_in_color(int comp, int i, int j, int b, int color) {
-  if (color < 0) return true;
-  const int cx = (i / b) & 1, cy = ((j / b) & 1) << 1;
-  if ((cx | cy) == color) return true;
-  if (comp == 0 && i % b == 0) return ((cx ^ 1) | cy) == color;
-  if (comp == 1 && j % b == 0) return (cx | (cy ^ 2)) == color;
-  return false;
-}
-
-// rE += coef * S_l J S*_l w restricted to the rows of boxes of one colour (-1:
-// all rows), for point k by an aligned quad of lanes: the force (force_quad),
-// then lane j spreads component j & 1 over patch rows 2 (j >> 1) and
-// 2 (j >> 1) + 1 with atomic additions.  Every lane of the quad must call this.
-template <typename T>
-__device__ __forceinline__ void force_spread_quad(const Patches<T>& pat, const Springs<T>& sp, const T* w, int N,
-                                                  T coef, int k, int j, unsigned qmask, int qlane0, int b, int color,
-                                                  T* rE) {
-  T gx, gy;
-  force_quad(pat, sp, w, N, coef, k, j, qmask, qlane0, &gx, &gy);
-  gx = __shfl_sync(qmask, gx, qlane0);
-  gy = __shfl_sync(qmask, gy, qlane0);
-  const int comp = j & 1;
-  const T g = comp ? gy : gx;
+  const T g = coef * (comp ? ay : ax);  // the quad sum is in every lane
   if (g == (T)0) return;
   const int m = N - 1;
-  const int x0 = pat.b_at(0, comp, 0, k), y0 = pat.b_at(0, comp, 1, k);
   T* yc = rE + (size_t)comp * N * N;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int bb = 2 * (j >> 1) + r;
-    const T wy = pat.w_at(0, comp, 1, bb, k) * g;
+    const T wy = swy[r] * g;
     if (wy == (T)0) continue;
-    const int jj = (y0 + bb) & m;
+    const int jj = (sy0 + r0 + r) & m;
 #pragma unroll
     for (int a = 0; a < PATCH; ++a) {
-      const T wx = pat.w_at(0, comp, 0, a, k);
-      const int ii = (x0 + a) & m;
-      if (wx != (T)0 && row_in_color(comp, ii, jj, b, color)) atomicAdd(&yc[jj * N + ii], wx * wy);
+      const int ii = (sx0 + a) & m;
+      if (swx[a] != (T)0 && row_in_color(comp, ii, jj, b, color)) atomicAdd(&yc[jj * N + ii], swx[a] * wy);
     }
   }
 }

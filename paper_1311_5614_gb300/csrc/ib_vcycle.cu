@@ -34,6 +34,37 @@ constexpr int kSeq[4] = {0, 3, 1, 2};  // forward colour sequence (host)
 __device__ __forceinline__ int seq_color(int cc) { return cc == 0 ? 0 : (cc == 1 ? 3 : (cc == 2 ? 1 : 2)); }
 constexpr int TAIL_THREADS = 1024;
 
+// Programmatic dependent launch.  Every V-cycle kernel is launched with
+// programmatic stream serialisation and calls pdl_enter() (ib_ops.cuh) before it
+// reads anything an earlier V-cycle kernel writes, so that its launch, ramp-up
+// and set-up-data loads overlap the previous kernel.
+
+template <typename... KArgs, typename... Args>
+void vlaunch(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+             Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// PDL inside the captured graph only (eager and profiled launches are plain);
+// the environment variable IB_PDL=0 turns it off.
+bool use_pdl(const Problem& P) {
+  static const bool on = [] {
+    const char* e = std::getenv("IB_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on && P.use_graph && !P.prof;
+}
+
 template <typename T>
 StokesCoef<T> coefs(const Problem& P, int l) {
   double h = P.lev[l].h;
@@ -104,7 +135,7 @@ __global__ void kv_force_spread(Patches<T> pat, Springs<T> sp, const T* __restri
   const int k = (int)(t >> 2), j = (int)(t & 3);
   if (k >= sp.np) return;  // whole quads: blockDim is a multiple of 4
   const int lane = threadIdx.x & 31;
-  force_spread_quad(pat, sp, w, N, coef, k, j, 0xFu << (lane & ~3), lane & ~3, b, color, rE);
+  force_spread_quad<T, true>(pat, sp, w, N, coef, k, j, 0xFu << (lane & ~3), lane & ~3, b, color, rE);
 }
 
 // n x n boxes (n >= 2) of one colour, residual inline (Stokes stencil plus rE on
@@ -142,7 +173,8 @@ __global__ void __launch_bounds__(BoxShape<BS, BPC>::THREADS) kv_boxn(T* w, cons
   __shared__ T rs[S::BPC][NB];
   const int tid = threadIdx.x;
   if (S::SMEM_MF)
-    for (int e = tid; e < NB * NB; e += S::THREADS) sMf[e] = Mf[e];
+    for (int e = tid; e < NB * NB; e += S::THREADS) sMf[e] = Mf[e];  // set-up data
+  pdl_enter();
   const int lb = tid / S::TPBOX, q = tid - lb * S::TPBOX;
   const int nb = N / BS, half = nb >> 1;
   const int t = blockIdx.x * S::BPC + lb;
@@ -175,6 +207,59 @@ __global__ void __launch_bounds__(BoxShape<BS, BPC>::THREADS) kv_boxn(T* w, cons
     TM d = 0;
 #pragma unroll 8
     for (int s = 0; s < NB; ++s) d += M[s * NB] * (TM)rs[lb][s];
+    w[gq] += (T)d;
+  }
+}
+
+// One box per CTA (small levels, n <= 4): the box's inverse, its FP64 structure
+// inverse or the shared free-box inverse, is staged in shared memory before the
+// programmatic-launch wait (set-up data), so the product reads shared memory.
+template <typename T, typename TM, int BS>
+__global__ void __launch_bounds__(BoxShape<BS, 1>::TPBOX) kv_boxs(T* w, const T* __restrict__ b, T* rE, int N,
+                                                                 StokesCoef<T> c, int color,
+                                                                 const int* __restrict__ slot,
+                                                                 const double* __restrict__ Ms,
+                                                                 const TM* __restrict__ Mf) {
+  using S = BoxShape<BS, 1>;
+  constexpr int NB = S::NB, NV = 2 * BS * (BS + 1);
+  __shared__ __align__(16) double sM[NB * NB];
+  __shared__ T rs[NB];
+  const int q = threadIdx.x;
+  const int nb = N / BS, half = nb >> 1, t = blockIdx.x;
+  const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+  const int sl = slot[J * nb + I];
+  if (sl >= 0) {
+    const double* M = Ms + (size_t)sl * NB * NB;
+    for (int e = q; e < NB * NB; e += S::TPBOX) sM[e] = M[e];
+  } else {
+    TM* sf = reinterpret_cast<TM*>(sM);
+    for (int e = q; e < NB * NB; e += S::TPBOX) sf[e] = Mf[e];
+  }
+  pdl_enter();
+  int gq = 0;
+  if (q < NB) {
+    int cc, i, j;
+    box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
+    gq = cc * N * N + j * N + i;
+    T r = b[gq] - stokes_row(w, N, c, cc, i, j);
+    if (rE && sl >= 0 && q < NV) {
+      r += rE[gq];
+      rE[gq] = (T)0;
+    }
+    rs[q] = r;
+  }
+  __syncthreads();
+  if (q >= NB) return;
+  if (sl >= 0) {
+    double d = 0.0;
+#pragma unroll 8
+    for (int s2 = 0; s2 < NB; ++s2) d += sM[s2 * NB + q] * (double)rs[s2];
+    w[gq] += (T)d;
+  } else {
+    const TM* sf = reinterpret_cast<const TM*>(sM);
+    TM d = 0;
+#pragma unroll 8
+    for (int s2 = 0; s2 < NB; ++s2) d += sf[s2 * NB + q] * (TM)rs[s2];
     w[gq] += (T)d;
   }
 }
@@ -222,7 +307,8 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
   const int tid = threadIdx.x;
   const int nb = N / BS, half = nb >> 1, nbox = half * half;
   const int box0 = blockIdx.x * G::BPC;
-  for (int e = tid; e < NB * NB; e += G::THREADS) sMf[e] = Mf[e];
+  for (int e = tid; e < NB * NB; e += G::THREADS) sMf[e] = Mf[e];  // set-up data
+  pdl_enter();
   if (tid < G::BPC) {
     const int t = box0 + tid;
     int sl = -2;  // -2: no box
@@ -319,26 +405,29 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const TM* Mf = Mfree_of<TM>(L);
   // the GEMM form pays off on large levels, one box per CTA on small ones
   const bool gemm = nbox >= P.box_gemm_min;
-  const bool one = nbox <= 512;
-#define IB_BOXN(BS_, BPC_)                                                                              \
-  kv_boxn<T, TM, BS_, BPC_><<<nblk(nbox, BPC_), BoxShape<BS_, BPC_>::THREADS, 0, P.stream>>>(w, b, E, L.N, c, \
-                                                                                           color, L.flag, Ms, Mf)
+  const bool one = nbox <= P.box_one_max;
+  const bool pdl = use_pdl(P);
+#define IB_BOXN(BS_, BPC_)                                                                                    \
+  vlaunch(pdl, kv_boxn<T, TM, BS_, BPC_>, nblk(nbox, BPC_), BoxShape<BS_, BPC_>::THREADS, 0, P.stream, w, b, E, \
+          L.N, c, color, L.flag, Ms, Mf)
   switch (P.prm.box) {
     case 2:
       if (gemm)
-        kv_boxg<T, TM, 2><<<nblk(nbox, BoxGemm<TM, 2>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag,
-                                                                               Ms, Mf);
+        vlaunch(pdl, kv_boxg<T, TM, 2>, nblk(nbox, BoxGemm<TM, 2>::BPC), 128, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
       else if (one)
-        IB_BOXN(2, 1);
+        vlaunch(pdl, kv_boxs<T, TM, 2>, (int)nbox, BoxShape<2, 1>::TPBOX, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
       else
         IB_BOXN(2, 8);
       break;
     case 4:
       if (gemm)
-        kv_boxg<T, TM, 4><<<nblk(nbox, BoxGemm<TM, 4>::BPC), 128, 0, P.stream>>>(w, b, E, L.N, c, color, L.flag,
-                                                                               Ms, Mf);
+        vlaunch(pdl, kv_boxg<T, TM, 4>, nblk(nbox, BoxGemm<TM, 4>::BPC), 128, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
       else if (one)
-        IB_BOXN(4, 1);
+        vlaunch(pdl, kv_boxs<T, TM, 4>, (int)nbox, BoxShape<4, 1>::TPBOX, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
       else
         IB_BOXN(4, 4);
       break;
@@ -356,6 +445,7 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
 template <typename T>
 __global__ void kv_colres1(const T* __restrict__ w, const T* __restrict__ b, T* rE, T* __restrict__ r, int N,
                            StokesCoef<T> c, int color, const int* __restrict__ slot) {
+  pdl_enter();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int half = N >> 1;
   if (t >= half * half) return;
@@ -381,6 +471,7 @@ template <typename T, typename TM>
 __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int color,
                         const int* __restrict__ slot, const double* __restrict__ Ms,
                         const TM* __restrict__ Mf) {
+  pdl_enter();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int half = N >> 1;
   if (t >= half * half) return;
@@ -399,6 +490,7 @@ __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int c
 template <typename T>
 __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, const T* __restrict__ rE,
                           T* __restrict__ bc, int Nc, StokesCoef<T> c) {
+  pdl_enter();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int nc = Nc * Nc;
   if (idx >= nc) return;
@@ -412,6 +504,7 @@ __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, cons
 // w += P e; also clears rE (the restriction's elasticity term; may be NULL).
 template <typename T>
 __global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N, T* __restrict__ rE) {
+  pdl_enter();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int n = N * N;
   if (idx >= n) return;
@@ -428,6 +521,7 @@ __global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N, 
 
 template <typename T>
 __global__ void kv_zero(T* x, long n) {
+  pdl_enter();
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) x[i] = (T)0;
 }
@@ -443,7 +537,8 @@ __device__ void tail_elastic(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A
   __syncthreads();
   // 4 np is a multiple of 4: the four lanes of a quad run the same iterations
   for (int t = threadIdx.x; t < 4 * np; t += blockDim.x)
-    force_spread_quad(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box, -1, r);
+    force_spread_quad<T, false>(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box,
+                                -1, r);
   __syncthreads();
 }
 
@@ -526,6 +621,7 @@ __device__ void tail_sweep(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, 
 
 template <typename T, typename TM>
 __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T, TM> A) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem[];
   T* W[MAX_LEVELS];
   T* B[MAX_LEVELS];
@@ -659,9 +755,8 @@ int fine_elastic(Problem& P, int l, const T* w, int color) {
   // FP64: small CTAs so that the interpolation FMAs spread over many SMs (the FP64
   // pipe is narrow); FP32: the usual block size (a multiple of 4 either way)
   const int tpb = sizeof(T) == 8 ? 64 : TPB;
-  kv_force_spread<T><<<nblk(4L * P.np, tpb), tpb, 0, P.stream>>>(pats<T>(L), sview<T>(P), w, L.N,
-                                                            (T)(-P.prm.dt / (P.lev[0].h * P.lev[0].h)),
-                                                            P.prm.box, color, rEbuf<T>(L));
+  vlaunch(use_pdl(P), kv_force_spread<T>, nblk(4L * P.np, tpb), tpb, 0, P.stream, pats<T>(L), sview<T>(P), w,
+          L.N, (T)(-P.prm.dt / (P.lev[0].h * P.lev[0].h)), P.prm.box, color, rEbuf<T>(L));
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
@@ -687,11 +782,12 @@ int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
     if (bs == 1) {
       {
         KScope ks(P, IB_KC_STOKES, nbox * 5.0 * (6 * sT + 2 * sT) + e_bytes);
-        kv_colres1<T><<<nblk(nbox), TPB, 0, P.stream>>>(B.w, B.b, E, B.r, N, c, color, L.flag);
+        vlaunch(use_pdl(P), kv_colres1<T>, nblk(nbox), TPB, 0, P.stream, B.w, B.b, E, B.r, N, c, color, L.flag);
         IB_LAUNCH_CHECK();
       }
       KScope ks(P, IB_KC_BOX, nbox * (15.0 * sT + 4) + 0.25 * L.n_struct * 25 * sT + 25 * sT);
-      kv_box1<T, TM><<<nblk(nbox), TPB, 0, P.stream>>>(B.r, B.w, N, color, L.flag, L.Mstruct, Mfree_of<TM>(L));
+      vlaunch(use_pdl(P), kv_box1<T, TM>, nblk(nbox), TPB, 0, P.stream, B.r, B.w, N, color, L.flag, L.Mstruct,
+              Mfree_of<TM>(L));
       IB_LAUNCH_CHECK();
     } else {
       // per box: its unknowns' rows read w (5-point stencils, counted once per
@@ -717,7 +813,7 @@ int vcycle_eager_t(Problem& P) {
     const long n3 = 3L * L.N * L.N;
     {
       KScope ks(P, IB_KC_OTHER, n3 * sizeof(T));
-      kv_zero<T><<<nblk(n3), TPB, 0, P.stream>>>(B.w, n3);
+      vlaunch(use_pdl(P), kv_zero<T>, nblk(n3), TPB, 0, P.stream, B.w, n3);
       IB_LAUNCH_CHECK();
     }
     for (int s = 0; s < P.prm.nu1; ++s) IB_TRY((fine_sweep<T, TM>(P, l, false, s == 0)));
@@ -728,8 +824,8 @@ int vcycle_eager_t(Problem& P) {
       // w read once per stencil (9 fine values per coarse cell incl. the halo), b, rE
       const double e_bytes = has_E ? 2.0 * L.N * L.N * sizeof(T) : 0.0;
       KScope ks(P, IB_KC_TRANSFER, (9.0 * L.N * L.N + 3.0 * Nc * Nc) * sizeof(T) + e_bytes);
-      kv_resres<T><<<nblk((long)Nc * Nc), TPB, 0, P.stream>>>(B.w, B.b, E, lbuf<T>(P.lev[l + 1]).b, Nc,
-                                                             coefs<T>(P, l));
+      vlaunch(use_pdl(P), kv_resres<T>, nblk((long)Nc * Nc), TPB, 0, P.stream, B.w, B.b, E,
+              lbuf<T>(P.lev[l + 1]).b, Nc, coefs<T>(P, l));
       IB_LAUNCH_CHECK();
     }
   }
@@ -738,7 +834,7 @@ int vcycle_eager_t(Problem& P) {
     size_t smem = 0;
     IB_TRY((build_tail_args<T, TM>(P, lt, &A, &smem)));
     KScope ks(P, IB_KC_COARSE, 0.0);
-    kv_tail<T, TM><<<1, TAIL_THREADS, smem, P.stream>>>(A);
+    vlaunch(use_pdl(P), kv_tail<T, TM>, 1, TAIL_THREADS, smem, P.stream, A);
     IB_LAUNCH_CHECK();
   }
   for (int l = lt - 1; l >= 0; --l) {
@@ -747,8 +843,8 @@ int vcycle_eager_t(Problem& P) {
     {
       const double e_bytes = has_E ? 2.0 * L.N * L.N * sizeof(T) : 0.0;
       KScope ks(P, IB_KC_TRANSFER, (6.0 * L.N * L.N + 0.75 * L.N * L.N) * sizeof(T) + e_bytes);
-      kv_prolong<T><<<nblk((long)L.N * L.N), TPB, 0, P.stream>>>(lbuf<T>(P.lev[l + 1]).w, B.w, L.N,
-                                                                 has_E ? rEbuf<T>(L) : nullptr);
+      vlaunch(use_pdl(P), kv_prolong<T>, nblk((long)L.N * L.N), TPB, 0, P.stream,
+              (const T*)lbuf<T>(P.lev[l + 1]).w, B.w, L.N, has_E ? rEbuf<T>(L) : (T*)nullptr);
       IB_LAUNCH_CHECK();
     }
     for (int s = 0; s < P.prm.nu2; ++s) IB_TRY((fine_sweep<T, TM>(P, l, P.prm.box == 1, false)));

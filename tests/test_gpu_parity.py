@@ -123,6 +123,13 @@ def test_vcycle_fp64_gemm_box_kernel(pkg, name, box, monkeypatch):
     test_vcycle_fp64(pkg, name, box)
 
 
+@pytest.mark.parametrize("name,box", [("c1_64", 2), ("c1_64", 4), ("stiff_32_exact", 4)])
+def test_vcycle_fp64_multi_box_cta(pkg, name, box, monkeypatch):
+    """The several-boxes-per-CTA kernel (used on mid-size levels) forced on every level."""
+    monkeypatch.setenv("IB_BOX_ONE_MAX", "0")
+    test_vcycle_fp64(pkg, name, box)
+
+
 @pytest.mark.parametrize("name,box", [("c1_64", 1), ("stiff_32_exact", 4)])
 def test_vcycle_fp32(pkg, name, box):
     p = make_case(name, box)
