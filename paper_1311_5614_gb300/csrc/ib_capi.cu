@@ -385,8 +385,9 @@ int learned_step(Problem& P, const double* vj, T* zj, double* z64, ib_stats* st,
 // residual estimate of iteration j - 1 is read, so the device never waits for
 // the host between iterations.  When j - 1 turns out to be the last one, the
 // work of iteration j is discarded: it only touched column j of H, g[j], g[j+1],
-// V[j+1] and Z[j], none of which the update with k = j directions reads.
-// Decisions taken from iteration j - 1 (escalation) apply from iteration j + 1.
+// V[j+1] and Z[j], none of which the update with k = j directions reads.  An
+// escalation to the mixed V-cycle also ends the cycle: FGMRES restarts from the
+// iterate, so a cycle's directions are all FP32 (Z) or all FP64 (Z64).
 template <typename T>
 int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
   const size_t n = 3ul * P.prm.N * P.prm.N;
@@ -445,7 +446,9 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     int k = 0;
     bool stopped = false;
     // Reads the scalars of iteration jj (waiting for them): 1 = stop after jj
-    // (converged or lucky breakdown), 0 = continue, -1 = non-finite or CUDA error.
+    // (converged, lucky breakdown, or escalation: the cycle ends and FGMRES restarts
+    // from the iterate with the mixed V-cycle and a fresh basis), 0 = continue,
+    // -1 = non-finite or CUDA error.
     auto check = [&](int jj) -> int {
       if (cudaEventSynchronize(P.pev[jj & 1]) != cudaSuccess) return -1;
       const double* h = P.scal_host + 24 + 4 * (jj & 1);
@@ -454,14 +457,15 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       if (h[2] != 0.0) return -1;
       if (est <= tol * bnorm) return 1;
       hist.push_back(est);
-      // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
-      // the last 4 iterations -> precondition with the mixed-precision V-cycle
-      // (FP64 residuals, which the stiff cancellation needs) from the next
-      // iteration not yet launched (jj + 2) on
-      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 4 &&
-          est > 0.5 * hist[hist.size() - 5])
-        st->escalated_at = cycle_start + jj + 2;
       if (!(h[1] > 0.0)) return 1;  // lucky breakdown: exact solution in the space
+      // stagnation of the FP32-preconditioned iteration: less than a factor 2 in
+      // the last 4 iterations -> restart with the mixed-precision V-cycle (FP64
+      // residuals, which the stiff cancellation needs)
+      if (!std::is_same<T, double>::value && P.has64 && st->escalated_at < 0 && hist.size() > 4 &&
+          est > 0.5 * hist[hist.size() - 5]) {
+        st->escalated_at = cycle_start + jj + 1;
+        return 1;
+      }
       return 0;
     };
     for (int j = 0; j < mav; ++j) {
@@ -516,7 +520,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
         if (rc < 0) return P.scal_host[24 + 4 * ((j - 1) & 1) + 2] != 0.0
                                ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
                                : fail(IB_ERR_CUDA, "FGMRES pipeline");
-        if (rc == 1) {  // iteration j - 1 was the last: drop iteration j
+        if (rc == 1) {  // iteration j - 1 was the last of the cycle: drop iteration j
           k = j;
           --total;
           stopped = true;
@@ -534,7 +538,8 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     if constexpr (std::is_same<T, double>::value) {
       IB_TRY(launch_update_x<T>(P, Z, k, x));
     } else {
-      // directions j < e are FP32 (Z), j >= e FP64 (Z64), e = escalation point in this cycle
+      // directions j < e are FP32 (Z), j >= e FP64 (Z64); e = k in the cycle that
+      // escalates, 0 in the cycles after it
       int e = k;
       if (st->escalated_at >= 0) e = std::max(0, std::min(k, st->escalated_at - cycle_start));
       IB_TRY(launch_update_x<float>(P, Z, e, x, 0));

@@ -172,11 +172,20 @@ __global__ void __launch_bounds__(BoxShape<BS, BPC>::THREADS) kv_boxn(T* w, cons
   __shared__ TM sMf[S::SMEM_MF ? NB * NB : 1];
   __shared__ T rs[S::BPC][NB];
   const int tid = threadIdx.x;
+  const int nb = N / BS, half = nb >> 1;
   if (S::SMEM_MF)
     for (int e = tid; e < NB * NB; e += S::THREADS) sMf[e] = Mf[e];  // set-up data
+  // set-up data too: pull the FP64 inverses of this CTA's structure boxes towards L1
+  for (int l2 = 0; l2 < S::BPC; ++l2) {
+    const int t2 = blockIdx.x * S::BPC + l2;
+    if (t2 >= half * half) break;
+    const int s2 = slot[(2 * (t2 / half) + (color >> 1)) * nb + 2 * (t2 % half) + (color & 1)];
+    if (s2 < 0) continue;
+    const double* M2 = Ms + (size_t)s2 * NB * NB;
+    for (int e = tid * 16; e < NB * NB; e += S::THREADS * 16) asm volatile("prefetch.global.L1 [%0];" ::"l"(M2 + e));
+  }
   pdl_enter();
   const int lb = tid / S::TPBOX, q = tid - lb * S::TPBOX;
-  const int nb = N / BS, half = nb >> 1;
   const int t = blockIdx.x * S::BPC + lb;
   const bool valid = t < half * half && q < NB;
   int gq = 0, sl = -1;
