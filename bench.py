@@ -43,8 +43,8 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # dominant kernel classes, averaged over every launch of one profiled sweep step
 # (sequential form, FP32 with escalation) in one ncu capture.  Valid only for the
 # V-cycle kernel sources it was taken on: reported as null once they change.
-TRAFFIC = {"sources_sha256": "e8a9969f3248f6cc794345db8907800b141f77d2a1ed347505c4d0696bec168d",
-           "box": 803444.0, "spread": 221742.0}
+TRAFFIC = {"sources_sha256": "e9adc53a207c087dfdb1a87c2da4a12239b730797661ad8da38679272b44f849",
+           "box": 867090.0, "spread": 211613.0}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh"]
 
 
