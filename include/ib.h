@@ -126,7 +126,7 @@ IB_API void ib_default_params(ib_params* p);
  *   stream   a cudaStream_t (NULL = legacy default stream) used by every later call
  * n_points may be 0 (no structure; then n_springs must be 0).  The spring
  * force law is F_i += kappa (1 - L0 / |d|) d with d = X_j - X_i (minimum image),
- * the discrete tension law of sec. 2.2 generalised to rest length (sec. 7).
+ * the discrete tension law of sec. 2.2 generalised to rest length (sec. 8).
  * On success *out receives the handle; on failure *out is NULL. */
 IB_API int ib_setup(const ib_params* params, int32_t n_points, const double* X,
              int32_t n_springs, const int32_t* springs, const double* kappa,

@@ -1,6 +1,6 @@
 // Lagrangian-point kernels: regularised delta weights, spreading S and
 // interpolation S^* (sec. 2.2), spring force and Jacobian (sec. 2.2 force law,
-// sec. 7 linearisation), the elasticity term dt * S J S^* on every level with
+// sec. 8 linearisation), the elasticity term dt * S J S^* on every level with
 // Galerkin-coarsened patches (sec. 3.2), and its contribution to the box and
 // coarsest-level matrices.
 #include <cmath>
