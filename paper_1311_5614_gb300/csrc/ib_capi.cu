@@ -165,8 +165,11 @@ int setup_hierarchy(Problem& P) {
     if (!P.free_ready) IB_TRY(launch_free_box(P, l));
     IB_TRY(launch_struct_fill(P, l));
     IB_TRY(launch_assemble_struct(P, l));
-    IB_TRY(launch_invert(P, L.Mstruct, nB, cnt));
   }
+  bool all_done = false;
+  IB_TRY(launch_invert_struct_all(P, &all_done));
+  if (!all_done)
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_struct));
   P.free_ready = true;
   IB_TRY(launch_coarse_fill(P));
   IB_TRY(launch_assemble_coarse(P));

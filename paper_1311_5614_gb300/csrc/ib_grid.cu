@@ -3,6 +3,7 @@
 // big-box smoother solves (secs. 5-6), dense box / coarsest-level matrices and
 // their Gauss-Jordan inverses, and the exact coarsest solve (Algorithm 1).
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "ib_internal.cuh"
@@ -168,6 +169,103 @@ __device__ void gj_invert(double* M, int n, int* err) {
 // One matrix per CTA, worked on in global memory (large n).
 __global__ void k_invert(double* Ms, int n, int* err) { gj_invert(Ms + (size_t)blockIdx.x * n * n, n, err); }
 
+// Gauss-Jordan with partial pivoting on a matrix in shared memory, organised for
+// the rank-1 update: thread t owns column t % n for the rows congruent to t / n
+// modulo R = blockDim / n (blockDim >= n), so the update needs no index division and the pivot
+// column is written in the same pass (M[i][k] = -f_i / pivot).
+__device__ void gj_invert_cols(double* M, int n, int* err) {
+  __shared__ double f[INV_MAXN];
+  __shared__ int perm[INV_MAXN];
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int prow;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = (bd + 31) >> 5;
+  const int R = bd / n > 0 ? bd / n : 1;
+  const int jc = tid % n, r0 = tid / n;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += bd) {
+      const double a = fabs(M[i * n + k]);
+      if (a > best) { best = a; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b0 = rv[0];
+      int i0 = ri[0];
+      for (int q = 1; q < nw; ++q)
+        if (rv[q] > b0 || (rv[q] == b0 && ri[q] < i0)) { b0 = rv[q]; i0 = ri[q]; }
+      if (i0 >= n) i0 = k;
+      prow = i0;
+      perm[k] = i0;
+    }
+    __syncthreads();
+    const int p = prow;
+    if (p != k)
+      for (int j = tid; j < n; j += bd) {
+        const double t = M[k * n + j];
+        M[k * n + j] = M[p * n + j];
+        M[p * n + j] = t;
+      }
+    __syncthreads();
+    double piv = M[k * n + k];
+    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+      if (tid == 0) atomicOr(err, DEV_ERR_SINGULAR);
+      piv = 1.0;
+    }
+    const double inv = 1.0 / piv;
+    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[i * n + k];
+    __syncthreads();
+    // row k scaled (its pivot entry becomes 1/pivot); other rows updated
+    if (r0 < R) {
+      const double mkj = (jc == k ? 1.0 : M[k * n + jc]) * inv;
+      for (int i = r0; i < n; i += R) {
+        if (i == k) M[k * n + jc] = mkj;
+        else if (jc == k) M[i * n + k] = -f[i] * mkj;
+        else M[i * n + jc] -= f[i] * mkj;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = tid; i < n; i += bd) {
+        const double t = M[i * n + k];
+        M[i * n + k] = M[i * n + p];
+        M[i * n + p] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// The matrices of several arrays (one per level) in one launch: CTA b inverts
+// matrix b - start[l] of array l, start[l] <= b < start[l + 1].
+struct InvBatch {
+  double* M[16];
+  int start[17];
+  int narr;
+};
+
+__global__ void k_invert_batch(InvBatch B, int n, int* err) {
+  extern __shared__ double sm[];
+  int l = 0;
+  while (l + 1 < B.narr && (int)blockIdx.x >= B.start[l + 1]) ++l;
+  double* M = B.M[l] + (size_t)(blockIdx.x - B.start[l]) * n * n;
+  const int nn = n * n;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) sm[e] = M[e];
+  __syncthreads();
+  gj_invert_cols(sm, n, err);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = sm[e];
+}
+
 // One matrix per CTA, staged in shared memory (n^2 doubles of dynamic shared memory).
 __global__ void k_invert_sm(double* Ms, int n, int* err) {
   extern __shared__ double sm[];
@@ -175,7 +273,7 @@ __global__ void k_invert_sm(double* Ms, int n, int* err) {
   const int nn = n * n;
   for (int e = threadIdx.x; e < nn; e += blockDim.x) sm[e] = M[e];
   __syncthreads();
-  gj_invert(sm, n, err);
+  gj_invert_cols(sm, n, err);
   for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = sm[e];
 }
 
@@ -336,6 +434,39 @@ int launch_invert(Problem& P, double* M, int n, int count) {
   } else {
     k_invert<<<count, 1024, 0, P.stream>>>(M, n, P.dev_err);
   }
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+// All structure-box inverses of the smoothing levels in one launch (n_B^2 doubles
+// of shared memory per CTA); returns false if they do not fit in shared memory,
+// in which case the caller inverts level by level.
+int launch_invert_struct_all(Problem& P, bool* done) {
+  *done = false;
+  const int n = P.nB;
+  const size_t smem = (size_t)n * n * sizeof(double);
+  if (n == 5 || smem > 160u * 1024u || P.nlev - 1 > 16) return IB_OK;
+  InvBatch B;
+  std::memset(&B, 0, sizeof(B));
+  int tot = 0;
+  for (int l = 0; l < P.nlev - 1; ++l) {
+    B.M[B.narr] = P.lev[l].Mstruct;
+    B.start[B.narr] = tot;
+    tot += P.lev[l].n_struct;
+    ++B.narr;
+  }
+  B.start[B.narr] = tot;
+  *done = true;
+  if (tot == 0) return IB_OK;
+  static std::once_flag once;
+  cudaError_t ae = cudaSuccess;
+  std::call_once(once, [&] {
+    ae = cudaFuncSetAttribute(k_invert_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  });
+  IB_CUDA_TRY(ae);
+  const int threads = n <= 32 ? 64 : (n <= 64 ? 128 : 256);
+  KScope ks(P, IB_KC_SETUP, 2.0 * tot * smem);
+  k_invert_batch<<<tot, threads, smem, P.stream>>>(B, n, P.dev_err);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }

@@ -305,6 +305,7 @@ int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool re
 int launch_free_box(Problem& P, int level);
 int launch_struct_fill(Problem& P, int level);
 int launch_invert(Problem& P, double* M, int n, int count);
+int launch_invert_struct_all(Problem& P, bool* done);
 int launch_coarse_fill(Problem& P);
 template <typename T>
 int launch_fill(Problem& P, T* x, size_t n, T v);
