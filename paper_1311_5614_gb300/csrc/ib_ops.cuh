@@ -117,23 +117,6 @@ __device__ __forceinline__ T interp_point(const Patches<T>& pat, const T* w, int
   return s;
 }
 
-// (J U)_k = sum over the springs at k of K_s (U_other - U_k).
-template <typename T>
-__device__ __forceinline__ void JU_point(const Springs<T>& sp, const T* U, int k, T* gx, T* gy) {
-  const int np = sp.np, ns = sp.ns;
-  const T ux = U[k], uy = U[np + k];
-  T ax = 0, ay = 0;
-  for (int q = sp.adj_ptr[k]; q < sp.adj_ptr[k + 1]; ++q) {
-    const int s = sp.adj_spring[q], o = sp.adj_other[q];
-    const T dx = U[o] - ux, dy = U[np + o] - uy;
-    const T kxx = sp.K[s], kxy = sp.K[ns + s], kyy = sp.K[2 * ns + s];
-    ax += kxx * dx + kxy * dy;
-    ay += kxy * dx + kyy * dy;
-  }
-  *gx = ax;
-  *gy = ay;
-}
-
 // Whether velocity row (comp, i, j) of a level with b x b boxes is an unknown of
 // a box of colour `color` (-1: any).  A face on the low edge of its box is also
 // the far-edge unknown of the neighbouring box, whose colour parity differs.
@@ -270,31 +253,6 @@ __device__ __forceinline__ void force_spread_quad(const Patches<T>& pat, const S
       if (swx[a] != (T)0 && row_in_color(comp, ii, jj, b, color)) atomicAdd(&yc[jj * N + ii], swx[a] * wy);
     }
   }
-}
-
-// y_c += g * (row bb of the spread patch of point k): 4 atomic additions.
-template <typename T>
-__device__ __forceinline__ void spread_row(const Patches<T>& pat, int N, int comp, int k, int bb, T g, T* y) {
-  const T wy = pat.w_at(0, comp, 1, bb, k) * g;
-  if (wy == (T)0) return;
-  const int m = N - 1;
-  const int x0 = pat.b_at(0, comp, 0, k), y0 = pat.b_at(0, comp, 1, k);
-  T* row = y + comp * N * N + ((y0 + bb) & m) * N;
-#pragma unroll
-  for (int a = 0; a < PATCH; ++a) {
-    const T wx = pat.w_at(0, comp, 0, a, k);
-    if (wx != (T)0) atomicAdd(&row[(x0 + a) & m], wx * wy);
-  }
-}
-
-// Zero row bb of the spread patch of point k in y (a velocity-row vector).
-template <typename T>
-__device__ __forceinline__ void zero_row(const Patches<T>& pat, int N, int comp, int k, int bb, T* y) {
-  const int m = N - 1;
-  const int x0 = pat.b_at(0, comp, 0, k), y0 = pat.b_at(0, comp, 1, k);
-  T* row = y + comp * N * N + ((y0 + bb) & m) * N;
-#pragma unroll
-  for (int a = 0; a < PATCH; ++a) row[(x0 + a) & m] = (T)0;
 }
 
 // delta = M r for a box of nB unknowns, M column-major (M[s * nB + q]); rows q
