@@ -91,8 +91,11 @@ typedef struct {
   int32_t jacobian;   /* IB_JAC_CLAMPED (default) or IB_JAC_EXACT spring Jacobian */
   double tol;         /* relative residual target ||b - A x|| / ||b|| (> 0) */
   int32_t max_iters;  /* FGMRES iteration cap, 1..512 (the paper stops at 100) */
-  int32_t escalate;   /* IB_FP32_PRECOND only: 1 = switch the preconditioner to the
-                         mixed-precision V-cycle when FGMRES stagnates (default), 0 = never */
+  int32_t escalate;   /* IB_FP32_PRECOND only: 1 (default) = use the mixed-precision
+                         V-cycle from the start when dt * max(kappa) / mu >= 3000
+                         (environment variable IB_STIFF_SIGMA overrides the value), and
+                         restart with it when the FP32-preconditioned FGMRES stagnates;
+                         0 = FP32 throughout */
   int32_t restart;    /* FGMRES restart length m (Krylov vectors kept), 0 = max_iters;
                          workspace grows with m: (m + 1) FP64 + m preconditioner vectors */
 } ib_params;
@@ -188,7 +191,9 @@ IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
 /* ---- Batches of independent problems (not in the paper) ----
  *
  * A batch holds nprob independent problems of any grid sizes and parameters.
- * Each problem gets its own CUDA stream and its own captured V-cycle graph, and
+ * Each problem gets its own CUDA stream (highest priority for problems with
+ * dt * max(kappa) / mu >= 3000, which set the batch's makespan) and its own
+ * captured V-cycle graph, and
  * a pool of host threads (up to 16; the environment variable IB_BATCH_THREADS
  * overrides the count) drives the problems' FGMRES iterations at the same time,
  * so the small, latency-bound launches of different problems overlap on the GPU.

@@ -76,6 +76,21 @@ namespace {
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// The elastic block dt S J S^* scales like dt kappa / h^2 against mu / h^2 for
+// the viscous one, so sigma = dt max(kappa) / mu measures how stiff the step is,
+// independently of h.  Measured on the 256^2 sweep: sigma = 1e3 converges with
+// the FP32 V-cycle like FP64, sigma = 1e4 stalls it.
+double stiffness(const ib_params& p, int n_springs, const double* kappa) {
+  double kmax = 0.0;
+  for (int s = 0; s < n_springs; ++s) kmax = std::max(kmax, kappa[s]);
+  return p.dt * kmax / p.mu;
+}
+
+double stiff_threshold() {
+  const char* e = std::getenv("IB_STIFF_SIGMA");
+  return e ? std::atof(e) : 3000.0;
+}
+
 int validate(const ib_params* p) {
   if (!p) return fail(IB_ERR_INVALID_ARG, "params is NULL");
   if (!(p->box == 1 || p->box == 2 || p->box == 4 || p->box == 8))
@@ -414,6 +429,8 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
   std::vector<double> hist;
   int nn_rejected = 0;  // consecutive rejections of the learned stage
   st->escalated_at = -1;
+  // a step stiff enough to stall the FP32 V-cycle starts on the mixed one
+  if (!std::is_same<T, double>::value && P.has64 && P.sigma >= P.stiff_sigma) st->escalated_at = 0;
   double* h1 = s + 8;
   double* h2 = h1 + m + 2;
   double* wn = h2 + m + 2;
@@ -681,6 +698,8 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   P.np = n_points;
   P.ns = n_springs;
   P.nB = box_nunk(params->box);
+  P.sigma = stiffness(*params, n_springs, kappa);
+  P.stiff_sigma = stiff_threshold();
   int Nc = params->box > 4 ? params->box : 4;
   for (int N = params->N; N >= Nc; N /= 2) {
     LevelInfo L;
@@ -1042,8 +1061,15 @@ int ib_setup_batch(int32_t nprob, const ib_params* params, const int32_t* pt_off
     xo += 2ul * (pt_off[k + 1] - pt_off[k]);
   }
   cudaError_t e = cudaEventCreateWithFlags(&B->start, cudaEventDisableTiming);
+  // stiff problems (the long FGMRES runs that set the batch's makespan) get the
+  // highest stream priority, so their latency-bound V-cycles are scheduled first
+  int prio_low = 0, prio_high = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  const double sig_c = stiff_threshold();
   for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
-    e = cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking);
+    const int s0 = sp_off[k], nsk = sp_off[k + 1] - s0;
+    const bool stiff = kappa && stiffness(params[k], nsk, kappa + s0) >= sig_c;
+    e = cudaStreamCreateWithPriority(&B->streams[k], cudaStreamNonBlocking, stiff ? prio_high : prio_low);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done[k], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {

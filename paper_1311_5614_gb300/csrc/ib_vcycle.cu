@@ -1011,7 +1011,9 @@ template <typename T>
 int vcycle_run(Problem& P) {
   if (P.prof || !P.use_graph) return vcycle_eager<T>(P);
   if (!P.gstream) {
-    IB_CUDA_TRY(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
+    int prio = 0;  // the private stream inherits the caller's stream priority
+    if (P.stream) IB_CUDA_TRY(cudaStreamGetPriority(P.stream, &prio));
+    IB_CUDA_TRY(cudaStreamCreateWithPriority(&P.gstream, cudaStreamNonBlocking, prio));
     IB_CUDA_TRY(cudaEventCreateWithFlags(&P.gev[0], cudaEventDisableTiming));
     IB_CUDA_TRY(cudaEventCreateWithFlags(&P.gev[1], cudaEventDisableTiming));
   }
