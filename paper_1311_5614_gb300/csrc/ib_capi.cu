@@ -209,8 +209,6 @@ void free_problem(Problem* P) {
   }
   if (P->gstream) cudaStreamDestroy(P->gstream);
   P->gstream = nullptr;
-  for (auto& e : P->gev)
-    if (e) cudaEventDestroy(e);
   dfree(P->X); dfree(P->springs); dfree(P->kappa); dfree(P->rest);
   dfree(P->adj_ptr); dfree(P->adj_spring); dfree(P->adj_other);
   dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->U64); dfree(P->U32);

@@ -196,8 +196,7 @@ struct Problem {
   long box_one_max = 512;             // boxes per colour up to which each box gets its own CTA
   double sigma = 0.0;                 // stiffness ratio dt * max(kappa) / mu of the structure
   double stiff_sigma = 3000.0;        // FP32 mode: from this sigma on, precondition with the mixed V-cycle
-  cudaStream_t gstream = nullptr;                 // private stream the graph is captured on and replayed on
-  cudaEvent_t gev[2] = {nullptr, nullptr};        // joins between the caller's stream and gstream
+  cudaStream_t gstream = nullptr;                 // private stream the graph is captured on
   long long graph_launches[2][IB_KC_COUNT] = {};
   cudaStream_t stream = nullptr;
   int np = 0, ns = 0;

@@ -1010,17 +1010,10 @@ template int vcycle_prepare<float>(Problem&);
 template <typename T>
 int vcycle_run(Problem& P) {
   if (P.prof || !P.use_graph) return vcycle_eager<T>(P);
-  if (!P.gstream) {
-    int prio = 0;  // the private stream inherits the caller's stream priority
-    if (P.stream) IB_CUDA_TRY(cudaStreamGetPriority(P.stream, &prio));
-    IB_CUDA_TRY(cudaStreamCreateWithPriority(&P.gstream, cudaStreamNonBlocking, prio));
-    IB_CUDA_TRY(cudaEventCreateWithFlags(&P.gev[0], cudaEventDisableTiming));
-    IB_CUDA_TRY(cudaEventCreateWithFlags(&P.gev[1], cudaEventDisableTiming));
-  }
   // the caller's stream may be the legacy default stream, which cannot be
-  // captured: capture and replay on a private stream joined by events
-  IB_CUDA_TRY(cudaEventRecord(P.gev[0], P.stream));
-  IB_CUDA_TRY(cudaStreamWaitEvent(P.gstream, P.gev[0], 0));
+  // captured: capture on a private stream (capture runs nothing), replay on the
+  // caller's stream
+  if (!P.gstream) IB_CUDA_TRY(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
   cudaStream_t user = P.stream;
   constexpr int ix = pix<T>();
   if (P.graph_dirty[ix] || !P.vgraph[ix]) {
@@ -1050,9 +1043,7 @@ int vcycle_run(Problem& P) {
     }
     P.graph_dirty[ix] = false;
   }
-  IB_CUDA_TRY(cudaGraphLaunch(P.vgraph[ix], P.gstream));
-  IB_CUDA_TRY(cudaEventRecord(P.gev[1], P.gstream));
-  IB_CUDA_TRY(cudaStreamWaitEvent(P.stream, P.gev[1], 0));
+  IB_CUDA_TRY(cudaGraphLaunch(P.vgraph[ix], P.stream));
   for (int c = 0; c < IB_KC_COUNT; ++c) P.nlaunch[c] += P.graph_launches[ix][c];
   return IB_OK;
 }
