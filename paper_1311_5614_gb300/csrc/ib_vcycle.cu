@@ -499,9 +499,11 @@ __global__ void kv_box1(const T* __restrict__ r, T* __restrict__ w, int N, int c
 }
 
 // b_{l+1} = R (b - A_l w + rE); rE (all rows, may be NULL) is cleared by kv_prolong.
+// Also zeroes the coarse correction w_{l+1} (the coarse level's initial guess),
+// one cell per thread like b_{l+1}.
 template <typename T>
 __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, const T* __restrict__ rE,
-                          T* __restrict__ bc, int Nc, StokesCoef<T> c) {
+                          T* __restrict__ bc, T* __restrict__ wc, int Nc, StokesCoef<T> c) {
   pdl_enter();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int nc = Nc * Nc;
@@ -511,6 +513,9 @@ __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, cons
   bc[idx] = ru;
   bc[nc + idx] = rv;
   bc[2 * nc + idx] = rp;
+  wc[idx] = (T)0;
+  wc[nc + idx] = (T)0;
+  wc[2 * nc + idx] = (T)0;
 }
 
 // w += P e; also clears rE (the restriction's elasticity term; may be NULL).
@@ -823,7 +828,7 @@ int vcycle_eager_t(Problem& P) {
     LevelInfo& L = P.lev[l];
     LevelBuf<T>& B = lbuf<T>(L);
     const long n3 = 3L * L.N * L.N;
-    {
+    if (l == 0) {  // coarser levels are zeroed by the restriction that fills their b
       KScope ks(P, IB_KC_OTHER, n3 * sizeof(T));
       vlaunch(use_pdl(P), kv_zero<T>, nblk(n3), TPB, 0, P.stream, B.w, n3);
       IB_LAUNCH_CHECK();
@@ -835,9 +840,9 @@ int vcycle_eager_t(Problem& P) {
     {
       // w read once per stencil (9 fine values per coarse cell incl. the halo), b, rE
       const double e_bytes = has_E ? 2.0 * L.N * L.N * sizeof(T) : 0.0;
-      KScope ks(P, IB_KC_TRANSFER, (9.0 * L.N * L.N + 3.0 * Nc * Nc) * sizeof(T) + e_bytes);
+      KScope ks(P, IB_KC_TRANSFER, (9.0 * L.N * L.N + 6.0 * Nc * Nc) * sizeof(T) + e_bytes);
       vlaunch(use_pdl(P), kv_resres<T>, nblk((long)Nc * Nc), TPB, 0, P.stream, B.w, B.b, E,
-              lbuf<T>(P.lev[l + 1]).b, Nc, coefs<T>(P, l));
+              lbuf<T>(P.lev[l + 1]).b, lbuf<T>(P.lev[l + 1]).w, Nc, coefs<T>(P, l));
       IB_LAUNCH_CHECK();
     }
   }
