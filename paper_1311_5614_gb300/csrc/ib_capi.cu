@@ -145,6 +145,7 @@ int check_dev_err(Problem& P) {
     if (h & DEV_ERR_NONFINITE)
       return fail(IB_ERR_INVALID_ARG, "a spring has coincident or non-finite end points");
     if (h & DEV_ERR_SINGULAR) return fail(IB_ERR_SINGULAR, "zero pivot in a box or coarsest factorisation");
+    if (h & DEV_ERR_TIMEOUT) return fail(IB_ERR_TIMEOUT, "a bulk copy of the Krylov basis did not complete");
     return fail(IB_ERR_INVALID_ARG, "internal index check failed (too many springs at a point?)");
   }
   return IB_OK;
@@ -296,8 +297,7 @@ int allocate(Problem& P) {
   }
   IB_TRY(dalloc(&P.H, (size_t)(m + 1) * m));
   IB_TRY(dalloc(&P.givens, 4ul * m + 1));
-  P.dot_blocks = (int)std::min<size_t>(608, (n + 1023) / 1024);
-  if (P.dot_blocks < 1) P.dot_blocks = 1;
+  IB_TRY(krylov_init(P));
   IB_TRY(dalloc(&P.dots, (size_t)P.dot_blocks * (m + 2)));
   IB_TRY(dalloc(&P.scal, 16ul + 2ul * (m + 2) + 8));
   IB_TRY(dalloc(&P.x64, n));
@@ -431,7 +431,6 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
   if (!std::is_same<T, double>::value && P.has64 && P.sigma >= P.stiff_sigma) st->escalated_at = 0;
   double* h1 = s + 8;
   double* h2 = h1 + m + 2;
-  double* wn = h2 + m + 2;
   double* g = P.givens + 2 * m;
   for (int restart = 0;; ++restart) {
     if (total == 0) {
@@ -521,12 +520,11 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
           nn_rejected = acc ? 0 : nn_rejected + 1;
         }
       }
+      // classical Gram-Schmidt applied twice: h1 = V^T w; w -= V h1 and h2 = V^T w in
+      // one pass over V; w -= V h2 with ||w||^2 and the Givens step
       IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h1));
-      IB_TRY(launch_multiaxpy(P, P.V, j + 1, h1, P.t64));
-      IB_TRY(launch_multidot(P, P.V, j + 1, P.t64, h2));
-      IB_TRY(launch_multiaxpy(P, P.V, j + 1, h2, P.t64));
-      IB_TRY(launch_dot(P, P.t64, P.t64, wn));
-      IB_TRY(launch_givens(P, j, 0.0, nullptr));
+      IB_TRY(launch_cgs_sub_dot(P, P.V, j + 1, h1, P.t64, h2));
+      IB_TRY(launch_cgs_finish(P, P.V, j + 1, P.t64, j));
       IB_TRY(launch_scale_copy(P, P.t64, s + 1, P.V + (size_t)(j + 1) * n, true));
       IB_CUDA_TRY(cudaMemcpyAsync(P.scal_host + 24 + 4 * (j & 1), P.scal, 3 * sizeof(double),
                                   cudaMemcpyDeviceToHost, P.stream));
@@ -566,6 +564,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     IB_TRY(residual64(P, x, b, P.t64));
     IB_TRY(launch_dot(P, P.t64, P.t64, s + 7));
     IB_TRY(read_scalars(P, 8));
+    IB_TRY(check_dev_err(P));
     double rt = std::sqrt(P.scal_host[7]) / bnorm;
     st->rel_res_true = rt;
     st->iters = total;

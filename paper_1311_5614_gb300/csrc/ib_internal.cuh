@@ -36,7 +36,7 @@ int fail(int code, const std::string& msg);
 #define IB_LAUNCH_CHECK() IB_CUDA_TRY(cudaGetLastError())
 
 // Device error flags (bit mask, one word per problem).
-enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_INDEX = 2, DEV_ERR_NONFINITE = 4 };
+enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_INDEX = 2, DEV_ERR_NONFINITE = 4, DEV_ERR_TIMEOUT = 8 };
 
 // ---------------------------------------------------------------- patches
 // Per level and point: for kind (0 spread, 1 interp) and component (0 u, 1 v)
@@ -247,7 +247,11 @@ struct Problem {
   double* nn_dz = nullptr;    // [3 N^2] proposed correction
   double* nn_adz = nullptr;   // [3 N^2] A dz
   int max_m = 0;
-  int dot_blocks = 0;
+  int dot_blocks = 0;         // rows of the partial-sum buffer
+  int n_sm = 0;               // SMs of the device
+  int cgs_smem_max = 0;       // dynamic shared memory limit of the fused Gram-Schmidt pass
+  int occ_multidot = 0;       // resident blocks per SM of the partial-dot kernel
+  int occ_subnorm = 0;        // ... and of the last Gram-Schmidt subtraction
   int* count = nullptr;       // device counter
   int* count_host = nullptr;  // pinned
 
@@ -326,7 +330,9 @@ int launch_multidot(Problem& P, const double* V, int nvec, const double* w, doub
 int launch_multiaxpy(Problem& P, const double* V, int nvec, const double* coef, double* w);
 int launch_dot(Problem& P, const double* a, const double* b, double* out);
 int launch_scale_copy(Problem& P, const double* x, const double* s, double* y, bool invert);
-int launch_givens(Problem& P, int j, double bnorm_tol, double* out_scalars);
+int launch_cgs_sub_dot(Problem& P, const double* V, int nvec, const double* coef, double* w, double* out);
+int launch_cgs_finish(Problem& P, const double* V, int nvec, double* w, int j);
+int krylov_init(Problem& P);
 int launch_backsolve(Problem& P, int k);
 template <typename T>
 int launch_update_x(Problem& P, const T* Z, int k, double* x, int first = 0);

@@ -4,6 +4,7 @@
 // bases (V, Z) are read with the streaming cache hint (evict first): at a few
 // hundred MB they would otherwise push the V-cycle's working set out of L2
 // between preconditioner applications.
+#include <algorithm>
 #include <cmath>
 
 #include "ib_internal.cuh"
@@ -28,42 +29,206 @@ __device__ inline double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// partial[blk * stride + i] = sum over the block's range of V_i . w.  The basis
-// vectors are taken MDG at a time: per element w is read once and MDG independent
-// loads are in flight, and one block reduction serves the whole group.
+// partial[bx * stride + i] = sum over the elements [bx * per, (bx + 1) * per) of
+// V_i . w, for the MDG vectors of block row blockIdx.y.  Per step every thread has
+// MDE x MDG independent loads in flight, and each block reduces once, at the end.
 constexpr int MDG = 8;
-__global__ void k_multidot_partial(const double* __restrict__ V, int nvec, long n,
-                                   const double* __restrict__ w, double* partial, int stride) {
-  __shared__ double sh[32][MDG];  // [warp][vector of the group]
-  const long per = (n + gridDim.x - 1) / gridDim.x;
-  const long lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i0 = 0; i0 < nvec; i0 += MDG) {
-    const int nv = nvec - i0 < MDG ? nvec - i0 : MDG;
-    const double* v0 = V + (size_t)i0 * n;
-    double acc[MDG];
+constexpr int MDE = 4;
+__global__ void __launch_bounds__(TPB) k_multidot_partial(const double* __restrict__ V, int nvec, long n,
+                                                          const double* __restrict__ w, double* partial,
+                                                          int stride, long per) {
+  __shared__ double sh[TPB / 32][MDG];
+  const int i0 = blockIdx.y * MDG;
+  const int nv = nvec - i0 < MDG ? nvec - i0 : MDG;
+  const double* v0 = V + (size_t)i0 * n;
+  double acc[MDG];
 #pragma unroll
-    for (int q = 0; q < MDG; ++q) acc[q] = 0.0;
-    for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-      const double we = w[e];
+  for (int q = 0; q < MDG; ++q) acc[q] = 0.0;
+  const long lo = (long)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  for (long e0 = lo + threadIdx.x; e0 < hi; e0 += (long)TPB * MDE) {
+    double we[MDE];
+#pragma unroll
+    for (int k = 0; k < MDE; ++k) we[k] = e0 + (long)k * TPB < hi ? w[e0 + (long)k * TPB] : 0.0;
+    if (nv == MDG && e0 + (long)(MDE - 1) * TPB < hi) {
 #pragma unroll
       for (int q = 0; q < MDG; ++q)
-        if (q < nv) acc[q] += __ldcs(v0 + (size_t)q * n + e) * we;
-    }
 #pragma unroll
-    for (int q = 0; q < MDG; ++q)
-      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-    if (lane == 0)
+        for (int k = 0; k < MDE; ++k) acc[q] += __ldcs(v0 + (size_t)q * n + e0 + (long)k * TPB) * we[k];
+    } else {
 #pragma unroll
-      for (int q = 0; q < MDG; ++q) sh[wid][q] = acc[q];
-    __syncthreads();
-    if (threadIdx.x < nv) {
-      double s = 0.0;
-      for (int q = 0; q < nw; ++q) s += sh[q][threadIdx.x];
-      partial[(size_t)blockIdx.x * stride + i0 + threadIdx.x] = s;
+      for (int q = 0; q < MDG; ++q)
+        if (q < nv)
+#pragma unroll
+          for (int k = 0; k < MDE; ++k)
+            if (e0 + (long)k * TPB < hi) acc[q] += __ldcs(v0 + (size_t)q * n + e0 + (long)k * TPB) * we[k];
     }
-    __syncthreads();
   }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < MDG; ++q) {
+    double a = acc[q];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[wid][q] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int q = 0; q < TPB / 32; ++q) t += sh[q][threadIdx.x];
+    partial[(size_t)blockIdx.x * stride + i0 + threadIdx.x] = t;
+  }
+}
+
+// ---- bulk copies global -> shared completing on an mbarrier (bounded waits)
+__device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ inline void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+// bytes: a multiple of 16; dst and src 16-byte aligned
+__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ inline bool mbar_try(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits until phase `parity` of the barrier completes, for at most limit_ns.
+__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // 1 s
+
+// Fused Gram-Schmidt pass: w <- w - sum_i coef_i V_i, then partial[bx * stride + i]
+// = the block's part of V_i . w (the updated w), so the basis is read from HBM
+// once for the first subtraction and the second projection of CGS2.  A block
+// takes chunks of CGS_CH elements: the lanes of warp 0 issue one bulk copy per
+// basis vector (its 512-byte slice) into shared memory, the block subtracts (one
+// thread per element), then thread t forms the dot products of vectors t, t + 64,
+// ... with the chunk (rows read at a per-row rotation of the column, so a warp's
+// 32 rows hit distinct banks) and keeps them in registers across chunks.  A bulk
+// copy that has not landed after 1 s sets DEV_ERR_TIMEOUT and ends the block.
+constexpr int CGS_CH = 64;
+constexpr int CGS_KMAX = (513 + CGS_CH - 1) / CGS_CH;  // vectors per thread (nvec <= 513)
+__global__ void __launch_bounds__(CGS_CH) k_cgs_sub_dot(const double* __restrict__ V, int nvec, long n,
+                                                        const double* __restrict__ coef, double* __restrict__ w,
+                                                        double* __restrict__ partial, int stride, int* err) {
+  extern __shared__ __align__(128) double sm[];
+  double* sV = sm;                          // [nvec][CGS_CH]
+  double* sw = sV + (size_t)nvec * CGS_CH;  // [CGS_CH] updated w of the chunk
+  double* sc = sw + CGS_CH;                 // [nvec] coefficients
+  __shared__ __align__(8) unsigned long long bar;
+  const int t = threadIdx.x;
+  for (int i = t; i < nvec; i += CGS_CH) sc[i] = coef[i];
+  if (t == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  double acc[CGS_KMAX];
+#pragma unroll
+  for (int k = 0; k < CGS_KMAX; ++k) acc[k] = 0.0;
+  const long nch = (n + CGS_CH - 1) / CGS_CH;
+  unsigned parity = 0;
+  for (long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long c0 = ch * CGS_CH;
+    const int len = (int)(n - c0 < CGS_CH ? n - c0 : CGS_CH);
+    if (t < 32) {
+      const unsigned bytes = (unsigned)len * 8u;
+      if (t == 0) mbar_arrive_expect_tx(&bar, bytes * (unsigned)nvec);
+      __syncwarp();
+      for (int i = t; i < nvec; i += 32) bulk_g2s(sV + (size_t)i * CGS_CH, V + (size_t)i * n + c0, bytes, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, parity, WAIT_LIMIT_NS);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        mbar_wait_bounded(&bar, parity, WAIT_LIMIT_NS);  // let copies in flight land
+      }
+      return;
+    }
+    parity ^= 1u;
+    double s = 0.0;
+    if (t < len) {
+      double s0 = w[c0 + t], s1 = 0.0;
+      int i = 0;
+#pragma unroll 4
+      for (; i + 1 < nvec; i += 2) {
+        s0 -= sc[i] * sV[(size_t)i * CGS_CH + t];
+        s1 -= sc[i + 1] * sV[(size_t)(i + 1) * CGS_CH + t];
+      }
+      if (i < nvec) s0 -= sc[i] * sV[(size_t)i * CGS_CH + t];
+      s = s0 + s1;
+      w[c0 + t] = s;
+    }
+    sw[t] = s;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < CGS_KMAX; ++k) {
+      const int i = t + k * CGS_CH;
+      if (i < nvec) {
+        const double* r = sV + (size_t)i * CGS_CH;
+        double d = 0.0;
+        if (len == CGS_CH) {
+#pragma unroll 16
+          for (int e = 0; e < CGS_CH; ++e) {
+            const int c = (e + i) & (CGS_CH - 1);
+            d += r[c] * sw[c];
+          }
+        } else {
+          for (int e = 0; e < len; ++e) d += r[e] * sw[e];
+        }
+        acc[k] += d;
+      }
+    }
+    __syncthreads();  // sV and sw are refilled by the next chunk
+  }
+#pragma unroll
+  for (int k = 0; k < CGS_KMAX; ++k) {
+    const int i = t + k * CGS_CH;
+    if (i < nvec) partial[(size_t)blockIdx.x * stride + i] = acc[k];
+  }
+}
+
+// Last Gram-Schmidt subtraction with the norm: w <- w - sum_i coef_i V_i over
+// the elements [bx * per, (bx + 1) * per), and partial[bx] = their part of ||w||^2.
+__global__ void __launch_bounds__(TPB) k_sub_norm(const double* __restrict__ V, int nvec, long n,
+                                                  const double* __restrict__ coef, double* __restrict__ w,
+                                                  double* __restrict__ partial, long per) {
+  __shared__ double c[520];
+  __shared__ double sh[32];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) c[i] = coef[i];
+  __syncthreads();
+  double s2 = 0.0;
+  const long lo = (long)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  for (long e = lo + threadIdx.x; e < hi; e += TPB) {
+    double s = w[e];
+#pragma unroll 16
+    for (int i = 0; i < nvec; ++i) s -= c[i] * __ldcs(V + (size_t)i * n + e);
+    w[e] = s;
+    s2 += s * s;
+  }
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s2;
 }
 
 __global__ void k_multidot_final(const double* __restrict__ partial, int nblocks, int stride,
@@ -99,34 +264,51 @@ __global__ void k_scale_copy(const double* __restrict__ x, const double* __restr
   y[e] = invert ? x[e] / a : x[e] * a;
 }
 
-// Givens step of FGMRES iteration j.  H (column-major, ld m + 1) column j is
-// h1 + h2 from the two Gram-Schmidt passes and ||w|| below the diagonal; the
-// previous rotations are applied, a new one is formed, and g is updated.
+// Givens step of FGMRES iteration j, one block.  H (column-major, ld m + 1)
+// column j is h1 + h2 from the two Gram-Schmidt passes and ||w|| below the
+// diagonal (||w||^2 summed here from the partials of k_sub_norm, in a fixed
+// order); the previous rotations are applied, a new one is formed, and g is
+// updated.  The column and the rotations are staged in shared memory so that the
+// sequential rotation loop carries only two FMAs per step.
 // scal layout: [0] |g_{j+1}|, [1] H_{j+1,j} (= ||w||), [2] non-finite flag.
-__global__ void k_givens(double* H, int ld, int j, const double* h1, const double* h2,
-                         const double* wnorm2, double* cs, double* sn, double* g, double* scal) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* col = H + (size_t)j * ld;
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  double hn = sqrt(fmax(*wnorm2, 0.0));
-  col[j + 1] = hn;
-  scal[1] = hn;
-  for (int i = 0; i < j; ++i) {
-    double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
+constexpr int GIV_MAX = 514;
+__global__ void k_norm_givens(const double* __restrict__ partial, int nb, double* wn2, double* H, int ld, int j,
+                              const double* h1, const double* h2, double* cs, double* sn, double* g,
+                              double* scal) {
+  __shared__ double sh[32];
+  __shared__ double col[GIV_MAX], scs[GIV_MAX], ssn[GIV_MAX];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[b];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = h1[i] + h2[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    scs[i] = cs[i];
+    ssn[i] = sn[i];
   }
-  double a = col[j], b = col[j + 1];
-  double den = hypot(a, b);
-  double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  scal[0] = fabs(g[j + 1]);
-  scal[2] = (isfinite(den) && isfinite(g[j + 1])) ? 0.0 : 1.0;
+  s = block_sum(s, sh);  // synchronises the block
+  if (threadIdx.x == 0) {
+    *wn2 = s;
+    const double hn = sqrt(fmax(s, 0.0));
+    scal[1] = hn;
+    double a = col[0];
+    for (int i = 0; i < j; ++i) {
+      const double b = col[i + 1];
+      col[i] = scs[i] * a + ssn[i] * b;
+      a = -ssn[i] * a + scs[i] * b;
+    }
+    const double den = hypot(a, hn);
+    const double c = den > 0.0 ? a / den : 1.0, sr = den > 0.0 ? hn / den : 0.0;
+    cs[j] = c;
+    sn[j] = sr;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sr * g[j];
+    g[j] = c * g[j];
+    scal[0] = fabs(g[j + 1]);
+    scal[2] = (isfinite(den) && isfinite(g[j + 1])) ? 0.0 : 1.0;
+  }
+  __syncthreads();
+  double* hc = H + (size_t)j * ld;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
 // y = R^{-1} g for the leading k x k triangle of H.
@@ -168,20 +350,49 @@ __global__ void k_sub_scalar(double* x, long n, const double* s, double scale) {
 
 static inline long nvec_len(const Problem& P) { return 3L * P.lev[0].N * P.lev[0].N; }
 
+// Block columns of k_multidot_partial: all block rows x columns resident at
+// once (one wave), each column an equal contiguous range of at least one warp
+// width per thread row.
+static inline int dot_cols(const Problem& P, long n, int rows) {
+  const long resident = (long)P.n_sm * std::max(1, P.occ_multidot);
+  const long want = std::max(1L, resident / rows);
+  const long most = std::max(1L, n / TPB);
+  return (int)std::max(1L, std::min({want, most, (long)P.dot_blocks}));
+}
+static inline long range_per(long n, int cols) { return ((n + cols - 1) / cols + 31) / 32 * 32; }
+
+int krylov_init(Problem& P) {
+  int dev = 0;
+  IB_CUDA_TRY(cudaGetDevice(&dev));
+  IB_CUDA_TRY(cudaDeviceGetAttribute(&P.n_sm, cudaDevAttrMultiProcessorCount, dev));
+  int optin = 0;
+  IB_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  P.cgs_smem_max = std::max(0, optin - 256);  // leaves room for the static shared memory (one mbarrier)
+  IB_CUDA_TRY(cudaFuncSetAttribute(k_cgs_sub_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, P.cgs_smem_max));
+  P.dot_blocks = 8 * std::max(1, P.n_sm);
+  IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_multidot, k_multidot_partial, TPB, 0));
+  IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_subnorm, k_sub_norm, TPB, 0));
+  return IB_OK;
+}
+
+static int multidot_final(Problem& P, int nvec, int cols, double* out) {
+  KScope ks(P, IB_KC_KRYLOV, (double)nvec * cols * 8.0);
+  k_multidot_final<<<nvec, TPB, 0, P.stream>>>(P.dots, cols, P.max_m + 2, out);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
 int launch_multidot(Problem& P, const double* V, int nvec, const double* w, double* out) {
   long n = nvec_len(P);
-  int stride = P.max_m + 2;
+  const int rows = (nvec + MDG - 1) / MDG;
+  const int cols = dot_cols(P, n, rows);
   {
     KScope ks(P, IB_KC_KRYLOV, (nvec + 1.0) * n * 8.0);
-    k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(V, nvec, n, w, P.dots, stride);
+    k_multidot_partial<<<dim3(cols, rows), TPB, 0, P.stream>>>(V, nvec, n, w, P.dots, P.max_m + 2,
+                                                               range_per(n, cols));
     IB_LAUNCH_CHECK();
   }
-  {
-    KScope ks(P, IB_KC_KRYLOV, (double)nvec * P.dot_blocks * 8.0);
-    k_multidot_final<<<nvec, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, out);
-    IB_LAUNCH_CHECK();
-  }
-  return IB_OK;
+  return multidot_final(P, nvec, cols, out);
 }
 
 int launch_multiaxpy(Problem& P, const double* V, int nvec, const double* coef, double* w) {
@@ -192,33 +403,36 @@ int launch_multiaxpy(Problem& P, const double* V, int nvec, const double* coef, 
   return IB_OK;
 }
 
-int launch_dot(Problem& P, const double* a, const double* b, double* out) {
-  long n = nvec_len(P);
-  int stride = P.max_m + 2;
-  {
-    KScope ks(P, IB_KC_KRYLOV, 2.0 * n * 8.0);
-    k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(a, 1, n, b, P.dots, stride);
-    IB_LAUNCH_CHECK();
-  }
-  {
-    KScope ks(P, IB_KC_KRYLOV, (double)P.dot_blocks * 8.0);
-    k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, out);
-    IB_LAUNCH_CHECK();
-  }
-  return IB_OK;
-}
+int launch_dot(Problem& P, const double* a, const double* b, double* out) { return launch_multidot(P, a, 1, b, out); }
 
-int launch_scale_copy(Problem& P, const double* x, const double* s, double* y, bool invert) {
-  long n = nvec_len(P);
-  KScope ks(P, IB_KC_KRYLOV, 2.0 * n * 8.0);
-  k_scale_copy<<<nblk(n), TPB, 0, P.stream>>>(x, s, y, n, invert ? 1 : 0);
-  IB_LAUNCH_CHECK();
-  return IB_OK;
+// w <- w - V coef, out = V^T w (the updated w): the first subtraction and the
+// second projection of classical Gram-Schmidt applied twice, in one pass over V.
+// Falls back to two passes when the chunk of V does not fit in shared memory.
+int launch_cgs_sub_dot(Problem& P, const double* V, int nvec, const double* coef, double* w, double* out) {
+  const long n = nvec_len(P);
+  const size_t smem = ((size_t)nvec * CGS_CH + CGS_CH + 2ul * nvec) * sizeof(double);
+  if (smem > (size_t)P.cgs_smem_max || (n & 1)) {
+    IB_TRY(launch_multiaxpy(P, V, nvec, coef, w));
+    return launch_multidot(P, V, nvec, w, out);
+  }
+  int per_sm = 0;
+  IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_sub_dot, CGS_CH, smem));
+  per_sm = std::max(1, std::min(per_sm, 8));
+  const long chunks = (n + CGS_CH - 1) / CGS_CH;
+  const int cols = (int)std::min<long>({chunks, (long)P.n_sm * per_sm, (long)P.dot_blocks});
+  {
+    KScope ks(P, IB_KC_KRYLOV, (nvec + 2.0) * n * 8.0);
+    k_cgs_sub_dot<<<cols, CGS_CH, smem, P.stream>>>(V, nvec, n, coef, w, P.dots, P.max_m + 2, P.dev_err);
+    IB_LAUNCH_CHECK();
+  }
+  return multidot_final(P, nvec, cols, out);
 }
 
 // givens layout: cs[m] | sn[m] | g[m + 1] | y[m];  scal: [0..2] Givens outputs,
 // [8 .. 8 + m + 1] h1, [8 + m + 2 ..] h2, then ||w||^2.
-int launch_givens(Problem& P, int j, double /*unused*/, double* /*unused*/) {
+// Last Gram-Schmidt subtraction w <- w - V h2, ||w||^2 and the Givens step of
+// iteration j (nvec = j + 1).
+int launch_cgs_finish(Problem& P, const double* V, int nvec, double* w, int j) {
   int m = P.max_m;
   double* cs = P.givens;
   double* sn = cs + m;
@@ -226,8 +440,24 @@ int launch_givens(Problem& P, int j, double /*unused*/, double* /*unused*/) {
   double* h1 = P.scal + 8;
   double* h2 = h1 + m + 2;
   double* wn = h2 + m + 2;
-  KScope ks(P, IB_KC_KRYLOV, 8.0 * (4.0 * j + 8));
-  k_givens<<<1, 32, 0, P.stream>>>(P.H, m + 1, j, h1, h2, wn, cs, sn, g, P.scal);
+  const long n = nvec_len(P);
+  const int cols = (int)std::min<long>({(long)P.n_sm * std::max(1, P.occ_subnorm), (long)nblk(n),
+                                         (long)P.dot_blocks});
+  {
+    KScope ks(P, IB_KC_KRYLOV, (nvec + 2.0) * n * 8.0);
+    k_sub_norm<<<cols, TPB, 0, P.stream>>>(V, nvec, n, h2, w, P.dots, range_per(n, cols));
+    IB_LAUNCH_CHECK();
+  }
+  KScope ks(P, IB_KC_KRYLOV, 8.0 * (4.0 * j + 8 + cols));
+  k_norm_givens<<<1, TPB, 0, P.stream>>>(P.dots, cols, wn, P.H, m + 1, j, h1, h2, cs, sn, g, P.scal);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+int launch_scale_copy(Problem& P, const double* x, const double* s, double* y, bool invert) {
+  long n = nvec_len(P);
+  KScope ks(P, IB_KC_KRYLOV, 2.0 * n * 8.0);
+  k_scale_copy<<<nblk(n), TPB, 0, P.stream>>>(x, s, y, n, invert ? 1 : 0);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
@@ -272,15 +502,16 @@ int launch_pressure_mean_remove(Problem& P, double* w) {
   double* ones = P.t64b;  // [0 | 0 | 1]
   IB_TRY(launch_fill<double>(P, ones, (size_t)(2 * n), 0.0));
   IB_TRY(launch_fill<double>(P, ones + 2 * n, (size_t)n, 1.0));
-  int stride = P.max_m + 2;
+  const int cols = dot_cols(P, 3 * n, 1);
   {
     KScope ks(P, IB_KC_OTHER, 6.0 * n * 8.0);
-    k_multidot_partial<<<P.dot_blocks, TPB, 0, P.stream>>>(ones, 1, 3 * n, w, P.dots, stride);
+    k_multidot_partial<<<dim3(cols, 1), TPB, 0, P.stream>>>(ones, 1, 3 * n, w, P.dots, P.max_m + 2,
+                                                            range_per(3 * n, cols));
     IB_LAUNCH_CHECK();
   }
   {
-    KScope ks(P, IB_KC_OTHER, (double)P.dot_blocks * 8.0);
-    k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, P.dot_blocks, stride, P.scal + 3);
+    KScope ks(P, IB_KC_OTHER, (double)cols * 8.0);
+    k_multidot_final<<<1, TPB, 0, P.stream>>>(P.dots, cols, P.max_m + 2, P.scal + 3);
     IB_LAUNCH_CHECK();
   }
   {
