@@ -43,7 +43,7 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # dominant kernel classes, averaged over every launch of one profiled sweep step
 # (sequential form, FP32 with escalation) in one ncu capture.  Valid only for the
 # V-cycle kernel sources it was taken on: reported as null once they change.
-TRAFFIC = {"sources_sha256": "ecc56e437348ffed4882cf92fabf79c978a6b84b13c164cfbfad7adfeb25b000",
+TRAFFIC = {"sources_sha256": "033cdc5ff4111697f961460915d3c1fb7616a3040b7707ecf7550c9f2facfb6f",
            "box": 867090.0, "spread": 211613.0}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh"]
 
@@ -284,6 +284,7 @@ def run_ours(args):
     for prec in (["fp64", "mixed", "fp32"] if args.forms else [args.precision]):
         solvers = make_seq(prec)
         forms.setdefault("tail_grid", {})[prec] = [s.tail_grid(prec) for s in solvers]
+        forms.setdefault("tail_cluster", {})[prec] = [s.tail_cluster(prec) for s in solvers]
         st = [None] * nc
         ms = _timed_steps(torch, lambda: seq_step(solvers, st), flush, stream, args.warmup, args.steps,
                           args.profile_range and prec == args.precision)
@@ -468,6 +469,7 @@ def run_vcycle(args):
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "V(1,1) on %d^2, ellipse of %d points, kappa=1e4, dt=1e-3" % (N, 2 * N),
                        "box": args.box, "precision": args.precision, "tail_grid": s.tail_grid(args.precision),
+                       "tail_cluster": s.tail_cluster(args.precision),
                        "note": "ib_vcycle includes the FP64<->FP32 conversion of b and w"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "alg_bytes_per_dof": bpd,

@@ -171,11 +171,20 @@ IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double
 IB_API int ib_num_levels(const ib_problem* prob);
 IB_API int ib_level_size(const ib_problem* prob, int32_t level);
 
-/* Grid size of the finest level run by the single-CTA coarse-level kernel in the
+/* Grid size of the finest level run by the coarse-level ("tail") kernel in the
  * V-cycle of the given precision (IB_FP32_PRECOND for the FP32 V-cycle, IB_FP64 or
- * IB_MIXED_PRECOND for the one on FP64 vectors), 0 if that V-cycle does not exist.  The split is timed at set-up unless the environment variable
- * IB_TAIL_NMAX (the largest grid size for that kernel) pins it. */
+ * IB_MIXED_PRECOND for the one on FP64 vectors), 0 if that V-cycle does not exist.
+ * The tail runs every sweep, transfer and the coarsest solve of its levels in
+ * one launch, on one CTA (arrays in shared memory) or on one thread-block
+ * cluster (arrays in global memory, levels up to 128^2).  The split and the form
+ * are timed at set-up unless the environment variable IB_TAIL_NMAX (the largest
+ * grid size for the tail) pins them; IB_TAIL_CLUSTER=1 then asks for the cluster
+ * form and IB_TAIL_CLUSTER=0 excludes it from the timing as well. */
 IB_API int ib_tail_grid(const ib_problem* prob, int32_t precision);
+
+/* CTAs of the thread-block cluster that runs the tail kernel of the V-cycle of the
+ * given precision, 0 for the single-CTA form or if that V-cycle does not exist. */
+IB_API int ib_tail_cluster(const ib_problem* prob, int32_t precision);
 
 /* Levels with at least IB_BOX_GEMM_MIN boxes per colour (environment variable,
  * default 2048) solve their n x n boxes (n = 2, 4) with a register-blocked kernel

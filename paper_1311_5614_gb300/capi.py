@@ -75,6 +75,7 @@ _SIGS = {
     "ib_level_size": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_num_struct_boxes": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_tail_grid": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_tail_cluster": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_launch_count": (ctypes.c_int64, [_P, ctypes.c_int32]),
     "ib_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -455,6 +456,9 @@ class IBSolver:
 
     def tail_grid(self, precision="fp32"):
         return lib().ib_tail_grid(self.handle, PRECISION[precision])
+
+    def tail_cluster(self, precision="fp32"):
+        return lib().ib_tail_cluster(self.handle, PRECISION[precision])
 
     def apply(self, level, w, y):
         ib_apply(self.handle, level, w, y)

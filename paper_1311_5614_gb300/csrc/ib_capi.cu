@@ -807,6 +807,14 @@ int ib_tail_grid(const ib_problem* H, int32_t precision) {
   return P.lev[P.tail_level[ix]].N;
 }
 
+int ib_tail_cluster(const ib_problem* H, int32_t precision) {
+  if (!H || (precision != IB_FP64 && precision != IB_FP32_PRECOND && precision != IB_MIXED_PRECOND)) return 0;
+  const Problem& P = H->P;
+  const int ix = precision == IB_FP32_PRECOND ? 0 : 1;
+  if ((ix == 1 && !P.has64) || (ix == 0 && !P.has32)) return 0;
+  return P.tail_cluster[ix];
+}
+
 int ib_num_struct_boxes(const ib_problem* H, int32_t level) {
   if (!H || level < 0 || level >= H->P.nlev - 1) return 0;
   return H->P.lev[level].n_struct;

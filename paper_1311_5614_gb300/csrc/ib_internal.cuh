@@ -187,7 +187,8 @@ struct Problem {
   std::vector<ProfRec> pending;
   // V-cycle engine
   // index [0] = FP32 V-cycle, [1] = FP64 V-cycle
-  int tail_level[2] = {0, 0};    // first level handled by the single-CTA kernel
+  int tail_level[2] = {0, 0};    // first level handled by the tail kernel
+  int tail_cluster[2] = {0, 0};  // CTAs of its cluster (0: one CTA, arrays in shared memory)
   bool use_graph = true;
   bool graph_dirty[2] = {true, true};
   cudaGraphExec_t vgraph[2] = {nullptr, nullptr};

@@ -11,9 +11,12 @@
 // their residual is formed by a separate kernel first (block-Jacobi semantics).
 // Residual and restriction are fused.
 //
-// The coarse levels (N_l <= 64 in FP32, <= 32 in FP64, all fitting in shared
-// memory) run in one kernel on a single CTA of 1024 threads: every sweep,
-// transfer and the bordered coarsest solve, separated by __syncthreads.
+// The coarse levels run in one "tail" kernel: every sweep, transfer and the
+// bordered coarsest solve, on a single CTA of 1024 threads with the arrays in
+// shared memory (N_l <= 64 in FP32, <= 32 in FP64) separated by __syncthreads,
+// or on one thread-block cluster of 8-16 such CTAs with the arrays in global
+// memory (N_l <= 128) separated by the cluster barrier.  The split between
+// grid-wide kernels and the tail, and its form, are timed per problem.
 //
 // The whole sequence is captured once into a CUDA graph and replayed for every
 // V-cycle; the graph is re-captured when a kernel argument changes.
@@ -53,6 +56,27 @@ void vlaunch(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// One thread-block cluster of csize CTAs (grid = the cluster); returns the launch status.
+template <typename... KArgs, typename... Args>
+cudaError_t claunch(bool pdl, int csize, void (*kern)(KArgs...), dim3 block, size_t smem, cudaStream_t stream,
+                    Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
 // PDL inside the captured graph only (eager and profiled launches are plain), and
@@ -543,49 +567,92 @@ __global__ void kv_zero(T* x, long n) {
   if (i < n) x[i] = (T)0;
 }
 
-// ------------------------------------------------------------------ single-CTA tail kernel
+// ------------------------------------------------------------------ tail kernel
+//
+// Two forms of the same code.  CL = false: one CTA, every array of the tail
+// levels in shared memory, phases separated by __syncthreads.  CL = true: the
+// CTAs of one thread-block cluster, the arrays in global memory (the levels' own
+// w and b buffers, L2-resident at these sizes), loops strided over every thread of
+// the cluster and phases separated by the cluster barrier, whose arrive/wait pair
+// has release/acquire semantics at cluster scope (a hardware barrier: no spin).
+// Every loop below has the same trip count in all threads, and the kernel has no
+// early exit, so every thread reaches every barrier.
 
-// rE = -dt E_l w of a tail level, all rows, into the velocity part of r (shared
-// memory): clear, then force + spread per point quad with shared-memory atomics.
-template <typename T, typename TM>
+template <bool CL>
+struct TailCtx;
+template <>
+struct TailCtx<false> {
+  __device__ static int id() { return threadIdx.x; }
+  __device__ static int n() { return blockDim.x; }
+  __device__ static void sync() { __syncthreads(); }
+};
+template <>
+struct TailCtx<true> {
+  __device__ static unsigned rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+  }
+  __device__ static unsigned size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+  }
+  // warps interleaved over the CTAs (work item k of a strided loop runs in CTA
+  // (k / 32) mod size), so that small phases spread over every SM of the cluster
+  __device__ static int id() { return (int)((((threadIdx.x >> 5) * size() + rank()) << 5) + (threadIdx.x & 31)); }
+  __device__ static int n() { return (int)(size() * blockDim.x); }
+  // release/acquire at cluster scope (the defaults of arrive and wait)
+  __device__ static void sync() { asm volatile("barrier.cluster.arrive;\n\tbarrier.cluster.wait;" ::: "memory"); }
+};
+
+// rE = -dt E_l w of a tail level, all rows, into the velocity part of r: clear,
+// then force + spread per point quad with atomic additions.
+template <typename T, typename TM, bool CL>
 __device__ void tail_elastic(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, T* r) {
+  using C = TailCtx<CL>;
+  const int tid = C::id(), nt = C::n();
   const int n2 = 2 * L.N * L.N, np = A.sp.np, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < n2; e += blockDim.x) r[e] = (T)0;
-  __syncthreads();
+  for (int e = tid; e < n2; e += nt) r[e] = (T)0;
+  C::sync();
   // 4 np is a multiple of 4: the four lanes of a quad run the same iterations
-  for (int t = threadIdx.x; t < 4 * np; t += blockDim.x)
+  for (int t = tid; t < 4 * np; t += nt)
     force_spread_quad<T, false>(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box,
                                 -1, r);
-  __syncthreads();
+  C::sync();
 }
 
 // Full residual r = b - A_l w of a tail level (for the restriction).
-template <typename T, typename TM>
+template <typename T, typename TM, bool CL>
 __device__ void tail_residual(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, const T* b, T* r) {
+  using C = TailCtx<CL>;
+  const int tid = C::id(), nt = C::n();
   const bool hasE = A.has_E;
-  if (hasE) tail_elastic(L, A, w, r);
+  if (hasE) tail_elastic<T, TM, CL>(L, A, w, r);
   const int N = L.N, n = N * N;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int e = tid; e < n; e += nt) {
     const int i = e & (N - 1), j = e / N;
     r[e] = (hasE ? r[e] : (T)0) + b[e] - stokes_row(w, N, L.c, 0, i, j);
     r[n + e] = (hasE ? r[n + e] : (T)0) + b[n + e] - stokes_row(w, N, L.c, 1, i, j);
     r[2 * n + e] = b[2 * n + e] - stokes_row(w, N, L.c, 2, i, j);
   }
-  __syncthreads();
+  C::sync();
 }
 
 // One colour of box solves on a tail level: every residual of the colour's boxes
 // is staged first (1 x 1 boxes of one colour are neighbours, so all residuals
 // must be taken before any update), then each (box, row) product of the box
-// inverse is split over G lanes (G as large as the CTA allows, at most 32).
-// rE: the level's elasticity term in shared memory, or NULL.
-template <typename T, typename TM>
+// inverse is split over G lanes (G as large as the thread count allows, at most 32).
+// rE: the level's elasticity term, or NULL.
+template <typename T, typename TM, bool CL>
 __device__ void tail_boxes(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* b, const T* rE, T* w,
                            int color, T* sr, int* sg) {
+  using C = TailCtx<CL>;
+  const int tid = C::id(), nt = C::n();
   const int N = L.N, n = N * N, bs = A.box, nB = A.nB;
   const int nb = N / bs, half = nb >> 1, nbox = half * half;
   const int items = nbox * nB;
-  for (int e = threadIdx.x; e < items; e += blockDim.x) {
+  for (int e = tid; e < items; e += nt) {
     const int t = e / nB, q = e - t * nB;
     const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
     int cc, i, j;
@@ -596,12 +663,12 @@ __device__ void tail_boxes(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, 
     sr[e] = r;
     sg[e] = gq;
   }
-  __syncthreads();
+  C::sync();
   int G = 32;
-  while (G > 1 && items * G > (int)blockDim.x) G >>= 1;
+  while (G > 1 && items * G > nt) G >>= 1;
   const int total = items * G;
-  for (int base = 0; base < total; base += blockDim.x) {  // same trip count in every thread
-    const int e = base + threadIdx.x, it = e / G, gl = e - it * G;
+  for (int base = 0; base < total; base += nt) {  // same trip count in every thread
+    const int e = base + tid, it = e / G, gl = e - it * G;
     T d = 0;
     if (it < items) {
       const int t = it / nB, q = it - t * nB;
@@ -623,89 +690,226 @@ __device__ void tail_boxes(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, 
     for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if (it < items && gl == 0) w[sg[it]] += d;
   }
-  __syncthreads();
+  C::sync();
 }
 
-template <typename T, typename TM>
+template <typename T, typename TM, bool CL>
 __device__ void tail_sweep(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, T* w, const T* b, T* r, bool rev,
                            T* sr, int* sg) {
   for (int cc = 0; cc < 4; ++cc) {
     const int color = rev ? seq_color(3 - cc) : seq_color(cc);
-    if (A.has_E) tail_elastic(L, A, w, r);
-    tail_boxes(L, A, b, A.has_E ? r : nullptr, w, color, sr, sg);
+    if (A.has_E) tail_elastic<T, TM, CL>(L, A, w, r);
+    tail_boxes<T, TM, CL>(L, A, b, A.has_E ? r : nullptr, w, color, sr, sg);
   }
 }
 
+// ---- cluster form: two cluster barriers per colour
+//
+// The elasticity term is spread with the colour filter into rE (the tail's finest
+// level's own buffer, zero between phases), and each box takes its rows back out
+// and clears them, as the grid-wide kernels do.  CTA r owns the boxes r, r + C,
+// r + 2C, ... of the colour (C CTAs): it stages their residuals in its shared
+// memory and applies their inverses behind a CTA barrier (n x n boxes, n >= 2, of
+// one colour are farther apart than the stencil reaches; 1 x 1 boxes need the
+// cluster barrier there).
+
 template <typename T, typename TM>
+__device__ void ctail_spread(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, int color, T* re) {
+  using C = TailCtx<true>;
+  const int tid = C::id(), nt = C::n(), np = A.sp.np, lane = threadIdx.x & 31;
+  for (int t = tid; t < 4 * np; t += nt)
+    force_spread_quad<T, false>(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box,
+                                color, re);
+  C::sync();
+}
+
+template <typename T, typename TM>
+__device__ void ctail_boxes(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* b, T* re, T* w, int color,
+                            T* sr, int* sg) {
+  using C = TailCtx<true>;
+  const int N = L.N, n = N * N, bs = A.box, nB = A.nB;
+  const int nb = N / bs, half = nb >> 1, nbox = half * half;
+  const int cs = (int)C::size(), rk = (int)C::rank();
+  const int mine = nbox > rk ? (nbox - rk + cs - 1) / cs : 0;  // boxes rk + cs k, k < mine
+  const int items = mine * nB;
+  for (int e = threadIdx.x; e < items; e += blockDim.x) {
+    const int k = e / nB, q = e - k * nB, t = rk + cs * k;
+    const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+    int cc, i, j;
+    box_unknown(q, bs, I * bs, J * bs, N, &cc, &i, &j);
+    const int gq = cc * n + j * N + i;
+    T r = b[gq] - stokes_row(w, N, L.c, cc, i, j);
+    if (re && cc < 2) {
+      r += re[gq];
+      re[gq] = (T)0;
+    }
+    sr[e] = r;
+    sg[e] = gq;
+  }
+  if (bs == 1) {
+    C::sync();
+  } else {
+    __syncthreads();
+  }
+  int G = 32;
+  while (G > 1 && items * G > (int)blockDim.x) G >>= 1;
+  const int total = items * G;
+  for (int base = 0; base < total; base += blockDim.x) {  // same trip count in every thread of the CTA
+    const int e = base + threadIdx.x, it = e / G, gl = e - it * G;
+    T d = 0;
+    if (it < items) {
+      const int k = it / nB, q = it - k * nB, t = rk + cs * k;
+      const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+      const int sl = L.slot[J * nb + I];
+      const T* rs = sr + k * nB;
+      if (sl >= 0) {
+        const double* M = L.Ms + (size_t)sl * nB * nB + q;
+        double dd = 0.0;
+        for (int s = gl; s < nB; s += G) dd += M[(size_t)s * nB] * (double)rs[s];
+        d = (T)dd;
+      } else {
+        const TM* M = L.Mf + q;
+        TM dm = 0;
+        for (int s = gl; s < nB; s += G) dm += M[(size_t)s * nB] * (TM)rs[s];
+        d = (T)dm;
+      }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (it < items && gl == 0) w[sg[it]] += d;
+  }
+  C::sync();
+}
+
+template <typename T, typename TM>
+__device__ void ctail_sweep(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, T* w, const T* b, T* re, bool rev,
+                            T* sr, int* sg) {
+  for (int cc = 0; cc < 4; ++cc) {
+    const int color = rev ? seq_color(3 - cc) : seq_color(cc);
+    if (A.has_E) ctail_spread(L, A, w, color, re);
+    ctail_boxes(L, A, b, A.has_E ? re : nullptr, w, color, sr, sg);
+  }
+}
+
+// r = b - A_l w, all rows; rE is read once per row and cleared.
+template <typename T, typename TM>
+__device__ void ctail_residual(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, const T* b, T* re,
+                               T* r) {
+  using C = TailCtx<true>;
+  const int tid = C::id(), nt = C::n();
+  const bool hasE = A.has_E;
+  if (hasE) ctail_spread(L, A, w, -1, re);
+  const int N = L.N, n = N * N;
+  for (int e = tid; e < n; e += nt) {
+    const int i = e & (N - 1), j = e / N;
+    T eu = 0, ev = 0;
+    if (hasE) {
+      eu = re[e];
+      ev = re[n + e];
+      re[e] = (T)0;
+      re[n + e] = (T)0;
+    }
+    r[e] = eu + b[e] - stokes_row(w, N, L.c, 0, i, j);
+    r[n + e] = ev + b[n + e] - stokes_row(w, N, L.c, 1, i, j);
+    r[2 * n + e] = b[2 * n + e] - stokes_row(w, N, L.c, 2, i, j);
+  }
+  C::sync();
+}
+
+template <typename T, typename TM, bool CL>
 __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T, TM> A) {
   pdl_enter();
+  using C = TailCtx<CL>;
+  const int tid = C::id(), nt = C::n();
   extern __shared__ __align__(16) unsigned char smem[];
   T* W[MAX_LEVELS];
   T* B[MAX_LEVELS];
   const int nl = A.nlev;
-  for (int l = 0; l < nl; ++l) {
-    W[l] = (T*)(smem + A.off_w[l]);
-    B[l] = (T*)(smem + A.off_b[l]);
-  }
-  T* r = (T*)(smem + A.off_r);
-  T* sr = (T*)(smem + A.off_sr);
-  int* sg = (int*)(smem + A.off_sg);
-  {
+  T *r, *sr;
+  int* sg;
+  T* re = nullptr;
+  if (CL) {
+    for (int l = 0; l < nl; ++l) {
+      W[l] = A.gw[l];
+      B[l] = A.gb[l];  // B[0] is the input b_in itself, W[0] the output w_out
+    }
+    r = A.gr;
+    re = A.gre;
+    sr = (T*)(smem + A.off_sr);  // this CTA's boxes
+    sg = (int*)(smem + A.off_sg);
+  } else {
+    for (int l = 0; l < nl; ++l) {
+      W[l] = (T*)(smem + A.off_w[l]);
+      B[l] = (T*)(smem + A.off_b[l]);
+    }
+    r = (T*)(smem + A.off_r);
+    sr = (T*)(smem + A.off_sr);
+    sg = (int*)(smem + A.off_sg);
     const int n0 = 3 * A.lev[0].N * A.lev[0].N;
-    for (int e = threadIdx.x; e < n0; e += blockDim.x) B[0][e] = A.b_in[e];
+    for (int e = tid; e < n0; e += nt) B[0][e] = A.b_in[e];
   }
-  __syncthreads();
+  C::sync();
   for (int l = 0; l < nl - 1; ++l) {
     const TailLevel<T, TM>& L = A.lev[l];
     const int n3 = 3 * L.N * L.N;
-    for (int e = threadIdx.x; e < n3; e += blockDim.x) W[l][e] = (T)0;
-    __syncthreads();
-    for (int s = 0; s < A.nu1; ++s) tail_sweep(L, A, W[l], B[l], r, false, sr, sg);
-    tail_residual(L, A, W[l], B[l], r);
+    for (int e = tid; e < n3; e += nt) W[l][e] = (T)0;
+    C::sync();
+    if constexpr (CL) {
+      for (int s = 0; s < A.nu1; ++s) ctail_sweep<T, TM>(L, A, W[l], B[l], re, false, sr, sg);
+      ctail_residual<T, TM>(L, A, W[l], B[l], re, r);
+    } else {
+      for (int s = 0; s < A.nu1; ++s) tail_sweep<T, TM, CL>(L, A, W[l], B[l], r, false, sr, sg);
+      tail_residual<T, TM, CL>(L, A, W[l], B[l], r);
+    }
     const int Nc = L.N / 2, ncell = Nc * Nc;
-    for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+    for (int e = tid; e < ncell; e += nt) {
       T ru, rv, rp;
       restrict_cell(r, L.N, e % Nc, e / Nc, &ru, &rv, &rp);
       B[l + 1][e] = ru;
       B[l + 1][ncell + e] = rv;
       B[l + 1][2 * ncell + e] = rp;
     }
-    __syncthreads();
+    C::sync();
   }
   {
     // exact bordered solve on the coarsest grid: w = (M^{-1})[0:nc, 0:nc] b
     const T* bc = B[nl - 1];
     T* wc = W[nl - 1];
-    for (int q = threadIdx.x; q < A.nc; q += blockDim.x) {
+    for (int q = tid; q < A.nc; q += nt) {
       double acc = 0.0;
       for (int s = 0; s < A.nc; ++s) acc += A.Mc[(size_t)s * A.ldc + q] * (double)bc[s];
       wc[q] = (T)acc;
     }
-    __syncthreads();
+    C::sync();
   }
   for (int l = nl - 2; l >= 0; --l) {
     const TailLevel<T, TM>& L = A.lev[l];
     const int N = L.N, n = N * N;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    for (int e = tid; e < n; e += nt) {
       T cu, cv, cp;
       prolong_cell(W[l + 1], N, e & (N - 1), e / N, &cu, &cv, &cp);
       W[l][e] += cu;
       W[l][n + e] += cv;
       W[l][2 * n + e] += cp;
     }
-    __syncthreads();
-    for (int s = 0; s < A.nu2; ++s) tail_sweep(L, A, W[l], B[l], r, A.post_rev != 0, sr, sg);
+    C::sync();
+    for (int s = 0; s < A.nu2; ++s) {
+      if constexpr (CL) {
+        ctail_sweep<T, TM>(L, A, W[l], B[l], re, A.post_rev != 0, sr, sg);
+      } else {
+        tail_sweep<T, TM, CL>(L, A, W[l], B[l], r, A.post_rev != 0, sr, sg);
+      }
+    }
   }
-  {
+  if (!CL) {
     const int n0 = 3 * A.lev[0].N * A.lev[0].N;
-    for (int e = threadIdx.x; e < n0; e += blockDim.x) A.w_out[e] = W[0][e];
+    for (int e = tid; e < n0; e += nt) A.w_out[e] = W[0][e];
   }
 }
 
 // ------------------------------------------------------------------ host side
 
 template <typename T, typename TM>
-int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes) {
+int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes, int cluster = 0) {
   std::memset((void*)A, 0, sizeof(*A));
   A->nlev = P.nlev - lt;
   if (A->nlev > MAX_LEVELS) return fail(IB_ERR_INVALID_ARG, "too many tail levels");
@@ -752,6 +956,21 @@ int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes) 
   A->b_in = lbuf<T>(P.lev[lt]).b;
   A->w_out = lbuf<T>(P.lev[lt]).w;
   *smem_bytes = off;
+  if (cluster > 0) {
+    for (int q = 0; q < A->nlev; ++q) {
+      A->gw[q] = lbuf<T>(P.lev[lt + q]).w;
+      A->gb[q] = lbuf<T>(P.lev[lt + q]).b;
+    }
+    A->gr = lbuf<T>(P.lev[lt]).r;
+    A->gre = rEbuf<T>(P.lev[lt]);
+    // shared memory: the staged residuals of one CTA's boxes on the finest tail level
+    const size_t half = (size_t)P.lev[lt].N / P.prm.box / 2;
+    const size_t items = (half * half + cluster - 1) / cluster * (size_t)P.nB;
+    off = 0;
+    A->off_sr = (int)take(items * sizeof(T));
+    A->off_sg = (int)take(items * sizeof(int));
+    *smem_bytes = off;
+  }
   return IB_OK;
 }
 
@@ -847,12 +1066,18 @@ int vcycle_eager_t(Problem& P) {
     }
   }
   {
+    const int csize = P.tail_cluster[pix<T>()];
     TailArgs<T, TM> A;
     size_t smem = 0;
-    IB_TRY((build_tail_args<T, TM>(P, lt, &A, &smem)));
+    IB_TRY((build_tail_args<T, TM>(P, lt, &A, &smem, csize)));
     KScope ks(P, IB_KC_COARSE, 0.0);
-    vlaunch(use_pdl(P), kv_tail<T, TM>, 1, TAIL_THREADS, smem, P.stream, A);
-    IB_LAUNCH_CHECK();
+    if (csize > 0) {
+      if (smem > 48u * 1024u) return fail(IB_ERR_INVALID_ARG, "cluster tail staging above 48 KB");
+      IB_CUDA_TRY(claunch(use_pdl(P), csize, kv_tail<T, TM, true>, TAIL_THREADS, smem, P.stream, A));
+    } else {
+      vlaunch(use_pdl(P), kv_tail<T, TM, false>, 1, TAIL_THREADS, smem, P.stream, A);
+      IB_LAUNCH_CHECK();
+    }
   }
   for (int l = lt - 1; l >= 0; --l) {
     LevelInfo& L = P.lev[l];
@@ -898,7 +1123,8 @@ int tail_raise_smem_t(size_t smem_max) {
   static size_t granted = 0;
   std::lock_guard<std::mutex> lock(mu);
   if (smem_max > granted) {
-    IB_CUDA_TRY(cudaFuncSetAttribute(kv_tail<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    IB_CUDA_TRY(
+        cudaFuncSetAttribute(kv_tail<T, TM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     granted = smem_max;
   }
   return IB_OK;
@@ -911,6 +1137,48 @@ int tail_smem(Problem& P, int lt, size_t* bytes) {
     return tail_smem_t<double, double>(P, lt, bytes);
   } else {
     return tail_smem_t<float, float>(P, lt, bytes);
+  }
+}
+
+// CTAs per cluster of the cluster tail (16 where the device can co-schedule a
+// non-portable cluster of 16 CTAs of 1024 threads, else 8, else 0 = no cluster
+// form), found once per process.
+template <typename T, typename TM>
+int tail_cluster_size_t() {
+  static std::mutex mu;
+  static int cs = -1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cs >= 0) return cs;
+  cs = 0;
+  cudaFuncSetAttribute(kv_tail<T, TM, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(TAIL_THREADS);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kv_tail<T, TM, true>, &cfg) == cudaSuccess && n > 0) {
+      cs = c;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return cs;
+}
+
+template <typename T>
+int tail_cluster_size(const Problem& P) {
+  if constexpr (sizeof(T) == 8) {
+    if (P.prm.precision != IB_FP64) return tail_cluster_size_t<double, float>();
+    return tail_cluster_size_t<double, double>();
+  } else {
+    return tail_cluster_size_t<float, float>();
   }
 }
 
@@ -929,49 +1197,72 @@ int tail_raise_smem(Problem& P, size_t smem_max) {
 template <typename T>
 int vcycle_run(Problem& P);
 
-// Candidate first levels of the single-CTA tail kernel: levels with N_l <= 64
+// Candidate forms of the tail: the single-CTA kernel from levels with N_l <= 64
 // (FP32) or <= 32 (FP64) whose arrays fit in shared memory, plus "coarsest grid
-// only".  vcycle_prepare times one graph-replayed V-cycle per candidate on the
-// problem's own hierarchy and keeps the fastest (the autotuner of the level
-// split between grid-wide kernels and the single-CTA kernel).
+// only"; and the cluster kernel from levels with 16 <= N_l <= 128.
+// vcycle_prepare times one graph-replayed V-cycle per candidate on the problem's
+// own hierarchy and keeps the fastest (the autotuner of the level split between
+// grid-wide kernels and the tail kernel).
 template <typename T>
 int vcycle_prepare(Problem& P) {
   const int nmax = sizeof(T) == 4 ? 64 : 32;
-  std::vector<int> cand;
+  struct Cand {
+    int l, cs;
+  };
+  std::vector<Cand> cand;
   size_t smem_max = 0;
   for (int l = 0; l < P.nlev; ++l) {
     if (P.lev[l].N > nmax) continue;
     size_t s = 0;
     IB_TRY(tail_smem<T>(P, l, &s));
     if (s <= 227u * 1024u) {
-      cand.push_back(l);
+      cand.push_back({l, 0});
       if (s > smem_max) smem_max = s;
     }
   }
-  if (cand.empty() || cand.back() != P.nlev - 1) {
+  if (cand.empty() || cand.back().l != P.nlev - 1) {
     size_t s = 0;
     IB_TRY(tail_smem<T>(P, P.nlev - 1, &s));
-    cand.push_back(P.nlev - 1);
+    cand.push_back({P.nlev - 1, 0});
     if (s > smem_max) smem_max = s;
   }
   IB_TRY(tail_raise_smem<T>(P, smem_max));
+  const int cs = P.use_graph ? tail_cluster_size<T>(P) : 0;
+  if (cs > 0)
+    for (int l = 0; l < P.nlev - 1; ++l)
+      if (P.lev[l].N <= 128 && P.lev[l].N >= 16) cand.push_back({l, cs});
   constexpr int ix = pix<T>();
   // IB_TAIL_NMAX pins the split instead of timing it (profiler runs distort the
-  // timings): the tail starts at the first candidate level with N_l <= value
+  // timings): the tail starts at the first candidate level with N_l <= value, in
+  // the single-CTA form where that level has one unless IB_TAIL_CLUSTER=1 (and
+  // IB_TAIL_CLUSTER=0 excludes the cluster form)
+  const char* ecl = std::getenv("IB_TAIL_CLUSTER");
+  const int want_cl = ecl ? (ecl[0] == '1' ? 1 : 0) : -1;
+  if (want_cl == 0) {
+    std::vector<Cand> keep;
+    for (const Cand& c : cand)
+      if (c.cs == 0) keep.push_back(c);
+    cand.swap(keep);
+  }
   if (const char* e = std::getenv("IB_TAIL_NMAX")) {
-    int nt = std::atoi(e);
-    int pick = cand.back();
-    for (int l : cand)
-      if (P.lev[l].N <= nt) {
-        pick = l;
-        break;
+    const int nt = std::atoi(e);
+    Cand pick = {-1, 0};
+    for (int pass = 0; pass < 2 && pick.l < 0; ++pass)
+      for (const Cand& c : cand) {
+        if (P.lev[c.l].N > nt) continue;
+        if (pass == 0 && want_cl == 1 && c.cs == 0) continue;
+        if (pass == 0 && want_cl != 1 && c.cs != 0) continue;
+        if (pick.l < 0 || c.l < pick.l) pick = c;
       }
-    P.tail_level[ix] = pick;
+    if (pick.l < 0) pick = {P.nlev - 1, 0};
+    P.tail_level[ix] = pick.l;
+    P.tail_cluster[ix] = pick.cs;
     P.graph_dirty[ix] = true;
     return IB_OK;
   }
   if (cand.size() == 1 || P.prof || !P.use_graph) {
-    P.tail_level[ix] = cand.front();
+    P.tail_level[ix] = cand.front().l;
+    P.tail_cluster[ix] = 0;
     P.graph_dirty[ix] = true;
     return IB_OK;
   }
@@ -981,11 +1272,12 @@ int vcycle_prepare(Problem& P) {
   long long saved[IB_KC_COUNT];
   std::memcpy(saved, P.nlaunch, sizeof(saved));
   float best = 1e30f;
-  int best_l = cand.front();
+  Cand best_c = cand.front();
   size_t n0 = 3ul * P.lev[0].N * P.lev[0].N;
   IB_CUDA_TRY(cudaMemsetAsync(lbuf<T>(P.lev[0]).b, 0, n0 * sizeof(T), P.stream));
-  for (int l : cand) {
-    P.tail_level[ix] = l;
+  for (const Cand& c : cand) {
+    P.tail_level[ix] = c.l;
+    P.tail_cluster[ix] = c.cs;
     P.graph_dirty[ix] = true;
     int rc = vcycle_run<T>(P);  // capture + warm-up
     if (rc != IB_OK) return rc;
@@ -997,13 +1289,14 @@ int vcycle_prepare(Problem& P) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      best_l = l;
+      best_c = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   std::memcpy(P.nlaunch, saved, sizeof(saved));
-  P.tail_level[ix] = best_l;
+  P.tail_level[ix] = best_c.l;
+  P.tail_cluster[ix] = best_c.cs;
   P.graph_dirty[ix] = true;
   return IB_OK;
 }

@@ -1,4 +1,5 @@
-// Launch arguments of the single-CTA coarse-level ("tail") kernel and the
+// Launch arguments of the coarse-level ("tail") kernel, on one CTA or one
+// thread-block cluster, and the
 // host entry points of the V-cycle engine.
 #pragma once
 
@@ -32,6 +33,12 @@ struct TailArgs {
   int nc, ldc;
   int nu1, nu2, box, nB, post_rev, has_E;
   int off_w[MAX_LEVELS], off_b[MAX_LEVELS], off_r, off_sr, off_sg;  // shared-memory offsets (bytes)
+  // cluster form (the tail spread over the CTAs of one thread-block cluster): the
+  // same arrays in global memory, W and B the levels' own buffers
+  T* gw[MAX_LEVELS];
+  T* gb[MAX_LEVELS];
+  T* gr;    // residual scratch (3 N^2 of the tail's finest level)
+  T* gre;   // elasticity term (2 N^2 of the tail's finest level; zero between phases)
 };
 
 template <typename T>

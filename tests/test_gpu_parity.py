@@ -130,6 +130,47 @@ def test_vcycle_fp64_multi_box_cta(pkg, name, box, monkeypatch):
     test_vcycle_fp64(pkg, name, box)
 
 
+@pytest.mark.parametrize("name,box,nmax", [("c1_64", 1, 64), ("c1_64", 2, 32), ("c1_64", 4, 64),
+                                           ("stiff_32_exact", 4, 32), ("c1_64", 8, 64), ("stiff_32", 2, 16)])
+def test_vcycle_fp64_cluster_tail(pkg, name, box, nmax, monkeypatch):
+    """The coarse levels from N = nmax down run on one thread-block cluster (arrays
+    in global memory, phases separated by the cluster barrier); nmax = N puts the
+    whole V-cycle there."""
+    monkeypatch.setenv("IB_TAIL_NMAX", str(nmax))
+    monkeypatch.setenv("IB_TAIL_CLUSTER", "1")
+    p = make_case(name, box)
+    rng = np.random.default_rng(11)
+    rhs = O.rhs_vector(p) + 0.1 * np.abs(O.rhs_vector(p)).max() * rng.standard_normal(3 * p.N * p.N)
+    n = p.N * p.N
+    rhs[2 * n:] -= rhs[2 * n:].mean()
+    ref = _oracle_vcycle(p, rhs)
+    s = pkg.IBSolver.from_problem(p)
+    w = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), w)
+    assert s.tail_cluster("fp64") >= 8 and s.tail_grid("fp64") == nmax
+    got = w.cpu().numpy()
+    assert rel_elementwise(got, ref) < 1e-10, (name, box, rel_elementwise(got, ref))
+    s.vcycle(dev(rhs), w)  # graph replay gives the same result
+    assert rel_elementwise(w.cpu().numpy(), ref) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_vcycle_cluster_tail_low_precision(pkg, prec, monkeypatch):
+    monkeypatch.setenv("IB_TAIL_NMAX", "32")
+    monkeypatch.setenv("IB_TAIL_CLUSTER", "1")
+    p = make_case("stiff_32_exact", 4)
+    rhs = O.rhs_vector(p)
+    ref = _oracle_vcycle(p, rhs)
+    s = pkg.IBSolver.from_problem(p, precision=prec)
+    w = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), w)
+    assert s.tail_cluster(prec) >= 8
+    got = w.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
+    s.close()
+
+
 @pytest.mark.parametrize("name,box", [("c1_64", 1), ("stiff_32_exact", 4)])
 def test_vcycle_fp32(pkg, name, box):
     p = make_case(name, box)
@@ -187,6 +228,14 @@ def test_solve_step(pkg, name, box, prec):
     Xn = X.cpu().numpy()
     assert np.abs(Xn - ref.X).max() <= 1e-6 * p.h
     s.close()
+
+
+@pytest.mark.parametrize("name,box,prec", [("c1_64", 1, "fp64"), ("stiff_32", 4, "mixed")])
+def test_solve_step_cluster_tail(pkg, name, box, prec, monkeypatch):
+    """One implicit step with the coarse levels on a thread-block cluster."""
+    monkeypatch.setenv("IB_TAIL_NMAX", "32")
+    monkeypatch.setenv("IB_TAIL_CLUSTER", "1")
+    test_solve_step(pkg, name, box, prec)
 
 
 def test_no_structure_and_zero_rhs(pkg):
