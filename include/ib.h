@@ -163,7 +163,12 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  *   stats  host, may be NULL
  * Re-forms S, J and the hierarchy from X^n, solves with MG-preconditioned
  * FGMRES to params.tol, then moves the points.  Returns IB_ERR_NOT_CONVERGED
- * if max_iters was reached (the best iterate is still written and X moved). */
+ * if max_iters was reached (the best iterate is still written and X moved),
+ * IB_ERR_TIMEOUT if a bulk copy of the Krylov basis did not land within 1 s.
+ * FGMRES orthogonalises by classical Gram-Schmidt applied twice, in three
+ * passes over the basis; the environment variable IB_CGS_FUSED=0 (read at
+ * ib_setup) splits the middle pass in two, the form otherwise taken only when a
+ * 64-element slice of the whole basis does not fit in shared memory. */
 IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,
                   ib_stats* stats);
 

@@ -253,6 +253,8 @@ struct Problem {
   int cgs_smem_max = 0;       // dynamic shared memory limit of the fused Gram-Schmidt pass
   int occ_multidot = 0;       // resident blocks per SM of the partial-dot kernel
   int occ_subnorm = 0;        // ... and of the last Gram-Schmidt subtraction
+  std::vector<int> occ_cgs;   // resident blocks per SM of the fused pass, by basis size
+  bool cgs_fused = true;      // middle Gram-Schmidt step as one fused pass
   int* count = nullptr;       // device counter
   int* count_host = nullptr;  // pinned
 

@@ -6,6 +6,7 @@
 // between preconditioner applications.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "ib_internal.cuh"
 
@@ -370,6 +371,10 @@ int krylov_init(Problem& P) {
   P.cgs_smem_max = std::max(0, optin - 256);  // leaves room for the static shared memory (one mbarrier)
   IB_CUDA_TRY(cudaFuncSetAttribute(k_cgs_sub_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, P.cgs_smem_max));
   P.dot_blocks = 8 * std::max(1, P.n_sm);
+  // IB_CGS_FUSED=0 takes the two-pass form of the middle Gram-Schmidt step always
+  // (to test it: it is otherwise reached only above ~450 basis vectors)
+  const char* e = std::getenv("IB_CGS_FUSED");
+  P.cgs_fused = !(e && e[0] == '0');
   IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_multidot, k_multidot_partial, TPB, 0));
   IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_subnorm, k_sub_norm, TPB, 0));
   return IB_OK;
@@ -411,13 +416,16 @@ int launch_dot(Problem& P, const double* a, const double* b, double* out) { retu
 int launch_cgs_sub_dot(Problem& P, const double* V, int nvec, const double* coef, double* w, double* out) {
   const long n = nvec_len(P);
   const size_t smem = ((size_t)nvec * CGS_CH + CGS_CH + 2ul * nvec) * sizeof(double);
-  if (smem > (size_t)P.cgs_smem_max || (n & 1)) {
+  if (!P.cgs_fused || smem > (size_t)P.cgs_smem_max || (n & 1)) {
     IB_TRY(launch_multiaxpy(P, V, nvec, coef, w));
     return launch_multidot(P, V, nvec, w, out);
   }
-  int per_sm = 0;
-  IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_sub_dot, CGS_CH, smem));
-  per_sm = std::max(1, std::min(per_sm, 8));
+  if ((int)P.occ_cgs.size() <= nvec) P.occ_cgs.resize((size_t)nvec + 1, 0);
+  int& per_sm = P.occ_cgs[nvec];
+  if (per_sm == 0) {
+    IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_sub_dot, CGS_CH, smem));
+    per_sm = std::max(1, std::min(per_sm, 8));
+  }
   const long chunks = (n + CGS_CH - 1) / CGS_CH;
   const int cols = (int)std::min<long>({chunks, (long)P.n_sm * per_sm, (long)P.dot_blocks});
   {

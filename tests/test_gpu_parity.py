@@ -238,6 +238,14 @@ def test_solve_step_cluster_tail(pkg, name, box, prec, monkeypatch):
     test_solve_step(pkg, name, box, prec)
 
 
+@pytest.mark.parametrize("name,box,prec", [("c1_64", 1, "fp64"), ("stiff_32", 4, "mixed")])
+def test_solve_step_two_pass_gram_schmidt(pkg, name, box, prec, monkeypatch):
+    """The middle Gram-Schmidt step as two passes (subtract, then project), the
+    form taken when the basis slice does not fit in shared memory."""
+    monkeypatch.setenv("IB_CGS_FUSED", "0")
+    test_solve_step(pkg, name, box, prec)
+
+
 def test_no_structure_and_zero_rhs(pkg):
     """Edge cases: no Lagrangian points (pure Stokes, b = 0 -> zero solution)."""
     p = W.single_ellipse(N=16, n_points=8)
