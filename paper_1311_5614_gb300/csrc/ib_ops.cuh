@@ -1,6 +1,6 @@
 // Element-level device functions of the V-cycle, shared by the grid-wide
-// kernels of the fine levels and the single-CTA kernel of the coarse levels.
-// Pointers may address global or shared memory.
+// kernels of the fine levels and the tail kernel of the coarse levels (one CTA
+// or one thread-block cluster).  Pointers may address global or shared memory.
 #pragma once
 
 #include "ib_internal.cuh"
