@@ -211,6 +211,11 @@ IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);
  * a pool of host threads (up to 16; the environment variable IB_BATCH_THREADS
  * overrides the count) drives the problems' FGMRES iterations at the same time,
  * so the small, latency-bound launches of different problems overlap on the GPU.
+ * ib_solve_step_batch takes the problems longest first by the estimate
+ * N^2 min(1 + sigma / 1000, max_iters / 8), sigma = dt * max(kappa) / mu, on the
+ * fewest threads whose longest-first schedule of these estimates ends within 5 %
+ * of the costliest problem (a few stiff problems and many cheap ones: the cheap
+ * ones run one after another beside the stiff ones instead of all at once).
  *   params   host [nprob]
  *   pt_off   host [nprob + 1] point offsets (pt_off[0] = 0); sp_off likewise for springs
  *   X, springs, kappa, rest   host, concatenated per problem; spring indices are

@@ -988,8 +988,9 @@ namespace {
 
 // Run f(k) for k in [0, n) on up to `threads` host threads; returns the first
 // failing status (IB_ERR_NOT_CONVERGED only if nothing worse happened) and its message.
+// ids (may be NULL) names the problem of each k in the messages.
 template <typename F>
-int parallel_for(int n, int threads, F f, std::string* msg) {
+int parallel_for(int n, int threads, F f, std::string* msg, const std::vector<int>* ids = nullptr) {
   std::atomic<int> next(0);
   std::vector<int> codes(n, IB_OK);
   std::vector<std::string> msgs(n);
@@ -998,7 +999,7 @@ int parallel_for(int n, int threads, F f, std::string* msg) {
       int k = next.fetch_add(1);
       if (k >= n) break;
       codes[k] = f(k);
-      if (codes[k] != IB_OK) msgs[k] = "problem " + std::to_string(k) + ": " + g_err;
+      if (codes[k] != IB_OK) msgs[k] = "problem " + std::to_string(ids ? (*ids)[k] : k) + ": " + g_err;
     }
   };
   int nt = std::max(1, std::min(threads, n));
@@ -1015,6 +1016,37 @@ int parallel_for(int n, int threads, F f, std::string* msg) {
     }
   }
   return worst;
+}
+
+// Work order and worker count of a batch solve.  Order: longest first by the cost
+// estimate N^2 g(sigma), g = min(1 + sigma / 1000, max_iters / 8) (the iteration
+// count grows with the stiffness ratio sigma = dt kappa_max / mu: on the 256^2
+// sweep 7-8 iterations up to sigma = 100, 15 at 1e3, ~105 at 1e4).  Workers: the
+// fewest (up to the batch's thread count) whose longest-first schedule of these
+// estimates ends within 5 % of the costliest problem, so that the long stiff
+// runs, which set the makespan, share the GPU with as few other streams as the
+// rest of the batch allows.
+void batch_schedule(const ib_batch* B, std::vector<int>* order, int* workers) {
+  const int n = (int)B->probs.size();
+  std::vector<double> cost(n);
+  for (int k = 0; k < n; ++k) {
+    const Problem& P = B->probs[k]->P;
+    const double g = std::min(1.0 + P.sigma / 1000.0, std::max(1.0, P.prm.max_iters / 8.0));
+    cost[k] = (double)P.prm.N * P.prm.N * g;
+  }
+  order->resize(n);
+  for (int k = 0; k < n; ++k) (*order)[k] = k;
+  std::stable_sort(order->begin(), order->end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  const double cmax = n ? cost[(*order)[0]] : 0.0;
+  *workers = std::max(1, B->threads);
+  for (int w = 1; w < B->threads; ++w) {
+    std::vector<double> load(w, 0.0);
+    for (int k : *order) *std::min_element(load.begin(), load.end()) += cost[k];
+    if (*std::max_element(load.begin(), load.end()) <= 1.05 * cmax) {
+      *workers = w;
+      break;
+    }
+  }
 }
 
 void free_batch(ib_batch* B) {
@@ -1109,15 +1141,19 @@ int ib_solve_step_batch(ib_batch* B, const double* u_n_all, double* up_all, doub
   const int nprob = (int)B->probs.size();
   IB_CUDA_TRY(cudaEventRecord(B->start, B->caller));
   for (int k = 0; k < nprob; ++k) IB_CUDA_TRY(cudaStreamWaitEvent(B->streams[k], B->start, 0));
+  std::vector<int> order;
+  int workers = 1;
+  batch_schedule(B, &order, &workers);
   std::string msg;
-  int rc = parallel_for(nprob, B->threads, [&](int k) {
+  int rc = parallel_for(nprob, workers, [&](int i) {
+    const int k = order[i];
     Problem& P = B->probs[k]->P;
     const double* un = u_n_all ? u_n_all + (B->up_off[k] / 3) * 2 : nullptr;
     double* Xk = (X_all && P.np > 0) ? X_all + B->x_off[k] : nullptr;
     int c = solve_step_impl(P, un, up_all + B->up_off[k], Xk, stats ? &stats[k] : nullptr);
     cudaEventRecord(B->done[k], B->streams[k]);
     return c;
-  }, &msg);
+  }, &msg, &order);
   for (int k = 0; k < nprob; ++k) IB_CUDA_TRY(cudaStreamWaitEvent(B->caller, B->done[k], 0));
   if (rc != IB_OK) return fail(rc, msg);
   return IB_OK;
