@@ -54,13 +54,15 @@ Pins (tests/test_oracle_pins.py) fix each part against the paper or the
 mathematics: delta-kernel moments and golden values, the S / S^* adjoint and
 conservation, spring force sums and finite-difference Jacobians, manufactured
 Stokes solutions (second order), transfer identities, E symmetric and
-negative semidefinite, the box count and free-box identity, V-cycle
+negative semidefinite, the box count and free-box identity, the colour
+sweep solving its last colour's n x n boxes exactly (pure Stokes), V-cycle
 contraction, FGMRES against a dense direct solve at 16 x 16, flat iteration
 counts under refinement, translation and mirror symmetry, and energy decay.
-Parity unpinned: the exact iterates of the four-colour V-cycle (fixed only
-through those properties; the paper's own order is lexicographic) and the
-exact iteration counts of the periodic workloads (the paper prints counts only
-for its lid-driven-cavity problem).
+Parity unpinned: the exact iterates of the four-colour V-cycle with structure
+(same-colour boxes then couple through the elasticity term, and the block-Jacobi
+update inside a colour is fixed only through the properties above; the paper's
+own order is lexicographic) and the exact iteration counts of the periodic
+workloads (the paper prints counts only for its lid-driven-cavity problem).
 
 Vector layout: w = [u | v | p], each an N x N array, row-major with x fastest
 (index j*N + i).  u[j, i] sits at (i h, (j + 1/2) h), v[j, i] at

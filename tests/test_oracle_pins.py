@@ -359,6 +359,55 @@ def test_vcycle_stokes_contraction():
         assert rs[0] < r0 and rate < 0.35, (order, rate)
 
 
+def _box_rows(N, b, color):
+    """Unknowns of every b x b box of a colour, from the box definition (sec. 8):
+    u faces x = I b .. I b + b on rows J b .. J b + b - 1, v faces y = J b .. J b + b
+    on columns I b .. I b + b - 1, cells I b .. I b + b - 1 x J b .. J b + b - 1;
+    layout [u | v | p], index j N + i, periodic wrap; colour (I mod 2) + 2 (J mod 2)."""
+    n = N * N
+    rows = set()
+    for J in range(N // b):
+        for I in range(N // b):
+            if (I % 2) + 2 * (J % 2) != color:
+                continue
+            for j in range(J * b, J * b + b):
+                for i in range(I * b, I * b + b + 1):
+                    rows.add((j % N) * N + i % N)
+            for j in range(J * b, J * b + b + 1):
+                for i in range(I * b, I * b + b):
+                    rows.add(n + (j % N) * N + i % N)
+            for j in range(J * b, J * b + b):
+                for i in range(I * b, I * b + b):
+                    rows.add(2 * n + j * N + i)
+    return np.array(sorted(rows))
+
+
+@pytest.mark.parametrize("b", [2, 4])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_colour_sweep_solves_last_colour_boxes_exactly(b, reverse):
+    """Four-colour box smoother (sec. 6): n x n boxes (n >= 2) of one colour are
+    farther apart than the 5-point stencil reaches, so without structure the last
+    colour phase of a sweep solves its boxes' equations exactly: the residual
+    vanishes on every unknown of that colour's boxes (colour 2 forward, colour 0
+    reversed) and on no other colour's."""
+    N = 16
+    p = _small_problem(N=N, n=8, kappa=0.0)
+    levels, _ = O.build_hierarchy(p)
+    lev = levels[0]
+    O.prepare_boxes(lev, b)
+    rng = np.random.default_rng(21)
+    rhs = rng.standard_normal(3 * N * N)
+    w = O.smooth_color4(lev, rhs, rng.standard_normal(3 * N * N), reverse=reverse)
+    r = rhs - lev.A @ w
+    scale = np.abs(rhs).max()
+    last = 0 if reverse else 2
+    assert np.abs(r[_box_rows(N, b, last)]).max() <= 1e-10 * scale
+    for c in range(4):
+        if c != last:
+            others = np.setdiff1d(_box_rows(N, b, c), _box_rows(N, b, last))
+            assert np.abs(r[others]).max() > 1e-3 * scale, c
+
+
 def test_fgmres_matches_dense_direct_solve_16():
     for rho, kap, rest in ((1.0, 1e3, None), (0.0, 1e2, 0.0)):
         p = W.single_ellipse(N=16, n_points=24, kappa=kap, dt=1e-2, rho=rho, rest=rest,
