@@ -55,14 +55,15 @@ mathematics: delta-kernel moments and golden values, the S / S^* adjoint and
 conservation, spring force sums and finite-difference Jacobians, manufactured
 Stokes solutions (second order), transfer identities, E symmetric and
 negative semidefinite, the box count and free-box identity, the colour
-sweep solving its last colour's n x n boxes exactly (pure Stokes), V-cycle
+sweep solving its last colour's n x n boxes exactly (pure Stokes), the block-
+Jacobi update inside a colour (with structure, the sweep does not depend on
+the order of a colour's boxes; a colour's boxes share no unknown), V-cycle
 contraction, FGMRES against a dense direct solve at 16 x 16, flat iteration
 counts under refinement, translation and mirror symmetry, and energy decay.
-Parity unpinned: the exact iterates of the four-colour V-cycle with structure
-(same-colour boxes then couple through the elasticity term, and the block-Jacobi
-update inside a colour is fixed only through the properties above; the paper's
-own order is lexicographic) and the exact iteration counts of the periodic
-workloads (the paper prints counts only for its lid-driven-cavity problem).
+Parity unpinned: the exact iteration counts of the periodic workloads (the
+paper prints counts only for its lid-driven-cavity problem, and sweeps its
+boxes in lexicographic order where this oracle, like the GPU path, uses four
+colours).
 
 Vector layout: w = [u | v | p], each an N x N array, row-major with x fastest
 (index j*N + i).  u[j, i] sits at (i h, (j + 1/2) h), v[j, i] at

@@ -408,6 +408,37 @@ def test_colour_sweep_solves_last_colour_boxes_exactly(b, reverse):
             assert np.abs(r[others]).max() > 1e-3 * scale, c
 
 
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_colour_phase_is_block_jacobi_with_structure(b):
+    """Reading of sec. 5-6 for the GPU order: inside a colour every box is solved
+    from the colour's starting state.  With a stiff structure (same-colour
+    boxes coupled through the elasticity term) the sweep is then independent of
+    the order of the boxes inside each colour, which an in-place (Gauss-Seidel)
+    update inside a colour would not be; and a colour's boxes share no unknown."""
+    N = 32
+    p = _small_problem(N=N, n=48, kappa=1e4)
+    levels, _ = O.build_hierarchy(p)
+    lev = levels[0]
+    O.prepare_boxes(lev, b)
+    for c in range(4):
+        idx = lev.boxes["color"][c][0]
+        assert np.unique(idx.ravel()).size == idx.size, c
+    rng = np.random.default_rng(8)
+    rhs = rng.standard_normal(3 * N * N)
+    w0 = rng.standard_normal(3 * N * N)
+    ref = O.smooth_color4(lev, rhs, w0)
+    perm = {}
+    for c in range(4):
+        idx, Abb = lev.boxes["color"][c]
+        q = rng.permutation(idx.shape[0])
+        perm[c] = (idx[q], Abb[q])
+    lev.boxes = dict(lev.boxes, color=perm)
+    got = O.smooth_color4(lev, rhs, w0)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    moved = np.abs(O.smooth_color4(lev, rhs, ref) - ref).max()
+    assert moved > 1e-6 * np.abs(ref).max()  # the sweep is not a fixed point
+
+
 def test_fgmres_matches_dense_direct_solve_16():
     for rho, kap, rest in ((1.0, 1e3, None), (0.0, 1e2, 0.0)):
         p = W.single_ellipse(N=16, n_points=24, kappa=kap, dt=1e-2, rho=rho, rest=rest,
