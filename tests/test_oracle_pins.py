@@ -473,6 +473,33 @@ def test_iterations_flat_under_refinement_and_rise_with_stiffness():
     assert stiff > soft, (soft, stiff)
 
 
+def _iters(kappa, b=4, nu=(1, 1)):
+    p = W.single_ellipse(N=32, n_points=64, kappa=kappa, dt=1e-2)
+    p.box, (p.nu1, p.nu2), p.max_iters = b, nu, 200
+    r = O.solve_step(p).solve
+    return r.iters if r.converged else None
+
+
+def test_bigger_boxes_fewer_iterations_most_when_stiff():
+    """Sec. 6 (MG-GMRES for box sizes 1-8): the larger the box, the fewer the
+    iterations, the more so the stiffer the structure, and for very stiff
+    structures the single-box smoother does not converge within the cap while
+    the big boxes do."""
+    mild = [_iters(1e4, b) for b in (1, 2, 4, 8)]
+    stiff = [_iters(1e6, b) for b in (1, 2, 4, 8)]
+    assert all(x is not None for x in mild) and mild == sorted(mild, reverse=True), mild
+    assert stiff[0] is None and None not in stiff[1:], stiff
+    assert stiff[1] > stiff[2] > stiff[3], stiff
+    assert stiff[1] - stiff[3] > mild[1] - mild[3], (mild, stiff)
+
+
+def test_more_smoothing_sweeps_fewer_iterations():
+    """Sec. 6 (table of nu1, nu2 for b = 4): the iteration count falls as the
+    number of pre- and post-smoothing sweeps grows."""
+    its = [_iters(1e5, 4, nu) for nu in ((1, 0), (1, 1), (2, 1), (2, 2))]
+    assert None not in its and its == sorted(its, reverse=True) and its[0] > its[-1], its
+
+
 def test_translation_by_one_cell_shifts_solution():
     N = 32
     p = W.single_ellipse(N=N, n_points=48, kappa=1e3, center=(0.45, 0.52))
