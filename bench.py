@@ -548,6 +548,48 @@ def run_multi1024(args):
     return 0
 
 
+def run_case256(args):
+    """One case of the 256^2 sweep on its own (--case K, CASES order; 7 = the stiff
+    kappa = 1e6, dt = 1e-2 case): a solver set up once, then W untimed and K timed
+    implicit steps, each from the case's initial points.  With --warmup 0 --steps 1
+    the process runs the set-up and exactly one step (the ncu captures of the
+    Gram-Schmidt kernels select launches by their index in that sequence)."""
+    import torch
+
+    import paper_1311_5614_gb300 as pkg
+
+    torch.cuda.set_device(args.local_rank)
+    p = workload_problems(args.box)[args.case]
+    s = pkg.IBSolver.from_problem(p, precision=args.precision, max_iters=args.max_iters)
+    up = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    X0 = torch.tensor(p.X, dtype=torch.float64, device="cuda")
+    X = X0.clone()
+    stream = torch.cuda.current_stream()
+    stats = []
+
+    def step():
+        X.copy_(X0)
+        stats.append(s.solve_step(None, up, X))
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clk = ClockSampler(args.local_rank)
+    clk.start()
+    ms = _timed_steps(torch, step, flush, stream, args.warmup, args.steps)
+    clocks = clk.stop()
+    s.close()
+    kappa, dt = CASES[args.case]
+    line = {"metric": METRIC, "value": sum(ms) / len(ms), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": DTYPE[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "256^2 MAC grid, 512-point ellipse, kappa=%g, dt=%g (one sweep case)" % (kappa, dt),
+                       "box": args.box, "precision": args.precision, "max_iters": args.max_iters},
+            "iters": [x["iters"] for x in stats], "status": [x["status"] for x in stats],
+            "escalated_at": [x["escalated_at"] for x in stats], "setup_ms": [x["t_setup_ms"] for x in stats],
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch256(args):
     """256 independent problems, grids drawn from {64, 128, 256, 512} (seed 5614), one
     ellipse each with 4 points per cell of perimeter, kappa log-uniform in [1, 1e6]:
@@ -606,12 +648,15 @@ def main(argv=None):
     ap.add_argument("--box", type=int, default=4)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--grid", type=int, default=2048, help="grid size of the vcycle workload")
+    ap.add_argument("--case", type=int, default=7, choices=range(len(CASES)),
+                    help="case256: index into the sweep's cases (7: kappa=1e6, dt=1e-2)")
     ap.add_argument("--learn-problems", type=int, default=40)
     ap.add_argument("--learn-pairs", type=int, default=256,
                     help="pairs per training problem (40 x 256 = 10240 pairs by default)")
     ap.add_argument("--save-params", default=None, help="learned512: write the trained U-Net parameters (.npy)")
     ap.add_argument("--learn-epochs", type=int, default=2)
-    ap.add_argument("--workload", default="sweep256", choices=["sweep256", "multi1024", "batch256", "vcycle", "learned512"],
+    ap.add_argument("--workload", default="sweep256",
+                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512"],
                     help="sweep256 (default): the 256^2 kappa x dt sweep; multi1024 / batch256: the "
                          "1024^2 multi-structure run and the 256-problem batch (extra lines)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
@@ -645,6 +690,8 @@ def main(argv=None):
             return run_multi1024(args)
         if args.workload == "batch256":
             return run_batch256(args)
+        if args.workload == "case256":
+            return run_case256(args)
         if args.workload == "vcycle":
             return run_vcycle(args)
         if args.workload == "learned512":
