@@ -551,9 +551,9 @@ def run_multi1024(args):
 def run_case256(args):
     """One case of the 256^2 sweep on its own (--case K, CASES order; 7 = the stiff
     kappa = 1e6, dt = 1e-2 case): a solver set up once, then W untimed and K timed
-    implicit steps, each from the case's initial points.  With --warmup 0 --steps 1
-    the process runs the set-up and exactly one step (the ncu captures of the
-    Gram-Schmidt kernels select launches by their index in that sequence)."""
+    implicit steps, each from the case's initial points.  The first step follows
+    the set-up directly, so an ncu capture can select a launch of that step by its
+    index (the Gram-Schmidt kernels launch nowhere else before it)."""
     import torch
 
     import paper_1311_5614_gb300 as pkg
