@@ -61,7 +61,9 @@ the order of a colour's boxes; a colour's boxes share no unknown), V-cycle
 contraction, FGMRES against a dense direct solve at 16 x 16, flat iteration
 counts under refinement, the paper's trends (sec. 6: bigger boxes and more
 smoothing sweeps take fewer iterations, the 1 x 1 box smoother fails on very
-stiff structures), translation and mirror symmetry, and energy decay.
+stiff structures), the stand-alone multigrid solver's contraction equal to the
+spectral radius of its iteration matrix and that spectrum's behaviour with
+stiffness (sec. 5), translation and mirror symmetry, and energy decay.
 Parity unpinned: the exact iteration counts of the periodic workloads (the
 paper prints counts only for its lid-driven-cavity problem, and sweeps its
 boxes in lexicographic order where this oracle, like the GPU path, uses four
@@ -746,3 +748,55 @@ def direct_solve(A, b, N, rho):
     M = np.block([[Ad, Z], [Z.T, np.zeros((k, k))]])
     sol = np.linalg.solve(M, np.concatenate([b, np.zeros(k)]))
     return sol[: Ad.shape[0]]
+
+
+# ----------------------------------------------------------------------------
+# Multigrid as a stand-alone solver and its iteration matrix (sec. 5)
+# ----------------------------------------------------------------------------
+
+
+def mg_solve(levels, b, tol=1e-8, max_iters=100, nu1=1, nu2=1, rho=1.0, order="color4", x0=None):
+    """Multigrid as a solver (sec. 5, solver performance): from x0 (zero by
+    default) repeat x <- x + MGV(0, b - A x), one V-cycle per iteration, until
+    ||b - A x|| <= tol ||b|| or max_iters cycles."""
+    A = levels[0].A
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    history = []
+    k = 0
+    while True:
+        r = b - A @ x
+        rel = np.linalg.norm(r) / bnorm if bnorm > 0.0 else 0.0
+        history.append(rel)
+        if rel <= tol or k == max_iters:
+            break
+        x = x + vcycle(levels, r, np.zeros_like(r), nu1, nu2, rho, order)
+        k += 1
+    return SolveResult(x, k, history[-1], history, history[-1] <= tol)
+
+
+def iteration_matrix(levels, nu1=1, nu2=1, rho=1.0, order="color4"):
+    """Multigrid iteration matrix (sec. 5, spectrum): column k is one cycle
+    applied to the error e_k (the k-th unit vector) with a zero right-hand
+    side, e_k - MGV(0, A e_k).  Dense: small grids only."""
+    A = levels[0].A
+    n = A.shape[0]
+    M = np.empty((n, n))
+    e = np.zeros(n)
+    for k in range(n):
+        e[k] = 1.0
+        M[:, k] = e - vcycle(levels, A @ e, np.zeros(n), nu1, nu2, rho, order)
+        e[k] = 0.0
+    return M
+
+
+def spectrum_mean_zero_pressure(M, N):
+    """Eigenvalues of the iteration matrix on the space of zero-mean pressure
+    (sec. 5: a constant pressure is a trivial eigenvector with eigenvalue 1,
+    which the paper excludes from the spectral radius).  Returns the eigenvalues
+    of Q M Q, Q the orthogonal projector onto that space (the constant pressure
+    maps to 0)."""
+    n = N * N
+    Q = np.eye(3 * n)
+    Q[2 * n:, 2 * n:] -= 1.0 / n
+    return np.linalg.eigvals(Q @ M @ Q)

@@ -500,6 +500,59 @@ def test_more_smoothing_sweeps_fewer_iterations():
     assert None not in its and its == sorted(its, reverse=True) and its[0] > its[-1], its
 
 
+# ---------------------------------------------------------------- MG as a solver, iteration matrix (sec. 5)
+
+def _mg16(kappa, b):
+    p = W.single_ellipse(N=16, n_points=32, kappa=kappa, dt=1e-2, a=0.23, b=0.17, center=(0.47, 0.53))
+    p.box, p.max_iters = b, 200
+    levels, _ = O.build_hierarchy(p)
+    for lev in levels[:-1]:
+        O.prepare_boxes(lev, b)
+    ev = O.spectrum_mean_zero_pressure(O.iteration_matrix(levels, p.nu1, p.nu2, p.rho), 16)
+    return p, levels, ev
+
+
+@pytest.mark.parametrize("kappa,b", [(1e5, 4), (1e6, 4), (1e5, 1)])
+def test_mg_solver_contraction_equals_iteration_matrix_spectral_radius(kappa, b):
+    """Two independent routes to one number: stand-alone multigrid (repeated
+    cycles on b = A x*) contracts the residual asymptotically by the spectral
+    radius of the iteration matrix built column by column from unit errors
+    (sec. 5), on the zero-mean-pressure space; with b = 1 and kappa = 1e5 both
+    exceed 1 (the stand-alone solver diverges)."""
+    p, levels, ev = _mg16(kappa, b)
+    rho = np.abs(ev).max()
+    assert rho > 0.4
+    rng = np.random.default_rng(2)
+    xs = rng.standard_normal(3 * 256)
+    xs[512:] -= xs[512:].mean()
+    h = O.mg_solve(levels, levels[0].A @ xs, tol=0.0, max_iters=40, rho=p.rho).history
+    rate = (h[-1] / h[-11]) ** 0.1
+    assert abs(rate - rho) <= 0.02 * rho, (rate, rho)
+
+
+def test_iteration_matrix_spectrum_and_solver_against_preconditioner():
+    """Sec. 5 with the single-box (1 x 1) smoother: for Stokes the nontrivial
+    eigenvalues lie in a small disc (the paper reports 0.24 for its cavity), a
+    mild structure leaves the radius about unchanged, and a stiff one pushes a
+    few eigenvalues out (radius above 1: the stand-alone solver fails) while
+    nearly all stay near the origin, so MG-preconditioned GMRES still converges
+    (multigrid a poor solver but an effective preconditioner).  With 4 x 4 boxes
+    (sec. 6) the stiff radius stays below 1 and the solver converges, in far more
+    iterations than MG-GMRES."""
+    _, _, e0 = _mg16(0.0, 1)
+    _, _, e2 = _mg16(1e2, 1)
+    p5, lv5, e5 = _mg16(1e5, 1)
+    r0, r2, r5 = (np.abs(e).max() for e in (e0, e2, e5))
+    assert r0 < 0.3 and r2 < 1.1 * r0, (r0, r2)
+    assert r5 > 1.0 and np.mean(np.abs(e5) > 0.25) < 0.1, (r5, np.mean(np.abs(e5) > 0.25))
+    assert O.solve_step(p5).solve.converged
+    p6, lv6, e6 = _mg16(1e6, 4)
+    assert np.abs(e6).max() < 1.0
+    mg = O.mg_solve(lv6, O.rhs_vector(p6), tol=p6.tol, max_iters=200, rho=p6.rho)
+    gm = O.solve_step(p6).solve
+    assert mg.converged and gm.converged and mg.iters > 2 * gm.iters, (mg.iters, gm.iters)
+
+
 def test_translation_by_one_cell_shifts_solution():
     N = 32
     p = W.single_ellipse(N=N, n_points=48, kappa=1e3, center=(0.45, 0.52))
