@@ -493,6 +493,24 @@ def test_bigger_boxes_fewer_iterations_most_when_stiff():
     assert stiff[1] - stiff[3] > mild[1] - mild[3], (mild, stiff)
 
 
+def test_refinement_small_boxes_grow_big_boxes_flat_when_stiff():
+    """Sec. 6 (grid refinement): for a stiff structure the MG-GMRES iteration
+    count grows as the grid is refined with 1 x 1 boxes and stays about flat with
+    8 x 8 boxes; for a milder one both stay flat."""
+    def its(N, kappa, b):
+        p = W.single_ellipse(N=N, n_points=2 * N, kappa=kappa, dt=1e-2)
+        p.box, p.max_iters = b, 200
+        r = O.solve_step(p).solve
+        assert r.converged
+        return r.iters
+
+    s1 = [its(N, 1e5, 1) for N in (32, 64)]
+    s8 = [its(N, 1e5, 8) for N in (32, 64)]
+    m1 = [its(N, 1e4, 1) for N in (32, 64)]
+    assert s1[1] >= 1.3 * s1[0], s1
+    assert abs(s8[1] - s8[0]) <= 2 and abs(m1[1] - m1[0]) <= 2, (s8, m1)
+
+
 def test_more_smoothing_sweeps_fewer_iterations():
     """Sec. 6 (table of nu1, nu2 for b = 4): the iteration count falls as the
     number of pre- and post-smoothing sweeps grows."""
