@@ -64,7 +64,9 @@ smoothing sweeps take fewer iterations, the 1 x 1 box smoother fails on very
 stiff structures, and under refinement a stiff problem's count grows with
 1 x 1 boxes and stays flat with 8 x 8 ones), the stand-alone multigrid solver's contraction equal to the
 spectral radius of its iteration matrix and that spectrum's behaviour with
-stiffness (sec. 5), translation and mirror symmetry, and energy decay.
+stiffness (sec. 5), the explicit-time operator's real nonpositive spectrum and
+translation kernel with alpha_exp falling under refinement (sec. 4.1),
+translation and mirror symmetry, and energy decay.
 Parity unpinned: the exact iteration counts of the periodic workloads (the
 paper prints counts only for its lid-driven-cavity problem, and sweeps its
 boxes in lexicographic order where this oracle, like the GPU path, uses four
@@ -81,6 +83,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 # ----------------------------------------------------------------------------
 # 1-D regularised delta kernels (sec. 2.2).  phi is dimensionless: delta_h^1(r)
@@ -801,3 +804,34 @@ def spectrum_mean_zero_pressure(M, N):
     Q = np.eye(3 * n)
     Q[2 * n:, 2 * n:] -= 1.0 / n
     return np.linalg.eigvals(Q @ M @ Q)
+
+
+# ----------------------------------------------------------------------------
+# Explicit-time stability limit (sec. 4.1, characterizing the elastic stiffness)
+# ----------------------------------------------------------------------------
+
+
+def explicit_stiffness_limit(prob, X=None):
+    """alpha_exp = 2 / rho(S* L^{-1} S A) (sec. 4.1): the largest alpha = kappa dt
+    for which the explicit-time method (forward Euler on dX/dt = S* L^{-1} S F(X))
+    is stable.  A is the spring-force Jacobian per unit stiffness (the paper's
+    A_f when the rest length is zero); L^{-1} maps a force density to the
+    velocity of the steady Stokes system (rho = 0; periodic, so the constant
+    velocities and pressure are bordered out).  Returns (alpha_exp, eigenvalues
+    of S* L^{-1} S A), which are real and nonpositive.  One sparse LU of the
+    Stokes system and a dense eigenproblem in the points: small problems only."""
+    X = prob.X if X is None else np.asarray(X, dtype=np.float64)
+    N, L = prob.N, prob.L
+    h = L / N
+    S = spread_matrix(X, N, L, prob.delta)
+    Ss = interp_matrix(S, h)
+    A = spring_jacobian(X, prob.springs, np.ones(prob.springs.shape[0]), prob.rest, L, prob.clamped)
+    Ast = stokes_matrix(N, h, prob.mu, 0.0, prob.dt)
+    Z = sp.csr_matrix(nullspace_basis(N, 0.0))
+    K = sp.bmat([[Ast, Z], [Z.T, None]], format="csc")
+    n2 = 2 * N * N
+    rhs = np.zeros((K.shape[0], A.shape[1]))
+    rhs[:n2] = -(S @ A).toarray()  # momentum rows carry -f (the system's sign)
+    u = spla.splu(K).solve(rhs)[:n2]
+    ev = np.linalg.eigvals(Ss @ u)
+    return 2.0 / np.abs(ev).max(), ev

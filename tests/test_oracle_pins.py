@@ -571,6 +571,26 @@ def test_iteration_matrix_spectrum_and_solver_against_preconditioner():
     assert mg.converged and gm.converged and mg.iters > 2 * gm.iters, (mg.iters, gm.iters)
 
 
+def test_explicit_stiffness_limit_spectrum_and_refinement():
+    """Sec. 4.1: S* L^{-1} S A (Stokes solution operator, symmetric positive
+    semidefinite, times the spring Jacobian per unit stiffness, symmetric
+    negative semidefinite) has real, nonpositive eigenvalues; with zero rest
+    length its kernel holds exactly the two rigid translations; and
+    alpha_exp = 2 / rho falls as the grid is refined with the structure (the
+    paper's table falls from 6.09 to 2.28 for its annulus, h = 2^-5 .. 2^-8)."""
+    a = {}
+    for N in (16, 32):
+        p = W.single_ellipse(N=N, n_points=2 * N, kappa=1.0, dt=1e-2)
+        a[N], ev = O.explicit_stiffness_limit(p)
+        big = np.abs(ev).max()
+        assert np.abs(ev.imag).max() <= 1e-10 * big and ev.real.max() <= 1e-10 * big
+        assert a[N] == pytest.approx(2.0 / big)
+    assert a[32] < a[16], a
+    p0 = W.single_ellipse(N=16, n_points=32, kappa=1.0, dt=1e-2, rest=0.0)
+    _, ev0 = O.explicit_stiffness_limit(p0)
+    assert int(np.sum(np.abs(ev0) < 1e-9 * np.abs(ev0).max())) == 2
+
+
 def test_translation_by_one_cell_shifts_solution():
     N = 32
     p = W.single_ellipse(N=N, n_points=48, kappa=1e3, center=(0.45, 0.52))
