@@ -526,8 +526,8 @@ def _mg16(kappa, b):
     levels, _ = O.build_hierarchy(p)
     for lev in levels[:-1]:
         O.prepare_boxes(lev, b)
-    ev = O.spectrum_mean_zero_pressure(O.iteration_matrix(levels, p.nu1, p.nu2, p.rho), 16)
-    return p, levels, ev
+    M = O.iteration_matrix(levels, p.nu1, p.nu2, p.rho)
+    return p, levels, O.spectrum_mean_zero_pressure(M, 16), M
 
 
 @pytest.mark.parametrize("kappa,b", [(1e5, 4), (1e6, 4), (1e5, 1)])
@@ -537,7 +537,7 @@ def test_mg_solver_contraction_equals_iteration_matrix_spectral_radius(kappa, b)
     radius of the iteration matrix built column by column from unit errors
     (sec. 5), on the zero-mean-pressure space; with b = 1 and kappa = 1e5 both
     exceed 1 (the stand-alone solver diverges)."""
-    p, levels, ev = _mg16(kappa, b)
+    p, levels, ev, _ = _mg16(kappa, b)
     rho = np.abs(ev).max()
     assert rho > 0.4
     rng = np.random.default_rng(2)
@@ -557,14 +557,17 @@ def test_iteration_matrix_spectrum_and_solver_against_preconditioner():
     (multigrid a poor solver but an effective preconditioner).  With 4 x 4 boxes
     (sec. 6) the stiff radius stays below 1 and the solver converges, in far more
     iterations than MG-GMRES."""
-    _, _, e0 = _mg16(0.0, 1)
-    _, _, e2 = _mg16(1e2, 1)
-    p5, lv5, e5 = _mg16(1e5, 1)
+    _, _, e0, M0 = _mg16(0.0, 1)
+    c = np.zeros(3 * 256)
+    c[512:] = 1.0  # constant pressure: the trivial eigenvector, eigenvalue 1 (sec. 5)
+    assert np.abs(M0 @ c - c).max() <= 1e-10
+    _, _, e2, _ = _mg16(1e2, 1)
+    p5, lv5, e5, _ = _mg16(1e5, 1)
     r0, r2, r5 = (np.abs(e).max() for e in (e0, e2, e5))
     assert r0 < 0.3 and r2 < 1.1 * r0, (r0, r2)
     assert r5 > 1.0 and np.mean(np.abs(e5) > 0.25) < 0.1, (r5, np.mean(np.abs(e5) > 0.25))
     assert O.solve_step(p5).solve.converged
-    p6, lv6, e6 = _mg16(1e6, 4)
+    p6, lv6, e6, _ = _mg16(1e6, 4)
     assert np.abs(e6).max() < 1.0
     mg = O.mg_solve(lv6, O.rhs_vector(p6), tol=p6.tol, max_iters=200, rho=p6.rho)
     gm = O.solve_step(p6).solve
