@@ -453,7 +453,7 @@ def run_vcycle(args):
     w = torch.zeros_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ms = _timed_steps(torch, lambda: s.vcycle(b, w), flush, torch.cuda.current_stream(), args.warmup,
-                      args.steps)
+                      args.steps, args.profile_range)
     per = sum(ms) / len(ms)
     # ib_vcycle converts the FP64 input and output around the cycle: time that part separately
     bpd = 56.0 if args.precision == "fp32" else 112.0  # vectors in FP64 for fp64 and mixed
@@ -532,7 +532,7 @@ def run_multi1024(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     clk = ClockSampler(args.local_rank)
     clk.start()
-    ms = _timed_steps(torch, step, flush, stream, args.warmup, args.steps)
+    ms = _timed_steps(torch, step, flush, stream, args.warmup, args.steps, args.profile_range)
     clocks = clk.stop()
     s.close()
     line = {"metric": METRIC, "value": sum(ms) / len(ms), "unit": UNIT, "n_gpus": 1, "steps": args.steps,

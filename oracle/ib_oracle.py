@@ -66,7 +66,9 @@ stiff structures, and under refinement a stiff problem's count grows with
 spectral radius of its iteration matrix and that spectrum's behaviour with
 stiffness (sec. 5), the explicit-time operator's real nonpositive spectrum and
 translation kernel with alpha_exp falling under refinement (sec. 4.1),
-translation and mirror symmetry, and energy decay.
+translation and mirror symmetry, energy decay, and the backward-Euler decay
+of a discretely divergence-free Fourier mode of u^n by (rho/dt) / (rho/dt +
+mu lambda_k) with no structure (the u^n term of the right-hand side).
 Parity unpinned: the exact iteration counts of the periodic workloads (the
 paper prints counts only for its lid-driven-cavity problem, and sweeps its
 boxes in lexicographic order where this oracle, like the GPU path, uses four
@@ -167,6 +169,8 @@ def spread_matrix(X, N, L, kernel="peskin4"):
             rows.append(r.ravel())
             cols.append(np.full(r.size, comp * Np + k))
             vals.append(W.ravel())
+    if Np == 0:  # no structure: an empty operator
+        return sp.csr_matrix((2 * N * N, 0))
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
     vals = np.concatenate(vals)

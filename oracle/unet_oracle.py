@@ -16,7 +16,10 @@ vector [W_0 b_0 W_1 b_1 ...] with W_l in [c_out][c_in][k][k].  With bf16=True th
 weights are rounded to bfloat16 (round to nearest even) before use, as the GPU
 kernels do; biases stay as given.  The backward pass is written out by hand
 (reverse-mode chain rule through every layer) and pinned against finite
-differences in the tests.
+differences in the tests.  The forward pass is pinned on its own: the
+convolution against an FFT circular cross-correlation, GELU at tabulated values
+of the normal CDF, pooling and upsampling on hand-worked arrays, and the skip
+order along single-channel paths.
 """
 from __future__ import annotations
 

@@ -254,6 +254,59 @@ def test_stokes_divergence_free_solution_check():
     assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
 
 
+def _divfree_mode(N, kx, ky, phase=0.3):
+    """A discretely divergence-free MAC velocity from a stream function psi on the
+    cell corners: u = (psi[i, j+1] - psi[i, j]) / h, v = -(psi[i+1, j] - psi[i, j]) / h.
+    psi is one real Fourier mode, so u and v are eigenvectors of the 5-point
+    Laplacian with eigenvalue -lambda_k, lambda_k = (4/h^2)(sin^2(pi kx h) + sin^2(pi ky h))."""
+    h = 1.0 / N
+    i = np.arange(N)[None, :]
+    j = np.arange(N)[:, None]
+
+    def psi(ii, jj):
+        return np.cos(2 * np.pi * (kx * ii + ky * jj) / N + phase)
+
+    u = (psi(i, j + 1) - psi(i, j)) / h
+    v = -(psi(i + 1, j) - psi(i, j)) / h
+    lam = 4.0 / h ** 2 * (math.sin(math.pi * kx * h) ** 2 + math.sin(math.pi * ky * h) ** 2)
+    return u, v, lam
+
+
+@pytest.mark.parametrize("kx,ky", [(1, 0), (2, 3), (5, 1)])
+def test_unsteady_step_decays_a_divergence_free_mode_exactly(kx, ky):
+    """The u^n term of the right-hand side (backward Euler, sec. 2.3; the unsteady
+    form named in sec. 8).  With no structure and u^n a discretely divergence-free
+    Fourier mode, (mu Lap - (rho/dt) I) u - G p = -(rho/dt) u^n, D u = 0 is solved by
+    u = c u^n, p = const, c = (rho/dt) / (rho/dt + mu lambda_k).  A sign slip in the
+    u^n term gives -c, a dropped 1/dt gives rho / (rho + mu lambda_k dt)."""
+    N, rho, mu, dt = 16, 2.0, 0.5, 0.1
+    u, v, lam = _divfree_mode(N, kx, ky)
+    n = N * N
+    prob = W.Problem(N=N, L=1.0, rho=rho, mu=mu, dt=dt, X=np.zeros((0, 2)),
+                     springs=np.zeros((0, 2), np.int32), kappa=np.zeros(0), rest=np.zeros(0))
+    u_n = np.concatenate([u.ravel(), v.ravel()])
+    A = O.stokes_matrix(N, 1.0 / N, mu, rho, dt)
+    assert np.abs((A @ np.concatenate([u_n, np.zeros(n)]))[2 * n:]).max() < 1e-9  # D u^n = 0
+    b = O.rhs_vector(prob, u_n=u_n)
+    w = O.direct_solve(A, b, N, rho)
+    c = (rho / dt) / (rho / dt + mu * lam)
+    assert np.abs(w[: 2 * n] - c * u_n).max() <= 1e-10 * np.abs(u_n).max()
+    assert np.abs(w[2 * n:] - w[2 * n:].mean()).max() <= 1e-10 * np.abs(u_n).max()
+    # the multigrid-preconditioned step reaches the same field to its tolerance
+    prob.box, prob.tol = 2, 1e-12
+    st = O.solve_step(prob, u_n=u_n)
+    assert np.abs(st.w[: 2 * n] - c * u_n).max() <= 1e-9 * np.abs(u_n).max()
+
+
+def test_fluid_at_rest_without_structure_stays_at_rest():
+    """u^n = None (and u^n = 0) with no structure: the right-hand side vanishes."""
+    N = 16
+    prob = W.Problem(N=N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, X=np.zeros((0, 2)),
+                     springs=np.zeros((0, 2), np.int32), kappa=np.zeros(0), rest=np.zeros(0))
+    assert not O.rhs_vector(prob).any()
+    assert not O.rhs_vector(prob, u_n=np.zeros(2 * N * N)).any()
+
+
 # ---------------------------------------------------------------- transfers (sec. 3.1)
 
 def test_transfer_constants_and_pressure_identity():
