@@ -164,7 +164,11 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * Re-forms S, J and the hierarchy from X^n, solves with MG-preconditioned
  * FGMRES to params.tol, then moves the points.  Returns IB_ERR_NOT_CONVERGED
  * if max_iters was reached (the best iterate is still written and X moved),
- * IB_ERR_TIMEOUT if a bulk copy of the Krylov basis did not land within 1 s.
+ * IB_ERR_TIMEOUT if a bulk copy of the Krylov basis did not land within the wait
+ * limit: 1 s, or the number of nanoseconds in the environment variable
+ * IB_WAIT_LIMIT_NS when it is set at ib_setup (0 makes every wait that does not
+ * find its copies already landed time out, which exercises this path; the
+ * iterate is then meaningless).
  * FGMRES orthogonalises by classical Gram-Schmidt applied twice, in three
  * passes over the basis; the environment variable IB_CGS_FUSED=0 (read at
  * ib_setup) splits the middle pass in two, the form otherwise taken only when a

@@ -533,9 +533,11 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       k = j + 1;
       if (j > 0) {
         int rc = check(j - 1);
-        if (rc < 0) return P.scal_host[24 + 4 * ((j - 1) & 1) + 2] != 0.0
-                               ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
-                               : fail(IB_ERR_CUDA, "FGMRES pipeline");
+        if (rc < 0) {
+          IB_TRY(check_dev_err(P));  // a device-side error explains what followed it
+          return P.scal_host[24 + 4 * ((j - 1) & 1) + 2] != 0.0 ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
+                                                                 : fail(IB_ERR_CUDA, "FGMRES pipeline");
+        }
         if (rc == 1) {  // iteration j - 1 was the last of the cycle: drop iteration j
           k = j;
           --total;
@@ -546,9 +548,11 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
     }
     if (!stopped && k > 0) {
       int rc = check(k - 1);
-      if (rc < 0) return P.scal_host[24 + 4 * ((k - 1) & 1) + 2] != 0.0
-                             ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
-                             : fail(IB_ERR_CUDA, "FGMRES pipeline");
+      if (rc < 0) {
+        IB_TRY(check_dev_err(P));
+        return P.scal_host[24 + 4 * ((k - 1) & 1) + 2] != 0.0 ? fail(IB_ERR_BREAKDOWN, "non-finite value in FGMRES")
+                                                               : fail(IB_ERR_CUDA, "FGMRES pipeline");
+      }
     }
     IB_TRY(launch_backsolve(P, k));
     if constexpr (std::is_same<T, double>::value) {
@@ -766,6 +770,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   if (st != IB_OK) return fail_free(st);
   if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
   if (const char* e = std::getenv("IB_BOX_ONE_MAX")) P.box_one_max = std::atol(e);
+  if (const char* e = std::getenv("IB_WAIT_LIMIT_NS")) P.wait_limit_ns = std::strtoull(e, nullptr, 10);
   P.has32 = params->precision == IB_FP32_PRECOND;
   P.has64 = params->precision != IB_FP32_PRECOND || params->escalate != 0;
   if (P.has32) {
@@ -989,12 +994,27 @@ namespace {
 // Run f(k) for k in [0, n) on up to `threads` host threads; returns the first
 // failing status (IB_ERR_NOT_CONVERGED only if nothing worse happened) and its message.
 // ids (may be NULL) names the problem of each k in the messages.
+// Every worker makes the caller's current device its own before it runs f: a
+// new host thread starts on device 0, whatever device the caller had selected.
 template <typename F>
 int parallel_for(int n, int threads, F f, std::string* msg, const std::vector<int>* ids = nullptr) {
   std::atomic<int> next(0);
   std::vector<int> codes(n, IB_OK);
   std::vector<std::string> msgs(n);
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    *msg = "cudaGetDevice failed";
+    return IB_ERR_CUDA;
+  }
   auto work = [&]() {
+    if (cudaSetDevice(device) != cudaSuccess) {
+      for (;;) {  // this worker cannot run anything: mark the items it takes
+        int k = next.fetch_add(1);
+        if (k >= n) return;
+        codes[k] = IB_ERR_CUDA;
+        msgs[k] = "problem " + std::to_string(ids ? (*ids)[k] : k) + ": cudaSetDevice failed";
+      }
+    }
     for (;;) {
       int k = next.fetch_add(1);
       if (k >= n) break;

@@ -255,6 +255,7 @@ struct Problem {
   int occ_subnorm = 0;        // ... and of the last Gram-Schmidt subtraction
   std::vector<int> occ_cgs;   // resident blocks per SM of the fused pass, by basis size
   bool cgs_fused = true;      // middle Gram-Schmidt step as one fused pass
+  unsigned long long wait_limit_ns = 1000000000ull;  // bounded device-side waits (IB_WAIT_LIMIT_NS)
   int* count = nullptr;       // device counter
   int* count_host = nullptr;  // pinned
 

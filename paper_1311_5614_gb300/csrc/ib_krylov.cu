@@ -118,15 +118,29 @@ __device__ inline unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Waits until phase `parity` of the barrier completes, for at most limit_ns.
-__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try(bar, parity))
-    if (global_ns() - t0 > limit_ns) return false;
-  return true;
+__device__ inline bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
 }
-constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // 1 s
+// Waits until phase `parity` of the barrier completes, for at most limit_ns: a
+// non-blocking test first, then potentially blocking try_wait probes until the
+// limit has passed (with limit_ns = 0 only the first test counts).
+__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (global_ns() - t0 >= limit_ns) return false;
+    if (mbar_try(bar, parity)) return true;
+  }
+}
+// After a timed-out wait the block still waits for its copies in flight before it
+// exits (they write into its shared memory), for at most this long.
+constexpr unsigned long long DRAIN_LIMIT_NS = 2000000000ull;  // 2 s
 
 // Fused Gram-Schmidt pass: w <- w - sum_i coef_i V_i, then partial[bx * stride + i]
 // = the block's part of V_i . w (the updated w), so the basis is read from HBM
@@ -136,12 +150,18 @@ constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // 1 s
 // thread per element), then thread t forms the dot products of vectors t, t + 64,
 // ... with the chunk (rows read at a per-row rotation of the column, so a warp's
 // 32 rows hit distinct banks) and keeps them in registers across chunks.  A bulk
-// copy that has not landed after 1 s sets DEV_ERR_TIMEOUT and ends the block.
+// copy that has not landed after limit_ns (1 s unless set at ib_setup) sets
+// DEV_ERR_TIMEOUT and ends the block once the copies in flight have landed (or
+// after DRAIN_LIMIT_NS more).  Before the copies of the next chunk are issued, the
+// issuing warp orders the block's earlier generic-proxy reads of sV and sw (made
+// visible to it by the barrier ending the chunk) before its async-proxy writes
+// with fence.proxy.async.
 constexpr int CGS_CH = 64;
 constexpr int CGS_KMAX = (513 + CGS_CH - 1) / CGS_CH;  // vectors per thread (nvec <= 513)
 __global__ void __launch_bounds__(CGS_CH) k_cgs_sub_dot(const double* __restrict__ V, int nvec, long n,
                                                         const double* __restrict__ coef, double* __restrict__ w,
-                                                        double* __restrict__ partial, int stride, int* err) {
+                                                        double* __restrict__ partial, int stride, int* err,
+                                                        unsigned long long limit_ns) {
   extern __shared__ __align__(128) double sm[];
   double* sV = sm;                          // [nvec][CGS_CH]
   double* sw = sV + (size_t)nvec * CGS_CH;  // [CGS_CH] updated w of the chunk
@@ -161,15 +181,18 @@ __global__ void __launch_bounds__(CGS_CH) k_cgs_sub_dot(const double* __restrict
     const int len = (int)(n - c0 < CGS_CH ? n - c0 : CGS_CH);
     if (t < 32) {
       const unsigned bytes = (unsigned)len * 8u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (t == 0) mbar_arrive_expect_tx(&bar, bytes * (unsigned)nvec);
       __syncwarp();
       for (int i = t; i < nvec; i += 32) bulk_g2s(sV + (size_t)i * CGS_CH, V + (size_t)i * n + c0, bytes, &bar);
     }
-    const bool ok = mbar_wait_bounded(&bar, parity, WAIT_LIMIT_NS);
+    const bool ok = mbar_wait_bounded(&bar, parity, limit_ns);
     if (__syncthreads_or(!ok)) {
+      // thread 0 stays until this chunk's copies have landed, so the block's shared
+      // memory outlives every write into it
       if (t == 0) {
         atomicOr(err, DEV_ERR_TIMEOUT);
-        mbar_wait_bounded(&bar, parity, WAIT_LIMIT_NS);  // let copies in flight land
+        mbar_wait_bounded(&bar, parity, DRAIN_LIMIT_NS);
       }
       return;
     }
@@ -436,7 +459,8 @@ int launch_cgs_sub_dot(Problem& P, const double* V, int nvec, const double* coef
   const int cols = (int)std::min<long>({chunks, (long)P.n_sm * per_sm, (long)P.dot_blocks});
   {
     KScope ks(P, IB_KC_KRYLOV, (nvec + 2.0) * n * 8.0);
-    k_cgs_sub_dot<<<cols, CGS_CH, smem, P.stream>>>(V, nvec, n, coef, w, P.dots, P.max_m + 2, P.dev_err);
+    k_cgs_sub_dot<<<cols, CGS_CH, smem, P.stream>>>(V, nvec, n, coef, w, P.dots, P.max_m + 2, P.dev_err,
+                                                     P.wait_limit_ns);
     IB_LAUNCH_CHECK();
   }
   return multidot_final(P, nvec, cols, out);

@@ -3,8 +3,15 @@
 Bars (written here, derived in the design notes):
 * FP64 operator apply, right-hand side, V-cycle: every element within 1e-10 of
   the oracle, relative to the largest oracle element (per-apply bar);
-* FP32 V-cycle: within 2e-4 relative (FP32 rounding through ~2 x nu sweeps on
-  every level, measured against the FP64 oracle);
+* FP32 V-cycle: every element within 2e-5 of the oracle, relative to the largest
+  oracle element of its component (u, v or p), and 2e-4 in the 2-norm.  FP32
+  rounding (unit roundoff 6e-8) through 2 x nu sweeps on every level, amplified by
+  the structure rows, whose elastic terms (dt kappa / h^2 against mu / h^2) cancel
+  in the FP32 residual; measured on GB300: at most 4.3e-6 (1 x 1 to 8 x 8 boxes,
+  kappa up to 1e6), 2.8e-7 without the 8 x 8 stiff case;
+* mixed V-cycle (FP64 vectors, FP32 free-box inverse): every element within 5e-7
+  per component (the FP32 inverse's rounding enters once per box solve and is
+  damped by the FP64 residual; measured at most 4.7e-8);
 * solves: both sides reach the 1e-8 relative residual; the solutions agree to
   1e-6 relative (tolerance times the conditioning margin) and the iteration
   counts agree within one for FP64.
@@ -36,6 +43,13 @@ def dev(a):
 
 def rel_elementwise(gpu, ref):
     return float(np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def rel_per_component(gpu, ref, N):
+    """Largest elementwise error of each component (u, v, p) relative to that
+    component's largest oracle element."""
+    n = N * N
+    return [rel_elementwise(gpu[c * n:(c + 1) * n], ref[c * n:(c + 1) * n]) for c in range(3)]
 
 
 CASES = {
@@ -168,10 +182,12 @@ def test_vcycle_cluster_tail_low_precision(pkg, prec, monkeypatch):
     assert s.tail_cluster(prec) >= 8
     got = w.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
+    assert max(rel_per_component(got, ref, p.N)) <= (2e-5 if prec == "fp32" else 5e-7)
     s.close()
 
 
-@pytest.mark.parametrize("name,box", [("c1_64", 1), ("stiff_32_exact", 4)])
+@pytest.mark.parametrize("name,box", [("c1_64", 1), ("c1_64", 4), ("stiff_32_exact", 4), ("stiff_32", 8),
+                                      ("steady_cos4_32", 2), ("offcentre_16", 2)])
 def test_vcycle_fp32(pkg, name, box):
     p = make_case(name, box)
     rhs = O.rhs_vector(p)
@@ -181,10 +197,12 @@ def test_vcycle_fp32(pkg, name, box):
     s.vcycle(dev(rhs), w)
     got = w.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
+    assert max(rel_per_component(got, ref, p.N)) <= 2e-5, rel_per_component(got, ref, p.N)
     s.close()
 
 
-@pytest.mark.parametrize("name,box", [("c1_64", 1), ("c1_64", 4), ("stiff_32_exact", 4), ("stiff_32", 8)])
+@pytest.mark.parametrize("name,box", [("c1_64", 1), ("c1_64", 4), ("stiff_32_exact", 4), ("stiff_32", 8),
+                                      ("steady_cos4_32", 2), ("offcentre_16", 2)])
 def test_vcycle_mixed(pkg, name, box):
     """FP64 vectors and residuals, FP32 box inverses: within FP32 rounding of the
     oracle's FP64 V-cycle."""
@@ -196,6 +214,7 @@ def test_vcycle_mixed(pkg, name, box):
     s.vcycle(dev(rhs), w)
     got = w.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 2e-4 * np.linalg.norm(ref)
+    assert max(rel_per_component(got, ref, p.N)) <= 5e-7, rel_per_component(got, ref, p.N)
     s.close()
 
 
