@@ -447,7 +447,8 @@ def run_vcycle(args):
     N = args.grid
     prob = W.single_ellipse(N=N, n_points=2 * N, kappa=1e4, dt=1e-3)
     prob.box = args.box
-    s = pkg.IBSolver.from_problem(prob, precision=args.precision)
+    # the V-cycle alone: a one-vector Krylov workspace keeps the device memory small
+    s = pkg.IBSolver.from_problem(prob, precision=args.precision, max_iters=1)
     n = 3 * N * N
     b = torch.randn(n, dtype=torch.float64, device="cuda")
     w = torch.zeros_like(b)

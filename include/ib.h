@@ -313,6 +313,18 @@ IB_API int ib_profile(ib_problem* prob, int32_t enable);
 IB_API int ib_profile_read(ib_problem* prob, int32_t kclass, int64_t* launches, double* ms,
                            double* bytes);
 
+/* enable = 1: from now on record an event pair on the problem's stream around every
+ * V-cycle replayed from its CUDA graph (the form FGMRES and ib_vcycle run; the
+ * kernels themselves are unchanged, unlike ib_profile's per-launch brackets);
+ * enable = 0: stop.  Either call resets the counts. */
+IB_API int ib_vcycle_timer(ib_problem* prob, int32_t enable);
+
+/* Synchronise the stream and return the number of V-cycles timed since
+ * ib_vcycle_timer and their summed device time (ms), for the V-cycle of the given
+ * precision: IB_FP32_PRECOND for the FP32 V-cycle, IB_FP64 or IB_MIXED_PRECOND for
+ * the one on FP64 vectors.  Output pointers may be NULL. */
+IB_API int ib_vcycle_timer_read(ib_problem* prob, int32_t precision, int64_t* count, double* ms);
+
 /* ---- Allocation-free operator apply (the paper has no counterpart) ----
  *
  * y = A_0 w on the fine grid, the same operator as ib_apply(prob, 0, w, y),

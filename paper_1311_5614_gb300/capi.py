@@ -80,6 +80,9 @@ _SIGS = {
     "ib_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ib_vcycle_timer": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_vcycle_timer_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_double)]),
     "ib_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(ib_params), ctypes.c_int32, _P, ctypes.c_int32, _P,
                                         _P, _P, _P, _P, _P]),
     "ib_setup_batch": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
@@ -264,6 +267,17 @@ def ib_profile_read(prob, kclass):
     by = ctypes.c_double()
     _check(lib().ib_profile_read(prob, int(kclass), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return int(n.value), float(ms.value), float(by.value)
+
+
+def ib_vcycle_timer(prob, enable):
+    _check(lib().ib_vcycle_timer(prob, 1 if enable else 0))
+
+
+def ib_vcycle_timer_read(prob, precision):
+    """(V-cycles timed, their total device ms) for the V-cycle of one precision."""
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().ib_vcycle_timer_read(prob, PRECISION[precision], ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 def ib_destroy(prob):
@@ -494,6 +508,12 @@ class IBSolver:
 
     def profile_read(self):
         return {name: ib_profile_read(self.handle, i) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def vcycle_timer(self, enable):
+        ib_vcycle_timer(self.handle, enable)
+
+    def vcycle_timer_read(self, precision):
+        return ib_vcycle_timer_read(self.handle, precision)
 
     def close(self):
         if self.handle:

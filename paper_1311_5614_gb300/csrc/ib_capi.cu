@@ -227,6 +227,11 @@ void free_problem(Problem* P) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  for (auto& r : P->vt_pending) {
+    cudaEventDestroy(r.first);
+    cudaEventDestroy(r.second);
+  }
+  P->vt_pending.clear();
   for (auto& e : P->ev_pool) cudaEventDestroy(e);
   P->pending.clear();
   P->ev_pool.clear();
@@ -771,6 +776,12 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
   if (const char* e = std::getenv("IB_BOX_ONE_MAX")) P.box_one_max = std::atol(e);
   if (const char* e = std::getenv("IB_WAIT_LIMIT_NS")) P.wait_limit_ns = std::strtoull(e, nullptr, 10);
+  if (const char* e = std::getenv("IB_BOX_STRIP")) P.box_strip = e[0] != '0';
+  if (const char* e = std::getenv("IB_BOX_STRIP_MIN")) P.box_strip_min = std::atol(e);
+  if (const char* e = std::getenv("IB_BOX_STRIP_W")) {
+    const int wv = std::atoi(e);
+    P.box_strip_w = (wv == 8 || wv == 16 || wv == 32) ? wv : 0;
+  }
   P.has32 = params->precision == IB_FP32_PRECOND;
   P.has64 = params->precision != IB_FP32_PRECOND || params->escalate != 0;
   if (P.has32) {
@@ -966,6 +977,54 @@ int ib_profile_read(ib_problem* H, int32_t kclass, int64_t* launches, double* ms
   if (launches) *launches = P.prof_n[kclass];
   if (ms) *ms = P.prof_ms[kclass];
   if (bytes) *bytes = P.prof_bytes[kclass];
+  return IB_OK;
+}
+
+}  // extern "C"
+
+namespace ib {
+namespace {
+int resolve_vtimer(Problem& P) {
+  if (P.vt_pending.empty()) return IB_OK;
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  for (size_t i = 0; i < P.vt_pending.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P.vt_pending[i].first, P.vt_pending[i].second);
+    P.vt_n[P.vt_kind[i]] += 1;
+    P.vt_ms[P.vt_kind[i]] += ms;
+    P.ev_pool.push_back(P.vt_pending[i].first);
+    P.ev_pool.push_back(P.vt_pending[i].second);
+  }
+  P.vt_pending.clear();
+  P.vt_kind.clear();
+  return IB_OK;
+}
+}  // namespace
+}  // namespace ib
+
+extern "C" {
+
+int ib_vcycle_timer(ib_problem* H, int32_t enable) {
+  g_err.clear();
+  if (!H) return fail(IB_ERR_INVALID_ARG, "problem is NULL");
+  Problem& P = H->P;
+  IB_TRY(resolve_vtimer(P));
+  P.vt_n[0] = P.vt_n[1] = 0;
+  P.vt_ms[0] = P.vt_ms[1] = 0.0;
+  P.vt_on = enable != 0;
+  return IB_OK;
+}
+
+int ib_vcycle_timer_read(ib_problem* H, int32_t precision, int64_t* count, double* ms) {
+  g_err.clear();
+  if (!H) return fail(IB_ERR_INVALID_ARG, "problem is NULL");
+  if (precision != IB_FP64 && precision != IB_FP32_PRECOND && precision != IB_MIXED_PRECOND)
+    return fail(IB_ERR_INVALID_ARG, "unknown precision");
+  Problem& P = H->P;
+  IB_TRY(resolve_vtimer(P));
+  const int ix = precision == IB_FP32_PRECOND ? 0 : 1;
+  if (count) *count = P.vt_n[ix];
+  if (ms) *ms = P.vt_ms[ix];
   return IB_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ib.h"
@@ -185,6 +186,12 @@ struct Problem {
   double prof_bytes[IB_KC_COUNT] = {};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<ProfRec> pending;
+  // V-cycle timer: an event pair around every V-cycle replayed from its graph
+  bool vt_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> vt_pending;
+  long long vt_n[2] = {0, 0};   // timed V-cycles: [0] FP32 V-cycle, [1] V-cycle on FP64 vectors
+  double vt_ms[2] = {0.0, 0.0};
+  std::vector<int> vt_kind;
   // V-cycle engine
   // index [0] = FP32 V-cycle, [1] = FP64 V-cycle
   int tail_level[2] = {0, 0};    // first level handled by the tail kernel
@@ -195,6 +202,9 @@ struct Problem {
   bool has64 = false, has32 = false;  // hierarchies available for the V-cycle
   long box_gemm_min = 2048;           // boxes per colour from which n x n boxes use the GEMM kernel
   long box_one_max = 512;             // boxes per colour up to which each box gets its own CTA
+  bool box_strip = true;             // 4 x 4 boxes: strip kernel on levels with N_l / 8 a multiple of 32
+  long box_strip_min = 2048;          // ... and at least this many boxes per colour
+  int box_strip_w = 0;                // strip width (8, 16 or 32; 0: chosen per level)
   double sigma = 0.0;                 // stiffness ratio dt * max(kappa) / mu of the structure
   double stiff_sigma = 3000.0;        // FP32 mode: from this sigma on, precondition with the mixed V-cycle
   cudaStream_t gstream = nullptr;                 // private stream the graph is captured on

@@ -20,9 +20,11 @@
 //
 // The whole sequence is captured once into a CUDA graph and replayed for every
 // V-cycle; the graph is re-captured when a kernel argument changes.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ib_ops.cuh"
@@ -431,6 +433,282 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
   }
 }
 
+// Strip kernel for 4 x 4 boxes on large levels (N_l >= 256).  A CTA takes a strip
+// of W boxes of one colour in one box row (every other box along x, so the strip
+// spans 8W cells) and:
+//   1. stages the strip's w rows with their one-cell halo in shared memory with
+//      16-byte vector loads (u: 6 rows, v: 7, p: 6; 8W + 8 columns, periodic);
+//   2. forms the residual b - A_S w (+ the elasticity term rE on the rows of
+//      structure boxes, which it clears) of every unknown of its boxes, one
+//      unknown per thread, from the staged tile;
+//   3. applies the shared free-box inverse to all W residuals as one register-
+//      blocked product (RB rows x CB boxes per thread), and the FP64 inverse of
+//      each structure box with one warp per box;
+//   4. writes w + delta back, one unknown per thread.
+// The CTAs are persistent over the strips of the colour, so the free-box inverse
+// is staged once per CTA (before the programmatic-launch wait: set-up data).
+template <typename T, typename TM, int W>
+struct Strip {
+  static constexpr int NB = 56, THREADS = 256;
+  static constexpr int SPAN = 8 * W;            // cells of one strip
+  static constexpr int LD = SPAN + 8;           // staged columns [X0 - 4, X0 + SPAN + 4)
+  static constexpr int TROWS = 6 + 7 + 6;       // staged rows of u, v, p
+  static constexpr int VE = 16 / (int)sizeof(T);  // elements per 16-byte chunk
+  static constexpr int CH = LD / VE;            // chunks per staged row
+  static constexpr int RLD = W + 4;             // row stride of the [q][box] blocks
+  static constexpr bool SPLIT = !std::is_same<T, TM>::value;  // separate TM copy of the residuals
+  static constexpr int RB = sizeof(TM) == 4 ? 4 : 2;  // rows per thread (one 16-byte load of M)
+  static constexpr int CB = sizeof(TM) == 4 ? 2 : 4;  // boxes per thread
+  static constexpr int RG = NB / RB, BG = W / CB;
+  static_assert(RG * BG <= THREADS, "product tiling");
+  static constexpr size_t OFF_TILE = ((size_t)NB * NB * sizeof(TM) + 15) / 16 * 16;
+  static constexpr size_t OFF_R = OFF_TILE + (size_t)TROWS * LD * sizeof(T);
+  static constexpr size_t OFF_D = OFF_R + (size_t)NB * RLD * sizeof(T);
+  static constexpr size_t OFF_RM = OFF_D + (size_t)NB * RLD * sizeof(T);
+  static constexpr size_t SMEM = OFF_RM + (SPLIT ? (size_t)NB * RLD * sizeof(TM) : 0);
+};
+
+template <typename TM, int n>
+struct VecLoad;
+template <>
+struct VecLoad<float, 4> {
+  __device__ static void get(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct VecLoad<float, 2> {
+  __device__ static void get(const float* p, float* o) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <>
+struct VecLoad<double, 2> {
+  __device__ static void get(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <>
+struct VecLoad<double, 4> {
+  __device__ static void get(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    const double2 u = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = v.x; o[1] = v.y; o[2] = u.x; o[3] = u.y;
+  }
+};
+
+// Unknown e (0 <= e < 56 W) of a strip in the order u rows, v rows, p rows (each
+// row: W boxes x 5 or 4 faces/cells): its component, box-relative row jr, box k,
+// column d inside the box and box-local index q.
+__device__ __forceinline__ void strip_unknown(int e, int W, int* comp, int* jr, int* k, int* d, int* q) {
+  if (e < 20 * W) {
+    const int r = e / (5 * W), t = e - r * 5 * W;
+    *comp = 0; *jr = r; *k = t / 5; *d = t - *k * 5; *q = r * 5 + *d;
+  } else if (e < 40 * W) {
+    e -= 20 * W;
+    const int r = e / (4 * W), t = e - r * 4 * W;
+    *comp = 1; *jr = r; *k = t >> 2; *d = t & 3; *q = 20 + r * 4 + *d;
+  } else {
+    e -= 40 * W;
+    const int r = e / (4 * W), t = e - r * 4 * W;
+    *comp = 2; *jr = r; *k = t >> 2; *d = t & 3; *q = 40 + r * 4 + *d;
+  }
+}
+
+template <typename T, typename TM, int W>
+__global__ void __launch_bounds__(256) kv_boxt(T* w, const T* __restrict__ b, T* rE, int N, StokesCoef<T> c,
+                                               int color, const int* __restrict__ slot,
+                                               const double* __restrict__ Ms, const TM* __restrict__ Mf) {
+  using S = Strip<T, TM, W>;
+  constexpr int NB = S::NB, LD = S::LD, RLD = S::RLD;
+  extern __shared__ __align__(16) unsigned char smem[];
+  TM* sMf = reinterpret_cast<TM*>(smem);
+  T* tile = reinterpret_cast<T*>(smem + S::OFF_TILE);
+  T* sR = reinterpret_cast<T*>(smem + S::OFF_R);
+  T* sD = reinterpret_cast<T*>(smem + S::OFF_D);
+  TM* sRM = S::SPLIT ? reinterpret_cast<TM*>(smem + S::OFF_RM) : reinterpret_cast<TM*>(sR);
+  __shared__ int sslot[W];
+  __shared__ int slist[W];
+  __shared__ int nsl;
+  const int tid = threadIdx.x;
+  {
+    constexpr int VM = 16 / (int)sizeof(TM);
+    const float4* src = reinterpret_cast<const float4*>(Mf);
+    float4* dst = reinterpret_cast<float4*>(sMf);
+    for (int e = tid; e < NB * NB / VM; e += S::THREADS) dst[e] = src[e];  // set-up data
+  }
+  pdl_enter();
+  const int nb = N >> 2, half = nb >> 1, spr = half / W, nstrips = spr * half;
+  const int cx = color & 1, cy = color >> 1, m = N - 1;
+  const size_t n = (size_t)N * N;
+  const int nchr = N / S::VE;
+  const T* U = tile;
+  const T* V = tile + 6 * LD;
+  const T* Pp = tile + 13 * LD;
+  for (int st = blockIdx.x; st < nstrips; st += gridDim.x) {
+    const int Jp = st / spr, sx = st - Jp * spr;
+    const int J = 2 * Jp + cy, I0 = 2 * sx * W + cx;
+    const int y0 = 4 * J, X0 = 4 * I0;
+    if (tid < W) sslot[tid] = slot[J * nb + I0 + 2 * tid];
+    // 1. stage the tile (16-byte chunks; a chunk never straddles a grid row)
+    const int c0 = (X0 - 4) / S::VE;
+    for (int e = tid; e < S::TROWS * S::CH; e += S::THREADS) {
+      const int r = e / S::CH, ch = e - r * S::CH;
+      const int comp = r < 6 ? 0 : (r < 13 ? 1 : 2);
+      const int ry = r - (comp == 0 ? 0 : (comp == 1 ? 6 : 13));
+      const int y = (y0 - 1 + ry) & m;
+      const int gch = (c0 + ch) & (nchr - 1);
+      const float4* src = reinterpret_cast<const float4*>(w + comp * n + (size_t)y * N) + gch;
+      reinterpret_cast<float4*>(tile + (size_t)r * LD)[ch] = *src;
+    }
+    __syncthreads();
+    // 2. residuals, one unknown per thread
+    for (int e = tid; e < NB * W; e += S::THREADS) {
+      int comp, jr, k, d, q;
+      strip_unknown(e, W, &comp, &jr, &k, &d, &q);
+      const int col = 8 * k + d, cc = col + 4;
+      const int x = (X0 + col) & m, y = (y0 + jr) & m;
+      const size_t g = comp * n + (size_t)y * N + x;
+      T a;
+      if (comp == 0) {
+        const T* ur = U + (jr + 1) * LD + cc;
+        const T* pr = Pp + (jr + 1) * LD + cc;
+        a = c.diag * ur[0] + c.off * (ur[1] + ur[-1] + ur[LD] + ur[-LD]) - c.g * (pr[0] - pr[-1]);
+      } else if (comp == 1) {
+        const T* vr = V + (jr + 1) * LD + cc;
+        const T* pr = Pp + (jr + 1) * LD + cc;
+        a = c.diag * vr[0] + c.off * (vr[1] + vr[-1] + vr[LD] + vr[-LD]) - c.g * (pr[0] - pr[-LD]);
+      } else {
+        const T* ur = U + (jr + 1) * LD + cc;
+        const T* vr = V + (jr + 1) * LD + cc;
+        a = c.g * (ur[1] - ur[0] + vr[LD] - vr[0]);
+      }
+      T r = b[g] - a;
+      if (rE && comp < 2 && sslot[k] >= 0) {
+        r += rE[g];
+        rE[g] = (T)0;
+      }
+      sR[q * RLD + k] = r;
+      if (S::SPLIT) sRM[q * RLD + k] = (TM)r;
+    }
+    __syncthreads();
+    // 3a. free-box product for every box of the strip: D[q][k] = sum_s Mf[s][q] R[s][k]
+    {
+      const int rg = tid % S::RG, bg = tid / S::RG;
+      if (bg < S::BG) {
+        TM acc[S::RB][S::CB];
+#pragma unroll
+        for (int a = 0; a < S::RB; ++a)
+#pragma unroll
+          for (int kk = 0; kk < S::CB; ++kk) acc[a][kk] = (TM)0;
+#pragma unroll 4
+        for (int s2 = 0; s2 < NB; ++s2) {
+          TM mv[S::RB], rv[S::CB];
+          VecLoad<TM, S::RB>::get(sMf + s2 * NB + rg * S::RB, mv);
+          VecLoad<TM, S::CB>::get(sRM + s2 * RLD + bg * S::CB, rv);
+#pragma unroll
+          for (int a = 0; a < S::RB; ++a)
+#pragma unroll
+            for (int kk = 0; kk < S::CB; ++kk) acc[a][kk] += mv[a] * rv[kk];
+        }
+#pragma unroll
+        for (int a = 0; a < S::RB; ++a)
+#pragma unroll
+          for (int kk = 0; kk < S::CB; ++kk) sD[(rg * S::RB + a) * RLD + bg * S::CB + kk] = (T)acc[a][kk];
+      }
+    }
+    if (tid == 0) {
+      int cnt = 0;
+      for (int k = 0; k < W; ++k)
+        if (sslot[k] >= 0) slist[cnt++] = k;
+      nsl = cnt;
+    }
+    __syncthreads();
+    // 3b. structure boxes: their own FP64 inverses, one warp per box (replaces 3a's result)
+    {
+      const int wp = tid >> 5, lane = tid & 31;
+      for (int i = wp; i < nsl; i += S::THREADS / 32) {
+        const int k = slist[i];
+        const double* M = Ms + (size_t)sslot[k] * NB * NB;
+        const int q1 = lane + 32;
+        double d0 = 0.0, d1 = 0.0;
+#pragma unroll 4
+        for (int s2 = 0; s2 < NB; ++s2) {
+          const double rs = (double)sR[s2 * RLD + k];
+          d0 += M[s2 * NB + lane] * rs;
+          if (q1 < NB) d1 += M[s2 * NB + q1] * rs;
+        }
+        sD[lane * RLD + k] = (T)d0;
+        if (q1 < NB) sD[q1 * RLD + k] = (T)d1;
+      }
+    }
+    __syncthreads();
+    // 4. w += delta on the strip's unknowns
+    for (int e = tid; e < NB * W; e += S::THREADS) {
+      int comp, jr, k, d, q;
+      strip_unknown(e, W, &comp, &jr, &k, &d, &q);
+      const int col = 8 * k + d, cc = col + 4;
+      const int x = (X0 + col) & m, y = (y0 + jr) & m;
+      const T* row = (comp == 0 ? U : (comp == 1 ? V : Pp)) + (jr + 1) * LD + cc;
+      w[comp * n + (size_t)y * N + x] = row[0] + sD[q * RLD + k];
+    }
+    __syncthreads();  // the tile, the residuals and the corrections are refilled by the next strip
+  }
+}
+
+template <typename T, typename TM, int W>
+int strip_occupancy() {
+  // the dynamic shared-memory limit and the resident CTAs per SM, once per instantiation
+  static std::mutex mu;
+  static int occ = -1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (occ >= 0) return occ;
+  using S = Strip<T, TM, W>;
+  occ = 0;
+  if (cudaFuncSetAttribute(kv_boxt<T, TM, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return occ;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kv_boxt<T, TM, W>, S::THREADS, S::SMEM) == cudaSuccess)
+    occ = n;
+  else
+    cudaGetLastError();
+  return occ;
+}
+
+// Launch kv_boxt with strip width W (boxes of one colour per strip; N_l / 8 must be
+// a multiple of W).  Returns false if the device cannot run it (no launch).
+template <typename T, typename TM, int W>
+bool launch_strip(Problem& P, bool pdl, T* w, const T* b, T* E, int N, StokesCoef<T> c, int color, const int* slot,
+                  const double* Ms, const TM* Mf) {
+  const int occ = strip_occupancy<T, TM, W>();
+  if (occ <= 0) return false;
+  const long half = N / 8, strips = half * half / W;
+  const int grid = (int)std::min<long>(strips, (long)P.n_sm * occ);
+  vlaunch(pdl, kv_boxt<T, TM, W>, grid, Strip<T, TM, W>::THREADS, Strip<T, TM, W>::SMEM, P.stream, w, b, E, N, c,
+          color, slot, Ms, Mf);
+  return true;
+}
+
+// Strip width: the widest of 32, 16, 8 that divides N_l / 8 and still gives at
+// least 2 strips per SM, else the narrowest that divides it (most CTAs).
+inline int strip_width(const Problem& P, int N) {
+  const long half = N / 8, nbox = half * half;
+  if (P.box_strip_w > 0) return half % P.box_strip_w == 0 ? P.box_strip_w : 0;
+  int pick = 0;
+  for (int W : {32, 16, 8}) {
+    if (half % W) continue;
+    pick = W;
+    if (nbox / W >= 2L * P.n_sm) break;
+  }
+  return pick;
+}
+
 template <typename T, typename TM>
 int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   LevelInfo& L = P.lev[l];
@@ -443,6 +721,19 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const bool gemm = nbox >= P.box_gemm_min;
   const bool one = nbox <= P.box_one_max;
   const bool pdl = use_pdl(P);
+  if (P.prm.box == 4 && P.box_strip && nbox >= P.box_strip_min) {
+    bool done = false;
+    switch (strip_width(P, L.N)) {
+      case 32: done = launch_strip<T, TM, 32>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf); break;
+      case 16: done = launch_strip<T, TM, 16>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf); break;
+      case 8: done = launch_strip<T, TM, 8>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf); break;
+      default: break;
+    }
+    if (done) {
+      IB_LAUNCH_CHECK();
+      return IB_OK;
+    }
+  }
 #define IB_BOXN(BS_, BPC_)                                                                                    \
   vlaunch(pdl, kv_boxn<T, TM, BS_, BPC_>, nblk(nbox, BPC_), BoxShape<BS_, BPC_>::THREADS, 0, P.stream, w, b, E, \
           L.N, c, color, L.flag, Ms, Mf)
@@ -1341,7 +1632,24 @@ int vcycle_run(Problem& P) {
     }
     P.graph_dirty[ix] = false;
   }
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if (P.vt_on) {
+    for (cudaEvent_t* e : {&ta, &tb}) {
+      if (!P.ev_pool.empty()) {
+        *e = P.ev_pool.back();
+        P.ev_pool.pop_back();
+      } else {
+        IB_CUDA_TRY(cudaEventCreate(e));
+      }
+    }
+    IB_CUDA_TRY(cudaEventRecord(ta, P.stream));
+  }
   IB_CUDA_TRY(cudaGraphLaunch(P.vgraph[ix], P.stream));
+  if (P.vt_on) {
+    IB_CUDA_TRY(cudaEventRecord(tb, P.stream));
+    P.vt_pending.emplace_back(ta, tb);
+    P.vt_kind.push_back(ix);
+  }
   for (int c = 0; c < IB_KC_COUNT; ++c) P.nlaunch[c] += P.graph_launches[ix][c];
   return IB_OK;
 }

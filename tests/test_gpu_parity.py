@@ -317,3 +317,49 @@ def test_full_size_256_apply_and_fp32_solve(pkg):
     assert np.linalg.norm((levels[0].A @ x)[2 * n:]) <= 1.01e-8 * np.linalg.norm(b)
     assert st["iters"] <= 30
     s.close()
+
+
+# ---------------------------------------------------------------- strip kernel for 4 x 4 boxes
+# Levels whose N_l / 8 is a multiple of the strip width run the colour phases of
+# 4 x 4 boxes with the strip kernel (a strip of W boxes of one colour per CTA
+# iteration, staged tile, register-blocked free-box product).  IB_BOX_STRIP_MIN=1
+# lets it run on every level it fits and IB_BOX_STRIP_W pins the width, so each
+# width is compared with the oracle; IB_BOX_STRIP=0 turns it off.
+
+def _strip_case(N):
+    if N == 64:
+        return make_case("c1_64", 4)
+    p = W.single_ellipse(N=N, n_points=2 * N, kappa=1e4, dt=1e-3)
+    p.box = 4
+    return p
+
+
+@pytest.mark.parametrize("N,width,prec", [(64, 8, "fp64"), (64, 8, "fp32"), (64, 8, "mixed"),
+                                          (128, 16, "fp64"), (128, 16, "mixed"),
+                                          (256, 32, "fp64"), (256, 32, "fp32"), (256, 8, "fp32")])
+def test_vcycle_strip_kernel(pkg, N, width, prec, monkeypatch):
+    monkeypatch.setenv("IB_BOX_STRIP_MIN", "1")
+    monkeypatch.setenv("IB_BOX_STRIP_W", str(width))
+    p = _strip_case(N)
+    rhs = O.rhs_vector(p)
+    ref = _oracle_vcycle(p, rhs)
+    s = pkg.IBSolver.from_problem(p, precision=prec)
+    assert s.struct_boxes(0) > 0
+    w = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), w)
+    got = w.cpu().numpy()
+    if prec == "fp64":
+        assert rel_elementwise(got, ref) < 1e-10, rel_elementwise(got, ref)
+    else:
+        bar = 2e-5 if prec == "fp32" else 5e-7
+        assert max(rel_per_component(got, ref, p.N)) <= bar, rel_per_component(got, ref, p.N)
+    s.vcycle(dev(rhs), w)  # graph replay: same result
+    got2 = w.cpu().numpy()
+    assert np.abs(got2 - got).max() <= (1e-12 if prec == "fp64" else 1e-6) * np.abs(got).max()
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_step_strip_kernel(pkg, prec, monkeypatch):
+    monkeypatch.setenv("IB_BOX_STRIP_MIN", "1")
+    test_solve_step(pkg, "c1_64", 4, prec)
