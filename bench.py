@@ -1,20 +1,33 @@
 #!/usr/bin/env python3
 """Benchmark: implicit IB step time to a 1e-8 relative residual on GB300.
 
-Workload (default): the 256^2 periodic MAC grid with the 512-point elastic
-ellipse (semi-axes 0.28/0.22 at (0.5, 0.5), rest length 2*pi*0.25/512), rho =
-mu = 1, swept over kappa in {1, 1e2, 1e4, 1e6} x dt in {1e-3, 1e-2}: one bench
-step = one backward-Euler IB step (set-up + MG-preconditioned FGMRES to 1e-8
-+ point update) for each of the 8 cases, solved together as one batch
-(ib_solve_step_batch, FP32 V-cycle in FP64 FGMRES), inputs resident on the
-device.  value = device time of the step / 8 (ms per implicit IB step), CUDA
-events, L2 flushed between timed steps.  The line also carries the same sweep
-solved case by case in FP64 and in FP32 ("forms").
+Default workload (multi1024): the 1024^2 periodic MAC grid with 16 non-overlapping
+elastic ellipses of 2048 points each (seed 1311, semi-axes U[0.02, 0.06]), kappa =
+1e4, dt = 1e-3, rho = mu = 1, b = 4, V(1,1), FP32 V-cycle inside FP64 FGMRES
+(restart 50).  One bench step = 20 consecutive implicit IB steps (set-up + MG-
+preconditioned FGMRES to 1e-8 + point update each; u^n and X carried from step to
+step), starting from rest at X^0; inputs resident on the device, L2 flushed before
+every bench step.  value = device ms per implicit step (CUDA events on the stream).
+
+The line also carries:
+  e2e           the same steps through the C ABI with host buffers (H2D of X^0,
+                D2H of u, v, p and X^{n+1}), host clock around the calls;
+  roofline      the V-cycle (replayed from its CUDA graph inside FGMRES), timed
+                with an event pair per V-cycle inside the timed region, against
+                the V(1,1) algorithmic traffic (56 B/DOF in FP32) and the measured
+                HBM bandwidth;
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload (its
+                set-up plus one FGMRES iteration, scaled by the iteration count),
+                and the GPU result's error against the oracle;
+  forms         the 256^2 kappa x dt sweep solved case by case (FP64, mixed,
+                FP32 V-cycles) and batched (FP32, FP64), for the precision and
+                batching comparisons.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|fp64|mixed] [--box B]
+                  [--workload multi1024|sweep256|case256|batch256|vcycle|learned512]
+                  [--precision fp32|fp64|mixed] [--box B] [--no-cpu] [--no-forms]
 
-Under torchrun each rank solves the whole sweep on its own GPU (independent
+Under torchrun each rank solves the whole workload on its own GPU (independent
 replicas, no collective on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
@@ -204,22 +217,43 @@ def oracle_sample_ms(box, case_index=2):
 
 
 def run_reference(args):
-    rank, world, _ = args.rank, args.world, args.local_rank
+    """The reference arm: the CPU oracle, as it stands, on the host cores, for the same
+    workload, metric and unit as the GPU arm.  Rank 0 alone runs it.
+
+    multi1024 (default): the oracle's first implicit step of the C3 workload.  Its
+    per-step set-up (hierarchy, Galerkin levels, box matrices, right-hand side) and one
+    full FGMRES solve (which fixes the iteration count) run during the first warm-up
+    step; every bench step then times one FGMRES iteration's V-cycle and operator apply.
+    value = set-up + iterations x the mean iteration sample (ms per implicit step).
+    sweep256: one implicit step of the kappa = 1e4, dt = 1e-3 case per bench step (the
+    config names that single case)."""
+    rank = args.rank
     if rank != 0:
         return 0
-    times = []
-    for s in range(args.warmup + args.steps):
-        ms, its = oracle_sample_ms(args.box, case_index=s % len(CASES) if args.rotate else 2)
-        if s >= args.warmup:
-            times.append(ms)
-    v = float(np.mean(times))
+    if args.workload == "multi1024":
+        prob = c3_problem(args.box)
+        o = oracle_c3(prob, samples=max(1, args.warmup - 1) + args.steps, full_solve=True,
+                      log=lambda m: print(m, file=sys.stderr))
+        v = 1e3 * o["step_s"]
+        sample = ("C3 first implicit step: oracle set-up %.1f s (measured once) + %d FGMRES iterations (the "
+                  "oracle's own count) x %.2f s (median of %d samples of one V-cycle + one operator apply; "
+                  "Gram-Schmidt not included); the full solve took %.1f s"
+                  % (o["t_setup_s"], o["iters"], o["t_iter_s"], o["samples"], o["t_solve_s"]))
+        config = c3_config(args)
+    else:
+        times = []
+        for s_ in range(args.warmup + args.steps):
+            ms, its = oracle_sample_ms(args.box, 2)
+            if s_ >= args.warmup:
+                times.append(ms)
+        v = float(np.mean(times))
+        sample = "one implicit step of the kappa=1e4, dt=1e-3 sweep case per bench step (%d iterations)" % its
+        config = dict(config_dict(args), workload="256^2 MAC grid, 512-point ellipse, kappa=1e4, dt=1e-3 "
+                                                  "(one case of the sweep)")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_dict(args),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one implicit step of the kappa=1e4, dt=1e-3 case per bench step "
-                                       "(scipy CSR oracle, single-threaded sparse kernels)"},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference", "config": config,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -507,45 +541,306 @@ def run_learned512(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- C2 forms (context)
+
+def sweep_forms(args, torch, pkg):
+    """The 256^2 kappa x dt sweep (8 cases) in five forms, ms per implicit step to 1e-8:
+    case by case with the FP64, mixed and FP32 V-cycles, and batched (all cases in one
+    ib_solve_step_batch) with the FP32 and FP64 V-cycles, so that precision and batching
+    are compared separately.  With the CPU leg on (rank 0, one GPU), each form's solution
+    of the kappa = 1e4, dt = 1e-3 case is compared with the oracle's."""
+    dev = torch.device("cuda", args.local_rank)
+    probs = workload_problems(args.box)
+    nc = len(probs)
+    nn = 3 * N_GRID * N_GRID
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    X0 = torch.tensor(np.concatenate([p.X for p in probs]), dtype=torch.float64, device=dev)
+    Xw = X0.clone()
+    up = torch.zeros(nc * nn, dtype=torch.float64, device=dev)
+    xoff = np.concatenate([[0], np.cumsum([p.n_points for p in probs])])
+    forms, sols = {}, {}
+    steps = max(2, min(args.steps, 5))
+    for prec in ("fp64", "mixed", "fp32"):
+        solvers = [pkg.IBSolver.from_problem(p, precision=prec, max_iters=args.max_iters) for p in probs]
+        st = [None] * nc
+
+        def seq_step():
+            Xw.copy_(X0)
+            for i, s_ in enumerate(solvers):
+                st[i] = s_.solve_step(None, up[i * nn:(i + 1) * nn], Xw[xoff[i]:xoff[i + 1]])
+
+        ms = _timed_steps(torch, seq_step, flush, stream, 3, steps)
+        forms["sequential_" + prec] = {"ms_per_ib_step": sum(ms) / (steps * nc), "iters": [x["iters"] for x in st],
+                                       "status": [x["status"] for x in st]}
+        sols["sequential_" + prec] = up[2 * nn:3 * nn].cpu().numpy()
+        for s_ in solvers:
+            s_.close()
+    for prec in ("fp32", "fp64"):
+        batch = pkg.IBBatch(probs, precision=prec, max_iters=args.max_iters)
+        bst = [None]
+
+        def batch_step():
+            Xw.copy_(X0)
+            bst[0] = batch.solve_step(None, up, Xw)
+
+        ms = _timed_steps(torch, batch_step, flush, stream, 3, steps)
+        forms["batched_" + prec] = {"ms_per_ib_step": sum(ms) / (steps * nc),
+                                    "iters": [x["iters"] for x in bst[0]], "status": [x["status"] for x in bst[0]]}
+        sols["batched_" + prec] = up[2 * nn:3 * nn].cpu().numpy()
+        batch.close()
+    forms["workload"] = "256^2, 512-point ellipse, kappa in {1,1e2,1e4,1e6} x dt in {1e-3,1e-2}, b = %d" % args.box
+    if args.rank == 0 and args.world == 1 and not args.no_cpu:
+        from oracle import ib_oracle as O
+
+        t = time.perf_counter()
+        ref = O.solve_step(probs[2])
+        t = time.perf_counter() - t
+        forms["error_vs_oracle"] = {
+            "case": "kappa=1e4, dt=1e-3 (oracle: %d iterations, %.1f s on one core)" % (ref.solve.iters, t),
+            **{k: float(np.linalg.norm(v - ref.w) / np.linalg.norm(ref.w)) for k, v in sols.items()}}
+    return forms
+
+
+# ----------------------------------------------------------------------------- C3: the headline
+
+C3 = dict(N=1024, count=16, n_per=2048, kappa=1e4, dt=1e-3, seed=1311, restart=50)
+C3_STEPS = 20  # consecutive implicit steps per bench step
+
+
+def c3_problem(box):
+    p = W.many_ellipses(N=C3["N"], count=C3["count"], n_per=C3["n_per"], kappa=C3["kappa"], dt=C3["dt"],
+                        seed=C3["seed"])
+    p.box = box
+    return p
+
+
+def c3_config(args):
+    return {"workload": "1024^2 MAC grid, 16 ellipses x 2048 points (seed 1311, semi-axes U[0.02, 0.06]), "
+                        "kappa=1e4, dt=1e-3, rho=mu=1; %d consecutive implicit steps per bench step "
+                        "(u^n and X carried), each from rest at X^0 per bench step" % args.c3_steps,
+            "N": C3["N"], "n_points": C3["count"] * C3["n_per"], "box": args.box, "nu": [1, 1],
+            "precision": args.precision, "tol": 1e-8, "restart": C3["restart"], "max_iters": args.max_iters,
+            "l2": "flushed (256 MiB write) before every timed bench step",
+            "parallelism": "replicas" if args.world > 1 else "single GPU"}
+
+
+def oracle_c3(prob, iters=None, samples=1, full_solve=False, gpu=None, log=None):
+    """CPU oracle on the C3 workload (first implicit step, fluid at rest): the per-step
+    set-up (hierarchy: S, J, Galerkin levels, box matrices; right-hand side) timed once,
+    then `samples` timings of one FGMRES iteration's preconditioner and operator work
+    (one V-cycle + one operator apply).  With full_solve the oracle's FGMRES runs to
+    the tolerance once (its iteration count and solution).  Estimated oracle step time =
+    set-up + iters x iteration sample.  gpu (dict: w = the GPU's first-step solution,
+    z = the GPU V-cycle applied to the first step's right-hand side) adds the GPU result's
+    errors against the oracle: the true residual on the oracle's CSR operator and the
+    relative difference of the preconditioner output."""
+    from oracle import ib_oracle as O
+
+    def note(m):
+        if log:
+            log(m)
+
+    t0 = time.perf_counter()
+    levels, _ = O.build_hierarchy(prob)
+    for lev in levels[:-1]:
+        O.prepare_boxes(lev, prob.box)
+    b = O.rhs_vector(prob)
+    t_setup = time.perf_counter() - t0
+    note("oracle set-up %.1f s" % t_setup)
+    A = levels[0].A
+    t_iter = []
+    z = None
+    for _ in range(samples):
+        t1 = time.perf_counter()
+        z = O.vcycle(levels, b, np.zeros_like(b), prob.nu1, prob.nu2, prob.rho, "color4")
+        _ = A @ z
+        t_iter.append(time.perf_counter() - t1)
+    note("oracle iteration sample %.2f s" % min(t_iter))
+    out = {"t_setup_s": t_setup, "t_iter_s": float(np.median(t_iter)), "samples": samples}
+    if full_solve:
+        t2 = time.perf_counter()
+        res = O.fgmres(A, b, lambda v: O.vcycle(levels, v, np.zeros_like(v), prob.nu1, prob.nu2, prob.rho,
+                                                 "color4"), prob.tol, prob.max_iters)
+        out["t_solve_s"] = time.perf_counter() - t2
+        out["oracle_iters"] = res.iters
+        out["oracle_w"] = O.remove_pressure_mean(res.x, prob.N)
+        iters = res.iters if iters is None else iters
+    out["iters"] = iters
+    out["step_s"] = t_setup + (iters or 0) * out["t_iter_s"]
+    if gpu is not None:
+        w = gpu["w"]
+        bn = np.linalg.norm(b)
+        n = prob.N * prob.N
+        out["error_vs_oracle"] = {
+            "rel_res_true_on_oracle_csr": float(np.linalg.norm(b - A @ w) / bn),
+            "div_on_oracle_csr": float(np.linalg.norm((A @ w)[2 * n:]) / bn),
+            "vcycle_rel_diff": float(np.linalg.norm(gpu["z"] - z) / np.linalg.norm(z)),
+            "vcycle_max_elem_rel": float(np.abs(gpu["z"] - z).max() / np.abs(z).max())}
+        if "oracle_w" in out:
+            ow = out["oracle_w"]
+            out["error_vs_oracle"]["solution_rel"] = float(np.linalg.norm(w - ow) / np.linalg.norm(ow))
+    out.pop("oracle_w", None)
+    return out
+
+
 def run_multi1024(args):
-    """1024^2 grid, 16 random ellipses of 2048 points, kappa = 1e4, dt = 1e-3: consecutive
-    implicit steps (u^n and X carried from step to step); value = ms per step."""
+    """Headline: the 1024^2 multi-structure workload.  One bench step = C3_STEPS
+    consecutive implicit IB steps (set-up + MG-preconditioned FGMRES to 1e-8 + point
+    update each, u^n and X carried), starting from rest at X^0.  value = device ms per
+    implicit step (CUDA events on the stream, L2 flushed before every bench step)."""
     import torch
 
     import paper_1311_5614_gb300 as pkg
+    from paper_1311_5614_gb300 import capi as C
 
-    torch.cuda.set_device(args.local_rank)
-    prob = W.many_ellipses(N=1024, count=16, n_per=2048, kappa=1e4, dt=1e-3, seed=1311)
-    prob.box = args.box
-    s = pkg.IBSolver.from_problem(prob, precision=args.precision, max_iters=args.max_iters, restart=50)
-    n = 3 * prob.N * prob.N
-    up = torch.zeros(n, dtype=torch.float64, device="cuda")
-    un = torch.zeros(2 * prob.N * prob.N, dtype=torch.float64, device="cuda")
-    X = torch.tensor(prob.X, dtype=torch.float64, device="cuda")
+    rank, world, local_rank = args.rank, args.world, args.local_rank
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = c3_problem(args.box)
+    N = prob.N
+    n3, n2 = 3 * N * N, 2 * N * N
+    s = pkg.IBSolver.from_problem(prob, precision=args.precision, max_iters=args.max_iters, restart=C3["restart"])
+    up = torch.zeros(n3, dtype=torch.float64, device=dev)
+    un = torch.zeros(n2, dtype=torch.float64, device=dev)
+    X0 = torch.tensor(prob.X, dtype=torch.float64, device=dev)
+    X = X0.clone()
     stream = torch.cuda.current_stream()
     stats = []
 
-    def step():
-        st = s.solve_step(un, up, X)
-        un.copy_(up[: 2 * prob.N * prob.N])
-        stats.append(st)
+    def steps():
+        stats.clear()
+        stats.append(s.solve_step(None, up, X))
+        for _ in range(args.c3_steps - 1):
+            un.copy_(up[:n2])
+            stats.append(s.solve_step(un, up, X))
 
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    clk = ClockSampler(args.local_rank)
+    def bench_step():
+        X.copy_(X0)
+        steps()
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = s.launch_count()
+    s.vcycle_timer(True)
+    clk = ClockSampler(local_rank)
     clk.start()
-    ms = _timed_steps(torch, step, flush, stream, args.warmup, args.steps, args.profile_range)
+    t_wall = time.perf_counter()
+    step_ms = _timed_steps(torch, bench_step, flush, stream, 0, args.steps, args.profile_range)
+    t_wall = time.perf_counter() - t_wall
     clocks = clk.stop()
+    vprec = "fp32" if args.precision == "fp32" else "fp64"
+    nv32 = s.vcycle_timer_read("fp32") if args.precision == "fp32" else (0, 0.0)
+    nv64 = s.vcycle_timer_read("fp64")
+    s.vcycle_timer(False)
+    barrier(world)
+    gpu_launches = s.launch_count() - launches0
+    step_stats = list(stats)
+    per_ib_ms, t_max = aggregate(step_ms, args.steps * args.c3_steps, world)
+
+    # end to end through the C ABI with host buffers: H2D of X^0 from pinned memory, the
+    # steps, D2H of the final u, v, p and X; host clock around the whole call sequence
+    Xh = torch.tensor(prob.X, dtype=torch.float64).pin_memory()
+    uph = torch.empty(n3, dtype=torch.float64).pin_memory()
+    Xoh = torch.empty_like(Xh).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        X.copy_(Xh, non_blocking=True)
+        steps()
+        uph.copy_(up, non_blocking=True)
+        Xoh.copy_(X, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e_per, _ = aggregate(e2e_ms, args.steps * args.c3_steps, world)
+
+    # roofline of the V-cycle (the preconditioner graph replayed inside FGMRES): the
+    # algorithmic traffic of a V(1,1) cycle, 56 B/DOF in FP32 (112 B/DOF on FP64
+    # vectors), over its mean device time inside the timed region
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    nv, vms = (nv32[0] + nv64[0], nv32[1] + nv64[1])
+    bpd32, bpd64 = 56.0, 112.0
+    alg_bytes = (nv32[0] * bpd32 + nv64[0] * bpd64) * n3
+    vcycle_ms = vms / max(nv, 1)
+    achieved = alg_bytes / (vms * 1e-3) / 1e9 if vms > 0 else 0.0
+    traffic = captured_traffic("vcycle1024")
+    roofline = {"bound": "hbm", "kernel": "V(1,1) cycle, replayed from its CUDA graph inside FGMRES",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "traffic": traffic, "alg_bytes_per_launch": alg_bytes / max(nv, 1), "launches": nv,
+                "avg_launch_ms": vcycle_ms, "dof": n3,
+                "alg_bytes_per_dof": bpd32 if nv32[0] >= nv64[0] else bpd64,
+                "share_of_step": vms / max(sum(step_ms), 1e-30),
+                "vcycle_dof_per_s": n3 / (vcycle_ms * 1e-3) if vcycle_ms > 0 else 0.0}
+
+    # first step again (from rest at X^0): its solution and the V-cycle applied to its
+    # right-hand side, for the comparison with the oracle in the CPU leg
+    X.copy_(X0)
+    st1 = s.solve_step(None, up, X)
+    w1 = up.cpu().numpy()
+    X.copy_(X0)
+    s.update_points(X)
+    b1 = torch.zeros(n3, dtype=torch.float64, device=dev)
+    s.rhs(None, b1)
+    z1 = torch.zeros_like(b1)
+    s.vcycle(b1, z1)
+    z1 = z1.cpu().numpy()
+
+    # per-class device time of one implicit step (a separate eager pass with an event pair
+    # around every launch: context for the V-cycle figure above)
+    s.profile(True)
+    X.copy_(X0)
+    s.solve_step(None, up, X)
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    tail = (s.tail_grid(args.precision), s.tail_cluster(args.precision))
     s.close()
-    line = {"metric": METRIC, "value": sum(ms) / len(ms), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": False, "dtype": "f32 V-cycle + f64 Krylov",
-            "data": "synthetic",
-            "config": {"workload": "1024^2, 16 ellipses x 2048 points (seed 1311), kappa=1e4, dt=1e-3, "
-                                   "consecutive steps", "box": args.box, "precision": args.precision,
-                       "restart": 50, "max_iters": args.max_iters},
-            "iters": [x["iters"] for x in stats], "status": [x["status"] for x in stats],
-            "rel_res_true": [x["rel_res_true"] for x in stats], "setup_ms": [x["t_setup_ms"] for x in stats],
-            "clocks": clocks}
-    print(json.dumps(line), flush=True)
+
+    forms = sweep_forms(args, torch, pkg) if args.forms else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        o = oracle_c3(prob, iters=st1["iters"], samples=1, gpu={"w": w1, "z": z1},
+                      log=lambda m: print(m, file=sys.stderr))
+        cpu = {"value": 1e3 * o["step_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "C3 first implicit step: the oracle's set-up (hierarchy, Galerkin levels, box "
+                         "matrices, right-hand side: %.1f s) plus %d x one FGMRES iteration's V-cycle and "
+                         "operator apply (%.2f s, measured once; %d = the GPU step's iteration count); "
+                         "Gram-Schmidt not included" % (o["t_setup_s"], o["iters"], o["t_iter_s"], o["iters"]),
+               "error_vs_oracle": o["error_vs_oracle"]}
+
+    if rank == 0:
+        its = [x["iters"] for x in step_stats]
+        line = {"metric": METRIC, "value": per_ib_ms, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+                "config": c3_config(args),
+                "e2e": {"value": e2e_per, "unit": UNIT, "h2d_bytes_per_step": Xh.numel() * 8,
+                        "d2h_bytes_per_step": uph.numel() * 8 + Xoh.numel() * 8,
+                        "clock": "host wall clock around the C-ABI calls, synchronised"},
+                "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": int(gpu_launches),
+                "clocks": clocks, "wall_s_timed": t_wall,
+                "iters_per_step": its, "rel_res_true": [x["rel_res_true"] for x in step_stats],
+                "status": sorted(set(x["status"] for x in step_stats)),
+                "setup_ms": float(np.mean([x["t_setup_ms"] for x in step_stats])),
+                "solve_ms": float(np.mean([x["t_solve_ms"] for x in step_stats])),
+                "tail": {"grid": tail[0], "cluster": tail[1]},
+                "profile": {k: {"launches": v[0], "ms": v[1], "bytes": v[2]} for k, v in prof.items()},
+                "forms": forms}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -656,10 +951,13 @@ def main(argv=None):
                     help="pairs per training problem (40 x 256 = 10240 pairs by default)")
     ap.add_argument("--save-params", default=None, help="learned512: write the trained U-Net parameters (.npy)")
     ap.add_argument("--learn-epochs", type=int, default=2)
-    ap.add_argument("--workload", default="sweep256",
+    ap.add_argument("--workload", default="multi1024",
                     choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512"],
-                    help="sweep256 (default): the 256^2 kappa x dt sweep; multi1024 / batch256: the "
-                         "1024^2 multi-structure run and the 256-problem batch (extra lines)")
+                    help="multi1024 (default): the 1024^2 sixteen-ellipse run, 20 consecutive steps per "
+                         "bench step; sweep256: the 256^2 kappa x dt sweep; batch256: the 256-problem "
+                         "batch; vcycle: the V-cycle alone (--grid); learned512: the learned stage")
+    ap.add_argument("--c3-steps", type=int, default=C3_STEPS,
+                    help="multi1024: consecutive implicit steps per bench step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the first timed step of the sequential form in the bench precision "
@@ -697,7 +995,9 @@ def main(argv=None):
             return run_vcycle(args)
         if args.workload == "learned512":
             return run_learned512(args)
-        return run_ours(args)
+        if args.workload == "sweep256":
+            return run_ours(args)
+        return run_multi1024(args)
     finally:
         if args.world > 1:
             import torch.distributed as dist

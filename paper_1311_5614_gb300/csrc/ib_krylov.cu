@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdlib>
 
+#include "ib_async.cuh"
 #include "ib_internal.cuh"
 
 namespace ib {
@@ -84,63 +85,6 @@ __global__ void __launch_bounds__(TPB) k_multidot_partial(const double* __restri
     partial[(size_t)blockIdx.x * stride + i0 + threadIdx.x] = t;
   }
 }
-
-// ---- bulk copies global -> shared completing on an mbarrier (bounded waits)
-__device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ inline void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile(
-      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
-      "r"(bytes)
-      : "memory");
-}
-// bytes: a multiple of 16; dst and src 16-byte aligned
-__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ inline bool mbar_try(unsigned long long* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-__device__ inline unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ inline bool mbar_test(unsigned long long* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// Waits until phase `parity` of the barrier completes, for at most limit_ns: a
-// non-blocking test first, then potentially blocking try_wait probes until the
-// limit has passed (with limit_ns = 0 only the first test counts).
-__device__ inline bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
-  if (mbar_test(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (;;) {
-    if (global_ns() - t0 >= limit_ns) return false;
-    if (mbar_try(bar, parity)) return true;
-  }
-}
-// After a timed-out wait the block still waits for its copies in flight before it
-// exits (they write into its shared memory), for at most this long.
-constexpr unsigned long long DRAIN_LIMIT_NS = 2000000000ull;  // 2 s
 
 // Fused Gram-Schmidt pass: w <- w - sum_i coef_i V_i, then partial[bx * stride + i]
 // = the block's part of V_i . w (the updated w), so the basis is read from HBM

@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "ib_async.cuh"
 #include "ib_ops.cuh"
 #include "ib_vcycle.cuh"
 
@@ -433,36 +434,41 @@ __global__ void __launch_bounds__(128) kv_boxg(T* w, const T* __restrict__ b, T*
   }
 }
 
-// Strip kernel for 4 x 4 boxes on large levels (N_l >= 256).  A CTA takes a strip
-// of W boxes of one colour in one box row (every other box along x, so the strip
-// spans 8W cells) and:
-//   1. stages the strip's w rows with their one-cell halo in shared memory with
-//      16-byte vector loads (u: 6 rows, v: 7, p: 6; 8W + 8 columns, periodic);
+// Strip kernel for 4 x 4 boxes on large levels.  A CTA takes strips of W boxes of
+// one colour in one box row (every other box along x, so a strip spans 8W cells),
+// persistent over the strips of the colour, and for each strip:
+//   1. has its w rows with their one-cell halo (u: 6 rows, v: 7, p: 6; 8W + 8
+//      columns, periodic) brought into shared memory by bulk copies (one to
+//      three per row, split where the row wraps) that complete on an mbarrier; the copies of the next strip go into
+//      a second buffer while this one is computed;
 //   2. forms the residual b - A_S w (+ the elasticity term rE on the rows of
-//      structure boxes, which it clears) of every unknown of its boxes, one
-//      unknown per thread, from the staged tile;
+//      structure boxes, which it clears) of every unknown of its boxes: the 56 W
+//      unknowns are split into units of 32 (one component per unit), each thread
+//      owns the same unknowns in every strip and keeps their positions in registers;
 //   3. applies the shared free-box inverse to all W residuals as one register-
-//      blocked product (RB rows x CB boxes per thread), and the FP64 inverse of
-//      each structure box with one warp per box;
-//   4. writes w + delta back, one unknown per thread.
-// The CTAs are persistent over the strips of the colour, so the free-box inverse
-// is staged once per CTA (before the programmatic-launch wait: set-up data).
+//      blocked product (RB rows x CB boxes per thread), then the FP64 inverses of
+//      the strip's structure boxes, one (box, row) dot product per thread;
+//   4. writes w + delta back.
+// The free-box inverse is staged once per CTA before the programmatic-launch wait.
 template <typename T, typename TM, int W>
 struct Strip {
-  static constexpr int NB = 56, THREADS = 256;
+  static constexpr int NB = 56, THREADS = 256, WARPS = THREADS / 32;
   static constexpr int SPAN = 8 * W;            // cells of one strip
   static constexpr int LD = SPAN + 8;           // staged columns [X0 - 4, X0 + SPAN + 4)
   static constexpr int TROWS = 6 + 7 + 6;       // staged rows of u, v, p
-  static constexpr int VE = 16 / (int)sizeof(T);  // elements per 16-byte chunk
-  static constexpr int CH = LD / VE;            // chunks per staged row
+  static constexpr int TILE = TROWS * LD;       // elements of one staging buffer
   static constexpr int RLD = W + 4;             // row stride of the [q][box] blocks
   static constexpr bool SPLIT = !std::is_same<T, TM>::value;  // separate TM copy of the residuals
   static constexpr int RB = sizeof(TM) == 4 ? 4 : 2;  // rows per thread (one 16-byte load of M)
   static constexpr int CB = sizeof(TM) == 4 ? 2 : 4;  // boxes per thread
   static constexpr int RG = NB / RB, BG = W / CB;
   static_assert(RG * BG <= THREADS, "product tiling");
+  // units of 32 unknowns: u rows (5W unknowns each), v rows (4W), p rows (4W)
+  static constexpr int UNITS = NB * W / 32, UPW = (UNITS + WARPS - 1) / WARPS;
+  static_assert((5 * W) % 32 == 0 || (20 * W) % 32 == 0, "u units");
+  static_assert((20 * W) % 32 == 0 && (16 * W) % 32 == 0, "unit boundaries");
   static constexpr size_t OFF_TILE = ((size_t)NB * NB * sizeof(TM) + 15) / 16 * 16;
-  static constexpr size_t OFF_R = OFF_TILE + (size_t)TROWS * LD * sizeof(T);
+  static constexpr size_t OFF_R = OFF_TILE + 2 * (size_t)TILE * sizeof(T);
   static constexpr size_t OFF_D = OFF_R + (size_t)NB * RLD * sizeof(T);
   static constexpr size_t OFF_RM = OFF_D + (size_t)NB * RLD * sizeof(T);
   static constexpr size_t SMEM = OFF_RM + (SPLIT ? (size_t)NB * RLD * sizeof(TM) : 0);
@@ -500,99 +506,181 @@ struct VecLoad<double, 4> {
   }
 };
 
-// Unknown e (0 <= e < 56 W) of a strip in the order u rows, v rows, p rows (each
-// row: W boxes x 5 or 4 faces/cells): its component, box-relative row jr, box k,
-// column d inside the box and box-local index q.
-__device__ __forceinline__ void strip_unknown(int e, int W, int* comp, int* jr, int* k, int* d, int* q) {
+// One unknown of a strip, as a thread keeps it across strips: its offset in a
+// staging buffer (toff), in the [q][box] blocks (roff = q * RLD + k), and its
+// component, box-relative row, box and strip column packed in one word.
+struct StripItem {
+  int toff, roff, pack;  // pack = comp << 28 | jr << 24 | k << 16 | col
+};
+
+// Unknown e (0 <= e < 56 W) in the order u rows, v rows, p rows (each row: W boxes
+// x 5 faces or 4 faces/cells), for a staging buffer with row stride LD and blocks
+// with row stride RLD.
+__device__ __forceinline__ StripItem strip_item(int e, int W, int LD, int RLD) {
+  int comp, jr, k, d, q;
   if (e < 20 * W) {
-    const int r = e / (5 * W), t = e - r * 5 * W;
-    *comp = 0; *jr = r; *k = t / 5; *d = t - *k * 5; *q = r * 5 + *d;
+    jr = e / (5 * W);
+    const int t = e - jr * 5 * W;
+    comp = 0; k = t / 5; d = t - k * 5; q = jr * 5 + d;
   } else if (e < 40 * W) {
     e -= 20 * W;
-    const int r = e / (4 * W), t = e - r * 4 * W;
-    *comp = 1; *jr = r; *k = t >> 2; *d = t & 3; *q = 20 + r * 4 + *d;
+    jr = e / (4 * W);
+    const int t = e - jr * 4 * W;
+    comp = 1; k = t >> 2; d = t & 3; q = 20 + jr * 4 + d;
   } else {
     e -= 40 * W;
-    const int r = e / (4 * W), t = e - r * 4 * W;
-    *comp = 2; *jr = r; *k = t >> 2; *d = t & 3; *q = 40 + r * 4 + *d;
+    jr = e / (4 * W);
+    const int t = e - jr * 4 * W;
+    comp = 2; k = t >> 2; d = t & 3; q = 40 + jr * 4 + d;
+  }
+  const int col = 8 * k + d;
+  const int trow = (comp == 0 ? 0 : (comp == 1 ? 6 : 13)) + jr + 1;  // staged row of the unknown
+  StripItem it;
+  it.toff = trow * LD + col + 4;
+  it.roff = q * RLD + k;
+  it.pack = (comp << 28) | (jr << 24) | (k << 16) | col;
+  return it;
+}
+
+// Issue the bulk copies of one strip's tile (rows y0 - 1 .. of u, v, p; columns
+// X0 - 4 .. X0 + 8W + 3, split where they wrap) into buf: lane r < TROWS of
+// the calling warp copies row r; lane 0 first announces the byte count.  The caller
+// has ordered earlier generic accesses of buf before these writes (barrier + proxy
+// fence).
+template <typename T, int W>
+__device__ __forceinline__ void strip_issue(const T* w, int N, int y0, int X0, T* buf, unsigned long long* bar,
+                                            int lane) {
+  constexpr int LD = 8 * W + 8, TROWS = 19;
+  if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(TROWS * LD * sizeof(T)));
+  __syncwarp();
+  if (lane < TROWS) {
+    const int r = lane;
+    const int comp = r < 6 ? 0 : (r < 13 ? 1 : 2);
+    const int ry = r - (comp == 0 ? 0 : (comp == 1 ? 6 : 13));
+    const int y = (y0 - 1 + ry) & (N - 1);
+    const T* row = w + (size_t)comp * N * N + (size_t)y * N;
+    T* dst = buf + r * LD;
+    // the staged columns X0 - 4 .. X0 + 8W + 3 wrap at most twice (8W + 8 <= 2N);
+    // every segment starts and ends on a multiple of 4 elements (16 bytes or more)
+    int x = (X0 - 4) & (N - 1), done = 0;
+    while (done < LD) {
+      const int seg = min(LD - done, N - x);
+      bulk_g2s(dst + done, row + x, (unsigned)(seg * sizeof(T)), bar);
+      done += seg;
+      x = 0;
+    }
   }
 }
 
 template <typename T, typename TM, int W>
-__global__ void __launch_bounds__(256) kv_boxt(T* w, const T* __restrict__ b, T* rE, int N, StokesCoef<T> c,
+__global__ void __launch_bounds__(256, 3) kv_boxt(T* w, const T* __restrict__ b, T* rE, int N, StokesCoef<T> c,
                                                int color, const int* __restrict__ slot,
-                                               const double* __restrict__ Ms, const TM* __restrict__ Mf) {
+                                               const double* __restrict__ Ms, const TM* __restrict__ Mf, int* err,
+                                               unsigned long long limit_ns) {
   using S = Strip<T, TM, W>;
   constexpr int NB = S::NB, LD = S::LD, RLD = S::RLD;
   extern __shared__ __align__(16) unsigned char smem[];
   TM* sMf = reinterpret_cast<TM*>(smem);
-  T* tile = reinterpret_cast<T*>(smem + S::OFF_TILE);
+  T* tiles = reinterpret_cast<T*>(smem + S::OFF_TILE);
   T* sR = reinterpret_cast<T*>(smem + S::OFF_R);
   T* sD = reinterpret_cast<T*>(smem + S::OFF_D);
   TM* sRM = S::SPLIT ? reinterpret_cast<TM*>(smem + S::OFF_RM) : reinterpret_cast<TM*>(sR);
+  __shared__ __align__(8) unsigned long long bar[2];
   __shared__ int sslot[W];
   __shared__ int slist[W];
   __shared__ int nsl;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   {
     constexpr int VM = 16 / (int)sizeof(TM);
     const float4* src = reinterpret_cast<const float4*>(Mf);
     float4* dst = reinterpret_cast<float4*>(sMf);
     for (int e = tid; e < NB * NB / VM; e += S::THREADS) dst[e] = src[e];  // set-up data
   }
+  // this thread's unknowns (the same in every strip)
+  StripItem items[S::UPW];
+#pragma unroll
+  for (int i = 0; i < S::UPW; ++i) {
+    const int unit = wp + S::WARPS * i;
+    items[i] = unit < S::UNITS ? strip_item(unit * 32 + lane, W, LD, RLD) : StripItem{0, 0, -1};
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
   pdl_enter();
   const int nb = N >> 2, half = nb >> 1, spr = half / W, nstrips = spr * half;
   const int cx = color & 1, cy = color >> 1, m = N - 1;
   const size_t n = (size_t)N * N;
-  const int nchr = N / S::VE;
-  const T* U = tile;
-  const T* V = tile + 6 * LD;
-  const T* Pp = tile + 13 * LD;
-  for (int st = blockIdx.x; st < nstrips; st += gridDim.x) {
+  unsigned phase = 0u;  // bit i: parity of the next completion of bar[i]
+  int st = blockIdx.x;
+  if (wp == 0 && st < nstrips) {
+    const int Jp = st / spr, sx = st - Jp * spr;
+    strip_issue<T, W>(w, N, 4 * (2 * Jp + cy), 4 * (2 * sx * W + cx), tiles, &bar[0], lane);
+  }
+  for (int it = 0; st < nstrips; ++it, st += gridDim.x) {
+    const int buf = it & 1;
     const int Jp = st / spr, sx = st - Jp * spr;
     const int J = 2 * Jp + cy, I0 = 2 * sx * W + cx;
     const int y0 = 4 * J, X0 = 4 * I0;
     if (tid < W) sslot[tid] = slot[J * nb + I0 + 2 * tid];
-    // 1. stage the tile (16-byte chunks; a chunk never straddles a grid row)
-    const int c0 = (X0 - 4) / S::VE;
-    for (int e = tid; e < S::TROWS * S::CH; e += S::THREADS) {
-      const int r = e / S::CH, ch = e - r * S::CH;
-      const int comp = r < 6 ? 0 : (r < 13 ? 1 : 2);
-      const int ry = r - (comp == 0 ? 0 : (comp == 1 ? 6 : 13));
-      const int y = (y0 - 1 + ry) & m;
-      const int gch = (c0 + ch) & (nchr - 1);
-      const float4* src = reinterpret_cast<const float4*>(w + comp * n + (size_t)y * N) + gch;
-      reinterpret_cast<float4*>(tile + (size_t)r * LD)[ch] = *src;
+    // 1. this strip's tile has landed (bounded wait); then the next strip's copies
+    const unsigned par = (phase >> buf) & 1u;
+    const bool ok = mbar_wait_bounded(&bar[buf], par, limit_ns);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        mbar_wait_bounded(&bar[buf], par, DRAIN_LIMIT_NS);  // copies in flight land first
+      }
+      return;
     }
-    __syncthreads();
-    // 2. residuals, one unknown per thread
-    for (int e = tid; e < NB * W; e += S::THREADS) {
-      int comp, jr, k, d, q;
-      strip_unknown(e, W, &comp, &jr, &k, &d, &q);
-      const int col = 8 * k + d, cc = col + 4;
-      const int x = (X0 + col) & m, y = (y0 + jr) & m;
-      const size_t g = comp * n + (size_t)y * N + x;
+    phase ^= 1u << buf;
+    const int nx = st + gridDim.x;
+    if (wp == 0 && nx < nstrips) {
+      // the other buffer was last read before the barrier that ended the previous strip
+      fence_proxy_async_smem();
+      const int Jn = nx / spr, sxn = nx - Jn * spr;
+      strip_issue<T, W>(w, N, 4 * (2 * Jn + cy), 4 * (2 * sxn * W + cx), tiles + (buf ^ 1) * S::TILE,
+                        &bar[buf ^ 1], lane);
+    }
+    const T* tile = tiles + buf * S::TILE;
+    // 2. residuals (the component of a unit is the same for its whole warp)
+    // element offsets fit 32 bits: 3 N^2 < 2^31 for N <= 16384
+    auto goff = [&](int pk) -> unsigned {
+      return (unsigned)(pk >> 28) * (unsigned)n + (unsigned)(((y0 + ((pk >> 24) & 15)) & m) * N) +
+             (unsigned)((X0 + (pk & 0xffff)) & m);
+    };
+    T bv[S::UPW];
+    unsigned gv[S::UPW];
+#pragma unroll
+    for (int i = 0; i < S::UPW; ++i) {
+      gv[i] = 0u;
+      bv[i] = (T)0;
+      if (items[i].pack < 0) continue;
+      gv[i] = goff(items[i].pack);
+      bv[i] = b[gv[i]];
+    }
+#pragma unroll
+    for (int i = 0; i < S::UPW; ++i) {
+      const int pk = items[i].pack;
+      if (pk < 0) continue;
+      const int comp = pk >> 28, k = (pk >> 16) & 0xff;
+      const T* t0 = tile + items[i].toff;
       T a;
-      if (comp == 0) {
-        const T* ur = U + (jr + 1) * LD + cc;
-        const T* pr = Pp + (jr + 1) * LD + cc;
-        a = c.diag * ur[0] + c.off * (ur[1] + ur[-1] + ur[LD] + ur[-LD]) - c.g * (pr[0] - pr[-1]);
-      } else if (comp == 1) {
-        const T* vr = V + (jr + 1) * LD + cc;
-        const T* pr = Pp + (jr + 1) * LD + cc;
-        a = c.diag * vr[0] + c.off * (vr[1] + vr[-1] + vr[LD] + vr[-LD]) - c.g * (pr[0] - pr[-LD]);
-      } else {
-        const T* ur = U + (jr + 1) * LD + cc;
-        const T* vr = V + (jr + 1) * LD + cc;
-        a = c.g * (ur[1] - ur[0] + vr[LD] - vr[0]);
+      if (comp == 0) {  // u: staged rows 0..5 of u, p at +13 LD
+        a = c.diag * t0[0] + c.off * (t0[1] + t0[-1] + t0[LD] + t0[-LD]) - c.g * (t0[13 * LD] - t0[13 * LD - 1]);
+      } else if (comp == 1) {  // v: rows 6..12, p of the same row at +7 LD, the row below at +6 LD
+        a = c.diag * t0[0] + c.off * (t0[1] + t0[-1] + t0[LD] + t0[-LD]) - c.g * (t0[7 * LD] - t0[6 * LD]);
+      } else {  // p: rows 13..18; u of the same row at -13 LD, v at -7 LD (and -6 LD above)
+        a = c.g * (t0[-13 * LD + 1] - t0[-13 * LD] + t0[-6 * LD] - t0[-7 * LD]);
       }
-      T r = b[g] - a;
+      T r = bv[i] - a;
       if (rE && comp < 2 && sslot[k] >= 0) {
-        r += rE[g];
-        rE[g] = (T)0;
+        r += rE[gv[i]];
+        rE[gv[i]] = (T)0;
       }
-      sR[q * RLD + k] = r;
-      if (S::SPLIT) sRM[q * RLD + k] = (TM)r;
+      sR[items[i].roff] = r;
+      if (S::SPLIT) sRM[items[i].roff] = (TM)r;
     }
     __syncthreads();
     // 3a. free-box product for every box of the strip: D[q][k] = sum_s Mf[s][q] R[s][k]
@@ -620,42 +708,33 @@ __global__ void __launch_bounds__(256) kv_boxt(T* w, const T* __restrict__ b, T*
           for (int kk = 0; kk < S::CB; ++kk) sD[(rg * S::RB + a) * RLD + bg * S::CB + kk] = (T)acc[a][kk];
       }
     }
-    if (tid == 0) {
-      int cnt = 0;
-      for (int k = 0; k < W; ++k)
-        if (sslot[k] >= 0) slist[cnt++] = k;
-      nsl = cnt;
+    if (wp == 0) {  // the strip's structure boxes, in box order
+      const bool isS = lane < W && sslot[lane] >= 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, isS);
+      if (isS) slist[__popc(bal & ((1u << lane) - 1u))] = lane;
+      if (lane == 0) nsl = __popc(bal);
     }
     __syncthreads();
-    // 3b. structure boxes: their own FP64 inverses, one warp per box (replaces 3a's result)
-    {
-      const int wp = tid >> 5, lane = tid & 31;
-      for (int i = wp; i < nsl; i += S::THREADS / 32) {
-        const int k = slist[i];
-        const double* M = Ms + (size_t)sslot[k] * NB * NB;
-        const int q1 = lane + 32;
-        double d0 = 0.0, d1 = 0.0;
-#pragma unroll 4
-        for (int s2 = 0; s2 < NB; ++s2) {
-          const double rs = (double)sR[s2 * RLD + k];
-          d0 += M[s2 * NB + lane] * rs;
-          if (q1 < NB) d1 += M[s2 * NB + q1] * rs;
-        }
-        sD[lane * RLD + k] = (T)d0;
-        if (q1 < NB) sD[q1 * RLD + k] = (T)d1;
+    // 3b. structure boxes: their own FP64 inverses, one (box, row) per thread (replaces 3a)
+    for (int e = tid; e < nsl * NB; e += S::THREADS) {
+      const int k = slist[e / NB], q = e - (e / NB) * NB;
+      const double* M = Ms + (size_t)sslot[k] * NB * NB + q;
+      double d0 = 0.0, d1 = 0.0;
+#pragma unroll 8
+      for (int s2 = 0; s2 < NB; s2 += 2) {
+        d0 += M[(size_t)s2 * NB] * (double)sR[s2 * RLD + k];
+        d1 += M[(size_t)(s2 + 1) * NB] * (double)sR[(s2 + 1) * RLD + k];
       }
+      sD[q * RLD + k] = (T)(d0 + d1);
     }
     __syncthreads();
     // 4. w += delta on the strip's unknowns
-    for (int e = tid; e < NB * W; e += S::THREADS) {
-      int comp, jr, k, d, q;
-      strip_unknown(e, W, &comp, &jr, &k, &d, &q);
-      const int col = 8 * k + d, cc = col + 4;
-      const int x = (X0 + col) & m, y = (y0 + jr) & m;
-      const T* row = (comp == 0 ? U : (comp == 1 ? V : Pp)) + (jr + 1) * LD + cc;
-      w[comp * n + (size_t)y * N + x] = row[0] + sD[q * RLD + k];
+#pragma unroll
+    for (int i = 0; i < S::UPW; ++i) {
+      if (items[i].pack < 0) continue;
+      w[goff(items[i].pack)] = tile[items[i].toff] + sD[items[i].roff];
     }
-    __syncthreads();  // the tile, the residuals and the corrections are refilled by the next strip
+    __syncthreads();  // the buffer, the residuals and the corrections are reused next
   }
 }
 
@@ -691,7 +770,7 @@ bool launch_strip(Problem& P, bool pdl, T* w, const T* b, T* E, int N, StokesCoe
   const long half = N / 8, strips = half * half / W;
   const int grid = (int)std::min<long>(strips, (long)P.n_sm * occ);
   vlaunch(pdl, kv_boxt<T, TM, W>, grid, Strip<T, TM, W>::THREADS, Strip<T, TM, W>::SMEM, P.stream, w, b, E, N, c,
-          color, slot, Ms, Mf);
+          color, slot, Ms, Mf, P.dev_err, P.wait_limit_ns);
   return true;
 }
 
