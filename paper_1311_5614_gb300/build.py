@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibmg.so")
-SOURCES = ["ib_points.cu", "ib_grid.cu", "ib_krylov.cu", "ib_capi.cu", "ib_static.cu", "ib_vcycle.cu", "ib_unet.cu"]
+SOURCES = ["ib_points.cu", "ib_grid.cu", "ib_krylov.cu", "ib_capi.cu", "ib_static.cu", "ib_vcycle.cu", "ib_unet.cu",
+           "ib_windows.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

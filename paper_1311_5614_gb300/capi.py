@@ -334,11 +334,12 @@ class IBBatch:
     """Independent problems solved together (each on its own stream)."""
 
     def __init__(self, problems, **kw):
+        """kw: parameters for every problem; a list or tuple gives one value per problem."""
         plist = []
-        for p in problems:
+        for k, p in enumerate(problems):
             d = dict(L=p.L, rho=p.rho, mu=p.mu, dt=p.dt, delta=p.delta, box=p.box, nu1=p.nu1, nu2=p.nu2,
                      tol=p.tol, max_iters=p.max_iters, jacobian="clamped" if p.clamped else "exact")
-            d.update(kw)
+            d.update({key: (v[k] if isinstance(v, (list, tuple)) else v) for key, v in kw.items()})
             plist.append(make_params(p.N, **d))
         self.params = plist
         self.sizes = [p.N for p in problems]

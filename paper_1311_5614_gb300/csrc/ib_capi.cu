@@ -74,6 +74,8 @@ int fail(int code, const std::string& msg) {
 
 namespace {
 
+constexpr int MAX_LEVELS_ALLOC = 32;  // per-level device counters
+
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // The elastic block dt S J S^* scales like dt kappa / h^2 against mu / h^2 for
@@ -151,21 +153,32 @@ int check_dev_err(Problem& P) {
   return IB_OK;
 }
 
-// Re-form S, J and everything that depends on them (per step, sec. 8).
+// Re-form S, J and everything that depends on them (per step, sec. 8).  With the
+// assembled elasticity rows (ib_windows.cu): mark the structure boxes and rows of
+// every level and read their counts (one synchronisation), assemble the level-0 rows
+// from the points, check that no coupling fell outside a row's window (a second
+// synchronisation; otherwise this step keeps the point-based path), coarsen the rows
+// level by level, and read the structure-box blocks and the coarsest matrix out of
+// them.
 int setup_hierarchy(Problem& P) {
   IB_TRY(launch_fine_patches(P));
   IB_TRY(launch_spring_force_jacobian(P));
   for (int l = 1; l < P.nlev; ++l) IB_TRY(launch_coarse_patches(P, l));
   if (P.prm.precision == IB_FP32_PRECOND)
     for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_cast_patches(P, l));
-  int ns = P.nlev - 1;  // smoothing levels
+  const int ns = P.nlev - 1;  // smoothing levels
+  const bool win = P.windows && P.np > 0 && P.ns > 0;
   for (int l = 0; l < ns; ++l) {
     IB_TRY(launch_mark_struct(P, l));
-    IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + l, P.count, sizeof(int), cudaMemcpyDeviceToHost,
+    IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + l, P.count, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+  }
+  if (win) {
+    for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_mark_rows(P, l));
+    IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + 32, P.count + 1, sizeof(int) * P.nlev, cudaMemcpyDeviceToHost,
                                 P.stream));
   }
   IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
-  int nB = P.nB;
+  const int nB = P.nB;
   for (int l = 0; l < ns; ++l) {
     LevelInfo& L = P.lev[l];
     int cnt = P.count_host[l];
@@ -178,9 +191,54 @@ int setup_hierarchy(Problem& P) {
       L.cap_struct = cap;
     }
     L.n_struct = cnt;
+  }
+  int max_rows = 0;
+  if (win) {
+    for (int l = 0; l < P.nlev; ++l) {
+      LevelInfo& L = P.lev[l];
+      const int cnt = P.count_host[32 + l];
+      if (cnt > L.cap_rows) {  // new storage: the captured V-cycle takes the new pointers
+        P.graph_dirty[0] = P.graph_dirty[1] = true;
+        dfree(L.Ew64);
+        dfree(L.Ew32);
+        const int cap = cnt + cnt / 4 + 64;
+        IB_TRY(dalloc(&L.Ew64, (size_t)cap * WIN));
+        if (P.has32 || P.prm.precision == IB_FP32_PRECOND) IB_TRY(dalloc(&L.Ew32, (size_t)cap * WIN));
+        L.cap_rows = cap;
+      }
+      L.n_rows = cnt;
+      max_rows = std::max(max_rows, cnt);
+    }
+    if (max_rows > P.cap_twin) {
+      dfree(P.Twin);
+      P.cap_twin = max_rows + max_rows / 4 + 64;
+      IB_TRY(dalloc(&P.Twin, (size_t)P.cap_twin * TWIN));
+    }
+  }
+  for (int l = 0; l < ns; ++l) {
     if (!P.free_ready) IB_TRY(launch_free_box(P, l));
     IB_TRY(launch_struct_fill(P, l));
-    IB_TRY(launch_assemble_struct(P, l));
+  }
+  bool use_win = false;
+  if (win) {
+    IB_TRY(launch_window_points(P));
+    IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + 64, P.dev_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    use_win = (P.count_host[64] & DEV_ERR_WINDOW) == 0;
+    if (!use_win) {  // a coupling outside a window: this step keeps the point path
+      P.count_host[64] &= ~DEV_ERR_WINDOW;
+      IB_CUDA_TRY(cudaMemcpyAsync(P.dev_err, &P.count_host[64], sizeof(int), cudaMemcpyHostToDevice, P.stream));
+      IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    }
+  }
+  if (use_win != P.win_step) P.graph_dirty[0] = P.graph_dirty[1] = true;
+  P.win_step = use_win;
+  if (use_win) {
+    for (int l = 1; l < P.nlev; ++l) IB_TRY(launch_window_galerkin(P, l));
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_struct_from_windows(P, l));
+    for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_window_cast(P, l));
+  } else {
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_assemble_struct(P, l));
   }
   bool all_done = false;
   IB_TRY(launch_invert_struct_all(P, &all_done));
@@ -188,7 +246,8 @@ int setup_hierarchy(Problem& P) {
     for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_struct));
   P.free_ready = true;
   IB_TRY(launch_coarse_fill(P));
-  IB_TRY(launch_assemble_coarse(P));
+  if (use_win) IB_TRY(launch_coarse_from_windows(P));
+  else IB_TRY(launch_assemble_coarse(P));
   IB_TRY(launch_invert(P, P.Mcoarse, P.nc + P.nborder, 1));
   IB_TRY(vcycle_reset_rE(P));
   if (P.nn_sch) IB_TRY(learned_struct_channel(P));
@@ -203,7 +262,9 @@ void free_problem(Problem* P) {
     dfree(L.v64.w); dfree(L.v64.b); dfree(L.v64.r);
     dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);
     dfree(L.rE64); dfree(L.rE32);
+    dfree(L.box_of_slot); dfree(L.rowslot); dfree(L.slot_row); dfree(L.Ew64); dfree(L.Ew32);
   }
+  dfree(P->Twin);
   for (auto& g : P->vgraph) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
@@ -243,8 +304,13 @@ int allocate(Problem& P) {
   for (int l = 0; l < nl; ++l) {
     LevelInfo& L = P.lev[l];
     size_t n3 = 3ul * L.N * L.N;
+    if (P.windows && P.np > 0 && P.ns > 0) {
+      IB_TRY(dalloc(&L.rowslot, 2ul * L.N * L.N));
+      IB_TRY(dalloc(&L.slot_row, 2ul * L.N * L.N));
+    }
     if (l < nl - 1) {
       IB_TRY(dalloc(&L.flag, (size_t)L.nb * L.nb));
+      IB_TRY(dalloc(&L.box_of_slot, (size_t)L.nb * L.nb));
       IB_TRY(dalloc(&L.Sfree, (size_t)P.nB * P.nB));
       IB_TRY(dalloc(&L.Mfree, (size_t)P.nB * P.nB));
       if (P.prm.precision != IB_FP64) IB_TRY(dalloc(&L.Mfree32, (size_t)P.nB * P.nB));
@@ -310,7 +376,7 @@ int allocate(Problem& P) {
   IB_TRY(dalloc(&P.t64, n));
   IB_TRY(dalloc(&P.t64b, n));
   IB_TRY(dalloc(&P.dev_err, 1));
-  IB_TRY(dalloc(&P.count, 1));
+  IB_TRY(dalloc(&P.count, 1 + MAX_LEVELS_ALLOC));
   IB_CUDA_TRY(cudaMemsetAsync(P.dev_err, 0, sizeof(int), P.stream));
   IB_CUDA_TRY(cudaMallocHost((void**)&P.scal_host, 64 * sizeof(double)));
   IB_CUDA_TRY(cudaMallocHost((void**)&P.count_host, 128 * sizeof(int)));
@@ -706,6 +772,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   P.nB = box_nunk(params->box);
   P.sigma = stiffness(*params, n_springs, kappa);
   P.stiff_sigma = stiff_threshold();
+  if (const char* e = std::getenv("IB_WINDOWS")) P.windows = e[0] != '0';
   int Nc = params->box > 4 ? params->box : 4;
   for (int N = params->N; N >= Nc; N /= 2) {
     LevelInfo L;

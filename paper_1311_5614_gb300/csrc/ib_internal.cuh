@@ -37,7 +37,19 @@ int fail(int code, const std::string& msg);
 #define IB_LAUNCH_CHECK() IB_CUDA_TRY(cudaGetLastError())
 
 // Device error flags (bit mask, one word per problem).
-enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_INDEX = 2, DEV_ERR_NONFINITE = 4, DEV_ERR_TIMEOUT = 8 };
+enum : int {
+  DEV_ERR_SINGULAR = 1,
+  DEV_ERR_INDEX = 2,
+  DEV_ERR_NONFINITE = 4,
+  DEV_ERR_TIMEOUT = 8,
+  DEV_ERR_WINDOW = 16  // a coupling outside the assembled rows' windows (not an error: point path)
+};
+
+// Assembled elasticity rows (ib_windows.cu): per structure row, the entries at
+// column offsets |di|, |dj| <= WR for both column components; the Galerkin product
+// keeps E_l P per fine row at coarse offsets |dI|, |dJ| <= TR.
+constexpr int WR = 5, WD = 2 * WR + 1, WSQ = WD * WD, WIN = 2 * WSQ;
+constexpr int TR = 3, TD = 2 * TR + 1, TWIN = 2 * TD * TD;
 
 // ---------------------------------------------------------------- patches
 // Per level and point: for kind (0 spread, 1 interp) and component (0 u, 1 v)
@@ -168,6 +180,14 @@ struct LevelInfo {
   Patches<float> pat32;       // FP32 patches (FP32 V-cycle)
   LevelBuf<double> v64;
   LevelBuf<float> v32;
+  int* box_of_slot = nullptr;  // [cap_struct] box index of each structure slot
+  // assembled elasticity rows: rowslot [2 N^2] (row -> slot or -1), slot_row [2 N^2]
+  // (slot -> row c N^2 + j N + i), windows [cap_rows][WIN] in FP64 and FP32
+  int* rowslot = nullptr;
+  int* slot_row = nullptr;
+  int n_rows = 0, cap_rows = 0;
+  double* Ew64 = nullptr;
+  float* Ew32 = nullptr;
 };
 
 struct ProfRec {
@@ -266,7 +286,11 @@ struct Problem {
   std::vector<int> occ_cgs;   // resident blocks per SM of the fused pass, by basis size
   bool cgs_fused = true;      // middle Gram-Schmidt step as one fused pass
   unsigned long long wait_limit_ns = 1000000000ull;  // bounded device-side waits (IB_WAIT_LIMIT_NS)
-  int* count = nullptr;       // device counter
+  int* count = nullptr;       // device counters: [0] structure boxes, [1 + l] structure rows of level l
+  bool windows = true;        // assembled elasticity rows available (IB_WINDOWS=0: point path only)
+  bool win_step = false;      // this step's hierarchy uses them (no coupling fell outside a window)
+  double* Twin = nullptr;     // Galerkin scratch [cap_twin][TWIN]
+  int cap_twin = 0;
   int* count_host = nullptr;  // pinned
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -316,6 +340,14 @@ int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U);
 int launch_mark_struct(Problem& P, int level);
 
 int launch_assemble_struct(Problem& P, int level);
+int launch_mark_rows(Problem& P, int level);
+int launch_window_points(Problem& P);
+int launch_window_galerkin(Problem& P, int level);
+int launch_struct_from_windows(Problem& P, int level);
+int launch_coarse_from_windows(Problem& P);
+int launch_window_cast(Problem& P, int level);
+template <typename T>
+int launch_window_apply(Problem& P, int level, const T* w, T* y, double coef, int color, bool pdl);
 int launch_assemble_coarse(Problem& P);
 
 // ---------------------------------------------------------------- launchers (grid)

@@ -274,10 +274,16 @@ __global__ void k_mark(Patches<double> pat, int np, int N, int b, int nb, int* f
   }
 }
 
-__global__ void k_assign_slots(int* flag, int nbox, int* count) {
+__global__ void k_assign_slots(int* flag, int nbox, int* count, int* box_of_slot) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nbox) return;
-  flag[t] = flag[t] ? atomicAdd(count, 1) : -1;
+  if (flag[t]) {
+    const int s = atomicAdd(count, 1);
+    flag[t] = s;
+    box_of_slot[s] = t;
+  } else {
+    flag[t] = -1;
+  }
 }
 
 // Add coef * (S_l J S^*_l) restricted to box rows/cols to the dense box blocks.
@@ -454,6 +460,9 @@ Patches<float> patches_of<float>(LevelInfo& L) { return L.pat32; }
 template <typename T>
 int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U) {
   if (P.np == 0 || P.ns == 0) return IB_OK;
+  // the assembled rows when this step has them (one gather per row, no atomics)
+  if (P.win_step && (sizeof(T) == 8 || P.lev[level].Ew32))
+    return launch_window_apply<T>(P, level, w, y, coef, -1, false);
   LevelInfo& L = P.lev[level];
   Patches<T> pat = patches_of<T>(L);
   const double sT = sizeof(T);
@@ -487,7 +496,7 @@ int launch_mark_struct(Problem& P, int level) {
     IB_LAUNCH_CHECK();
   }
   KScope ks(P, IB_KC_SETUP, nbox * 8.0);
-  k_assign_slots<<<nblk(nbox), TPB, 0, P.stream>>>(L.flag, nbox, P.count);
+  k_assign_slots<<<nblk(nbox), TPB, 0, P.stream>>>(L.flag, nbox, P.count, L.box_of_slot);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }

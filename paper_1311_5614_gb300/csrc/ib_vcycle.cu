@@ -136,6 +136,13 @@ template <>
 const float* Mfree_of<float>(const LevelInfo& L) { return L.Mfree32; }
 
 template <typename T>
+const T* Ewin_of(const LevelInfo& L);
+template <>
+const double* Ewin_of<double>(const LevelInfo& L) { return L.Ew64; }
+template <>
+const float* Ewin_of<float>(const LevelInfo& L) { return L.Ew32; }
+
+template <typename T>
 Springs<T> sview(Problem& P) {
   Springs<T> s;
   s.np = P.np;
@@ -978,6 +985,21 @@ struct TailCtx<true> {
 
 // rE = -dt E_l w of a tail level, all rows, into the velocity part of r: clear,
 // then force + spread per point quad with atomic additions.
+// One structure row of the assembled elasticity (window slot t) applied to w: the
+// row index and sum_e Ew[t][e] w[column of e].
+template <typename T, typename TM>
+__device__ __forceinline__ T window_row(const TailLevel<T, TM>& L, const T* w, int t, int* row) {
+  const int N = L.N, n = N * N, r = L.wrow[t], c = r / n, rr = r - c * n, i = rr % N, j = rr / N;
+  *row = r;
+  const T* e0 = L.Ew + (size_t)t * WIN;
+  T acc = 0;
+  for (int e = 0; e < WIN; ++e) {
+    const int cc = e / WSQ, rem = e - cc * WSQ;
+    acc += e0[e] * w[cc * n + wrapi(j + rem / WD - WR, N) * N + wrapi(i + rem % WD - WR, N)];
+  }
+  return acc;
+}
+
 template <typename T, typename TM, bool CL>
 __device__ void tail_elastic(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, T* r) {
   using C = TailCtx<CL>;
@@ -985,6 +1007,16 @@ __device__ void tail_elastic(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A
   const int n2 = 2 * L.N * L.N, np = A.sp.np, lane = threadIdx.x & 31;
   for (int e = tid; e < n2; e += nt) r[e] = (T)0;
   C::sync();
+  if (L.Ew) {  // assembled rows: one row per thread, each written once
+    const int nr = *L.wn;
+    for (int t = tid; t < nr; t += nt) {
+      int row;
+      const T v = window_row(L, w, t, &row);
+      r[row] = A.coefE * v;
+    }
+    C::sync();
+    return;
+  }
   // 4 np is a multiple of 4: the four lanes of a quad run the same iterations
   for (int t = tid; t < 4 * np; t += nt)
     force_spread_quad<T, false>(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box,
@@ -1087,6 +1119,18 @@ template <typename T, typename TM>
 __device__ void ctail_spread(const TailLevel<T, TM>& L, const TailArgs<T, TM>& A, const T* w, int color, T* re) {
   using C = TailCtx<true>;
   const int tid = C::id(), nt = C::n(), np = A.sp.np, lane = threadIdx.x & 31;
+  if (L.Ew) {  // assembled rows of the colour (re is zero there: one writer per row)
+    const int nr = *L.wn, N = L.N, n = N * N;
+    for (int t = tid; t < nr; t += nt) {
+      const int r = L.wrow[t], c = r / n, rr = r - c * n;
+      if (!row_in_color(c, rr % N, rr / N, A.box, color)) continue;
+      int row;
+      const T v = window_row(L, w, t, &row);
+      re[row] += A.coefE * v;
+    }
+    C::sync();
+    return;
+  }
   for (int t = tid; t < 4 * np; t += nt)
     force_spread_quad<T, false>(L.pat, A.sp, w, L.N, A.coefE, t >> 2, t & 3, 0xFu << (lane & ~3), lane & ~3, A.box,
                                 color, re);
@@ -1301,6 +1345,9 @@ int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes, 
     t.slot = L.flag;
     t.Ms = L.Mstruct;
     t.Mf = Mfree_of<TM>(L);
+    t.wrow = P.win_step ? L.slot_row : nullptr;
+    t.wn = P.win_step ? P.count + 1 + l : nullptr;
+    t.Ew = P.win_step ? Ewin_of<T>(L) : nullptr;
     size_t n3 = 3ul * L.N * L.N * sizeof(T);
     A->off_w[q] = (int)take(n3);
     A->off_b[q] = (int)take(n3);
@@ -1348,6 +1395,8 @@ int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes, 
 template <typename T>
 int fine_elastic(Problem& P, int l, const T* w, int color) {
   LevelInfo& L = P.lev[l];
+  if (P.win_step)  // assembled rows: one gather per structure row of the colour
+    return launch_window_apply<T>(P, l, w, rEbuf<T>(L), -P.prm.dt / (P.lev[0].h * P.lev[0].h), color, use_pdl(P));
   const double sT = sizeof(T);
   double deg = P.np ? 2.0 * P.ns / P.np : 0.0;
   // algorithmic bytes per point (the re-interpolation of neighbours is redundant

@@ -19,6 +19,10 @@ struct TailLevel {
   const int* slot;  // box -> structure slot (-1 free)
   const double* Ms; // structure-box inverses (FP64)
   const TM* Mf;     // shared inverse of the structure-free boxes
+  // assembled elasticity rows of the level (NULL Ew: the point path)
+  const int* wrow;  // slot -> row
+  const int* wn;    // row count (device)
+  const T* Ew;      // windows [rows][WIN]
 };
 
 template <typename T, typename TM = T>

@@ -87,13 +87,15 @@ def test_multi_ellipse_1024_apply_and_step(pkg):
 
 
 def test_full_batch_256(pkg):
-    """All 256 problems of the batched workload (seed 5614, restart 30): every
-    problem either meets the tolerance (checked against the oracle on a seeded
-    sample) or reports IB_ERR_NOT_CONVERGED at the iteration cap."""
+    """All 256 problems of the batched workload (seed 5614; FGMRES restarted every 30
+    iterations, unrestarted for stiffness ratios dt kappa / mu >= 3000): every problem
+    meets the FP64 tolerance 1e-8, and a seeded sample matches the oracle."""
+    import bench
+
     probs = W.batch(count=256, seed=5614)
     for p in probs:
         p.box = 4
-    B = pkg.IBBatch(probs, precision="fp32", max_iters=200, restart=30)
+    B = pkg.IBBatch(probs, precision="fp32", max_iters=200, restart=bench.batch_restarts(probs))
     sizes = [3 * p.N * p.N for p in probs]
     up = torch.zeros(sum(sizes), dtype=torch.float64, device="cuda")
     X = dev(np.concatenate([p.X for p in probs]))
@@ -102,17 +104,11 @@ def test_full_batch_256(pkg):
     upc, Xc = up.cpu().numpy(), X.cpu().numpy()
     off = np.concatenate([[0], np.cumsum(sizes)])
     xoff = np.concatenate([[0], np.cumsum([p.n_points for p in probs])])
-    ok = [st["status"] == 0 for st in stats]
     for st in stats:
-        assert st["status"] in (0, 4), st
-        assert np.isfinite(st["rel_res_true"])
-        if st["status"] == 0:
-            assert st["rel_res_true"] <= 1e-8
-        else:
-            assert st["iters"] == 200
-    assert sum(ok) >= 250
+        assert st["status"] == 0 and st["rel_res_true"] <= 1e-8, st
     rng = np.random.default_rng(3)
-    sample = [k for k in rng.permutation(256) if ok[k]][:4]
+    stiff = [k for k, p in enumerate(probs) if p.dt * p.kappa.max() / p.mu >= 3000 and p.N <= 256]
+    sample = [int(k) for k in rng.permutation(256)[:4]] + stiff[:1]
     for k in sample:
         p = probs[k]
         A, Ss = fine_operator(p)

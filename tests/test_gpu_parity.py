@@ -324,7 +324,8 @@ def test_full_size_256_apply_and_fp32_solve(pkg):
 # 4 x 4 boxes with the strip kernel (a strip of W boxes of one colour per CTA
 # iteration, staged tile, register-blocked free-box product).  IB_BOX_STRIP_MIN=1
 # lets it run on every level it fits and IB_BOX_STRIP_W pins the width, so each
-# width is compared with the oracle; IB_BOX_STRIP=0 turns it off.
+# width is compared with the oracle, with one strip per box row (N_l = 8 W) and with
+# several (the staged rows then wrap only at the row ends); IB_BOX_STRIP=0 turns it off.
 
 def _strip_case(N):
     if N == 64:
@@ -336,7 +337,8 @@ def _strip_case(N):
 
 @pytest.mark.parametrize("N,width,prec", [(64, 8, "fp64"), (64, 8, "fp32"), (64, 8, "mixed"),
                                           (128, 16, "fp64"), (128, 16, "mixed"),
-                                          (256, 32, "fp64"), (256, 32, "fp32"), (256, 8, "fp32")])
+                                          (256, 32, "fp64"), (256, 32, "fp32"), (256, 8, "fp32"),
+                                          (256, 16, "mixed"), (512, 32, "fp64"), (512, 32, "fp32")])
 def test_vcycle_strip_kernel(pkg, N, width, prec, monkeypatch):
     monkeypatch.setenv("IB_BOX_STRIP_MIN", "1")
     monkeypatch.setenv("IB_BOX_STRIP_W", str(width))
@@ -363,3 +365,38 @@ def test_vcycle_strip_kernel(pkg, N, width, prec, monkeypatch):
 def test_solve_step_strip_kernel(pkg, prec, monkeypatch):
     monkeypatch.setenv("IB_BOX_STRIP_MIN", "1")
     test_solve_step(pkg, "c1_64", 4, prec)
+
+
+# ---------------------------------------------------------------- assembled elasticity rows
+# By default every level's elasticity block is kept as assembled rows (level 0 from
+# the points, coarse levels by Galerkin products of them), which the operator apply
+# and the V-cycle gather from.  IB_WINDOWS=0 keeps the point-based path (patches,
+# atomics); a spring too long for a row's window makes a step fall back to it.
+
+@pytest.mark.parametrize("name", ["c1_64", "stiff_32_exact", "offcentre_16"])
+def test_point_path_apply_and_vcycle(pkg, name, monkeypatch):
+    monkeypatch.setenv("IB_WINDOWS", "0")
+    test_apply_every_level_fp64(pkg, name)
+    test_vcycle_fp64(pkg, name, 4 if name != "offcentre_16" else 2)
+
+
+def test_long_spring_falls_back_to_point_path(pkg):
+    """A spring spanning about 2.5 cells: its coupling leaves the level-0 windows,
+    so the step uses the point path; operator and V-cycle still match the oracle."""
+    p = W.single_ellipse(N=32, n_points=24, kappa=1e3, dt=1e-2)
+    p.box = 2
+    assert np.abs(np.diff(p.X, axis=0)).max() > 1.6 * p.h
+    levels, _ = O.build_hierarchy(p)
+    s = pkg.IBSolver.from_problem(p)
+    rng = np.random.default_rng(4)
+    for li, lev in enumerate(levels):
+        w = rng.standard_normal(3 * lev.N * lev.N)
+        y = torch.zeros(3 * lev.N * lev.N, dtype=torch.float64, device="cuda")
+        s.apply(li, dev(w), y)
+        assert rel_elementwise(y.cpu().numpy(), lev.A @ w) < 1e-10, li
+    rhs = O.rhs_vector(p)
+    ref = _oracle_vcycle(p, rhs)
+    z = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(rhs), z)
+    assert rel_elementwise(z.cpu().numpy(), ref) < 1e-10
+    s.close()
