@@ -282,6 +282,13 @@ IB_API int ib_set_learned_stage(ib_problem* prob, ib_unet* net);
  * in4 [4][N][N] and the scaled error (as the network's output is defined) to target
  * [3][N][N].  x: device 3N^2 doubles. */
 IB_API int ib_learned_pair(ib_problem* prob, const double* x, float* in4, float* target);
+/* One step of multigrid as a stand-alone solver (sec. 5) on an error: with e = x* - x_k
+ * (device, 3N^2 doubles, updated in place to e - MG(A e) = x* - x_{k+1}) writes the
+ * pair of ib_learned_pair for x = e, i.e. the network input for the residual
+ * r_{k+1} = A e_{k+1} left after the V-cycle and the scaled error e_{k+1}.  Repeated
+ * from e = x* (x_0 = 0) it yields the residual -> error pairs the method produces
+ * while it solves. */
+IB_API int ib_learned_chain(ib_problem* prob, double* e, float* in4, float* target);
 
 /* Kernel classes for launch counting and event timing. */
 enum {

@@ -100,6 +100,7 @@ _SIGS = {
     "ib_unet_destroy": (None, [_P]),
     "ib_set_learned_stage": (ctypes.c_int, [_P, _P]),
     "ib_learned_pair": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ib_learned_chain": (ctypes.c_int, [_P, _P, _P, _P]),
     "ib_destroy": (None, [_P]),
     "ib_last_error": (ctypes.c_char_p, []),
     "ib_version": (ctypes.c_char_p, []),
@@ -500,6 +501,11 @@ class IBSolver:
         n = self.N * self.N
         _check(lib().ib_learned_pair(self.handle, _dev_ptr(x, 3 * n, "x"), _f32_ptr(in4, 4 * n, "in4"),
                                      _f32_ptr(target, 3 * n, "target")))
+
+    def learned_chain(self, e, in4, target):
+        n = self.N * self.N
+        _check(lib().ib_learned_chain(self.handle, _dev_ptr(e, 3 * n, "e"), _f32_ptr(in4, 4 * n, "in4"),
+                                      _f32_ptr(target, 3 * n, "target")))
 
     def launch_count(self, kclass=-1):
         return ib_launch_count(self.handle, kclass)

@@ -983,6 +983,18 @@ int ib_set_learned_stage(ib_problem* H, ib_unet* net) {
   return IB_OK;
 }
 
+int ib_learned_chain(ib_problem* H, double* e, float* in4, float* target) {
+  g_err.clear();
+  if (!H || !e || !in4 || !target) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  IB_TRY(ib_learned_pair(H, e, in4, target));
+  Problem& P = H->P;
+  const size_t n = 3ul * P.prm.N * P.prm.N;
+  // ib_learned_pair left e - MG(A e) in nn_dz
+  IB_CUDA_TRY(cudaMemcpyAsync(e, P.nn_dz, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return IB_OK;
+}
+
 int ib_learned_pair(ib_problem* H, const double* x, float* in4, float* target) {
   g_err.clear();
   if (!H || !x || !in4 || !target) return fail(IB_ERR_INVALID_ARG, "NULL argument");

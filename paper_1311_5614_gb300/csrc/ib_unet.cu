@@ -15,6 +15,7 @@
 // Direct convolution on CUDA cores: a CTA computes a 16 x 16 pixel tile for 16
 // output channels, staging an 18 x 18 input halo and the weights in shared memory.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -88,6 +89,7 @@ struct ib_unet {
   double* red = nullptr;      // reductions
   double* red_host = nullptr;
   std::vector<void*> allocs;
+  bool tc = true;  // convolutions on the tensor cores (IB_UNET_TC=0: CUDA cores)
 };
 
 namespace ib {
@@ -169,6 +171,134 @@ __global__ void __launch_bounds__(TILE * TILE) k_conv(const float* __restrict__ 
   (void)Wco;
 }
 
+// ---------------------------------------------------------------- tensor-core convolution
+//
+// The same convolution as an implicit GEMM on the tensor cores (mma.sync
+// m16n8k16, BF16 operands, FP32 accumulation): rows = output channels (MT tiles of
+// 16), columns = pixels, and the reduction runs over blocks of 16 input channels at
+// each tap.  A CTA computes a 16 x 16 pixel tile for all its output channels; warp w
+// takes pixel rows 2w and 2w + 1 (four column tiles of 8 pixels).  Each block of 16
+// input channels is staged with its one-pixel halo in two planes of 8 channels
+// ([pixel][8], 16 bytes per pixel), so the 32 lanes of a fragment load read 32
+// consecutive words; the weights likewise ([tap][plane][co][8]).  The FP32
+// activations enter as two BF16 terms, hi = bf16(v) and lo = bf16(v - hi), and both
+// are multiplied by the BF16 weight (two products per fragment), so the result is the
+// BF16-weight convolution of the FP32 activations to about 2^-16 relative, as the
+// CUDA-core kernel computes it.
+__device__ __forceinline__ void mma_bf16_16816(float* d, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int K, int MT>
+struct ConvTC {
+  static constexpr int HALO = TILE + 2, HP = HALO * HALO;  // staged pixels (18 x 18)
+  static constexpr int COP = MT * 16;                      // output channels (padded)
+  // shared memory: input hi / lo [2 planes][HP][8] bf16, weights [K*K][2 planes][COP][8] bf16
+  static constexpr size_t IN_BYTES = 2ul * HP * 8 * 2;
+  static constexpr size_t W_BYTES = (size_t)K * K * 2 * COP * 8 * 2;
+  static constexpr size_t SMEM = 2 * IN_BYTES + W_BYTES;
+};
+
+template <int K, int MT>
+__global__ void __launch_bounds__(TILE * TILE) k_conv_tc(const float* __restrict__ in, int Ci,
+                                                         const __nv_bfloat16* __restrict__ Wt,
+                                                         const float* __restrict__ bias, float* __restrict__ out,
+                                                         int Co, int out_cstride_off, float* __restrict__ pre, int H,
+                                                         int act, int mode, int Wci, int accumulate) {
+  using S = ConvTC<K, MT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* s_hi = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* s_lo = reinterpret_cast<__nv_bfloat16*>(smem + S::IN_BYTES);
+  __nv_bfloat16* s_w = reinterpret_cast<__nv_bfloat16*>(smem + 2 * S::IN_BYTES);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  const int HW = H * H, m = H - 1, R = K / 2, KK = K * K;
+  float acc[MT][4][4];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  for (int ci0 = 0; ci0 < Ci; ci0 += 16) {
+    // input block: pixel fastest across threads (coalesced), split into hi / lo
+    for (int e = tid; e < 16 * S::HP; e += TILE * TILE) {
+      const int c = e / S::HP, px = e - c * S::HP;
+      const int yy = px / S::HALO, xx = px - yy * S::HALO;
+      const int gy = (y0 + yy - 1) & m, gx = (x0 + xx - 1) & m;
+      const float v = (ci0 + c < Ci) ? in[(size_t)(ci0 + c) * HW + gy * H + gx] : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      const int o = ((c >> 3) * S::HP + px) * 8 + (c & 7);
+      s_hi[o] = hi;
+      s_lo[o] = lo;
+    }
+    // weights of this block (mode 1: the transposed, flipped kernel of the data gradient)
+    for (int e = tid; e < KK * 16 * S::COP; e += TILE * TILE) {
+      const int tap = e / (16 * S::COP), r = e - tap * 16 * S::COP;
+      const int co = r >> 4, c = r & 15;
+      const int gco = co, gci = ci0 + c;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (gco < Co && gci < Ci) {
+        v = (mode == 0) ? Wt[((size_t)gco * Wci + gci) * KK + tap] : Wt[((size_t)gci * Wci + gco) * KK + (KK - 1 - tap)];
+      }
+      s_w[((tap * 2 + (c >> 3)) * S::COP + co) * 8 + (c & 7)] = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int tap = 0; tap < KK; ++tap) {
+      const int dy = tap / K - R + 1, dx = tap % K - R + 1;  // halo offsets of the tap
+      unsigned bh[4][2], bl[4][2];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int y = 2 * wp + (nt >> 1), x = (nt & 1) * 8 + gid;
+        const int px = (y + dy) * S::HALO + (x + dx);
+        bh[nt][0] = *reinterpret_cast<const unsigned*>(s_hi + (size_t)px * 8 + 2 * tig);
+        bh[nt][1] = *reinterpret_cast<const unsigned*>(s_hi + (size_t)(S::HP + px) * 8 + 2 * tig);
+        bl[nt][0] = *reinterpret_cast<const unsigned*>(s_lo + (size_t)px * 8 + 2 * tig);
+        bl[nt][1] = *reinterpret_cast<const unsigned*>(s_lo + (size_t)(S::HP + px) * 8 + 2 * tig);
+      }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const __nv_bfloat16* w0 = s_w + ((size_t)(tap * 2 + 0) * S::COP + mt * 16) * 8;
+        const __nv_bfloat16* w1 = s_w + ((size_t)(tap * 2 + 1) * S::COP + mt * 16) * 8;
+        unsigned a[4];
+        a[0] = *reinterpret_cast<const unsigned*>(w0 + gid * 8 + 2 * tig);
+        a[1] = *reinterpret_cast<const unsigned*>(w0 + (gid + 8) * 8 + 2 * tig);
+        a[2] = *reinterpret_cast<const unsigned*>(w1 + gid * 8 + 2 * tig);
+        a[3] = *reinterpret_cast<const unsigned*>(w1 + (gid + 8) * 8 + 2 * tig);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          mma_bf16_16816(acc[mt][nt], a, bh[nt]);
+          mma_bf16_16816(acc[mt][nt], a, bl[nt]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int co = mt * 16 + gid + (q >> 1) * 8;
+        if (co >= Co) continue;
+        const int y = 2 * wp + (nt >> 1), x = (nt & 1) * 8 + 2 * tig + (q & 1);
+        const int p = (y0 + y) * H + x0 + x;
+        float v = acc[mt][nt][q] + (bias ? bias[co] : 0.f);
+        const size_t o = (size_t)(co + out_cstride_off) * HW + p;
+        if (pre) pre[(size_t)co * HW + p] = v;
+        if (act) v = gelu_f(v);
+        if (accumulate) out[o] += v;
+        else out[o] = v;
+      }
+}
+
 // dW[co][ci][tap] += sum_p g[co][p] in[ci][p + off(tap)] over a chunk of tiles.
 template <int K>
 __global__ void __launch_bounds__(TILE * TILE) k_conv_wgrad(const float* __restrict__ in, int Ci, const float* __restrict__ g,
@@ -218,6 +348,123 @@ __global__ void __launch_bounds__(TILE * TILE) k_conv_wgrad(const float* __restr
     const int co = e / (CIT * K * K), r = e % (CIT * K * K);
     const int ci = r / (K * K), tap = r % (K * K);
     if (co0 + co < Co && ci0 + ci < Ci) atomicAdd(&dW[((size_t)(co0 + co) * Ci + ci0 + ci) * K * K + tap], acc[q]);
+  }
+}
+
+// Weight gradient on the tensor cores: for each tap, dW[co][ci] += sum_p g[co][p]
+// in[ci][p + off(tap)], a product with rows = output channels (MT tiles of 16),
+// columns = 16 input channels (two tiles of 8) and the reduction over pixels (one
+// row of 16 pixels per mma).  A CTA owns all output channels and one block of 16
+// input channels and sweeps a chunk of 16 x 16 pixel tiles; warp w takes the
+// (tap, column tile) pairs w, w + 8, w + 16.  Both operands are FP32 and enter as
+// hi + lo BF16 pairs; hi*hi + hi*lo + lo*hi keeps the products to about 2^-16.
+// Shared memory: g [co][256 + 8] and the input halo [16][18 * 18 + 4], hi and lo.
+template <int K, int MT>
+struct WgradTC {
+  static constexpr int COP = MT * 16;
+  static constexpr int LDA = TILE * TILE + 8;          // 264: rows of g 4 banks apart
+  static constexpr int LDB = (TILE + 2) * (TILE + 2) + 4;  // 328: input channels 4 banks apart
+  static constexpr int PAIRS = K * K * 2;
+  static constexpr int PPW = (PAIRS + 7) / 8;          // pairs per warp
+  static constexpr size_t A_BYTES = (size_t)COP * LDA * 2;
+  static constexpr size_t B_BYTES = (size_t)16 * LDB * 2;
+  static constexpr size_t SMEM = 2 * A_BYTES + 2 * B_BYTES;
+};
+
+__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo_k, __nv_bfloat16 hi_k) {
+  return (unsigned)__bfloat16_as_ushort(lo_k) | ((unsigned)__bfloat16_as_ushort(hi_k) << 16);
+}
+
+template <int K, int MT>
+__global__ void __launch_bounds__(TILE * TILE) k_conv_wgrad_tc(const float* __restrict__ in, int Ci,
+                                                               const float* __restrict__ g, int Co, int H,
+                                                               float* __restrict__ dW, int tiles_per_block) {
+  using S = WgradTC<K, MT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* a_hi = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* a_lo = reinterpret_cast<__nv_bfloat16*>(smem + S::A_BYTES);
+  __nv_bfloat16* b_hi = reinterpret_cast<__nv_bfloat16*>(smem + 2 * S::A_BYTES);
+  __nv_bfloat16* b_lo = reinterpret_cast<__nv_bfloat16*>(smem + 2 * S::A_BYTES + S::B_BYTES);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  const int ci0 = blockIdx.y * 16;
+  const int HW = H * H, m = H - 1, tpr = H / TILE, ntiles = tpr * tpr, R = K / 2, KK = K * K;
+  constexpr int HALO = TILE + 2;
+  float acc[MT][S::PPW][4];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int b = 0; b < S::PPW; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const int t_end = min(ntiles, (blockIdx.x + 1) * tiles_per_block);
+  for (int t = blockIdx.x * tiles_per_block; t < t_end; ++t) {
+    const int x0 = (t % tpr) * TILE, y0 = (t / tpr) * TILE;
+    for (int e = tid; e < S::COP * TILE * TILE; e += TILE * TILE) {
+      const int co = e >> 8, px = e & 255;
+      const float v = co < Co ? g[(size_t)co * HW + (y0 + (px >> 4)) * H + x0 + (px & 15)] : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      a_hi[co * S::LDA + px] = hi;
+      a_lo[co * S::LDA + px] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+    for (int e = tid; e < 16 * HALO * HALO; e += TILE * TILE) {
+      const int c = e / (HALO * HALO), px = e - c * HALO * HALO;
+      const int yy = px / HALO, xx = px - yy * HALO;
+      const float v = (ci0 + c < Ci) ? in[(size_t)(ci0 + c) * HW + ((y0 + yy - 1) & m) * H + ((x0 + xx - 1) & m)] : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      b_hi[c * S::LDB + px] = hi;
+      b_lo[c * S::LDB + px] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int y = 0; y < TILE; ++y) {  // reduction step: pixel row y (16 pixels)
+      unsigned ah[MT][4], al[MT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int r0 = (mt * 16 + gid) * S::LDA + y * TILE + 2 * tig, r1 = r0 + 8 * S::LDA;
+        ah[mt][0] = *reinterpret_cast<const unsigned*>(a_hi + r0);
+        ah[mt][1] = *reinterpret_cast<const unsigned*>(a_hi + r1);
+        ah[mt][2] = *reinterpret_cast<const unsigned*>(a_hi + r0 + 8);
+        ah[mt][3] = *reinterpret_cast<const unsigned*>(a_hi + r1 + 8);
+        al[mt][0] = *reinterpret_cast<const unsigned*>(a_lo + r0);
+        al[mt][1] = *reinterpret_cast<const unsigned*>(a_lo + r1);
+        al[mt][2] = *reinterpret_cast<const unsigned*>(a_lo + r0 + 8);
+        al[mt][3] = *reinterpret_cast<const unsigned*>(a_lo + r1 + 8);
+      }
+#pragma unroll
+      for (int q = 0; q < S::PPW; ++q) {
+        const int pair = wp + 8 * q;
+        if (pair >= S::PAIRS) break;
+        const int tap = pair >> 1, nt = pair & 1;
+        const int dy = tap / K - R + 1, dx = tap % K - R + 1;
+        // column gid of the tile: input channel nt * 8 + gid; rows: pixels x = 2 tig (+1), (+8)
+        const int base = (nt * 8 + gid) * S::LDB + (y + dy) * HALO + dx + 2 * tig;
+        unsigned bh[2], bl[2];
+        bh[0] = pack_bf16(b_hi[base], b_hi[base + 1]);
+        bh[1] = pack_bf16(b_hi[base + 8], b_hi[base + 9]);
+        bl[0] = pack_bf16(b_lo[base], b_lo[base + 1]);
+        bl[1] = pack_bf16(b_lo[base + 8], b_lo[base + 9]);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          mma_bf16_16816(acc[mt][q], ah[mt], bh);
+          mma_bf16_16816(acc[mt][q], ah[mt], bl);
+          mma_bf16_16816(acc[mt][q], al[mt], bh);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < S::PPW; ++q) {
+    const int pair = wp + 8 * q;
+    if (pair >= S::PAIRS) break;
+    const int tap = pair >> 1, nt = pair & 1;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int co = mt * 16 + gid + (r >> 1) * 8, ci = ci0 + nt * 8 + 2 * tig + (r & 1);
+        if (co < Co && ci < Ci) atomicAdd(&dW[((size_t)co * Ci + ci) * KK + tap], acc[mt][q][r]);
+      }
   }
 }
 
@@ -393,10 +640,71 @@ int ualloc_t(ib_unet* U, T** p, size_t count) {
   return ualloc(U, (void**)p, count * sizeof(T));
 }
 
+// Tensor-core launch of one convolution: MT tiles of 16 output channels (Co <= 96).
+template <int K, int MT>
+int conv_tc_launch(cudaStream_t st, int H, const float* in, int Ci, const __nv_bfloat16* Wt, const float* bias,
+                   float* out, int Co, int off, float* pre, int act, int mode, int Wci, int accumulate) {
+  static bool ready = false;  // raise the dynamic shared-memory limit once per instantiation
+  if (!ready) {
+    IB_CUDA_TRY(cudaFuncSetAttribute(k_conv_tc<K, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ConvTC<K, MT>::SMEM));
+    ready = true;
+  }
+  dim3 grid(H / TILE, H / TILE);
+  k_conv_tc<K, MT><<<grid, TILE * TILE, ConvTC<K, MT>::SMEM, st>>>(in, Ci, Wt, bias, out, Co, off, pre, H, act, mode,
+                                                                   Wci, accumulate);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+template <int K>
+int conv_tc(cudaStream_t st, int H, const float* in, int Ci, const __nv_bfloat16* Wt, const float* bias, float* out,
+            int Co, int off, float* pre, int act, int mode, int Wci, int accumulate) {
+  switch ((Co + 15) / 16) {
+    case 1: return conv_tc_launch<K, 1>(st, H, in, Ci, Wt, bias, out, Co, off, pre, act, mode, Wci, accumulate);
+    case 2: return conv_tc_launch<K, 2>(st, H, in, Ci, Wt, bias, out, Co, off, pre, act, mode, Wci, accumulate);
+    case 3: return conv_tc_launch<K, 3>(st, H, in, Ci, Wt, bias, out, Co, off, pre, act, mode, Wci, accumulate);
+    case 4: return conv_tc_launch<K, 4>(st, H, in, Ci, Wt, bias, out, Co, off, pre, act, mode, Wci, accumulate);
+    case 6: return conv_tc_launch<K, 6>(st, H, in, Ci, Wt, bias, out, Co, off, pre, act, mode, Wci, accumulate);
+    default: return fail(IB_ERR_INVALID_ARG, "convolution channel count not supported on the tensor-core path");
+  }
+}
+
+template <int K, int MT>
+int wgrad_tc_launch(cudaStream_t st, dim3 grid, const float* in, int Ci, const float* g, int Co, int H, float* dW,
+                    int tpb) {
+  static bool ready = false;
+  if (!ready) {
+    IB_CUDA_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<K, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)WgradTC<K, MT>::SMEM));
+    ready = true;
+  }
+  k_conv_wgrad_tc<K, MT><<<grid, TILE * TILE, WgradTC<K, MT>::SMEM, st>>>(in, Ci, g, Co, H, dW, tpb);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+template <int K>
+int wgrad_tc(cudaStream_t st, dim3 grid, const float* in, int Ci, const float* g, int Co, int H, float* dW, int tpb) {
+  switch ((Co + 15) / 16) {
+    case 1: return wgrad_tc_launch<K, 1>(st, grid, in, Ci, g, Co, H, dW, tpb);
+    case 2: return wgrad_tc_launch<K, 2>(st, grid, in, Ci, g, Co, H, dW, tpb);
+    case 4: return wgrad_tc_launch<K, 4>(st, grid, in, Ci, g, Co, H, dW, tpb);
+    default: return fail(IB_ERR_INVALID_ARG, "weight-gradient channel count not supported on the tensor-core path");
+  }
+}
+
 int conv_fwd(ib_unet* U, int li, const float* in, float* out, int out_off, bool keep_pre) {
   const UConv& c = U->L[li];
   dim3 grid(c.H / TILE, c.H / TILE, (c.co + COT - 1) / COT);
   float* pre = keep_pre ? U->pre[li] : nullptr;
+  if (U->tc) {
+    if (c.k == 3)
+      return conv_tc<3>(U->stream, c.H, in, c.ci, U->wb + c.w_off, U->w + c.b_off, out, c.co, out_off, pre, c.act, 0,
+                        c.ci, 0);
+    return conv_tc<1>(U->stream, c.H, in, c.ci, U->wb + c.w_off, U->w + c.b_off, out, c.co, out_off, pre, c.act, 0,
+                      c.ci, 0);
+  }
   if (c.k == 3)
     k_conv<3><<<grid, TILE * TILE, 0, U->stream>>>(in, c.ci, U->wb + c.w_off, U->w + c.b_off, out, c.co, out_off, pre,
                                                    c.H, c.act, 0, c.co, c.ci, 0);
@@ -420,13 +728,22 @@ int conv_bwd(ib_unet* U, int li, const float* in, float* g_out, float* g_in) {
   const int ntiles = (c.H / TILE) * (c.H / TILE);
   const int tpb = ntiles >= 64 ? 16 : 1;
   dim3 gw((ntiles + tpb - 1) / tpb, (c.co + COT - 1) / COT, (c.ci + CIT - 1) / CIT);
-  if (c.k == 3)
+  if (U->tc) {
+    const dim3 gt((ntiles + tpb - 1) / tpb, (c.ci + 15) / 16);
+    if (c.k == 3) IB_TRY(wgrad_tc<3>(U->stream, gt, in, c.ci, g_out, c.co, c.H, U->g + c.w_off, tpb));
+    else IB_TRY(wgrad_tc<1>(U->stream, gt, in, c.ci, g_out, c.co, c.H, U->g + c.w_off, tpb));
+  } else if (c.k == 3)
     k_conv_wgrad<3><<<gw, TILE * TILE, 0, U->stream>>>(in, c.ci, g_out, c.co, c.H, U->g + c.w_off, tpb);
   else
     k_conv_wgrad<1><<<gw, TILE * TILE, 0, U->stream>>>(in, c.ci, g_out, c.co, c.H, U->g + c.w_off, tpb);
   IB_LAUNCH_CHECK();
   k_bias_grad<<<c.co, 256, 0, U->stream>>>(g_out, (int)HW, U->g + c.b_off);
   IB_LAUNCH_CHECK();
+  if (g_in && U->tc) {
+    if (c.k == 3) return conv_tc<3>(U->stream, c.H, g_out, c.co, U->wb + c.w_off, nullptr, g_in, c.ci, 0, nullptr, 0, 1,
+                                    c.ci, 1);
+    return conv_tc<1>(U->stream, c.H, g_out, c.co, U->wb + c.w_off, nullptr, g_in, c.ci, 0, nullptr, 0, 1, c.ci, 1);
+  }
   if (g_in) {
     dim3 grid(c.H / TILE, c.H / TILE, (c.ci + COT - 1) / COT);
     if (c.k == 3)
@@ -616,6 +933,7 @@ int ib_unet_create(int32_t N, const float* params, void* stream, ib_unet** out) 
   if (!U) return fail(IB_ERR_OOM, "host allocation failed");
   U->N = N;
   U->stream = (cudaStream_t)stream;
+  if (const char* e = std::getenv("IB_UNET_TC")) U->tc = e[0] != '0';
   U->L = unet_layers(N);
   U->np = unet_param_count();
   auto bail = [&](int code) {

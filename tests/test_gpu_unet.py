@@ -39,7 +39,19 @@ def test_param_count(pkg):
     assert pkg.ib_unet_num_params() == UO.param_count()
 
 
-def test_forward_matches_oracle(pkg):
+# The convolutions run on the tensor cores (mma.sync, BF16 operands, FP32
+# accumulation; FP32 activations as hi + lo BF16 pairs) unless IB_UNET_TC=0 selects
+# the CUDA-core kernels; both are compared with the FP64 oracle.
+PATHS = ["tensor", "cuda-core"]
+
+
+@pytest.fixture(params=PATHS)
+def conv_path(request, monkeypatch):
+    monkeypatch.setenv("IB_UNET_TC", "1" if request.param == "tensor" else "0")
+    return request.param
+
+
+def test_forward_matches_oracle(pkg, conv_path):
     th, x, _ = _data()
     net = pkg.UNet(N, th)
     y = torch.zeros(3 * N * N, dtype=torch.float32, device="cuda")
@@ -51,7 +63,7 @@ def test_forward_matches_oracle(pkg):
     net.close()
 
 
-def test_loss_and_gradient_match_oracle(pkg):
+def test_loss_and_gradient_match_oracle(pkg, conv_path):
     th, x, t = _data(1)
     net = pkg.UNet(N, th)
     L, g = net.loss_grad(f32(x).reshape(-1), f32(t).reshape(-1))
@@ -61,7 +73,7 @@ def test_loss_and_gradient_match_oracle(pkg):
     net.close()
 
 
-def test_training_lowers_the_loss(pkg):
+def test_training_lowers_the_loss(pkg, conv_path):
     th, x, t = _data(2)
     net = pkg.UNet(N, th)
     xs, ts = f32(x).reshape(-1), f32(t).reshape(-1)
