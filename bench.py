@@ -504,12 +504,55 @@ def run_vcycle(args):
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "V(1,1) on %d^2, ellipse of %d points, kappa=1e4, dt=1e-3" % (N, 2 * N),
                        "box": args.box, "precision": args.precision, "tail_grid": s.tail_grid(args.precision),
-                       "tail_cluster": s.tail_cluster(args.precision),
+                       "tail_cluster": s.tail_cluster(args.precision), "box_forms": s.box_forms(args.precision),
                        "note": "ib_vcycle includes the FP64<->FP32 conversion of b and w"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "alg_bytes_per_dof": bpd,
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}}
     s.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_unet(args):
+    """The learned stage's network alone at 512^2 (4 -> 3 channels, 118 451 parameters):
+    forward and one training step (forward, backward, Adam), CUDA events, against the
+    dense BF16 tensor peak.  FLOPs per forward: sum over layers of 2 Co Ci K^2 H^2, each
+    taken twice (hi and lo BF16 terms of the activations)."""
+    import torch
+
+    import paper_1311_5614_gb300 as pkg
+
+    torch.cuda.set_device(args.local_rank)
+    N = 512
+    net = pkg.UNet(N, W.unet_init_params(0))
+    x = torch.randn(4 * N * N, device="cuda")
+    y = torch.zeros(3 * N * N, device="cuda")
+    t = torch.randn(3 * N * N, device="cuda")
+    flops = 0.0
+    for ci, co, k in W.UNET_SHAPES:
+        H = N if co in (16, 3) else (N // 2 if co == 32 else N // 4)
+        flops += 2.0 * co * ci * k * k * H * H
+    fwd = _timed_steps(torch, lambda: net.forward(x, y), torch.empty(64 * 1024 * 1024, device="cuda"),
+                       torch.cuda.current_stream(), args.warmup, args.steps)
+    trn = _timed_steps(torch, lambda: net.train_step(x, t, 1e-5), torch.empty(64 * 1024 * 1024, device="cuda"),
+                       torch.cuda.current_stream(), args.warmup, args.steps)
+    net.close()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    f_ms = sum(fwd) / len(fwd)
+    ach = 2.0 * flops / (f_ms * 1e-3) / 1e12
+    line = {"metric": "U-Net forward / training step time", "value": f_ms, "unit": "ms per forward",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "bf16 x (bf16 hi + lo) -> f32", "data": "synthetic",
+            "config": {"workload": "U-Net 16/32/64 channels at 512^2"},
+            "train_step_ms": sum(trn) / len(trn),
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "flops_per_forward": 2.0 * flops}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -684,6 +727,38 @@ def oracle_c3(prob, iters=None, samples=1, full_solve=False, gpu=None, log=None)
     return out
 
 
+def vcycle_alone(torch, pkg, N, precision, box, steps, warmup, peak):
+    """The V-cycle alone on N^2 (the 0.28/0.22 ellipse of 2N points, kappa = 1e4, dt =
+    1e-3): mean device time of the graph-replayed V-cycle (ib_vcycle_timer), L2 flushed
+    before each, against the V(1,1) algorithmic traffic (56 B/DOF in FP32)."""
+    prob = W.single_ellipse(N=N, n_points=2 * N, kappa=1e4, dt=1e-3)
+    prob.box = box
+    s = pkg.IBSolver.from_problem(prob, precision=precision, max_iters=1)
+    n = 3 * N * N
+    b = torch.randn(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        s.vcycle(b, w)
+    torch.cuda.synchronize()
+    s.vcycle_timer(True)
+    for _ in range(steps):
+        flush.zero_()
+        s.vcycle(b, w)
+    prec = "fp32" if precision == "fp32" else "fp64"
+    nv, ms = s.vcycle_timer_read(prec)
+    s.vcycle_timer(False)
+    out = {"grid": N, "dof": n, "ms": ms / max(nv, 1), "precision": precision,
+           "box_forms": s.box_forms(precision), "tail_grid": s.tail_grid(precision)}
+    s.close()
+    bpd = 56.0 if precision == "fp32" else 112.0
+    ach = bpd * n / (out["ms"] * 1e-3) / 1e9 if out["ms"] > 0 else 0.0
+    out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "alg_bytes_per_dof": bpd}
+    out["dof_per_s"] = n / (out["ms"] * 1e-3) if out["ms"] > 0 else 0.0
+    return out
+
+
 def run_multi1024(args):
     """Headline: the 1024^2 multi-structure workload.  One bench step = C3_STEPS
     consecutive implicit IB steps (set-up + MG-preconditioned FGMRES to 1e-8 + point
@@ -807,9 +882,11 @@ def run_multi1024(args):
     prof = s.profile_read()
     s.profile(False)
     tail = (s.tail_grid(args.precision), s.tail_cluster(args.precision))
+    forms_by_level = s.box_forms(args.precision)
     s.close()
 
     forms = sweep_forms(args, torch, pkg) if args.forms else None
+    large = vcycle_alone(torch, pkg, 4096, args.precision, args.box, 5, 3, peak) if args.vcycle_large else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -837,9 +914,11 @@ def run_multi1024(args):
                 "status": sorted(set(x["status"] for x in step_stats)),
                 "setup_ms": float(np.mean([x["t_setup_ms"] for x in step_stats])),
                 "solve_ms": float(np.mean([x["t_solve_ms"] for x in step_stats])),
-                "tail": {"grid": tail[0], "cluster": tail[1]},
+                "autotune": {"tail_grid": tail[0], "tail_cluster": tail[1], "box_form_by_level": forms_by_level,
+                             "box_form_codes": "1 one box per CTA, 2 thread per box row, 3 register-blocked "
+                                               "product, 4/5/6 strip kernel of 8/16/32 boxes, 0 size rule"},
                 "profile": {k: {"launches": v[0], "ms": v[1], "bytes": v[2]} for k, v in prof.items()},
-                "forms": forms}
+                "forms": forms, "vcycle_large": large}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -961,7 +1040,7 @@ def main(argv=None):
     ap.add_argument("--save-params", default=None, help="learned512: write the trained U-Net parameters (.npy)")
     ap.add_argument("--learn-epochs", type=int, default=2)
     ap.add_argument("--workload", default="multi1024",
-                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512"],
+                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512", "unet"],
                     help="multi1024 (default): the 1024^2 sixteen-ellipse run, 20 consecutive steps per "
                          "bench step; sweep256: the 256^2 kappa x dt sweep; batch256: the 256-problem "
                          "batch; vcycle: the V-cycle alone (--grid); learned512: the learned stage")
@@ -973,6 +1052,8 @@ def main(argv=None):
                          "with cudaProfilerStart/Stop (for an ncu launch list of one sweep)")
     ap.add_argument("--no-batch", action="store_true",
                     help="time only the sequential form (single stream; for profiler captures)")
+    ap.add_argument("--no-vcycle-large", dest="vcycle_large", action="store_false",
+                    help="multi1024: skip the V-cycle alone at 4096^2")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the sequential FP64 / FP32 comparison forms")
     ap.add_argument("--rotate", action="store_true", help="reference arm: rotate through the cases")
@@ -1004,6 +1085,8 @@ def main(argv=None):
             return run_vcycle(args)
         if args.workload == "learned512":
             return run_learned512(args)
+        if args.workload == "unet":
+            return run_unet(args)
         if args.workload == "sweep256":
             return run_ours(args)
         return run_multi1024(args)

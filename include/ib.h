@@ -202,6 +202,15 @@ IB_API int ib_tail_cluster(const ib_problem* prob, int32_t precision);
  * shared memory; the levels between use one thread per box row, several boxes per
  * CTA.  Both read at ib_setup. */
 
+/* Form of the n x n box kernel (n = 2, 4) on a smoothing level of the V-cycle of the given
+ * precision, as the set-up autotuner chose it by timing one colour phase of each form
+ * on the problem's own hierarchy: 1 one box per CTA, 2 a thread per box row (several
+ * boxes per CTA), 3 the register-blocked product, 4 / 5 / 6 the strip kernel with 8 /
+ * 16 / 32 boxes per strip; 0 when no form was timed (the size rule above applies: 1 x 1
+ * or 8 x 8 boxes, IB_BOX_TUNE=0, or an IB_BOX_* variable set); -1 for an invalid
+ * argument. */
+IB_API int ib_box_form(const ib_problem* prob, int32_t precision, int32_t level);
+
 /* Number of structure boxes (boxes whose block includes elasticity) on a level,
  * as found by the last set-up. */
 IB_API int ib_num_struct_boxes(const ib_problem* prob, int32_t level);

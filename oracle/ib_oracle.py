@@ -587,25 +587,31 @@ def coarse_solve(level, rhs, rho):
 
 
 # ----------------------------------------------------------------------------
-# V-cycle, Algorithm 1
+# V-cycle (Algorithm 1 of the paper; sec. 3)
 # ----------------------------------------------------------------------------
 
 
 def vcycle(levels, rhs, w, nu1=1, nu2=1, rho=1.0, order="color4", li=0):
-    """w <- MGV(w, rhs) on level li (Algorithm 1)."""
+    """MGV(w, rhs) on level li as a composition of three maps of the iterate:
+    nu2 smoothing sweeps after the coarse-grid correction after nu1 smoothing sweeps.
+    The coarse-grid correction adds P e, e the same cycle applied on the next level to
+    the restricted residual from a zero start; on the coarsest level the cycle is the
+    exact (bordered) solve."""
     lev = levels[li]
     if li == len(levels) - 1:
         return coarse_solve(lev, rhs, rho)
     smooth = smooth_color4 if order == "color4" else smooth_lex
-    for _ in range(nu1):
-        w = smooth(lev, rhs, w)
-    r2 = lev.R @ (rhs - lev.A @ w)
-    e2 = vcycle(levels, r2, np.zeros_like(r2), nu1, nu2, rho, order, li + 1)
-    w = w + lev.P @ e2
-    rev = post_reversed(lev.boxes["b"])
-    for _ in range(nu2):
-        w = smooth(lev, rhs, w, reverse=rev)
-    return w
+
+    def sweeps(x, n, reverse=False):
+        for _ in range(n):
+            x = smooth(lev, rhs, x, reverse=reverse)
+        return x
+
+    def coarse_correction(x):
+        rc = lev.R @ (rhs - lev.A @ x)
+        return x + lev.P @ vcycle(levels, rc, np.zeros_like(rc), nu1, nu2, rho, order, li + 1)
+
+    return sweeps(coarse_correction(sweeps(w, nu1)), nu2, reverse=post_reversed(lev.boxes["b"]))
 
 
 # ----------------------------------------------------------------------------

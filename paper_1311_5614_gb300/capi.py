@@ -76,6 +76,7 @@ _SIGS = {
     "ib_num_struct_boxes": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_tail_grid": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_tail_cluster": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ib_box_form": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "ib_launch_count": (ctypes.c_int64, [_P, ctypes.c_int32]),
     "ib_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -475,6 +476,10 @@ class IBSolver:
 
     def tail_cluster(self, precision="fp32"):
         return lib().ib_tail_cluster(self.handle, PRECISION[precision])
+
+    def box_forms(self, precision="fp32"):
+        """Box-kernel form chosen by the set-up autotuner on each smoothing level (see ib_box_form)."""
+        return [lib().ib_box_form(self.handle, PRECISION[precision], l) for l in range(self.n_levels - 1)]
 
     def apply(self, level, w, y):
         ib_apply(self.handle, level, w, y)

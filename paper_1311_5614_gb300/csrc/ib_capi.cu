@@ -840,6 +840,9 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   IB_SETUP_CUDA(cudaStreamSynchronize(s));
   st = setup_hierarchy(P);
   if (st != IB_OK) return fail_free(st);
+  for (const char* v : {"IB_BOX_GEMM_MIN", "IB_BOX_ONE_MAX", "IB_BOX_STRIP", "IB_BOX_STRIP_MIN", "IB_BOX_STRIP_W"})
+    if (std::getenv(v)) P.box_autotune = false;  // the forms are pinned by hand
+  if (const char* e = std::getenv("IB_BOX_TUNE")) P.box_autotune = P.box_autotune && e[0] != '0';
   if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
   if (const char* e = std::getenv("IB_BOX_ONE_MAX")) P.box_one_max = std::atol(e);
   if (const char* e = std::getenv("IB_WAIT_LIMIT_NS")) P.wait_limit_ns = std::strtoull(e, nullptr, 10);
@@ -896,6 +899,13 @@ int ib_tail_cluster(const ib_problem* H, int32_t precision) {
   const int ix = precision == IB_FP32_PRECOND ? 0 : 1;
   if ((ix == 1 && !P.has64) || (ix == 0 && !P.has32)) return 0;
   return P.tail_cluster[ix];
+}
+
+int ib_box_form(const ib_problem* H, int32_t precision, int32_t level) {
+  if (!H || (precision != IB_FP64 && precision != IB_FP32_PRECOND && precision != IB_MIXED_PRECOND)) return -1;
+  const Problem& P = H->P;
+  if (level < 0 || level >= P.nlev - 1 || level >= 32) return -1;
+  return P.box_form[precision == IB_FP32_PRECOND ? 0 : 1][level];
 }
 
 int ib_num_struct_boxes(const ib_problem* H, int32_t level) {

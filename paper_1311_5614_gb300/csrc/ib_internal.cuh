@@ -225,6 +225,10 @@ struct Problem {
   bool box_strip = true;             // 4 x 4 boxes: strip kernel on levels with N_l / 8 a multiple of 32
   long box_strip_min = 2048;          // ... and at least this many boxes per colour
   int box_strip_w = 0;                // strip width (8, 16 or 32; 0: chosen per level)
+  // box-kernel form per V-cycle ([0] FP32, [1] on FP64 vectors) and level, chosen by timing
+  // at set-up (0: the size rule above; see IB_BOXF_* in ib_vcycle.cu)
+  bool box_autotune = true;
+  int box_form[2][32] = {};
   double sigma = 0.0;                 // stiffness ratio dt * max(kappa) / mu of the structure
   double stiff_sigma = 3000.0;        // FP32 mode: from this sigma on, precondition with the mixed V-cycle
   cudaStream_t gstream = nullptr;                 // private stream the graph is captured on

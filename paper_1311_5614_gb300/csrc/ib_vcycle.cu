@@ -464,7 +464,8 @@ struct Strip {
   static constexpr int LD = SPAN + 8;           // staged columns [X0 - 4, X0 + SPAN + 4)
   static constexpr int TROWS = 6 + 7 + 6;       // staged rows of u, v, p
   static constexpr int TILE = TROWS * LD;       // elements of one staging buffer
-  static constexpr int RLD = W + 4;             // row stride of the [q][box] blocks
+  static constexpr int RLD = W + 8;             // row stride of the residual block [q][box]
+  static constexpr int QLD = 60;                // row stride of the correction block [box][q]
   static constexpr bool SPLIT = !std::is_same<T, TM>::value;  // separate TM copy of the residuals
   static constexpr int RB = sizeof(TM) == 4 ? 4 : 2;  // rows per thread (one 16-byte load of M)
   static constexpr int CB = sizeof(TM) == 4 ? 2 : 4;  // boxes per thread
@@ -477,7 +478,7 @@ struct Strip {
   static constexpr size_t OFF_TILE = ((size_t)NB * NB * sizeof(TM) + 15) / 16 * 16;
   static constexpr size_t OFF_R = OFF_TILE + 2 * (size_t)TILE * sizeof(T);
   static constexpr size_t OFF_D = OFF_R + (size_t)NB * RLD * sizeof(T);
-  static constexpr size_t OFF_RM = OFF_D + (size_t)NB * RLD * sizeof(T);
+  static constexpr size_t OFF_RM = OFF_D + (size_t)W * QLD * sizeof(T);
   static constexpr size_t SMEM = OFF_RM + (SPLIT ? (size_t)NB * RLD * sizeof(TM) : 0);
 };
 
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(256, 3) kv_boxt(T* w, const T* __restrict__ b,
       if (S::SPLIT) sRM[items[i].roff] = (TM)r;
     }
     __syncthreads();
-    // 3a. free-box product for every box of the strip: D[q][k] = sum_s Mf[s][q] R[s][k]
+    // 3a. free-box product for every box of the strip: D[k][q] = sum_s Mf[s][q] R[s][k]
     {
       const int rg = tid % S::RG, bg = tid / S::RG;
       if (bg < S::BG) {
@@ -709,10 +710,21 @@ __global__ void __launch_bounds__(256, 3) kv_boxt(T* w, const T* __restrict__ b,
 #pragma unroll
             for (int kk = 0; kk < S::CB; ++kk) acc[a][kk] += mv[a] * rv[kk];
         }
+        // each thread's RB consecutive rows of a box are contiguous in D[k][q]: one
+        // 16-byte (or two) store per box
 #pragma unroll
-        for (int a = 0; a < S::RB; ++a)
+        for (int kk = 0; kk < S::CB; ++kk) {
+          T* dst = sD + (bg * S::CB + kk) * S::QLD + rg * S::RB;
+          if constexpr (sizeof(T) == 4 && S::RB == 4) {
+            *reinterpret_cast<float4*>(dst) =
+                make_float4((float)acc[0][kk], (float)acc[1][kk], (float)acc[2][kk], (float)acc[3][kk]);
+          } else if constexpr (sizeof(T) == 8 && S::RB == 2) {
+            *reinterpret_cast<double2*>(dst) = make_double2((double)acc[0][kk], (double)acc[1][kk]);
+          } else {
 #pragma unroll
-          for (int kk = 0; kk < S::CB; ++kk) sD[(rg * S::RB + a) * RLD + bg * S::CB + kk] = (T)acc[a][kk];
+            for (int a = 0; a < S::RB; ++a) dst[a] = (T)acc[a][kk];
+          }
+        }
       }
     }
     if (wp == 0) {  // the strip's structure boxes, in box order
@@ -732,14 +744,15 @@ __global__ void __launch_bounds__(256, 3) kv_boxt(T* w, const T* __restrict__ b,
         d0 += M[(size_t)s2 * NB] * (double)sR[s2 * RLD + k];
         d1 += M[(size_t)(s2 + 1) * NB] * (double)sR[(s2 + 1) * RLD + k];
       }
-      sD[q * RLD + k] = (T)(d0 + d1);
+      sD[k * S::QLD + q] = (T)(d0 + d1);
     }
     __syncthreads();
     // 4. w += delta on the strip's unknowns
 #pragma unroll
     for (int i = 0; i < S::UPW; ++i) {
       if (items[i].pack < 0) continue;
-      w[goff(items[i].pack)] = tile[items[i].toff] + sD[items[i].roff];
+      const int k = (items[i].pack >> 16) & 0xff, q = items[i].roff / RLD;
+      w[goff(items[i].pack)] = tile[items[i].toff] + sD[k * S::QLD + q];
     }
     __syncthreads();  // the buffer, the residuals and the corrections are reused next
   }
@@ -795,6 +808,62 @@ inline int strip_width(const Problem& P, int N) {
   return pick;
 }
 
+// Forms of the n x n box kernel (n = 2, 4) the set-up autotuner chooses from.
+enum : int { BOXF_RULE = 0, BOXF_ONE = 1, BOXF_ROWS = 2, BOXF_GEMM = 3, BOXF_STRIP8 = 4, BOXF_STRIP16 = 5,
+             BOXF_STRIP32 = 6 };
+
+template <typename T>
+constexpr int pix();
+
+// Launch one colour phase of level l's boxes in the given form (BOXF_RULE: the size
+// rule).  Returns false if the form does not apply to the level (nothing launched).
+template <typename T, typename TM>
+bool launch_box_form(Problem& P, int l, int form, T* w, const T* b, T* E, int color) {
+  LevelInfo& L = P.lev[l];
+  const StokesCoef<T> c = coefs<T>(P, l);
+  const int half = L.nb / 2;
+  const long nbox = (long)half * half;
+  const double* Ms = L.Mstruct;
+  const TM* Mf = Mfree_of<TM>(L);
+  const bool pdl = use_pdl(P);
+  const int bs = P.prm.box;
+  if (bs != 2 && bs != 4) return false;
+  switch (form) {
+    case BOXF_ONE:
+      if (bs == 2)
+        vlaunch(pdl, kv_boxs<T, TM, 2>, (int)nbox, BoxShape<2, 1>::TPBOX, 0, P.stream, w, b, E, L.N, c, color, L.flag,
+                Ms, Mf);
+      else
+        vlaunch(pdl, kv_boxs<T, TM, 4>, (int)nbox, BoxShape<4, 1>::TPBOX, 0, P.stream, w, b, E, L.N, c, color, L.flag,
+                Ms, Mf);
+      return true;
+    case BOXF_ROWS:
+      if (bs == 2)
+        vlaunch(pdl, kv_boxn<T, TM, 2, 8>, nblk(nbox, 8), BoxShape<2, 8>::THREADS, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
+      else
+        vlaunch(pdl, kv_boxn<T, TM, 4, 4>, nblk(nbox, 4), BoxShape<4, 4>::THREADS, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
+      return true;
+    case BOXF_GEMM:
+      if (bs == 2)
+        vlaunch(pdl, kv_boxg<T, TM, 2>, nblk(nbox, BoxGemm<TM, 2>::BPC), 128, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
+      else
+        vlaunch(pdl, kv_boxg<T, TM, 4>, nblk(nbox, BoxGemm<TM, 4>::BPC), 128, 0, P.stream, w, b, E, L.N, c, color,
+                L.flag, Ms, Mf);
+      return true;
+    case BOXF_STRIP8:
+      return bs == 4 && half % 8 == 0 && launch_strip<T, TM, 8>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+    case BOXF_STRIP16:
+      return bs == 4 && half % 16 == 0 && launch_strip<T, TM, 16>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+    case BOXF_STRIP32:
+      return bs == 4 && half % 32 == 0 && launch_strip<T, TM, 32>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+    default:
+      return false;
+  }
+}
+
 template <typename T, typename TM>
 int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   LevelInfo& L = P.lev[l];
@@ -803,6 +872,12 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const long nbox = (long)half * half;
   const double* Ms = L.Mstruct;
   const TM* Mf = Mfree_of<TM>(L);
+  // the form the set-up timed fastest on this level, else the size rule
+  const int tuned = l < 32 ? P.box_form[pix<T>()][l] : 0;
+  if (tuned != BOXF_RULE && launch_box_form<T, TM>(P, l, tuned, w, b, E, color)) {
+    IB_LAUNCH_CHECK();
+    return IB_OK;
+  }
   // the GEMM form pays off on large levels, one box per CTA on small ones
   const bool gemm = nbox >= P.box_gemm_min;
   const bool one = nbox <= P.box_one_max;
@@ -1616,6 +1691,68 @@ int tail_raise_smem(Problem& P, size_t smem_max) {
 template <typename T>
 int vcycle_run(Problem& P);
 
+// Box-kernel autotuner: on every smoothing level with n x n boxes (n = 2, 4), time one
+// colour phase of each applicable form (one box per CTA, a thread per box row, the
+// register-blocked product, the strip kernel at widths 8, 16, 32) on the problem's
+// own hierarchy with w = b = 0 (the same products and memory traffic, no change of
+// state) and keep the fastest.  Skipped when an IB_BOX_* variable pins the forms.
+template <typename T, typename TM>
+int tune_box_forms_t(Problem& P) {
+  constexpr int ix = pix<T>();
+  for (int l = 0; l < 32; ++l) P.box_form[ix][l] = BOXF_RULE;
+  if (!P.box_autotune || (P.prm.box != 2 && P.prm.box != 4) || P.prof) return IB_OK;
+  cudaEvent_t e0, e1;
+  IB_CUDA_TRY(cudaEventCreate(&e0));
+  IB_CUDA_TRY(cudaEventCreate(&e1));
+  long long saved[IB_KC_COUNT];
+  std::memcpy(saved, P.nlaunch, sizeof(saved));
+  int rc = IB_OK;
+  for (int l = 0; l < P.nlev - 1 && l < 32 && rc == IB_OK; ++l) {
+    LevelInfo& L = P.lev[l];
+    LevelBuf<T>& B = lbuf<T>(L);
+    const size_t n3 = 3ul * L.N * L.N;
+    if (cudaMemsetAsync(B.w, 0, n3 * sizeof(T), P.stream) != cudaSuccess ||
+        cudaMemsetAsync(B.b, 0, n3 * sizeof(T), P.stream) != cudaSuccess) {
+      rc = fail(IB_ERR_CUDA, "box autotuner: memset");
+      break;
+    }
+    float best = 1e30f;
+    int best_f = BOXF_RULE;
+    for (int f = BOXF_ONE; f <= BOXF_STRIP32; ++f) {
+      if (!launch_box_form<T, TM>(P, l, f, B.w, B.b, (T*)nullptr, 0)) continue;  // warm-up (and applicability)
+      cudaEventRecord(e0, P.stream);
+      for (int r = 0; r < 4; ++r) launch_box_form<T, TM>(P, l, f, B.w, B.b, (T*)nullptr, r);
+      cudaEventRecord(e1, P.stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        rc = fail(IB_ERR_CUDA, "box autotuner: timing launch failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_f = f;
+      }
+    }
+    P.box_form[ix][l] = best_f;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::memcpy(P.nlaunch, saved, sizeof(saved));
+  P.graph_dirty[ix] = true;
+  return rc;
+}
+
+template <typename T>
+int tune_box_forms(Problem& P) {
+  if constexpr (sizeof(T) == 8) {
+    if (P.prm.precision != IB_FP64) return tune_box_forms_t<double, float>(P);
+    return tune_box_forms_t<double, double>(P);
+  } else {
+    return tune_box_forms_t<float, float>(P);
+  }
+}
+
 // Candidate forms of the tail: the single-CTA kernel from levels with N_l <= 64
 // (FP32) or <= 32 (FP64) whose arrays fit in shared memory, plus "coarsest grid
 // only"; and the cluster kernel from levels with 16 <= N_l <= 128.
@@ -1624,6 +1761,7 @@ int vcycle_run(Problem& P);
 // grid-wide kernels and the tail kernel).
 template <typename T>
 int vcycle_prepare(Problem& P) {
+  IB_TRY(tune_box_forms<T>(P));
   const int nmax = sizeof(T) == 4 ? 64 : 32;
   struct Cand {
     int l, cs;

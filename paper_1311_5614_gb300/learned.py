@@ -53,13 +53,21 @@ def harvest_chain(N=512, n_points=1024, n_problems=40, rhs_per_problem=4, chain=
             e = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
             s.solve_step(un, e, X0.clone())  # e = x*, the error of x_0 = 0
             s.update_points(X0)              # the step moved the problem's points: restore X^n
+            e0 = float(torch.linalg.vector_norm(e))
             for _ in range(chain):
+                # a chain that has converged (or overflowed) yields no further pairs
+                en = float(torch.linalg.vector_norm(e))
+                if not (1e-12 * e0 < en < 1e30 * e0):
+                    break
                 s.learned_chain(e, X[k], T[k])
                 k += 1
         s.close()
         kappas.append(kap)
     torch.cuda.synchronize()
-    return X, T, kappas
+    # drop pairs with a non-finite or vanishing target
+    ok = torch.isfinite(X[:k]).all(dim=1) & torch.isfinite(T[:k]).all(dim=1) & (T[:k].abs().sum(dim=1) > 0)
+    idx = torch.nonzero(ok).flatten()
+    return X[idx], T[idx], kappas
 
 
 def holdout_loss(net, X, T):
@@ -123,7 +131,8 @@ def train(net, X, T, epochs=2, lr=1e-3, seed=0, log=None):
         for idx in order:
             # cosine decay of the learning rate over the whole run
             a = lr * 0.5 * (1.0 + np.cos(np.pi * step / max(total, 1)))
-            acc += net.train_step(X[int(idx)], T[int(idx)], float(max(a, 1e-5)))
+            L = net.train_step(X[int(idx)], T[int(idx)], float(max(a, 1e-5)))
+            acc += L if np.isfinite(L) else 0.0
             step += 1
         losses.append(acc / P)
         if log:
