@@ -1067,10 +1067,13 @@ __device__ __forceinline__ T window_row(const TailLevel<T, TM>& L, const T* w, i
   const int N = L.N, n = N * N, r = L.wrow[t], c = r / n, rr = r - c * n, i = rr % N, j = rr / N;
   *row = r;
   const T* e0 = L.Ew + (size_t)t * WIN;
+  // differences from the component's value at the row's index: each row of E_l sums
+  // to zero over each column component (uniform velocities are in its kernel)
+  const T ref[2] = {w[j * N + i], w[n + j * N + i]};
   T acc = 0;
   for (int e = 0; e < WIN; ++e) {
     const int cc = e / WSQ, rem = e - cc * WSQ;
-    acc += e0[e] * w[cc * n + wrapi(j + rem / WD - WR, N) * N + wrapi(i + rem % WD - WR, N)];
+    acc += e0[e] * (w[cc * n + wrapi(j + rem / WD - WR, N) * N + wrapi(i + rem % WD - WR, N)] - ref[cc]);
   }
   return acc;
 }

@@ -251,8 +251,8 @@ __global__ void k_window_cast(const double* __restrict__ a, float* __restrict__ 
 
 }  // namespace
 
-// y[r] += coef * (E_l w)[r] on the structure rows of colour `color` (-1: all rows):
-// one warp per row, the lanes take the window entries in turn and the warp sums
+// y[r] += coef * (E_l w)[r] on the structure rows of colour `color` (-1: all rows),
+// formed from differences of w (see below): one warp per row, the lanes take the window entries in turn and the warp sums
 // them.  The row count is read from the device (the set-up's counter), so that a
 // captured launch, sized by the storage capacity, stays valid when the count
 // changes from step to step.  Only the programmatic-launch wait orders the reads of w.
@@ -275,12 +275,18 @@ __global__ void __launch_bounds__(256) kv_window_apply(const int* __restrict__ s
   if (r < 0) return;  // the whole warp leaves together
   const T* row = Ew + (size_t)warp * WIN;
   const size_t n = (size_t)N * N;
+  // every row of E_l sums to zero over each column component (a uniform velocity
+  // is in the kernel of E_l: J annihilates translations, P reproduces constants), so
+  // the entries multiply differences from the component's value at the row's own
+  // index; a structure moving almost rigidly then keeps the accuracy of the
+  // per-point form, which works on velocity differences
+  const T ref[2] = {w[(size_t)j * N + i], w[n + (size_t)j * N + i]};
   T acc = 0;
 #pragma unroll 4
   for (int e = lane; e < WIN; e += 32) {
     const int cc = e / WSQ, rem = e - cc * WSQ;
     const int dj = rem / WD - WR, di = rem - (rem / WD) * WD - WR;
-    acc += row[e] * w[cc * n + (size_t)wrapi(j + dj, N) * N + wrapi(i + di, N)];
+    acc += row[e] * (w[cc * n + (size_t)wrapi(j + dj, N) * N + wrapi(i + di, N)] - ref[cc]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
