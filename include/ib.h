@@ -208,7 +208,9 @@ IB_API int ib_tail_cluster(const ib_problem* prob, int32_t precision);
  * boxes per CTA), 3 the register-blocked product, 4 / 5 / 6 the strip kernel with 8 /
  * 16 / 32 boxes per strip; 0 when no form was timed (the size rule above applies: 1 x 1
  * or 8 x 8 boxes, IB_BOX_TUNE=0, or an IB_BOX_* variable set); -1 for an invalid
- * argument. */
+ * argument.  The environment variable IB_BOX_FORMS (comma-separated codes, finest
+ * level first, read at ib_setup) gives the forms instead of timing them (a form that
+ * does not apply to its level falls back to the size rule). */
 IB_API int ib_box_form(const ib_problem* prob, int32_t precision, int32_t level);
 
 /* Number of structure boxes (boxes whose block includes elasticity) on a level,

@@ -843,6 +843,15 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   for (const char* v : {"IB_BOX_GEMM_MIN", "IB_BOX_ONE_MAX", "IB_BOX_STRIP", "IB_BOX_STRIP_MIN", "IB_BOX_STRIP_W"})
     if (std::getenv(v)) P.box_autotune = false;  // the forms are pinned by hand
   if (const char* e = std::getenv("IB_BOX_TUNE")) P.box_autotune = P.box_autotune && e[0] != '0';
+  if (const char* e = std::getenv("IB_BOX_FORMS")) {  // comma-separated forms, finest level first
+    int l = 0;
+    for (const char* c = e; *c && l < 32;) {
+      P.box_form_pin[l++] = std::atoi(c);
+      while (*c && *c != ',') ++c;
+      if (*c == ',') ++c;
+    }
+    P.box_form_pinned = true;
+  }
   if (const char* e = std::getenv("IB_BOX_GEMM_MIN")) P.box_gemm_min = std::atol(e);
   if (const char* e = std::getenv("IB_BOX_ONE_MAX")) P.box_one_max = std::atol(e);
   if (const char* e = std::getenv("IB_WAIT_LIMIT_NS")) P.wait_limit_ns = std::strtoull(e, nullptr, 10);

@@ -229,6 +229,8 @@ struct Problem {
   // at set-up (0: the size rule above; see IB_BOXF_* in ib_vcycle.cu)
   bool box_autotune = true;
   int box_form[2][32] = {};
+  int box_form_pin[32] = {};  // IB_BOX_FORMS: forms given per level (0: none given)
+  bool box_form_pinned = false;
   double sigma = 0.0;                 // stiffness ratio dt * max(kappa) / mu of the structure
   double stiff_sigma = 3000.0;        // FP32 mode: from this sigma on, precondition with the mixed V-cycle
   cudaStream_t gstream = nullptr;                 // private stream the graph is captured on

@@ -1703,6 +1703,11 @@ template <typename T, typename TM>
 int tune_box_forms_t(Problem& P) {
   constexpr int ix = pix<T>();
   for (int l = 0; l < 32; ++l) P.box_form[ix][l] = BOXF_RULE;
+  if (P.box_form_pinned) {  // forms given by hand (profiler runs distort the timings)
+    for (int l = 0; l < 32; ++l) P.box_form[ix][l] = P.box_form_pin[l];
+    P.graph_dirty[ix] = true;
+    return IB_OK;
+  }
   if (!P.box_autotune || (P.prm.box != 2 && P.prm.box != 4) || P.prof) return IB_OK;
   cudaEvent_t e0, e1;
   IB_CUDA_TRY(cudaEventCreate(&e0));

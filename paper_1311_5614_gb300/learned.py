@@ -155,7 +155,7 @@ def evaluate(net, N=512, n_points=1024, kappas=(1e2, 1e4, 1e6), dt=1e-2, box=4, 
         prob.box = box
         row = {"kappa": kap}
         for mode in ("plain", "learned"):
-            s = C.IBSolver.from_problem(prob, precision=precision, max_iters=200)
+            s = C.IBSolver.from_problem(prob, precision=precision, max_iters=400)
             if mode == "learned":
                 s.set_learned_stage(net)
             up = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
