@@ -52,13 +52,16 @@ import ib_workloads as W  # noqa: E402
 METRIC = "implicit IB step time to 1e-8 residual; V-cycle DOF/s; mixed/learned vs FP64"
 UNIT = "ms per implicit IB step"
 CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the two
-# dominant kernel classes, averaged over every launch of one profiled sweep step
-# (sequential form, FP32 with escalation) in one ncu capture.  Valid only for the
-# V-cycle kernel sources it was taken on: reported as null once they change.
-TRAFFIC = {"sources_sha256": "bbca7ce2c6a0fc936a4d77340394c769cc3f688a62e87e8ec186d06330dc8084",
-           "box": 867090.0, "spread": 211613.0}
-VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh"]
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one
+# ncu capture each.  "vcycle1024": one V(1,1) cycle of the 1024^2 sixteen-ellipse
+# step (146 kernel launches from one kv_zero to the next, summed; ncu replays each
+# launch with cold caches, so this is an upper bound of the graph-replayed cycle's
+# traffic).  Valid only for the V-cycle kernel sources it was taken on: reported as
+# null once they change.
+TRAFFIC = {"sources_sha256": "442f191dfc57b6cde774a3fd9e86b52d112950e072db55d370bab1eee905cf04",
+           "vcycle1024": 746.1e6}
+VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh", "ib_windows.cu",
+                  "ib_async.cuh"]
 
 
 def captured_traffic(kclass):
