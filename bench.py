@@ -560,6 +560,55 @@ def run_unet(args):
     return 0
 
 
+CAVITY_CASES = [(N, b, a) for N in (64, 256, 1024) for b in (4, 8) for a in (6.0, 60.0, 600.0, 3000.0)]
+
+
+def run_cavity(args):
+    """The paper's own problem on the GPU (sec. 4, the refinement study of sec. 6):
+    the lid-driven cavity with the thick annulus, steady Stokes, cosine kernel, zero
+    rest length, stiffness alpha = 6, 60, 600, 3000 (non-stiff ... very stiff), box
+    sizes 4 and 8, V(1,1), MG-GMRES from zero to a 1e-6 residual reduction (100
+    iterations at most), at N = 64, 256 and 1024.  Right-hand side from the library
+    (ib_rhs: the lid's ghost term and -S F(X)); each case is solved warmup + steps
+    times and its median FGMRES device time reported (events inside ib_solve).  The
+    GPU sweeps the boxes in four colours, the paper lexicographically, so the
+    iteration counts are the colour order's (the paper plots its counts)."""
+    import torch
+
+    from paper_1311_5614_gb300 import capi as C
+
+    torch.cuda.set_device(args.local_rank)
+    cases = []
+    for N, b, alpha in CAVITY_CASES:
+        p = W.cavity_annulus(N, kappa=alpha, dt=1.0)
+        s = C.IBSolver(N, p.X, p.springs, p.kappa, p.rest, L=1.0, rho=0.0, mu=1.0, dt=1.0, delta="cos4", box=b,
+                       walls="noslip", lid=1.0, precision=args.precision, tol=1e-6, max_iters=100)
+        rhs = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(rhs)
+        s.rhs(None, rhs)
+        times, st = [], None
+        for r in range(args.warmup + args.steps):
+            st = s.solve(rhs, x)
+            if r >= args.warmup:
+                times.append(st["t_solve_ms"])
+        s.close()
+        cases.append({"N": N, "box": b, "alpha": alpha, "iters": st["iters"], "status": st["status"],
+                      "rel_res_true": st["rel_res_true"], "ms": float(np.median(times)),
+                      "escalated_at": st["escalated_at"]})
+    big = [c for c in cases if c["N"] == 1024 and c["box"] == 8 and c["alpha"] == 3000.0][0]
+    line = {"metric": "MG-GMRES solve time to a 1e-6 residual reduction, the paper's cavity problem",
+            "value": big["ms"], "unit": "ms per solve (N = 1024, b = 8, alpha = 3000)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "f32 V-cycle + f64 Krylov" if args.precision == "fp32" else args.precision,
+            "data": "synthetic (the paper's geometry, no randomness)",
+            "config": {"workload": "lid-driven cavity, thick annulus (r = 1/4, w = 1/16), M1 = 19N/8, "
+                                   "M2 = 3N/32 + 1, steady Stokes, cosine kernel, V(1,1), colour order",
+                       "precision": args.precision},
+            "cases": cases, "clocks": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned512(args):
     """Learned stage at 512^2 (1024-point ellipse): pairs harvested from the method's own
     V-cycles on problems with kappa = 10^U[2,6], U-Net trained on the GPU with the
@@ -1043,7 +1092,7 @@ def main(argv=None):
     ap.add_argument("--save-params", default=None, help="learned512: write the trained U-Net parameters (.npy)")
     ap.add_argument("--learn-epochs", type=int, default=2)
     ap.add_argument("--workload", default="multi1024",
-                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512", "unet"],
+                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512", "unet", "cavity"],
                     help="multi1024 (default): the 1024^2 sixteen-ellipse run, 20 consecutive steps per "
                          "bench step; sweep256: the 256^2 kappa x dt sweep; batch256: the 256-problem "
                          "batch; vcycle: the V-cycle alone (--grid); learned512: the learned stage")
@@ -1088,6 +1137,8 @@ def main(argv=None):
             return run_vcycle(args)
         if args.workload == "learned512":
             return run_learned512(args)
+        if args.workload == "cavity":
+            return run_cavity(args)
         if args.workload == "unet":
             return run_unet(args)
         if args.workload == "sweep256":

@@ -18,6 +18,11 @@ Workload recipes (Lagrangian structures immersed in a 2-D periodic box):
 * ``batch``: independent problems with grids drawn from a set of sizes, each
   with one ellipse sampled at 4 points per grid cell of perimeter and a
   log-uniform stiffness.
+* ``cavity_annulus``: the paper's own test structure (sec. 4), no randomness:
+  the thick annulus of inner radius 1/4 and width 1/16 centred at (0.5, 0.5),
+  M1 = 19N/8 points on each of M2 = 3N/32 + 1 concentric closed fibres, every
+  fibre a closed chain of zero-rest-length springs, in the unit square with
+  no-slip walls.
 """
 from __future__ import annotations
 
@@ -36,6 +41,7 @@ __all__ = [
     "batch",
     "random_field",
     "random_points_field",
+    "cavity_annulus",
 ]
 
 
@@ -103,6 +109,29 @@ def single_ellipse(N=64, n_points=128, kappa=1e2, dt=1e-2, rho=1.0, mu=1.0, L=1.
     ns = springs.shape[0]
     return Problem(N=N, L=L, rho=rho, mu=mu, dt=dt, X=X, springs=springs,
                    kappa=np.full(ns, float(kappa)), rest=np.full(ns, float(rest)), **kw)
+
+
+def cavity_annulus(N, kappa=1.0, dt=1.0, r=0.25, w=1.0 / 16.0, center=(0.5, 0.5), **kw):
+    """The thick annulus of sec. 4 at h = 1/N: nodes (xc + (r + s2) cos(s1 / r),
+    yc + (r + s2) sin(s1 / r)) for s1 = k ds1 (k < M1 = 19N/8, ds1 = 2 pi r / M1)
+    and s2 = l ds2 (l < M2 = 3N/32 + 1, ds2 = w / (M2 - 1)), point l*M1 + k; each
+    fibre (fixed l) a closed chain of springs with stiffness kappa and zero rest
+    length.  Steady Stokes (rho = 0, mu = 1), the cosine kernel, no-slip walls
+    (meta["walls"]).  meta carries M1, M2, ds1, ds2 and the nodes as [M2, M1, 2]."""
+    if N % 32 != 0:
+        raise ValueError("M1 = 19N/8 and M2 = 3N/32 + 1 need N a multiple of 32")
+    M1, M2 = 19 * N // 8, 3 * N // 32 + 1
+    ds1, ds2 = 2.0 * math.pi * r / M1, w / (M2 - 1)
+    s1 = np.arange(M1) * ds1
+    s2 = np.arange(M2) * ds2
+    R = r + s2[:, None]
+    nodes = np.stack([center[0] + R * np.cos(s1[None, :] / r), center[1] + R * np.sin(s1[None, :] / r)], axis=-1)
+    springs = np.concatenate([closed_chain(M1, offset=l * M1) for l in range(M2)])
+    ns = springs.shape[0]
+    kw.setdefault("delta", "cos4")
+    return Problem(N=N, L=1.0, rho=0.0, mu=1.0, dt=dt, X=nodes.reshape(-1, 2).copy(), springs=springs,
+                   kappa=np.full(ns, float(kappa)), rest=np.zeros(ns),
+                   meta=dict(M1=M1, M2=M2, ds1=ds1, ds2=ds2, nodes=nodes, walls="noslip"), **kw)
 
 
 def _periodic_dist(p, q, L):

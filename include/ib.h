@@ -77,6 +77,38 @@ enum { IB_DELTA_PESKIN4 = 0, IB_DELTA_COS4 = 1 };
 enum { IB_FP64 = 0, IB_FP32_PRECOND = 1, IB_MIXED_PRECOND = 2 };
 enum { IB_JAC_CLAMPED = 0, IB_JAC_EXACT = 1 };
 
+/* Boundary of the square (sec. 4):
+ *   IB_WALLS_PERIODIC  the periodic unit square (the default);
+ *   IB_WALLS_NOSLIP    the square with no-slip walls of the paper's tests (the lid-
+ *                      driven cavity's operator): the normal velocity is zero on
+ *                      each wall, and the tangential velocity of the first row of
+ *                      faces sees the ghost value -u (the wall value, the mean of the
+ *                      two, is zero).  In every [u | v | p] vector the faces u(0, j)
+ *                      (x = 0; x = 1 has no face of its own) and v(i, 0) (y = 0) are
+ *                      the walls: they are not unknowns, inputs must hold zero there,
+ *                      ib_apply returns them unchanged, and right-hand sides are
+ *                      zeroed there (a moving lid enters the right-hand side through
+ *                      the ghost, 2 u_lid - u, as a known term the caller adds).
+ *                      Coarse levels use the same ghost rule in the prolongation
+ *                      (fine row next to a wall = half the coarse one).  Points must
+ *                      stay at least 2h from every wall (checked at ib_setup; a
+ *                      point that moves closer fails the next set-up), and the
+ *                      structure's couplings must fit the assembled rows (springs
+ *                      up to about 1.5 cells).  The strip form of the box kernel and
+ *                      the learned stage are periodic only.  With rho = 0 only the
+ *                      constant pressure is bordered out of the coarsest solve. */
+enum { IB_WALLS_PERIODIC = 0, IB_WALLS_NOSLIP = 1 };
+
+/* Time-stepping method (sec. 2.3):
+ *   IB_IMPLICIT  backward Euler for the structure (sec. 2.3.2, Eqs. 17-22): the
+ *                operator carries dt S J S^*, the system this library is about;
+ *   IB_EXPLICIT  the explicit-time method (sec. 2.3.1): the operator is the
+ *                Stokes system alone, the structure's force F(X^n) stays on the
+ *                right-hand side, and X^{n+1} = X^n + dt S^* u^{n+1} as before.
+ *                Stable only for gamma dt below alpha_exp (sec. 4.1); it is here to
+ *                measure what the implicit method saves (sec. 7). */
+enum { IB_IMPLICIT = 0, IB_EXPLICIT = 1 };
+
 /* Problem parameters (sec. 2: grid, fluid, time step; secs. 5-6: smoother). */
 typedef struct {
   int32_t N;          /* cells per side: power of two, N >= 2 * max(4, box) */
@@ -98,6 +130,13 @@ typedef struct {
                          0 = FP32 throughout */
   int32_t restart;    /* FGMRES restart length m (Krylov vectors kept), 0 = max_iters;
                          workspace grows with m: (m + 1) FP64 + m preconditioner vectors */
+  int32_t walls;      /* IB_WALLS_PERIODIC (default) or IB_WALLS_NOSLIP (see above) */
+  double lid;         /* IB_WALLS_NOSLIP only: the top wall y = L moves with the tangential
+                         velocity u(x, L) = lid * (1 - cos(2 pi x / L)) / 2, the lid of the
+                         paper's cavity (sec. 4); it enters the right-hand side of ib_rhs and
+                         ib_solve_step through the ghost 2 u_lid - u of the faces next to the
+                         lid.  0 (default): all walls at rest. */
+  int32_t time_method; /* IB_IMPLICIT (default) or IB_EXPLICIT (see above) */
 } ib_params;
 
 /* Statistics of one ib_solve_step call. */
@@ -153,7 +192,9 @@ IB_API int ib_apply(ib_problem* prob, int32_t level, const double* w, double* y)
 IB_API int ib_vcycle(ib_problem* prob, const double* b, double* w);
 
 /* b = [-(rho/dt) u^n - S F(X); 0] for the current points (device, 3N^2
- * doubles).  u_n: device [2][N][N] doubles or NULL for a fluid at rest. */
+ * doubles).  u_n: device [2][N][N] doubles or NULL for a fluid at rest.  With
+ * IB_WALLS_NOSLIP the wall faces are zero and the moving lid (params.lid) adds
+ * -2 mu u_lid(x_i) / h^2 to the u rows next to it. */
 IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
 
 /* One implicit IB step (sec. 2.3):
@@ -175,6 +216,15 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * 64-element slice of the whole basis does not fit in shared memory. */
 IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,
                   ib_stats* stats);
+
+/* Solve A_0 x = b for a given right-hand side with the current hierarchy (the
+ * points of ib_setup or the last ib_update_points / ib_solve_step), by the same
+ * MG-preconditioned FGMRES from x = 0 (sec. 3.3):
+ *   b      device [3][N][N] doubles (with no-slip walls its wall faces are zeroed)
+ *   x      device [3][N][N] output, pressure with zero mean (may not alias b)
+ *   stats  host, may be NULL (t_setup_ms = 0)
+ * The points do not move.  Returns as ib_solve_step. */
+IB_API int ib_solve(ib_problem* prob, const double* b, double* x, ib_stats* stats);
 
 /* Number of levels in the hierarchy and the grid size of a level. */
 IB_API int ib_num_levels(const ib_problem* prob);
@@ -351,7 +401,8 @@ IB_API int ib_vcycle_timer_read(ib_problem* prob, int32_t precision, int64_t* co
  * stall on cudaMalloc's implicit device synchronisation in the middle of a time
  * step, or a host framework that owns all device memory through its own pool and
  * does not let libraries allocate.
- *   params   host; uses N, L, rho, mu, dt, delta and jacobian
+ *   params   host; uses N, L, rho, mu, dt, delta and jacobian (periodic square only:
+ *            walls must be IB_WALLS_PERIODIC)
  *   X        device [n_points][2];  springs device int32 [n_springs][2];
  *   kappa, rest  device [n_springs];  w, y  device 3 N^2 doubles (must not alias)
  *   stream   cudaStream_t (NULL = legacy default stream)

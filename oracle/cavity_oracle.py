@@ -433,12 +433,16 @@ def cavity_box_unknowns(N, b, I, J):
     return np.array(out, dtype=np.int64)
 
 
-def cavity_hierarchy(N, alpha, b, ann=None, weight="ds1^2"):
+def cavity_hierarchy(N, alpha, b, ann=None, weight="ds1^2", order="lex"):
     """Levels N, N/2, ..., N_c = max(4, b) (sec. 6): the re-discretised wall Stokes
     operator plus alpha times the elasticity, level 0's S A_f S^* from the annulus
     and each coarser one the Galerkin product R E P of the velocity blocks
-    (sec. 3.2).  Each non-coarsest level gets its boxes in lexicographic order
-    (rows of boxes bottom to top, x fastest) with their dense A_BB blocks."""
+    (sec. 3.2).  Each non-coarsest level gets its boxes with their dense A_BB
+    blocks, in lexicographic order (rows of boxes bottom to top, x fastest;
+    order="lex", the paper's) or in the four colours of the parallel order
+    (order="color4": box (I, J) has colour (I mod 2) + 2 (J mod 2), the colours
+    visited as in ``ib_oracle.COLOR_SEQUENCE``).  ann: any object with N, M1,
+    M2, ds1, ds2 and points() (default: ``Annulus(N)``)."""
     ann = Annulus(N) if ann is None else ann
     wts = {"ds1ds2": ann.ds1 * ann.ds2, "ds1^2": ann.ds1 ** 2, "ds2^2": ann.ds2 ** 2}
     X = ann.points()
@@ -466,12 +470,18 @@ def cavity_hierarchy(N, alpha, b, ann=None, weight="ds1^2"):
     for lev in levels[:-1]:
         nb = lev.N // b
         boxes = []
+        colors = {c: [] for c in range(4)}
         for J in range(nb):
             for I in range(nb):
                 idx = cavity_box_unknowns(lev.N, b, I, J)
                 rows = lev.A[idx, :].tocsr()
-                boxes.append((idx, rows, np.linalg.inv(rows[:, idx].toarray())))
+                box = (idx, rows, np.linalg.inv(rows[:, idx].toarray()))
+                boxes.append(box)
+                colors[(I % 2) + 2 * (J % 2)].append(box)
         lev.boxes = boxes
+        lev.colors = colors
+        lev.order = order
+        lev.b = b
     return levels
 
 
@@ -483,6 +493,21 @@ def cavity_smooth_lex(level, rhs, w):
     for idx, rows, inv in level.boxes:
         r = rhs[idx] - rows @ w
         w[idx] += inv @ r
+    return w
+
+
+def cavity_smooth_color4(level, rhs, w, reverse=False):
+    """One sweep in the parallel order: the colours in ``COLOR_SEQUENCE`` (reversed
+    when ``reverse``); every box of a colour is solved from the colour's starting
+    residual, then all are updated (block Jacobi inside a colour; a colour's boxes
+    share no unknown)."""
+    from .ib_oracle import COLOR_SEQUENCE
+
+    w = w.copy()
+    for c in (COLOR_SEQUENCE[::-1] if reverse else COLOR_SEQUENCE):
+        r = rhs - level.A @ w
+        for idx, rows, inv in level.colors[c]:
+            w[idx] += inv @ r[idx]
     return w
 
 
@@ -499,17 +524,23 @@ def cavity_coarse_solve(level, rhs):
 
 
 def cavity_vcycle(levels, rhs, w, nu1=1, nu2=1, li=0):
-    """MGV(w, rhs) of Algorithm 1 with lexicographic box smoothing before and after
-    the coarse-grid correction."""
+    """MGV(w, rhs) of Algorithm 1 with box smoothing before and after the
+    coarse-grid correction: lexicographic (the same order both times), or the
+    colour order (post-smoothing in reverse for 1 x 1 boxes, as
+    ``ib_oracle.post_reversed``)."""
+    from .ib_oracle import post_reversed
+
     lev = levels[li]
     if li == len(levels) - 1:
         return cavity_coarse_solve(lev, rhs)
+    color = getattr(lev, "order", "lex") == "color4"
     for _ in range(nu1):
-        w = cavity_smooth_lex(lev, rhs, w)
+        w = cavity_smooth_color4(lev, rhs, w) if color else cavity_smooth_lex(lev, rhs, w)
     rc = lev.R @ (rhs - lev.A @ w)
     w = w + lev.P @ cavity_vcycle(levels, rc, np.zeros_like(rc), nu1, nu2, li + 1)
     for _ in range(nu2):
-        w = cavity_smooth_lex(lev, rhs, w)
+        w = (cavity_smooth_color4(lev, rhs, w, reverse=post_reversed(lev.b)) if color
+             else cavity_smooth_lex(lev, rhs, w))
     return w
 
 

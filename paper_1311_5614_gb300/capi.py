@@ -32,6 +32,8 @@ STATUS_NAMES = {0: "IB_OK", 1: "IB_ERR_INVALID_ARG", 2: "IB_ERR_CUDA", 3: "IB_ER
 DELTA = {"peskin4": 0, "cos4": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 JACOBIAN = {"clamped": 0, "exact": 1}
+WALLS = {"periodic": 0, "noslip": 1}
+TIME_METHOD = {"implicit": 0, "explicit": 1}
 
 
 class ib_params(ctypes.Structure):
@@ -39,7 +41,8 @@ class ib_params(ctypes.Structure):
                 ("mu", ctypes.c_double), ("dt", ctypes.c_double), ("delta", ctypes.c_int32),
                 ("box", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("jacobian", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int32), ("escalate", ctypes.c_int32), ("restart", ctypes.c_int32)]
+                ("max_iters", ctypes.c_int32), ("escalate", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("walls", ctypes.c_int32), ("lid", ctypes.c_double), ("time_method", ctypes.c_int32)]
 
 
 class ib_stats(ctypes.Structure):
@@ -71,6 +74,7 @@ _SIGS = {
     "ib_vcycle": (ctypes.c_int, [_P, _P, _P]),
     "ib_rhs": (ctypes.c_int, [_P, _P, _P]),
     "ib_solve_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ib_stats)]),
+    "ib_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ib_stats)]),
     "ib_num_levels": (ctypes.c_int, [_P]),
     "ib_level_size": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ib_num_struct_boxes": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -149,7 +153,8 @@ def ib_default_params():
 
 
 def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=1, nu2=1,
-                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100, escalate=True, restart=0):
+                precision="fp64", jacobian="clamped", tol=1e-8, max_iters=100, escalate=True, restart=0,
+                walls="periodic", lid=0.0, time_method="implicit"):
     p = ib_default_params()
     p.N, p.L, p.rho, p.mu, p.dt = int(N), float(L), float(rho), float(mu), float(dt)
     p.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
@@ -159,6 +164,9 @@ def make_params(N, L=1.0, rho=1.0, mu=1.0, dt=1e-2, delta="peskin4", box=1, nu1=
     p.tol, p.max_iters = float(tol), int(max_iters)
     p.escalate = 1 if escalate else 0
     p.restart = int(restart)
+    p.walls = WALLS[walls] if isinstance(walls, str) else int(walls)
+    p.lid = float(lid)
+    p.time_method = TIME_METHOD[time_method] if isinstance(time_method, str) else int(time_method)
     return p
 
 
@@ -206,6 +214,16 @@ def ib_solve_step(prob, u_n, up, X, n_points, raise_on_not_converged=False):
     st = ib_stats()
     code = lib().ib_solve_step(prob, _dev_ptr(u_n, 2 * n * n, "u_n"), _dev_ptr(up, 3 * n * n, "up"),
                                _dev_ptr(X, 2 * n_points, "X") if n_points else None, ctypes.byref(st))
+    if code != IB_OK and (code != IB_ERR_NOT_CONVERGED or raise_on_not_converged):
+        _check(code)
+    return st.as_dict()
+
+
+def ib_solve(prob, b, x, raise_on_not_converged=False):
+    """Solve A_0 x = b with the current hierarchy; returns the ib_stats as a dict."""
+    n = ib_level_size(prob, 0)
+    st = ib_stats()
+    code = lib().ib_solve(prob, _dev_ptr(b, 3 * n * n, "b"), _dev_ptr(x, 3 * n * n, "x"), ctypes.byref(st))
     if code != IB_OK and (code != IB_ERR_NOT_CONVERGED or raise_on_not_converged):
         _check(code)
     return st.as_dict()
@@ -498,6 +516,10 @@ class IBSolver:
 
     def solve_step(self, u_n, up, X, raise_on_not_converged=False):
         return ib_solve_step(self.handle, u_n, up, X, self.n_points, raise_on_not_converged)
+
+    def solve(self, b, x, raise_on_not_converged=False):
+        """x = A_0^{-1} b by MG-preconditioned FGMRES (the points do not move)."""
+        return ib_solve(self.handle, b, x, raise_on_not_converged)
 
     def set_learned_stage(self, net):
         _check(lib().ib_set_learned_stage(self.handle, net.handle if net is not None else None))

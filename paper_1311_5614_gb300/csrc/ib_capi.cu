@@ -117,6 +117,12 @@ int validate(const ib_params* p) {
     return fail(IB_ERR_INVALID_ARG, "max_iters must be in 1..512");
   if (p->escalate != 0 && p->escalate != 1) return fail(IB_ERR_INVALID_ARG, "escalate must be 0 or 1");
   if (p->restart < 0 || p->restart > 512) return fail(IB_ERR_INVALID_ARG, "restart must be in 0..512");
+  if (p->time_method != IB_IMPLICIT && p->time_method != IB_EXPLICIT)
+    return fail(IB_ERR_INVALID_ARG, "time_method must be IB_IMPLICIT or IB_EXPLICIT");
+  if (p->walls != IB_WALLS_PERIODIC && p->walls != IB_WALLS_NOSLIP)
+    return fail(IB_ERR_INVALID_ARG, "walls must be IB_WALLS_PERIODIC or IB_WALLS_NOSLIP");
+  if (!std::isfinite(p->lid) || (p->lid != 0.0 && p->walls != IB_WALLS_NOSLIP))
+    return fail(IB_ERR_INVALID_ARG, "lid must be finite, and 0 without no-slip walls");
   return IB_OK;
 }
 
@@ -129,9 +135,14 @@ __global__ void k_axpy_n(double a, const double* __restrict__ x, double* y, long
   if (e < n) y[e] += a * x[e];
 }
 
-// y = A_l w in FP64.
+// y = A_l w in FP64.  The elasticity of a coarse level with no-slip walls comes from
+// its assembled rows (the per-point coarse patches are periodic Galerkin products).
 int apply64(Problem& P, int l, const double* w, double* y) {
   IB_TRY(launch_stokes<double>(P, l, w, nullptr, y, false));
+  if (P.prm.walls && l > 0) {
+    if (op_elastic(P)) IB_TRY(launch_window_apply<double>(P, l, w, y, efac(P), -1, false));
+    return IB_OK;
+  }
   IB_TRY(launch_elastic<double>(P, l, w, y, efac(P), P.U64));
   return IB_OK;
 }
@@ -148,6 +159,8 @@ int check_dev_err(Problem& P) {
       return fail(IB_ERR_INVALID_ARG, "a spring has coincident or non-finite end points");
     if (h & DEV_ERR_SINGULAR) return fail(IB_ERR_SINGULAR, "zero pivot in a box or coarsest factorisation");
     if (h & DEV_ERR_TIMEOUT) return fail(IB_ERR_TIMEOUT, "a bulk copy of the Krylov basis did not complete");
+    if (h & DEV_ERR_WALL)
+      return fail(IB_ERR_INVALID_ARG, "a point is closer than 2h to a no-slip wall (its kernel reaches the wall)");
     return fail(IB_ERR_INVALID_ARG, "internal index check failed (too many springs at a point?)");
   }
   return IB_OK;
@@ -167,7 +180,7 @@ int setup_hierarchy(Problem& P) {
   if (P.prm.precision == IB_FP32_PRECOND)
     for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_cast_patches(P, l));
   const int ns = P.nlev - 1;  // smoothing levels
-  const bool win = P.windows && P.np > 0 && P.ns > 0;
+  const bool win = P.windows && op_elastic(P);
   for (int l = 0; l < ns; ++l) {
     IB_TRY(launch_mark_struct(P, l));
     IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + l, P.count, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
@@ -231,6 +244,10 @@ int setup_hierarchy(Problem& P) {
       IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
     }
   }
+  if (P.prm.walls && op_elastic(P) && !use_win)
+    return fail(IB_ERR_INVALID_ARG,
+                "no-slip walls need the assembled elasticity rows: a coupling leaves the row window "
+                "(springs longer than about 1.5 cells) or IB_WINDOWS=0");
   if (use_win != P.win_step) P.graph_dirty[0] = P.graph_dirty[1] = true;
   P.win_step = use_win;
   if (use_win) {
@@ -304,7 +321,7 @@ int allocate(Problem& P) {
   for (int l = 0; l < nl; ++l) {
     LevelInfo& L = P.lev[l];
     size_t n3 = 3ul * L.N * L.N;
-    if (P.windows && P.np > 0 && P.ns > 0) {
+    if (P.windows && op_elastic(P)) {
       IB_TRY(dalloc(&L.rowslot, 2ul * L.N * L.N));
       IB_TRY(dalloc(&L.slot_row, 2ul * L.N * L.N));
     }
@@ -673,6 +690,7 @@ int solve_step_impl(Problem& P, const double* u_n, double* up, double* X, ib_sta
     k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, P.b64, n2);
     IB_LAUNCH_CHECK();
   }
+  if (P.prm.walls) IB_TRY(launch_wall_rhs(P, P.b64));
   IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
   if (P.prm.precision != IB_FP32_PRECOND) rc = fgmres<double>(P, P.b64, P.x64, st);
   else rc = fgmres<float>(P, P.b64, P.x64, st);
@@ -749,6 +767,12 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
     return fail(IB_ERR_INVALID_ARG, "spring arrays are NULL");
   for (int k = 0; k < 2 * n_points; ++k)
     if (!std::isfinite(X[k])) return fail(IB_ERR_INVALID_ARG, "non-finite point position");
+  if (params->walls == IB_WALLS_NOSLIP) {
+    const double h = params->L / params->N;
+    for (int k = 0; k < 2 * n_points; ++k)
+      if (X[k] < 2.0 * h || X[k] > params->L - 2.0 * h)
+        return fail(IB_ERR_INVALID_ARG, "with no-slip walls every point must lie at least 2h from the walls");
+  }
   std::vector<int> deg(n_points + 1, 0);
   for (int s = 0; s < n_springs; ++s) {
     int i = springs[2 * s], j = springs[2 * s + 1];
@@ -770,7 +794,8 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   P.np = n_points;
   P.ns = n_springs;
   P.nB = box_nunk(params->box);
-  P.sigma = stiffness(*params, n_springs, kappa);
+  // the explicit method's operator is Stokes alone: nothing stiff to escalate for
+  P.sigma = params->time_method == IB_EXPLICIT ? 0.0 : stiffness(*params, n_springs, kappa);
   P.stiff_sigma = stiff_threshold();
   if (const char* e = std::getenv("IB_WINDOWS")) P.windows = e[0] != '0';
   int Nc = params->box > 4 ? params->box : 4;
@@ -783,7 +808,9 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   }
   P.nlev = (int)P.lev.size();
   P.nc = 3 * Nc * Nc;
-  P.nborder = params->rho == 0.0 ? 3 : 1;
+  // bordered null space of the coarsest solve: the constant pressure, and with
+  // rho = 0 on the periodic square also the constant velocities
+  P.nborder = (params->rho == 0.0 && params->walls == IB_WALLS_PERIODIC) ? 3 : 1;
   P.max_m = (params->restart > 0 && params->restart < params->max_iters) ? params->restart : params->max_iters;
   int st = allocate(P);
   if (st != IB_OK) {
@@ -967,6 +994,7 @@ int ib_rhs(ib_problem* H, const double* u_n, double* b) {
     k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, b, n2);
     IB_LAUNCH_CHECK();
   }
+  if (P.prm.walls) IB_TRY(launch_wall_rhs(P, b));
   IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
   return IB_OK;
 }
@@ -975,6 +1003,37 @@ int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_st
   g_err.clear();
   if (!H || !up) return fail(IB_ERR_INVALID_ARG, "NULL argument");
   return solve_step_impl(H->P, u_n, up, X, stats);
+}
+
+int ib_solve(ib_problem* H, const double* b, double* x, ib_stats* stats) {
+  g_err.clear();
+  if (!H || !b || !x) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  Problem& P = H->P;
+  ib_stats local;
+  ib_stats* st = stats ? stats : &local;
+  std::memset(st, 0, sizeof(*st));
+  st->escalated_at = -1;
+  const size_t n = 3ul * P.prm.N * P.prm.N;
+  IB_CUDA_TRY(cudaMemcpyAsync(P.b64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  if (P.prm.walls) IB_TRY(launch_zero_walls(P, P.b64));
+  IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
+  int rc = (P.prm.precision != IB_FP32_PRECOND) ? fgmres<double>(P, P.b64, P.x64, st)
+                                                : fgmres<float>(P, P.b64, P.x64, st);
+  IB_CUDA_TRY(cudaEventRecord(P.ev[2], P.stream));
+  if (rc != IB_OK && rc != IB_ERR_NOT_CONVERGED) { st->status = rc; return rc; }
+  std::string msg = g_err;
+  IB_TRY(launch_pressure_mean_remove(P, P.x64));
+  IB_CUDA_TRY(cudaMemcpyAsync(x, P.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  float t1 = 0;
+  cudaEventElapsedTime(&t1, P.ev[1], P.ev[2]);
+  st->t_solve_ms = t1;
+  int nsb = 0;
+  for (int l = 0; l < P.nlev - 1; ++l) nsb += P.lev[l].n_struct;
+  st->n_struct_boxes = nsb;
+  st->status = rc;
+  g_err = msg;
+  return rc;
 }
 
 static int learned_buffers(Problem& P) {
@@ -996,6 +1055,8 @@ int ib_set_learned_stage(ib_problem* H, ib_unet* net) {
   Problem& P = H->P;
   if (net && learned_unet_size(net) != P.prm.N)
     return fail(IB_ERR_INVALID_ARG, "the network's grid size differs from the problem's");
+  if (net && P.prm.walls != IB_WALLS_PERIODIC)
+    return fail(IB_ERR_INVALID_ARG, "the learned stage's convolutions are periodic: not with no-slip walls");
   if (net) IB_TRY(learned_buffers(P));
   P.net = net;
   IB_CUDA_TRY(cudaStreamSynchronize(P.stream));

@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "ib_internal.cuh"
+#include "ib_ops.cuh"
 
 namespace ib {
 
@@ -17,7 +18,7 @@ inline int nblk(long n, int t = TPB) { return (int)((n + t - 1) / t); }
 
 // y = A_S w  (apply) or  y = b - A_S w  (residual), one thread per cell (i, j)
 // computing the u row of face (i, j), the v row of face (i, j) and the p row of
-// cell (i, j).
+// cell (i, j).  With no-slip walls (c.walls) the rows are those of stokes_row.
 template <typename T, bool RES>
 __global__ void k_stokes(const T* __restrict__ w, const T* __restrict__ b, T* __restrict__ out,
                          int N, int shift, StokesCoef<T> c) {
@@ -25,16 +26,23 @@ __global__ void k_stokes(const T* __restrict__ w, const T* __restrict__ b, T* __
   int n = N * N;
   if (idx >= n) return;
   int i = idx & (N - 1), j = idx >> shift;
-  int ip = (i + 1) & (N - 1), im = (i - 1) & (N - 1);
-  int jp = (j + 1) & (N - 1), jm = (j - 1) & (N - 1);
-  const T* u = w;
-  const T* v = w + n;
-  const T* p = w + 2 * n;
-  int e = j * N + ip, wq = j * N + im, nq = jp * N + i, sq = jm * N + i;
-  T pc = p[idx];
-  T au = c.diag * u[idx] + c.off * (u[e] + u[wq] + u[nq] + u[sq]) - c.g * (pc - p[wq]);
-  T av = c.diag * v[idx] + c.off * (v[e] + v[wq] + v[nq] + v[sq]) - c.g * (pc - p[sq]);
-  T ap = c.g * (u[e] - u[idx] + v[nq] - v[idx]);
+  T au, av, ap;
+  if (c.walls) {
+    au = stokes_row(w, N, c, 0, i, j);
+    av = stokes_row(w, N, c, 1, i, j);
+    ap = stokes_row(w, N, c, 2, i, j);
+  } else {
+    int ip = (i + 1) & (N - 1), im = (i - 1) & (N - 1);
+    int jp = (j + 1) & (N - 1), jm = (j - 1) & (N - 1);
+    const T* u = w;
+    const T* v = w + n;
+    const T* p = w + 2 * n;
+    int e = j * N + ip, wq = j * N + im, nq = jp * N + i, sq = jm * N + i;
+    T pc = p[idx];
+    au = c.diag * u[idx] + c.off * (u[e] + u[wq] + u[nq] + u[sq]) - c.g * (pc - p[wq]);
+    av = c.diag * v[idx] + c.off * (v[e] + v[wq] + v[nq] + v[sq]) - c.g * (pc - p[sq]);
+    ap = c.g * (u[e] - u[idx] + v[nq] - v[idx]);
+  }
   if (RES) {
     out[idx] = b[idx] - au;
     out[n + idx] = b[n + idx] - av;
@@ -57,6 +65,45 @@ __global__ void k_box_stokes(double* M, int N, int b, StokesCoef<double> c) {
   box_unknown(q, b, 0, 0, N, &cq, &iq, &jq);
   box_unknown(s, b, 0, 0, N, &cs, &is, &js);
   M[e] = stokes_entry(c, N, cq, iq, jq, cs, is, js);
+}
+
+// Stokes block of each structure slot's box at its own position (no-slip walls:
+// the boxes along a wall differ from the free box), column-major n_B x n_B.
+__global__ void k_struct_stokes(double* M, const int* __restrict__ box_of_slot, int nslot, int N, int b,
+                                StokesCoef<double> c) {
+  const int nB = box_nunk(b);
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)nslot * nB * nB) return;
+  const int s = (int)(e / ((long)nB * nB)), rem = (int)(e - (long)s * nB * nB);
+  const int q = rem % nB, t = rem / nB;
+  const int nb = N / b, box = box_of_slot[s], x0 = (box % nb) * b, y0 = (box / nb) * b;
+  int cq, iq, jq, ct, it, jt;
+  box_unknown(q, b, x0, y0, N, &cq, &iq, &jq);
+  box_unknown(t, b, x0, y0, N, &ct, &it, &jt);
+  M[e] = stokes_entry(c, N, cq, iq, jq, ct, it, jt);
+}
+
+// The wall faces of a no-slip level (u at x = 0, v at y = 0) set to zero.
+__global__ void k_zero_walls(double* w, int N) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  w[(size_t)t * N] = 0.0;              // u(0, t)
+  w[(size_t)N * N + t] = 0.0;          // v(t, 0)
+}
+
+// The moving lid of the cavity (sec. 4): u(x, L) = lid (1 - cos(2 pi x / L)) / 2.  The
+// face row next to the lid, j = N - 1, reads the ghost 2 u_lid - u; its known part
+// moves to the right-hand side: b -= 2 mu u_lid / h^2 (walls zeroed as well).
+__global__ void k_wall_rhs(double* b, int N, double h, double mu, double lid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  b[(size_t)i * N] = 0.0;
+  b[(size_t)N * N + i] = 0.0;
+  if (i > 0 && lid != 0.0) {
+    const double x = i * h, L = N * h;
+    const double ul = lid * 0.5 * (1.0 - cos(2.0 * M_PI * x / L));
+    b[(size_t)(N - 1) * N + i] -= 2.0 * mu * ul / (h * h);
+  }
 }
 
 __global__ void k_replicate(const double* __restrict__ src, double* dst, int m, long count) {
@@ -361,6 +408,7 @@ StokesCoef<T> coef_of(const Problem& P, int level) {
   c.diag = (T)(-4.0 * P.prm.mu / (h * h) - reac);
   c.off = (T)(P.prm.mu / (h * h));
   c.g = (T)(1.0 / h);
+  c.walls = P.prm.walls;
   return c;
 }
 
@@ -388,6 +436,7 @@ int launch_free_box(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
   int nB = P.nB;
   StokesCoef<double> c = coef_of<double>(P, level);
+  c.walls = 0;  // the free box is an interior box: no wall rows (the boxes along walls are structure slots)
   {
     KScope ks(P, IB_KC_SETUP, nB * nB * 8.0);
     k_box_stokes<<<nblk((long)nB * nB), TPB, 0, P.stream>>>(L.Sfree, L.N, P.prm.box, c);
@@ -399,14 +448,35 @@ int launch_free_box(Problem& P, int level) {
   return IB_OK;
 }
 
-// Every structure slot starts from the Stokes block of the free box.
+int launch_zero_walls(Problem& P, double* w) {
+  const int N = P.prm.N;
+  KScope ks(P, IB_KC_OTHER, 16.0 * N);
+  k_zero_walls<<<nblk(N), TPB, 0, P.stream>>>(w, N);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+int launch_wall_rhs(Problem& P, double* b) {
+  const int N = P.prm.N;
+  KScope ks(P, IB_KC_OTHER, 32.0 * N);
+  k_wall_rhs<<<nblk(N), TPB, 0, P.stream>>>(b, N, P.prm.L / N, P.prm.mu, P.prm.lid);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+// Every structure slot starts from the Stokes block of its box: the free box's
+// (periodic), or with no-slip walls the block at the box's own position.
 int launch_struct_fill(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
   int nB = P.nB;
   if (L.n_struct > 0) {
     long tot = (long)nB * nB * L.n_struct;
-    KScope ks(P, IB_KC_SETUP, tot * 16.0);
-    k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Sfree, L.Mstruct, nB * nB, L.n_struct);
+    KScope ks(P, IB_KC_SETUP, tot * (P.prm.walls ? 8.0 : 16.0));
+    if (P.prm.walls)
+      k_struct_stokes<<<nblk(tot), TPB, 0, P.stream>>>(L.Mstruct, L.box_of_slot, L.n_struct, L.N, P.prm.box,
+                                                      coef_of<double>(P, level));
+    else
+      k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Sfree, L.Mstruct, nB * nB, L.n_struct);
     IB_LAUNCH_CHECK();
   }
   return IB_OK;

@@ -42,7 +42,8 @@ enum : int {
   DEV_ERR_INDEX = 2,
   DEV_ERR_NONFINITE = 4,
   DEV_ERR_TIMEOUT = 8,
-  DEV_ERR_WINDOW = 16  // a coupling outside the assembled rows' windows (not an error: point path)
+  DEV_ERR_WINDOW = 16,  // a coupling outside the assembled rows' windows (not an error: point path)
+  DEV_ERR_WALL = 32     // a point whose kernel support reaches a no-slip wall
 };
 
 // Assembled elasticity rows (ib_windows.cu): per structure row, the entries at
@@ -88,10 +89,20 @@ struct Springs {
 };
 
 // Stokes coefficients of one level: diag = -4 mu / h^2 - rho / dt, off = mu / h^2, g = 1 / h.
+// walls = 1: the no-slip square (IB_WALLS_NOSLIP): the faces u(0, j) and v(i, 0) are
+// the walls x = 0 (= x = 1 after the wrap) and y = 0 (= y = 1); they hold zero and
+// their rows are the identity.  A tangential row next to a wall sees the ghost value
+// minus itself instead of the wrapped neighbour.
 template <typename T>
 struct StokesCoef {
   T diag, off, g;
+  int walls = 0;
 };
+
+// Whether (comp, i, j) is a wall face of a level with no-slip walls.
+__host__ __device__ inline bool wall_face(int comp, int i, int j) {
+  return (comp == 0 && i == 0) || (comp == 1 && j == 0);
+}
 
 // ---------------------------------------------------------------- device helpers
 __host__ __device__ inline int wrapi(int i, int N) { return i & (N - 1); }
@@ -120,19 +131,30 @@ __device__ inline void box_unknown(int q, int b, int x0, int y0, int N, int* com
   *j &= (N - 1);
 }
 
-// Entry A_S[(ca, ia, ja), (cb, ib, jb)] of the periodic MAC Stokes operator
-// [[mu Lap - rho/dt, -G], [D, 0]] of one level (N >= 4).
+// Entry A_S[(ca, ia, ja), (cb, ib, jb)] of the MAC Stokes operator
+// [[mu Lap - rho/dt, -G], [D, 0]] of one level (N >= 4): periodic, or with no-slip
+// walls (c.walls), where a wall face's row is the identity, no other row reads a
+// wall face, and a tangential row next to a wall takes -off onto its diagonal (the
+// ghost) instead of the wrapped neighbour.
 __device__ inline double stokes_entry(const StokesCoef<double>& c, int N, int ca, int ia, int ja,
                                       int cb, int ib, int jb) {
+  if (c.walls) {
+    if (ca < 2 && wall_face(ca, ia, ja)) return (cb == ca && ib == ia && jb == ja) ? 1.0 : 0.0;
+    if (cb < 2 && wall_face(cb, ib, jb)) return 0.0;
+  }
   int di = (ib - ia) & (N - 1), dj = (jb - ja) & (N - 1);
   double v = 0.0;
   if (ca < 2) {
     if (cb == ca) {
-      if (di == 0 && dj == 0) v += c.diag;
-      if (dj == 0 && di == 1) v += c.off;
-      if (dj == 0 && di == N - 1) v += c.off;
-      if (di == 0 && dj == 1) v += c.off;
-      if (di == 0 && dj == N - 1) v += c.off;
+      // tangential neighbours across a wall: u rows j = 0 and N - 1, v rows i = 0 and N - 1
+      const int t = (ca == 0) ? ja : ia;
+      const bool lo_wall = c.walls && t == 0, hi_wall = c.walls && t == N - 1;
+      const int dn = (ca == 0) ? di : dj, dt = (ca == 0) ? dj : di;  // normal / tangential offsets
+      if (dn == 0 && dt == 0) v += c.diag - (lo_wall ? c.off : 0.0) - (hi_wall ? c.off : 0.0);
+      if (dt == 0 && dn == 1) v += c.off;
+      if (dt == 0 && dn == N - 1) v += c.off;
+      if (dn == 0 && dt == 1 && !hi_wall) v += c.off;
+      if (dn == 0 && dt == N - 1 && !lo_wall) v += c.off;
     } else if (cb == 2) {
       // (G p) on a u face (i, j) = (p_{i,j} - p_{i-1,j}) / h; on a v face with j - 1.
       if (di == 0 && dj == 0) v -= c.g;
@@ -390,5 +412,10 @@ template <typename T>
 int launch_update_x(Problem& P, const T* Z, int k, double* x, int first = 0);
 int launch_axpby(Problem& P, double a, const double* x, double b, const double* y, double* z);
 int launch_pressure_mean_remove(Problem& P, double* w);
+// Whether the operator carries the elasticity block: a structure, and the implicit
+// method (IB_EXPLICIT keeps the structure's force on the right-hand side only).
+inline bool op_elastic(const Problem& P) { return P.np > 0 && P.ns > 0 && P.prm.time_method == IB_IMPLICIT; }
+int launch_zero_walls(Problem& P, double* w);  // no-slip walls: w = 0 on the wall faces
+int launch_wall_rhs(Problem& P, double* b);    // ... and the moving lid's ghost term
 
 }  // namespace ib

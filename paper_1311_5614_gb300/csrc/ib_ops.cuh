@@ -7,8 +7,10 @@
 
 namespace ib {
 
-// (A_S w) at the unknown (comp, i, j) of a periodic N x N level (sec. 2.2
-// stencils: mu Lap - rho/dt on velocities, -G p on faces, D w on cells).
+// (A_S w) at the unknown (comp, i, j) of an N x N level (sec. 2.2 stencils: mu Lap -
+// rho/dt on velocities, -G p on faces, D w on cells), periodic or with no-slip walls
+// (c.walls: a wall face's row is the identity; w holds zero on the wall faces, so
+// the rows that read them need no change except the tangential ghost -u).
 template <typename T>
 __device__ __forceinline__ T stokes_row(const T* __restrict__ w, int N, const StokesCoef<T>& c, int comp,
                                         int i, int j) {
@@ -18,24 +20,36 @@ __device__ __forceinline__ T stokes_row(const T* __restrict__ w, int N, const St
   const T* v = w + n;
   const T* p = w + 2 * n;
   if (comp == 0) {
-    return c.diag * u[j * N + i] + c.off * (u[j * N + ip] + u[j * N + im] + u[jp * N + i] + u[jm * N + i]) -
+    const T uc = u[j * N + i];
+    if (c.walls) {
+      if (i == 0) return uc;
+      const T un = (j == m) ? -uc : u[jp * N + i], us = (j == 0) ? -uc : u[jm * N + i];
+      return c.diag * uc + c.off * (u[j * N + ip] + u[j * N + im] + un + us) - c.g * (p[j * N + i] - p[j * N + im]);
+    }
+    return c.diag * uc + c.off * (u[j * N + ip] + u[j * N + im] + u[jp * N + i] + u[jm * N + i]) -
            c.g * (p[j * N + i] - p[j * N + im]);
   }
   if (comp == 1) {
-    return c.diag * v[j * N + i] + c.off * (v[j * N + ip] + v[j * N + im] + v[jp * N + i] + v[jm * N + i]) -
+    const T vc = v[j * N + i];
+    if (c.walls) {
+      if (j == 0) return vc;
+      const T ve = (i == m) ? -vc : v[j * N + ip], vw = (i == 0) ? -vc : v[j * N + im];
+      return c.diag * vc + c.off * (ve + vw + v[jp * N + i] + v[jm * N + i]) - c.g * (p[j * N + i] - p[jm * N + i]);
+    }
+    return c.diag * vc + c.off * (v[j * N + ip] + v[j * N + im] + v[jp * N + i] + v[jm * N + i]) -
            c.g * (p[j * N + i] - p[jm * N + i]);
   }
   return c.g * (u[j * N + ip] - u[j * N + i] + v[jp * N + i] - v[j * N + i]);
 }
 
 // Residual r = b - A_S w + rE at (comp, i, j); rE (-dt E w, velocity rows only)
-// may be NULL.
+// may be NULL.  A wall face's residual is b - w (no elasticity row there).
 template <typename T>
 __device__ __forceinline__ T resid_at(const T* w, const T* b, const T* rE, int N, const StokesCoef<T>& c,
                                       int comp, int i, int j) {
   const int g = comp * N * N + j * N + i;
   T r = b[g] - stokes_row(w, N, c, comp, i, j);
-  if (rE && comp < 2) r += rE[g];
+  if (rE && comp < 2 && !(c.walls && wall_face(comp, i, j))) r += rE[g];
   return r;
 }
 
@@ -55,11 +69,16 @@ __device__ __forceinline__ void restrict_resid_cell(const T* w, const T* b, cons
         (T)0.25 * (resid_at(w, b, E, N, c, 1, x0, y0) + resid_at(w, b, E, N, c, 1, x1, y0));
   *rp = (T)0.25 * (resid_at(w, b, E, N, c, 2, x0, y0) + resid_at(w, b, E, N, c, 2, x1, y0) +
                    resid_at(w, b, E, N, c, 2, x0, y1) + resid_at(w, b, E, N, c, 2, x1, y1));
+  if (c.walls) {  // coarse wall faces hold zero
+    if (I == 0) *ru = (T)0;
+    if (J == 0) *rv = (T)0;
+  }
 }
 
-// Same restriction applied to a stored residual vector r.
+// Same restriction applied to a stored residual vector r (walls: the coarse wall
+// faces get zero).
 template <typename T>
-__device__ __forceinline__ void restrict_cell(const T* r, int N, int I, int J, T* ru, T* rv, T* rp) {
+__device__ __forceinline__ void restrict_cell(const T* r, int N, int I, int J, T* ru, T* rv, T* rp, int walls) {
   const int n = N * N, m = N - 1;
   const T* u = r;
   const T* v = r + n;
@@ -71,24 +90,35 @@ __device__ __forceinline__ void restrict_cell(const T* r, int N, int I, int J, T
   *rv = (T)0.125 * (v[ym * N + x0] + v[ym * N + x1] + v[y1 * N + x0] + v[y1 * N + x1]) +
         (T)0.25 * (v[y0 * N + x0] + v[y0 * N + x1]);
   *rp = (T)0.25 * (p[y0 * N + x0] + p[y0 * N + x1] + p[y1 * N + x0] + p[y1 * N + x1]);
+  if (walls) {
+    if (I == 0) *ru = (T)0;
+    if (J == 0) *rv = (T)0;
+  }
 }
 
 // Prolongation (sec. 3.1) of the coarse correction e (Nc = N/2) to fine cell
-// (i, j): returns the three fine corrections.
+// (i, j): returns the three fine corrections.  With no-slip walls the coarse row
+// beyond a wall is its ghost, minus the row itself (so the fine row next to the
+// wall takes half the coarse one); the coarse wall faces hold zero.
 template <typename T>
-__device__ __forceinline__ void prolong_cell(const T* e, int N, int i, int j, T* cu, T* cv, T* cp) {
+__device__ __forceinline__ void prolong_cell(const T* e, int N, int i, int j, T* cu, T* cv, T* cp, int walls) {
   const int Nc = N / 2, nc = Nc * Nc, mc = Nc - 1;
   const int I = i >> 1, J = j >> 1;
   const T* u = e;
   const T* v = e + nc;
   const T* p = e + 2 * nc;
-  const int Jn = ((j & 1) ? J + 1 : J - 1) & mc;
-  const int In = ((i & 1) ? I + 1 : I - 1) & mc;
+  const int Ju = (j & 1) ? J + 1 : J - 1, Iu = (i & 1) ? I + 1 : I - 1;
+  const int Jn = Ju & mc, In = Iu & mc;
   const int I1 = (I + 1) & mc, J1 = (J + 1) & mc;
-  if ((i & 1) == 0) *cu = (T)0.75 * u[J * Nc + I] + (T)0.25 * u[Jn * Nc + I];
-  else *cu = (T)0.375 * (u[J * Nc + I] + u[J * Nc + I1]) + (T)0.125 * (u[Jn * Nc + I] + u[Jn * Nc + I1]);
-  if ((j & 1) == 0) *cv = (T)0.75 * v[J * Nc + I] + (T)0.25 * v[J * Nc + In];
-  else *cv = (T)0.375 * (v[J * Nc + I] + v[J1 * Nc + I]) + (T)0.125 * (v[J * Nc + In] + v[J1 * Nc + In]);
+  // weights of the far row / column; at a wall the ghost folds onto the near one
+  const bool gy = walls && (Ju < 0 || Ju > mc), gx = walls && (Iu < 0 || Iu > mc);
+  const int Jf = gy ? J : Jn, If = gx ? I : In;
+  const T fy = gy ? (T)-0.25 : (T)0.25, hy = gy ? (T)-0.125 : (T)0.125;
+  const T fx = gx ? (T)-0.25 : (T)0.25, hx = gx ? (T)-0.125 : (T)0.125;
+  if ((i & 1) == 0) *cu = (T)0.75 * u[J * Nc + I] + fy * u[Jf * Nc + I];
+  else *cu = (T)0.375 * (u[J * Nc + I] + u[J * Nc + I1]) + hy * (u[Jf * Nc + I] + u[Jf * Nc + I1]);
+  if ((j & 1) == 0) *cv = (T)0.75 * v[J * Nc + I] + fx * v[J * Nc + If];
+  else *cv = (T)0.375 * (v[J * Nc + I] + v[J1 * Nc + I]) + hx * (v[J * Nc + If] + v[J1 * Nc + If]);
   *cp = p[J * Nc + I];
 }
 

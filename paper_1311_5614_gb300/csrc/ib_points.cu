@@ -28,11 +28,14 @@ __device__ inline double phi1(double r, int kind) {
 // Level-0 patches: for each component, the x and y 1-D weights over the 4 grid
 // lines within 2h of the point.  A "normal" direction has nodes at integer
 // multiples of h, a "centred" direction at half-integers.
+// With no-slip walls a point must keep its kernel support off the walls (2h from
+// every wall); otherwise DEV_ERR_WALL.
 __global__ void k_fine_patches(Patches<double> pat, const double* __restrict__ X, int np, int N,
-                               double h, int kind) {
+                               double h, int kind, int walls, int* err) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= np) return;
   double s[2] = {X[2 * k] / h, X[2 * k + 1] / h};
+  if (walls && !(s[0] >= 2.0 && s[0] <= N - 2.0 && s[1] >= 2.0 && s[1] <= N - 2.0)) atomicOr(err, DEV_ERR_WALL);
   for (int comp = 0; comp < 2; ++comp) {
     for (int xy = 0; xy < 2; ++xy) {
       // u: x normal, y centred; v: x centred, y normal
@@ -274,6 +277,16 @@ __global__ void k_mark(Patches<double> pat, int np, int N, int b, int nb, int* f
   }
 }
 
+// No-slip walls: the boxes along the walls (first and last row and column of boxes)
+// hold wall faces and ghost rows, so their blocks differ from the free box's: they
+// get structure slots (their own inverses).
+__global__ void k_mark_ring(int nb, int* flag) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * nb) return;
+  const int I = t % nb, J = t / nb;
+  if (I == 0 || J == 0 || I == nb - 1 || J == nb - 1) flag[t] = 1;
+}
+
 __global__ void k_assign_slots(int* flag, int nbox, int* count, int* box_of_slot) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nbox) return;
@@ -378,7 +391,8 @@ int launch_fine_patches(Problem& P) {
   if (P.np == 0) return IB_OK;
   LevelInfo& L0 = P.lev[0];
   KScope ks(P, IB_KC_SETUP, P.np * (16.0 + 8 * 36.0));
-  k_fine_patches<<<nblk(P.np), TPB, 0, P.stream>>>(L0.pat64, P.X, P.np, L0.N, L0.h, P.prm.delta);
+  k_fine_patches<<<nblk(P.np), TPB, 0, P.stream>>>(L0.pat64, P.X, P.np, L0.N, L0.h, P.prm.delta, P.prm.walls,
+                                                    P.dev_err);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
@@ -459,7 +473,7 @@ Patches<float> patches_of<float>(LevelInfo& L) { return L.pat32; }
 
 template <typename T>
 int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U) {
-  if (P.np == 0 || P.ns == 0) return IB_OK;
+  if (!op_elastic(P)) return IB_OK;
   // The operator FGMRES is judged by stays in the factored form S J (S^* w): its
   // cancellation happens on small velocity differences.  An assembled row's entries
   // are sums of large per-point terms that nearly cancel (a second difference along
@@ -493,9 +507,14 @@ int launch_mark_struct(Problem& P, int level) {
   int nbox = L.nb * L.nb;
   IB_CUDA_TRY(cudaMemsetAsync(L.flag, 0, sizeof(int) * nbox, P.stream));
   IB_CUDA_TRY(cudaMemsetAsync(P.count, 0, sizeof(int), P.stream));
-  if (P.np > 0 && P.ns > 0) {
+  if (op_elastic(P)) {
     KScope ks(P, IB_KC_SETUP, 2.0 * P.np * (8 * 8 + 8 + 32 * 4));
     k_mark<<<nblk(2L * P.np), TPB, 0, P.stream>>>(L.pat64, P.np, L.N, P.prm.box, L.nb, L.flag);
+    IB_LAUNCH_CHECK();
+  }
+  if (P.prm.walls) {
+    KScope ksr(P, IB_KC_SETUP, nbox * 4.0);
+    k_mark_ring<<<nblk(nbox), TPB, 0, P.stream>>>(L.nb, L.flag);
     IB_LAUNCH_CHECK();
   }
   KScope ks(P, IB_KC_SETUP, nbox * 8.0);
@@ -506,7 +525,7 @@ int launch_mark_struct(Problem& P, int level) {
 
 int launch_assemble_struct(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
-  if (P.np == 0 || P.ns == 0 || L.n_struct == 0) return IB_OK;
+  if (!op_elastic(P) || L.n_struct == 0) return IB_OK;
   double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
   KScope ks(P, IB_KC_SETUP, 0.0);
   k_assemble_E<0><<<nblk(256L * P.np), TPB, 0, P.stream>>>(L.pat64, springs_view<double>(P), L.N,
@@ -517,7 +536,7 @@ int launch_assemble_struct(Problem& P, int level) {
 }
 
 int launch_assemble_coarse(Problem& P) {
-  if (P.np == 0 || P.ns == 0) return IB_OK;
+  if (!op_elastic(P)) return IB_OK;
   LevelInfo& L = P.lev[P.nlev - 1];
   double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
   KScope ks(P, IB_KC_SETUP, 0.0);

@@ -187,6 +187,8 @@ extern "C" int ib_apply_noalloc(const ib_params* prm, int32_t n_points, const do
     return fail(IB_ERR_INVALID_ARG, "L, mu, dt must be > 0 and rho >= 0");
   if (prm->delta != IB_DELTA_PESKIN4 && prm->delta != IB_DELTA_COS4)
     return fail(IB_ERR_INVALID_ARG, "unknown delta kernel");
+  if (prm->walls != IB_WALLS_PERIODIC)
+    return fail(IB_ERR_INVALID_ARG, "ib_apply_noalloc is for the periodic square only");
   if (n_points < 0 || n_springs < 0) return fail(IB_ERR_INVALID_ARG, "negative counts");
   if (n_points > IB_NOALLOC_MAX_POINTS)
     return fail(IB_ERR_INVALID_ARG, "n_points exceeds IB_NOALLOC_MAX_POINTS (65536), the size of the "

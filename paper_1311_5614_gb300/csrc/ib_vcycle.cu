@@ -103,6 +103,7 @@ StokesCoef<T> coefs(const Problem& P, int l) {
   c.diag = (T)(-4.0 * P.prm.mu / (h * h) - reac);
   c.off = (T)(P.prm.mu / (h * h));
   c.g = (T)(1.0 / h);
+  c.walls = P.prm.walls;
   return c;
 }
 
@@ -853,12 +854,12 @@ bool launch_box_form(Problem& P, int l, int form, T* w, const T* b, T* E, int co
         vlaunch(pdl, kv_boxg<T, TM, 4>, nblk(nbox, BoxGemm<TM, 4>::BPC), 128, 0, P.stream, w, b, E, L.N, c, color,
                 L.flag, Ms, Mf);
       return true;
-    case BOXF_STRIP8:
-      return bs == 4 && half % 8 == 0 && launch_strip<T, TM, 8>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+    case BOXF_STRIP8:  // the strip kernel stages periodic rows: not with walls
+      return bs == 4 && !P.prm.walls && half % 8 == 0 && launch_strip<T, TM, 8>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
     case BOXF_STRIP16:
-      return bs == 4 && half % 16 == 0 && launch_strip<T, TM, 16>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+      return bs == 4 && !P.prm.walls && half % 16 == 0 && launch_strip<T, TM, 16>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
     case BOXF_STRIP32:
-      return bs == 4 && half % 32 == 0 && launch_strip<T, TM, 32>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+      return bs == 4 && !P.prm.walls && half % 32 == 0 && launch_strip<T, TM, 32>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
     default:
       return false;
   }
@@ -882,7 +883,7 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const bool gemm = nbox >= P.box_gemm_min;
   const bool one = nbox <= P.box_one_max;
   const bool pdl = use_pdl(P);
-  if (P.prm.box == 4 && P.box_strip && nbox >= P.box_strip_min) {
+  if (P.prm.box == 4 && P.box_strip && !P.prm.walls && nbox >= P.box_strip_min) {
     bool done = false;
     switch (strip_width(P, L.N)) {
       case 32: done = launch_strip<T, TM, 32>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf); break;
@@ -996,13 +997,13 @@ __global__ void kv_resres(const T* __restrict__ w, const T* __restrict__ b, cons
 
 // w += P e; also clears rE (the restriction's elasticity term; may be NULL).
 template <typename T>
-__global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N, T* __restrict__ rE) {
+__global__ void kv_prolong(const T* __restrict__ ec, T* __restrict__ wf, int N, T* __restrict__ rE, int walls) {
   pdl_enter();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int n = N * N;
   if (idx >= n) return;
   T cu, cv, cp;
-  prolong_cell(ec, N, idx & (N - 1), idx / N, &cu, &cv, &cp);
+  prolong_cell(ec, N, idx & (N - 1), idx / N, &cu, &cv, &cp, walls);
   wf[idx] += cu;
   wf[n + idx] += cv;
   wf[2 * n + idx] += cp;
@@ -1068,8 +1069,9 @@ __device__ __forceinline__ T window_row(const TailLevel<T, TM>& L, const T* w, i
   *row = r;
   const T* e0 = L.Ew + (size_t)t * WIN;
   // differences from the component's value at the row's index: each row of E_l sums
-  // to zero over each column component (uniform velocities are in its kernel)
-  const T ref[2] = {w[j * N + i], w[n + j * N + i]};
+  // to zero over each column component (uniform velocities are in its kernel); with
+  // no-slip walls the plain sum (the wall prolongation does not keep constants)
+  const T ref[2] = {L.c.walls ? (T)0 : w[j * N + i], L.c.walls ? (T)0 : w[n + j * N + i]};
   T acc = 0;
   for (int e = 0; e < WIN; ++e) {
     const int cc = e / WSQ, rem = e - cc * WSQ;
@@ -1355,7 +1357,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T, TM> A) {
     const int Nc = L.N / 2, ncell = Nc * Nc;
     for (int e = tid; e < ncell; e += nt) {
       T ru, rv, rp;
-      restrict_cell(r, L.N, e % Nc, e / Nc, &ru, &rv, &rp);
+      restrict_cell(r, L.N, e % Nc, e / Nc, &ru, &rv, &rp, L.c.walls);
       B[l + 1][e] = ru;
       B[l + 1][ncell + e] = rv;
       B[l + 1][2 * ncell + e] = rp;
@@ -1378,7 +1380,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) kv_tail(TailArgs<T, TM> A) {
     const int N = L.N, n = N * N;
     for (int e = tid; e < n; e += nt) {
       T cu, cv, cp;
-      prolong_cell(W[l + 1], N, e & (N - 1), e / N, &cu, &cv, &cp);
+      prolong_cell(W[l + 1], N, e & (N - 1), e / N, &cu, &cv, &cp, L.c.walls);
       W[l][e] += cu;
       W[l][n + e] += cv;
       W[l][2 * n + e] += cp;
@@ -1412,7 +1414,7 @@ int build_tail_args(Problem& P, int lt, TailArgs<T, TM>* A, size_t* smem_bytes, 
     return o;
   };
   int max_boxes = 1;
-  A->has_E = P.np > 0 && P.ns > 0;
+  A->has_E = op_elastic(P);
   for (int q = 0; q < A->nlev; ++q) {
     int l = lt + q;
     LevelInfo& L = P.lev[l];
@@ -1499,7 +1501,7 @@ int fine_sweep(Problem& P, int l, bool rev, bool w_is_zero) {
   LevelInfo& L = P.lev[l];
   LevelBuf<T>& B = lbuf<T>(L);
   const int N = L.N, bs = P.prm.box;
-  const bool has_E = P.np > 0 && P.ns > 0;
+  const bool has_E = op_elastic(P);
   const StokesCoef<T> c = coefs<T>(P, l);
   const int half = L.nb / 2;
   const long nbox = (long)half * half;
@@ -1539,7 +1541,7 @@ constexpr int pix() { return sizeof(T) == 8 ? 1 : 0; }
 template <typename T, typename TM>
 int vcycle_eager_t(Problem& P) {
   const int lt = P.tail_level[pix<T>()];
-  const bool has_E = P.np > 0 && P.ns > 0;
+  const bool has_E = op_elastic(P);
   for (int l = 0; l < lt; ++l) {
     LevelInfo& L = P.lev[l];
     LevelBuf<T>& B = lbuf<T>(L);
@@ -1583,7 +1585,7 @@ int vcycle_eager_t(Problem& P) {
       const double e_bytes = has_E ? 2.0 * L.N * L.N * sizeof(T) : 0.0;
       KScope ks(P, IB_KC_TRANSFER, (6.0 * L.N * L.N + 0.75 * L.N * L.N) * sizeof(T) + e_bytes);
       vlaunch(use_pdl(P), kv_prolong<T>, nblk((long)L.N * L.N), TPB, 0, P.stream,
-              (const T*)lbuf<T>(P.lev[l + 1]).w, B.w, L.N, has_E ? rEbuf<T>(L) : (T*)nullptr);
+              (const T*)lbuf<T>(P.lev[l + 1]).w, B.w, L.N, has_E ? rEbuf<T>(L) : (T*)nullptr, (int)P.prm.walls);
       IB_LAUNCH_CHECK();
     }
     for (int s = 0; s < P.prm.nu2; ++s) IB_TRY((fine_sweep<T, TM>(P, l, P.prm.box == 1, false)));

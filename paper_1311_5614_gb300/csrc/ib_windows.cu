@@ -137,8 +137,11 @@ __device__ __forceinline__ double pw(bool normal, int o) {
 // T[s][cc][dJ + TR][dI + TR] is the entry at coarse column (cc, I0 + dI, J0 + dJ),
 // (I0, J0) = (i >> 1, j >> 1) of the fine row (i, j); |dI|, |dJ| <= TR = 3 covers
 // every coarse column P reaches from the row's window.
+// With no-slip walls (walls = 1) P is the wall prolongation: coarse columns beyond
+// the grid and coarse wall faces have no entries, and next to a wall the ghost folds
+// the far row's 1/4 onto the near one (fine row 0 takes 1/2 of coarse row 0).
 __global__ void k_window_EP(const int* __restrict__ slot_row, int nrows, int Nf, const double* __restrict__ Ef,
-                            double* __restrict__ T) {
+                            double* __restrict__ T, int walls) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= (long)nrows * TWIN) return;
   const int s = (int)(t / TWIN), e = (int)(t - (long)s * TWIN);
@@ -151,17 +154,32 @@ __global__ void k_window_EP(const int* __restrict__ slot_row, int nrows, int Nf,
   // coarse column (cc, I0 + dI, J0 + dJ): fine columns 2 (I0 + dI) + ox, 2 (J0 + dJ) + oy
   const bool nx = cc == 0, ny = cc == 1;  // u: normal in x; v: normal in y
   const double* row = Ef + (size_t)s * WIN + cc * WSQ;
+  const int Nc = Nf / 2, Cx = I0 + dI, Cy = J0 + dJ;
   double acc = 0.0;
+  if (walls && (Cx < 0 || Cx >= Nc || Cy < 0 || Cy >= Nc || (nx && Cx == 0) || (ny && Cy == 0))) {
+    T[(size_t)s * TWIN + e] = 0.0;
+    return;
+  }
   for (int oy = -1; oy <= 2; ++oy) {
-    const double wy = pw(ny, oy);
+    double wy = pw(ny, oy);
     if (wy == 0.0) continue;
-    const int dj = 2 * (J0 + dJ) + oy - j;
+    const int dj = 2 * Cy + oy - j;
     if (dj < -WR || dj > WR) continue;
+    if (walls) {
+      const int F = 2 * Cy + oy;
+      if (F < 0 || F >= Nf) continue;
+      if (!ny && ((Cy == 0 && oy == 0) || (Cy == Nc - 1 && oy == 1))) wy = 0.5;
+    }
     for (int ox = -1; ox <= 2; ++ox) {
-      const double wx = pw(nx, ox);
+      double wx = pw(nx, ox);
       if (wx == 0.0) continue;
-      const int di = 2 * (I0 + dI) + ox - i;
+      const int di = 2 * Cx + ox - i;
       if (di < -WR || di > WR) continue;
+      if (walls) {
+        const int F = 2 * Cx + ox;
+        if (F < 0 || F >= Nf) continue;
+        if (!nx && ((Cx == 0 && ox == 0) || (Cx == Nc - 1 && ox == 1))) wx = 0.5;
+      }
       acc += row[(dj + WR) * WD + di + WR] * wx * wy;
     }
   }
@@ -171,9 +189,10 @@ __global__ void k_window_EP(const int* __restrict__ slot_row, int nrows, int Nf,
 // Galerkin step 2: E_c = R T for every coarse structure row (one thread per window
 // entry).  R (sec. 3.1, Eqs. 25-26): u at coarse (I, J) from fine faces 2I - 1, 2I,
 // 2I + 1 (weights 1, 2, 1) on rows 2J, 2J + 1, times 1/8; v transposed.
+// With no-slip walls a coarse wall face has no row (its entries are zero).
 __global__ void k_window_R(const int* __restrict__ slot_row_c, int nrows_c, int Nc,
                            const int* __restrict__ rowslot_f, const double* __restrict__ T,
-                           double* __restrict__ Ec) {
+                           double* __restrict__ Ec, int walls) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= (long)nrows_c * WIN) return;
   const int S = (int)(t / WIN), e = (int)(t - (long)S * WIN);
@@ -183,6 +202,10 @@ __global__ void k_window_R(const int* __restrict__ slot_row_c, int nrows_c, int 
   const int nc = Nc * Nc, c = R / nc, Rr = R - c * nc, I = Rr % Nc, J = Rr / Nc;
   const int Nf = 2 * Nc, nf = Nf * Nf;
   double acc = 0.0;
+  if (walls && wall_face(c, I, J)) {
+    Ec[(size_t)S * WIN + e] = 0.0;
+    return;
+  }
   for (int a = -1; a <= 1; ++a) {      // normal direction offset: weights 1, 2, 1
     for (int bb = 0; bb <= 1; ++bb) {  // centred direction: rows 2J, 2J + 1 (v: columns)
       const double wr = (a == 0 ? 0.25 : 0.125);
@@ -259,7 +282,7 @@ __global__ void k_window_cast(const double* __restrict__ a, float* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) kv_window_apply(const int* __restrict__ slot_row, const int* __restrict__ nrows_dev,
                                                        const T* __restrict__ Ew, const T* __restrict__ w, int N,
-                                                       T coef, int b, int color, T* __restrict__ y) {
+                                                       T coef, int b, int color, int walls, T* __restrict__ y) {
   const int warp = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   int r = -1, c = 0, i = 0, j = 0;
   if (warp < *nrows_dev) {
@@ -269,7 +292,7 @@ __global__ void __launch_bounds__(256) kv_window_apply(const int* __restrict__ s
     const int rr = r - c * n;
     i = rr % N;
     j = rr / N;
-    if (!row_in_color(c, i, j, b, color)) r = -1;
+    if (!row_in_color(c, i, j, b, color) || (walls && wall_face(c, i, j))) r = -1;
   }
   pdl_enter();
   if (r < 0) return;  // the whole warp leaves together
@@ -279,8 +302,10 @@ __global__ void __launch_bounds__(256) kv_window_apply(const int* __restrict__ s
   // is in the kernel of E_l: J annihilates translations, P reproduces constants), so
   // the entries multiply differences from the component's value at the row's own
   // index; a structure moving almost rigidly then keeps the accuracy of the
-  // per-point form, which works on velocity differences
-  const T ref[2] = {w[(size_t)j * N + i], w[n + (size_t)j * N + i]};
+  // per-point form, which works on velocity differences.  With no-slip walls the
+  // prolongation does not reproduce constants next to a wall, so the coarse rows
+  // need not sum to zero there: the plain sum is taken.
+  const T ref[2] = {walls ? (T)0 : w[(size_t)j * N + i], walls ? (T)0 : w[n + (size_t)j * N + i]};
   T acc = 0;
 #pragma unroll 4
   for (int e = lane; e < WIN; e += 32) {
@@ -293,9 +318,9 @@ __global__ void __launch_bounds__(256) kv_window_apply(const int* __restrict__ s
   if (lane == 0) y[r] += coef * acc;
 }
 template __global__ void kv_window_apply<double>(const int*, const int*, const double*, const double*, int, double,
-                                                 int, int, double*);
+                                                 int, int, int, double*);
 template __global__ void kv_window_apply<float>(const int*, const int*, const float*, const float*, int, float, int,
-                                                int, float*);
+                                                int, int, float*);
 
 // ---------------------------------------------------------------- launchers
 
@@ -334,12 +359,13 @@ int launch_window_galerkin(Problem& P, int level) {
   if (C.n_rows == 0) return IB_OK;
   if (F.n_rows > 0) {
     KScope ks(P, IB_KC_SETUP, (double)F.n_rows * (WIN + TWIN) * 8.0);
-    k_window_EP<<<nblk((long)F.n_rows * TWIN), TPB, 0, P.stream>>>(F.slot_row, F.n_rows, F.N, F.Ew64, P.Twin);
+    k_window_EP<<<nblk((long)F.n_rows * TWIN), TPB, 0, P.stream>>>(F.slot_row, F.n_rows, F.N, F.Ew64, P.Twin,
+                                                                    P.prm.walls);
     IB_LAUNCH_CHECK();
   }
   KScope ks(P, IB_KC_SETUP, (double)C.n_rows * (6.0 * TWIN + WIN) * 8.0);
   k_window_R<<<nblk((long)C.n_rows * WIN), TPB, 0, P.stream>>>(C.slot_row, C.n_rows, C.N, F.rowslot, P.Twin,
-                                                                C.Ew64);
+                                                                C.Ew64, P.prm.walls);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
@@ -404,7 +430,7 @@ int launch_window_apply(Problem& P, int level, const T* w, T* y, double coef, in
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
   IB_CUDA_TRY(cudaLaunchKernelEx(&cfg, kv_window_apply<T>, (const int*)L.slot_row, (const int*)(P.count + 1 + level),
-                                 window_of<T>(L), w, L.N, (T)coef, P.prm.box, color, y));
+                                 window_of<T>(L), w, L.N, (T)coef, P.prm.box, color, (int)P.prm.walls, y));
   return IB_OK;
 }
 template int launch_window_apply<double>(Problem&, int, const double*, double*, double, int, bool);

@@ -48,8 +48,9 @@ def test_version_and_defaults(capi):
     p = capi.ib_default_params()
     assert (p.N, p.box, p.nu1, p.nu2, p.max_iters) == (64, 1, 1, 1, 100)
     assert p.tol == 1e-8 and p.rho == 1.0 and p.mu == 1.0 and p.dt == 1e-2
-    assert ctypes.sizeof(capi.ib_params) == 88
+    assert ctypes.sizeof(capi.ib_params) == 104  # include/ib.h's ib_params, natural alignment
     assert p.escalate == 1 and p.restart == 0
+    assert p.walls == 0 and p.lid == 0.0 and p.time_method == 0  # periodic, at rest, implicit
 
 
 @pytest.mark.parametrize("field,value", [

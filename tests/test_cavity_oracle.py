@@ -273,3 +273,20 @@ def test_table2_iteration_counts():
                 else:
                     want = int(r[col])
                     assert lo is not None and lo <= want <= hi, (b, nu1, nu2, rel, want, lo, hi)
+
+
+def test_workload_annulus_matches_oracle():
+    """The shared input generator builds the same annulus the oracle pins (both restate
+    sec. 4's formula), its fibres closed chains of zero-rest-length springs."""
+    import ib_workloads as W
+
+    for N in (32, 64):
+        p = W.cavity_annulus(N, kappa=3.0)
+        a = C.Annulus(N)
+        assert np.array_equal(p.X, a.points())
+        assert (p.meta["M1"], p.meta["M2"]) == (a.M1, a.M2) and p.meta["ds1"] == a.ds1
+        assert p.springs.shape == (a.M1 * a.M2, 2) and np.all(p.rest == 0.0) and np.all(p.kappa == 3.0)
+        # every point has exactly two springs, to its neighbours on the same fibre
+        deg = np.bincount(p.springs.ravel(), minlength=p.X.shape[0])
+        assert np.all(deg == 2)
+        assert np.all(p.springs[:, 0] // a.M1 == p.springs[:, 1] // a.M1)
