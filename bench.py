@@ -609,6 +609,65 @@ def run_cavity(args):
     return 0
 
 
+def run_cavity_time(args):
+    """What the implicit method saves (sec. 7), on the paper's cavity: the lid-driven
+    cavity with the thick annulus (lid velocity 1) advanced to t = 1 by the
+    implicit-time method (dt = 1/40, 40 steps, the paper's step) and by the explicit-
+    time method at 0.9 of its stability limit (dt = 0.9 alpha_exp / gamma; 40 steps
+    run and the work extrapolated to t = 1, as the paper does), at relative
+    stiffness gamma dt / alpha_exp = 1, 10, 100, 500 for the implicit step, box
+    sizes 4 and 8, MG-GMRES to 1e-6 per step.  The efficiency factor is the ratio of
+    the explicit method's work to the implicit one's, counted in MG-GMRES
+    iterations (the paper's measure) and in GPU time (set-up + solve per step, CUDA
+    events inside ib_solve_step).  alpha_exp = 3.93 at N = 64 is the paper's Table 1
+    value (the cavity oracle reproduces it)."""
+    import torch
+
+    from paper_1311_5614_gb300 import capi as C
+
+    torch.cuda.set_device(args.local_rank)
+    N, T, dt_i, a_exp = 64, 1.0, 1.0 / 40.0, 3.93
+    rows = []
+    for b in (4, 8):
+        for rel in (1.0, 10.0, 100.0, 500.0):
+            gamma = rel * a_exp / dt_i
+            res = {"box": b, "rel_stiffness": rel, "gamma": gamma}
+            for method, dt in (("implicit", dt_i), ("explicit", 0.9 * a_exp / gamma)):
+                p = W.cavity_annulus(N, kappa=gamma, dt=dt)
+                s = C.IBSolver(N, p.X, p.springs, p.kappa, p.rest, L=1.0, rho=0.0, mu=1.0, dt=dt, delta="cos4",
+                               box=b, walls="noslip", lid=1.0, precision=args.precision, tol=1e-6, max_iters=100,
+                               time_method=method)
+                X = torch.tensor(p.X, device="cuda")
+                up = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
+                its, ms, bad = [], [], 0
+                for _ in range(40):
+                    st = s.solve_step(None, up, X)
+                    bad += st["status"] != 0
+                    its.append(st["iters"])
+                    ms.append(st["t_setup_ms"] + st["t_solve_ms"])
+                s.close()
+                steps = T / dt
+                res[method] = {"dt": dt, "steps_to_t1": steps, "iters_per_step": float(np.mean(its)),
+                               "ms_per_step": float(np.mean(ms)), "failed_steps": bad,
+                               "iters_to_t1": steps * float(np.mean(its)), "ms_to_t1": steps * float(np.mean(ms))}
+            res["efficiency_iters"] = res["explicit"]["iters_to_t1"] / res["implicit"]["iters_to_t1"]
+            res["efficiency_time"] = res["explicit"]["ms_to_t1"] / res["implicit"]["ms_to_t1"]
+            rows.append(res)
+    big = [r for r in rows if r["box"] == 8 and r["rel_stiffness"] == 100.0][0]
+    line = {"metric": "implicit vs explicit time to t = 1 on the paper's cavity (efficiency factor, GPU time)",
+            "value": big["efficiency_time"], "unit": "x (explicit GPU time / implicit GPU time, b = 8, "
+                                                     "relative stiffness 100)",
+            "n_gpus": 1, "steps": 40, "warmup": 0, "higher_is_better": True,
+            "dtype": "f32 V-cycle + f64 Krylov" if args.precision == "fp32" else args.precision,
+            "data": "synthetic (the paper's geometry, no randomness)",
+            "config": {"workload": "lid-driven cavity 64^2, thick annulus, lid velocity 1, t in [0, 1]; "
+                                   "implicit dt = 1/40, explicit dt = 0.9 alpha_exp / gamma",
+                       "precision": args.precision},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned512(args):
     """Learned stage at 512^2 (1024-point ellipse): pairs harvested from the method's own
     V-cycles on problems with kappa = 10^U[2,6], U-Net trained on the GPU with the
@@ -1092,7 +1151,7 @@ def main(argv=None):
     ap.add_argument("--save-params", default=None, help="learned512: write the trained U-Net parameters (.npy)")
     ap.add_argument("--learn-epochs", type=int, default=2)
     ap.add_argument("--workload", default="multi1024",
-                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512", "unet", "cavity"],
+                    choices=["sweep256", "case256", "multi1024", "batch256", "vcycle", "learned512", "unet", "cavity", "cavity_time"],
                     help="multi1024 (default): the 1024^2 sixteen-ellipse run, 20 consecutive steps per "
                          "bench step; sweep256: the 256^2 kappa x dt sweep; batch256: the 256-problem "
                          "batch; vcycle: the V-cycle alone (--grid); learned512: the learned stage")
@@ -1139,6 +1198,8 @@ def main(argv=None):
             return run_learned512(args)
         if args.workload == "cavity":
             return run_cavity(args)
+        if args.workload == "cavity_time":
+            return run_cavity_time(args)
         if args.workload == "unet":
             return run_unet(args)
         if args.workload == "sweep256":

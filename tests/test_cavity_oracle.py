@@ -290,3 +290,30 @@ def test_workload_annulus_matches_oracle():
         deg = np.bincount(p.springs.ravel(), minlength=p.X.shape[0])
         assert np.all(deg == 2)
         assert np.all(p.springs[:, 0] // a.M1 == p.springs[:, 1] // a.M1)
+
+
+@pytest.mark.parametrize("frac,stable", [(0.9, True), (1.3, False)])
+def test_explicit_method_stability_matches_alpha_exp(frac, stable):
+    """Sec. 4.1 by a second route: forward Euler X <- X + alpha S^* L^{-1} S A_f X (the
+    explicit-time method with the structure held at X^0 in S) started from a random
+    X decays for alpha = 0.9 alpha_exp and grows for alpha = 1.3 alpha_exp, alpha_exp
+    from the Lanczos eigenvalue."""
+    N = 32
+    a_exp = _alpha_exp(N)
+    ann = C.Annulus(N)
+    X0 = ann.points()
+    S = C.spread_matrix(X0, N, ann.ds1 ** 2)
+    Ss = C.interp_matrix_from_kernel(X0, N)
+    Af = C.force_operator(ann)
+    solve = C.stokes_velocity_solver(N)
+    alpha = frac * a_exp
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(Af.shape[0])
+    norms = []
+    for _ in range(25):
+        x = x + alpha * (Ss @ solve(S @ (Af @ x)))
+        norms.append(np.linalg.norm(Af @ x))
+    if stable:
+        assert norms[-1] < norms[4], norms
+    else:
+        assert norms[-1] > 100.0 * norms[4], norms

@@ -174,3 +174,71 @@ def test_cavity_point_near_wall_is_refused():
     with pytest.raises(CA.IBError):
         CA.IBSolver(32, X, p.springs, p.kappa, p.rest, rho=0.0, mu=1.0, dt=1.0, delta="cos4", box=4,
                     walls="noslip")
+
+
+def _explicit_solver(p, b, dt, lid=0.0, tol=1e-8):
+    from paper_1311_5614_gb300 import capi as CA
+
+    return CA.IBSolver(p.N, p.X, p.springs, p.kappa, p.rest, L=1.0, rho=0.0, mu=1.0, dt=dt, delta="cos4",
+                       box=b, walls="noslip", tol=tol, max_iters=200, lid=lid, time_method="explicit")
+
+
+def test_cavity_explicit_step_matches_oracle():
+    """One step of the explicit-time method (sec. 2.3.1): the Stokes system alone with
+    the force F(X^n) on the right-hand side, then X^{n+1} = X^n + dt S^* u."""
+    import torch
+
+    N, b, gamma, dt = 64, 4, 50.0, 0.01
+    p = W.cavity_annulus(N, kappa=gamma, dt=dt)
+    lev0 = C.cavity_hierarchy(N, 0.0, b, ann=_geom(p))  # Stokes alone
+    want_b = C.cavity_rhs(N, lev0, ann=_geom(p), force_scale=gamma)
+    s = _explicit_solver(p, b, dt, lid=1.0)
+    try:
+        up = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
+        X = torch.tensor(p.X, device="cuda")
+        st = s.solve_step(None, up, X)
+        assert st["status"] == 0 and st["n_struct_boxes"] > 0
+        x = up.cpu().numpy()
+        A = lev0[0].A
+        assert np.linalg.norm(want_b - A @ x) / np.linalg.norm(want_b) <= 1.05e-8
+        Ss = C.interp_matrix_from_kernel(p.X, N)
+        U = Ss @ x[: 2 * N * N]
+        npt = p.X.shape[0]
+        assert np.abs(X.cpu().numpy() - (p.X + dt * np.stack([U[:npt], U[npt:]], axis=1))).max() <= 1e-12
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("frac,stable", [(0.9, True), (1.3, False)])
+def test_cavity_explicit_stability_limit(frac, stable):
+    """The explicit-time method is stable for gamma dt below alpha_exp (sec. 4.1, Table
+    1: 6.09 at h = 2^-5, the oracle's value) and unstable above: from a small
+    high-frequency perturbation of the annulus, the step-to-step displacement decays
+    at 0.9 alpha_exp and grows at 1.3 alpha_exp (amplification |1 - 2 frac| per step of
+    the stiffest mode)."""
+    import torch
+
+    N, b, gamma = 32, 4, 1.0e4
+    a_exp = C.explicit_limit(N, "ds1^2")[0]
+    dt = frac * a_exp / gamma
+    p = W.cavity_annulus(N, kappa=gamma, dt=dt)
+    rng = np.random.default_rng(3)
+    X0 = p.X + (1e-3 / N) * rng.standard_normal(p.X.shape)
+    s = _explicit_solver(p, b, dt)
+    try:
+        up = torch.zeros(3 * N * N, dtype=torch.float64, device="cuda")
+        X = torch.tensor(X0, device="cuda")
+        s.update_points(X)
+        disp = []
+        for _ in range(12):
+            Xp = X.clone()
+            st = s.solve_step(None, up, X)
+            assert st["status"] == 0
+            disp.append(float(torch.linalg.vector_norm(X - Xp)))
+        growth = disp[-1] / disp[1]
+        if stable:
+            assert growth < 1.0, disp
+        else:
+            assert growth > 10.0, disp
+    finally:
+        s.close()
