@@ -213,7 +213,9 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * FGMRES orthogonalises by classical Gram-Schmidt applied twice, in three
  * passes over the basis; the environment variable IB_CGS_FUSED=0 (read at
  * ib_setup) splits the middle pass in two, the form otherwise taken only when a
- * 64-element slice of the whole basis does not fit in shared memory. */
+ * 64-element slice of the whole basis does not fit in shared memory.  Bases of up
+ * to 16 vectors take a register form of the middle pass; IB_CGS_REG=0 (read at
+ * ib_setup) keeps them on the bulk-copy form. */
 IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,
                   ib_stats* stats);
 

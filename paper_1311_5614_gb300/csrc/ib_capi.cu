@@ -74,7 +74,6 @@ int fail(int code, const std::string& msg) {
 
 namespace {
 
-constexpr int MAX_LEVELS_ALLOC = 32;  // per-level device counters
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -185,6 +184,9 @@ int setup_hierarchy(Problem& P) {
     IB_TRY(launch_mark_struct(P, l));
     IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + l, P.count, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
   }
+  if (P.prm.walls)  // wall boxes without elasticity, per level
+    IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + 65, P.count + 1 + MAX_LEVELS_ALLOC, sizeof(int) * ns,
+                                cudaMemcpyDeviceToHost, P.stream));
   if (win) {
     for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_mark_rows(P, l));
     IB_CUDA_TRY(cudaMemcpyAsync(P.count_host + 32, P.count + 1, sizeof(int) * P.nlev, cudaMemcpyDeviceToHost,
@@ -194,7 +196,9 @@ int setup_hierarchy(Problem& P) {
   const int nB = P.nB;
   for (int l = 0; l < ns; ++l) {
     LevelInfo& L = P.lev[l];
-    int cnt = P.count_host[l];
+    const int ring = P.prm.walls ? P.count_host[65 + l] : 0;
+    int cnt = P.count_host[l] + ring;
+    L.n_form = P.count_host[l];
     if (cnt > L.cap_struct) {
       P.graph_dirty[0] = P.graph_dirty[1] = true;  // the box kernels take the new pointer
       dfree(L.Mstruct);
@@ -230,8 +234,10 @@ int setup_hierarchy(Problem& P) {
   }
   for (int l = 0; l < ns; ++l) {
     if (!P.free_ready) IB_TRY(launch_free_box(P, l));
+    if (P.prm.walls && !P.ring_ready) IB_TRY(launch_ring_prepare(P, l));
     IB_TRY(launch_struct_fill(P, l));
   }
+  if (P.prm.walls) P.ring_ready = true;
   bool use_win = false;
   if (win) {
     IB_TRY(launch_window_points(P));
@@ -260,7 +266,9 @@ int setup_hierarchy(Problem& P) {
   bool all_done = false;
   IB_TRY(launch_invert_struct_all(P, &all_done));
   if (!all_done)
-    for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_struct));
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_form));
+  if (P.prm.walls)
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_ring_copy(P, l));
   P.free_ready = true;
   IB_TRY(launch_coarse_fill(P));
   if (use_win) IB_TRY(launch_coarse_from_windows(P));
@@ -280,6 +288,7 @@ void free_problem(Problem* P) {
     dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);
     dfree(L.rE64); dfree(L.rE32);
     dfree(L.box_of_slot); dfree(L.rowslot); dfree(L.slot_row); dfree(L.Ew64); dfree(L.Ew32);
+    dfree(L.Mring);
   }
   dfree(P->Twin);
   for (auto& g : P->vgraph) {
@@ -393,7 +402,7 @@ int allocate(Problem& P) {
   IB_TRY(dalloc(&P.t64, n));
   IB_TRY(dalloc(&P.t64b, n));
   IB_TRY(dalloc(&P.dev_err, 1));
-  IB_TRY(dalloc(&P.count, 1 + MAX_LEVELS_ALLOC));
+  IB_TRY(dalloc(&P.count, 1 + 2 * MAX_LEVELS_ALLOC));
   IB_CUDA_TRY(cudaMemsetAsync(P.dev_err, 0, sizeof(int), P.stream));
   IB_CUDA_TRY(cudaMallocHost((void**)&P.scal_host, 64 * sizeof(double)));
   IB_CUDA_TRY(cudaMallocHost((void**)&P.count_host, 128 * sizeof(int)));

@@ -106,6 +106,45 @@ __global__ void k_wall_rhs(double* b, int N, double h, double mu, double lid) {
   }
 }
 
+// Position of box (I, J) in the ring of wall boxes of an nb x nb box grid: the first
+// row, the last row, then the first and last column between them.
+__host__ __device__ inline int ring_index(int I, int J, int nb) {
+  if (nb == 1) return 0;
+  if (J == 0) return I;
+  if (J == nb - 1) return nb + I;
+  return 2 * nb + 2 * (J - 1) + (I == 0 ? 0 : 1);
+}
+__host__ __device__ inline int ring_count(int nb) { return nb == 1 ? 1 : 4 * nb - 4; }
+
+// Stokes blocks of all wall boxes of a level, in ring order (for their inverses).
+__global__ void k_ring_stokes(double* M, int nring, int N, int b, StokesCoef<double> c) {
+  const int nB = box_nunk(b), nb = N / b;
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)nring * nB * nB) return;
+  const int r = (int)(e / ((long)nB * nB)), rem = (int)(e - (long)r * nB * nB);
+  int I = 0, J = 0;
+  if (nb > 1) {
+    if (r < nb) { I = r; J = 0; }
+    else if (r < 2 * nb) { I = r - nb; J = nb - 1; }
+    else { const int q = r - 2 * nb; J = 1 + q / 2; I = (q & 1) ? nb - 1 : 0; }
+  }
+  const int q = rem % nB, t = rem / nB;
+  int cq, iq, jq, ct, it, jt;
+  box_unknown(q, b, I * b, J * b, N, &cq, &iq, &jq);
+  box_unknown(t, b, I * b, J * b, N, &ct, &it, &jt);
+  M[e] = stokes_entry(c, N, cq, iq, jq, ct, it, jt);
+}
+
+// Slots [first, first + count) take their wall box's cached inverse.
+__global__ void k_ring_copy(double* __restrict__ Ms, const int* __restrict__ box_of_slot, int first, int count,
+                            const double* __restrict__ Mring, int nb, int nB2) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)count * nB2) return;
+  const int k = (int)(e / nB2), rem = (int)(e - (long)k * nB2);
+  const int s = first + k, box = box_of_slot[s];
+  Ms[(size_t)s * nB2 + rem] = Mring[(size_t)ring_index(box % nb, box / nb, nb) * nB2 + rem];
+}
+
 __global__ void k_replicate(const double* __restrict__ src, double* dst, int m, long count) {
   long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= (long)m * count) return;
@@ -464,19 +503,45 @@ int launch_wall_rhs(Problem& P, double* b) {
   return IB_OK;
 }
 
+// The inverses of every wall box of a level (no-slip walls), computed once.
+int launch_ring_prepare(Problem& P, int level) {
+  LevelInfo& L = P.lev[level];
+  const int nB = P.nB, nring = ring_count(L.nb);
+  if (!L.Mring) IB_TRY(dalloc(&L.Mring, (size_t)nring * nB * nB));
+  L.nring = nring;
+  const long tot = (long)nring * nB * nB;
+  {
+    KScope ks(P, IB_KC_SETUP, tot * 8.0);
+    k_ring_stokes<<<nblk(tot), TPB, 0, P.stream>>>(L.Mring, nring, L.N, P.prm.box, coef_of<double>(P, level));
+    IB_LAUNCH_CHECK();
+  }
+  return launch_invert(P, L.Mring, nB, nring);
+}
+
+int launch_ring_copy(Problem& P, int level) {
+  LevelInfo& L = P.lev[level];
+  const int count = L.n_struct - L.n_form, nB2 = P.nB * P.nB;
+  if (count <= 0) return IB_OK;
+  const long tot = (long)count * nB2;
+  KScope ks(P, IB_KC_SETUP, tot * 16.0);
+  k_ring_copy<<<nblk(tot), TPB, 0, P.stream>>>(L.Mstruct, L.box_of_slot, L.n_form, count, L.Mring, L.nb, nB2);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
 // Every structure slot starts from the Stokes block of its box: the free box's
 // (periodic), or with no-slip walls the block at the box's own position.
 int launch_struct_fill(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
   int nB = P.nB;
-  if (L.n_struct > 0) {
-    long tot = (long)nB * nB * L.n_struct;
+  if (L.n_form > 0) {
+    long tot = (long)nB * nB * L.n_form;
     KScope ks(P, IB_KC_SETUP, tot * (P.prm.walls ? 8.0 : 16.0));
     if (P.prm.walls)
-      k_struct_stokes<<<nblk(tot), TPB, 0, P.stream>>>(L.Mstruct, L.box_of_slot, L.n_struct, L.N, P.prm.box,
+      k_struct_stokes<<<nblk(tot), TPB, 0, P.stream>>>(L.Mstruct, L.box_of_slot, L.n_form, L.N, P.prm.box,
                                                       coef_of<double>(P, level));
     else
-      k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Sfree, L.Mstruct, nB * nB, L.n_struct);
+      k_replicate<<<nblk(tot), TPB, 0, P.stream>>>(L.Sfree, L.Mstruct, nB * nB, L.n_form);
     IB_LAUNCH_CHECK();
   }
   return IB_OK;
@@ -522,7 +587,7 @@ int launch_invert_struct_all(Problem& P, bool* done) {
   for (int l = 0; l < P.nlev - 1; ++l) {
     B.M[B.narr] = P.lev[l].Mstruct;
     B.start[B.narr] = tot;
-    tot += P.lev[l].n_struct;
+    tot += P.lev[l].n_form;
     ++B.narr;
   }
   B.start[B.narr] = tot;

@@ -174,6 +174,8 @@ __device__ inline double stokes_entry(const StokesCoef<double>& c, int N, int ca
   return v;
 }
 
+constexpr int MAX_LEVELS_ALLOC = 32;  // per-level device counters
+
 // ---------------------------------------------------------------- problem state
 template <typename T>
 struct LevelBuf {
@@ -186,8 +188,13 @@ struct LevelInfo {
   int N = 0;
   double h = 0.0;
   int nb = 0;          // boxes per side (smoothing levels)
-  int n_struct = 0;    // structure boxes found at the last set-up
+  int n_struct = 0;    // structure boxes found at the last set-up (slots in use)
+  int n_form = 0;      // of them formed and inverted at each set-up: slots [0, n_form); slots
+                       // [n_form, n_struct) are no-slip wall boxes without elasticity, whose
+                       // inverses are copied from Mring
   int cap_struct = 0;  // allocated structure-box slots
+  double* Mring = nullptr;  // no-slip walls: [4 (nb - 1)][nB * nB] inverses of the wall boxes
+  int nring = 0;            // (their blocks depend on the grid only: computed once)
   int* flag = nullptr;        // [nb * nb] structure flag -> slot (-1 free)
   double* Mstruct = nullptr;  // [cap][nB * nB] inverse (column-major), FP64
   double* Sfree = nullptr;    // [nB * nB] Stokes block of a box (column-major), FP64
@@ -262,6 +269,7 @@ struct Problem {
   int nlev = 0;
   int nB = 0;  // unknowns per box
   bool free_ready = false;  // free-box inverses computed (they do not depend on the points)
+  bool ring_ready = false;  // no-slip wall-box inverses computed (likewise)
   std::vector<LevelInfo> lev;
 
   // structure (device)
@@ -312,6 +320,8 @@ struct Problem {
   int occ_multidot = 0;       // resident blocks per SM of the partial-dot kernel
   int occ_subnorm = 0;        // ... and of the last Gram-Schmidt subtraction
   std::vector<int> occ_cgs;   // resident blocks per SM of the fused pass, by basis size
+  int occ_cgs_reg[2] = {0, 0};  // ... of its register form for bases of <= 8 and <= 16 vectors
+  bool cgs_reg = true;          // register form for bases of <= 16 vectors (IB_CGS_REG=0: off)
   bool cgs_fused = true;      // middle Gram-Schmidt step as one fused pass
   unsigned long long wait_limit_ns = 1000000000ull;  // bounded device-side waits (IB_WAIT_LIMIT_NS)
   int* count = nullptr;       // device counters: [0] structure boxes, [1 + l] structure rows of level l
@@ -416,6 +426,8 @@ int launch_pressure_mean_remove(Problem& P, double* w);
 // method (IB_EXPLICIT keeps the structure's force on the right-hand side only).
 inline bool op_elastic(const Problem& P) { return P.np > 0 && P.ns > 0 && P.prm.time_method == IB_IMPLICIT; }
 int launch_zero_walls(Problem& P, double* w);  // no-slip walls: w = 0 on the wall faces
+int launch_ring_prepare(Problem& P, int level); // ... the wall boxes' inverses (once)
+int launch_ring_copy(Problem& P, int level);    // ... into their slots (every set-up)
 int launch_wall_rhs(Problem& P, double* b);    // ... and the moving lid's ghost term
 
 }  // namespace ib

@@ -229,13 +229,63 @@ __global__ void k_multiaxpy(const double* __restrict__ V, int nvec, long n,
   w[e] = s;
 }
 
-// y = x * s or y = x / s with the scalar s on the device
+// y = x * s or y = x * (1 / s) with the scalar s on the device; the reciprocal is
+// formed once per block (an FP64 division per element would cost more than the copy)
 __global__ void k_scale_copy(const double* __restrict__ x, const double* __restrict__ s, double* y,
                              long n, int invert) {
+  __shared__ double sa;
+  if (threadIdx.x == 0) sa = invert ? 1.0 / *s : *s;
+  __syncthreads();
   long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  double a = *s;
-  y[e] = invert ? x[e] / a : x[e] * a;
+  y[e] = x[e] * sa;
+}
+
+// The fused middle step of classical Gram-Schmidt applied twice for a small basis
+// (nvec <= K): w <- w - sum_i coef_i V_i and partial[block][i] = V_i . w (the
+// updated w) over the block's contiguous range of elements.  Each thread keeps its
+// element's nvec basis values in registers between the subtraction and the dots,
+// so V is read once; the partial sums go through warp shuffles and shared memory
+// in a fixed order.
+template <int K>
+__global__ void __launch_bounds__(TPB) k_cgs_sub_dot_reg(const double* __restrict__ V, int nvec, long n,
+                                                         const double* __restrict__ coef, double* __restrict__ w,
+                                                         double* __restrict__ partial, int stride, long per) {
+  __shared__ double c[K];
+  __shared__ double red[TPB / 32][K];
+  if (threadIdx.x < K) c[threadIdx.x] = threadIdx.x < nvec ? coef[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  const long e0 = (long)blockIdx.x * per, e1 = e0 + per < n ? e0 + per : n;
+  for (long e = e0 + threadIdx.x; e < e1; e += TPB) {
+    double v[K];
+    double s = w[e];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      v[i] = i < nvec ? V[(size_t)i * n + e] : 0.0;
+      s -= c[i] * v[i];
+    }
+    w[e] = s;
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] += v[i] * s;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    double a = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) red[wid][i] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < nvec) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < TPB / 32; ++q) t += red[q][threadIdx.x];
+    partial[(size_t)blockIdx.x * stride + threadIdx.x] = t;
+  }
 }
 
 // Givens step of FGMRES iteration j, one block.  H (column-major, ld m + 1)
@@ -348,6 +398,10 @@ int krylov_init(Problem& P) {
   // (to test it: it is otherwise reached only above ~450 basis vectors)
   const char* e = std::getenv("IB_CGS_FUSED");
   P.cgs_fused = !(e && e[0] == '0');
+  // IB_CGS_REG=0 keeps bases of up to 16 vectors on the bulk-copy form too (its
+  // bounded waits are what the wait-limit test exercises)
+  const char* er = std::getenv("IB_CGS_REG");
+  P.cgs_reg = !(er && er[0] == '0');
   IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_multidot, k_multidot_partial, TPB, 0));
   IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_subnorm, k_sub_norm, TPB, 0));
   return IB_OK;
@@ -388,6 +442,26 @@ int launch_dot(Problem& P, const double* a, const double* b, double* out) { retu
 // Falls back to two passes when the chunk of V does not fit in shared memory.
 int launch_cgs_sub_dot(Problem& P, const double* V, int nvec, const double* coef, double* w, double* out) {
   const long n = nvec_len(P);
+  if (nvec <= 16 && P.cgs_fused && P.cgs_reg) {  // small basis: the register form, one wave of blocks
+    if (P.occ_cgs_reg[0] == 0) {
+      IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_cgs_reg[0], k_cgs_sub_dot_reg<8>, TPB, 0));
+      IB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ_cgs_reg[1], k_cgs_sub_dot_reg<16>, TPB, 0));
+      P.occ_cgs_reg[0] = std::max(1, P.occ_cgs_reg[0]);
+      P.occ_cgs_reg[1] = std::max(1, P.occ_cgs_reg[1]);
+    }
+    const int occ = nvec <= 8 ? P.occ_cgs_reg[0] : P.occ_cgs_reg[1];
+    const int cols = (int)std::min<long>({(long)P.n_sm * occ, (long)nblk(n), (long)P.dot_blocks});
+    {
+      KScope ks(P, IB_KC_KRYLOV, (nvec + 2.0) * n * 8.0);
+      if (nvec <= 8)
+        k_cgs_sub_dot_reg<8><<<cols, TPB, 0, P.stream>>>(V, nvec, n, coef, w, P.dots, P.max_m + 2, range_per(n, cols));
+      else
+        k_cgs_sub_dot_reg<16><<<cols, TPB, 0, P.stream>>>(V, nvec, n, coef, w, P.dots, P.max_m + 2,
+                                                          range_per(n, cols));
+      IB_LAUNCH_CHECK();
+    }
+    return multidot_final(P, nvec, cols, out);
+  }
   const size_t smem = ((size_t)nvec * CGS_CH + CGS_CH + 2ul * nvec) * sizeof(double);
   if (!P.cgs_fused || smem > (size_t)P.cgs_smem_max || (n & 1)) {
     IB_TRY(launch_multiaxpy(P, V, nvec, coef, w));

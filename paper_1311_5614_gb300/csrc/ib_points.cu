@@ -279,24 +279,35 @@ __global__ void k_mark(Patches<double> pat, int np, int N, int b, int nb, int* f
 
 // No-slip walls: the boxes along the walls (first and last row and column of boxes)
 // hold wall faces and ghost rows, so their blocks differ from the free box's: they
-// get structure slots (their own inverses).
+// get structure slots (their own inverses).  Those no structure row reaches are
+// marked -2: their blocks do not change from step to step, so their slots come
+// after the others' and take inverses computed once (k_assign_ring).
 __global__ void k_mark_ring(int nb, int* flag) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb * nb) return;
   const int I = t % nb, J = t / nb;
-  if (I == 0 || J == 0 || I == nb - 1 || J == nb - 1) flag[t] = 1;
+  if ((I == 0 || J == 0 || I == nb - 1 || J == nb - 1) && flag[t] == 0) flag[t] = -2;
 }
 
 __global__ void k_assign_slots(int* flag, int nbox, int* count, int* box_of_slot) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nbox) return;
-  if (flag[t]) {
+  if (flag[t] > 0) {
     const int s = atomicAdd(count, 1);
     flag[t] = s;
     box_of_slot[s] = t;
-  } else {
+  } else if (flag[t] == 0) {
     flag[t] = -1;
   }
+}
+
+// Slots after the formed ones (count_form of them) for the wall boxes marked -2.
+__global__ void k_assign_ring(int* flag, int nbox, const int* count_form, int* count_ring, int* box_of_slot) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nbox || flag[t] != -2) return;
+  const int s = *count_form + atomicAdd(count_ring, 1);
+  flag[t] = s;
+  box_of_slot[s] = t;
 }
 
 // Add coef * (S_l J S^*_l) restricted to box rows/cols to the dense box blocks.
@@ -520,6 +531,12 @@ int launch_mark_struct(Problem& P, int level) {
   KScope ks(P, IB_KC_SETUP, nbox * 8.0);
   k_assign_slots<<<nblk(nbox), TPB, 0, P.stream>>>(L.flag, nbox, P.count, L.box_of_slot);
   IB_LAUNCH_CHECK();
+  if (P.prm.walls) {
+    int* cring = P.count + 1 + MAX_LEVELS_ALLOC + level;
+    IB_CUDA_TRY(cudaMemsetAsync(cring, 0, sizeof(int), P.stream));
+    k_assign_ring<<<nblk(nbox), TPB, 0, P.stream>>>(L.flag, nbox, P.count, cring, L.box_of_slot);
+    IB_LAUNCH_CHECK();
+  }
   return IB_OK;
 }
 

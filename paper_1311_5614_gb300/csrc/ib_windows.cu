@@ -372,12 +372,12 @@ int launch_window_galerkin(Problem& P, int level) {
 
 int launch_struct_from_windows(Problem& P, int level) {
   LevelInfo& L = P.lev[level];
-  if (L.n_struct == 0 || L.n_rows == 0) return IB_OK;
+  if (L.n_form == 0 || L.n_rows == 0) return IB_OK;
   const int nv = 2 * P.prm.box * (P.prm.box + 1);
   const double coef = P.prm.dt / (P.lev[0].h * P.lev[0].h);
-  KScope ks(P, IB_KC_SETUP, (double)L.n_struct * nv * (WIN * 8.0 + 8.0 * nv));
-  k_struct_from_windows<<<nblk((long)L.n_struct * nv), TPB, 0, P.stream>>>(
-      L.box_of_slot, L.n_struct, L.N, P.prm.box, L.rowslot, L.Ew64, coef, L.Mstruct, P.nB);
+  KScope ks(P, IB_KC_SETUP, (double)L.n_form * nv * (WIN * 8.0 + 8.0 * nv));
+  k_struct_from_windows<<<nblk((long)L.n_form * nv), TPB, 0, P.stream>>>(
+      L.box_of_slot, L.n_form, L.N, P.prm.box, L.rowslot, L.Ew64, coef, L.Mstruct, P.nB);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }

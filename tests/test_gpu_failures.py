@@ -11,7 +11,8 @@ problem in the same process:
 * an iteration cap of 1 on a stiff step: IB_ERR_NOT_CONVERGED with the iterate
   written and the points moved;
 * a bounded device-side wait forced to run out: the environment variable
-  IB_WAIT_LIMIT_NS = 0 at set-up makes every wait of the Gram-Schmidt pass for
+  IB_WAIT_LIMIT_NS = 0 at set-up (with IB_CGS_REG = 0, so that small bases also
+  take the bulk-copy form) makes every wait of the Gram-Schmidt pass for
   its bulk copies give up at once (the copies still land: the block waits for
   them before it exits), which the solve reports as IB_ERR_TIMEOUT.
 """
@@ -104,9 +105,11 @@ def test_iteration_cap_reports_not_converged(pkg, prec):
 
 def test_zero_wait_limit_reports_timeout(pkg, monkeypatch):
     monkeypatch.setenv("IB_WAIT_LIMIT_NS", "0")
+    monkeypatch.setenv("IB_CGS_REG", "0")  # small bases on the bulk-copy form, whose waits are bounded
     p = W.single_ellipse(N=32, n_points=64, kappa=1e2, dt=1e-2)
     s = pkg.IBSolver.from_problem(p)
     monkeypatch.delenv("IB_WAIT_LIMIT_NS")
+    monkeypatch.delenv("IB_CGS_REG")
     up = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.capi.IBError) as e:
         s.solve_step(None, up, dev(p.X))

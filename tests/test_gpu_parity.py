@@ -265,6 +265,14 @@ def test_solve_step_two_pass_gram_schmidt(pkg, name, box, prec, monkeypatch):
     test_solve_step(pkg, name, box, prec)
 
 
+@pytest.mark.parametrize("name,box,prec", [("c1_64", 1, "fp64"), ("stiff_32", 4, "mixed")])
+def test_solve_step_bulk_copy_gram_schmidt(pkg, name, box, prec, monkeypatch):
+    """Bases of up to 16 vectors on the bulk-copy form of the fused Gram-Schmidt
+    step (by default they take the register form)."""
+    monkeypatch.setenv("IB_CGS_REG", "0")
+    test_solve_step(pkg, name, box, prec)
+
+
 def test_no_structure_and_zero_rhs(pkg):
     """Edge cases: no Lagrangian points (pure Stokes, b = 0 -> zero solution)."""
     p = W.single_ellipse(N=16, n_points=8)
