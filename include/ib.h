@@ -215,7 +215,16 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * ib_setup) splits the middle pass in two, the form otherwise taken only when a
  * 64-element slice of the whole basis does not fit in shared memory.  Bases of up
  * to 16 vectors take a register form of the middle pass; IB_CGS_REG=0 (read at
- * ib_setup) keeps them on the bulk-copy form. */
+ * ib_setup) keeps them on the bulk-copy form.
+ * Reproducibility: with the assembled elasticity rows (the default), the same
+ * inputs give bit-identical results from run to run: the right-hand side's
+ * spread, the operator's spread and the level-0 row assembly gather through
+ * per-row point lists in a fixed order, and every reduction sums in a fixed
+ * order.  IB_ROW_LISTS=0 (read at ib_setup) takes the scatter forms with FP64
+ * atomic additions instead (about 1 ms less set-up on a 1024^2 grid with 32 768
+ * points; results then vary at the rounding level).  IB_POISON=1 (read at the
+ * library's first allocation) fills every new device allocation with all-ones
+ * bytes (NaN), a test aid that makes reads of unwritten memory show. */
 IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,
                   ib_stats* stats);
 

@@ -238,6 +238,8 @@ int setup_hierarchy(Problem& P) {
     IB_TRY(launch_struct_fill(P, l));
   }
   if (P.prm.walls) P.ring_ready = true;
+  P.rows_ready = false;
+  if (win) IB_TRY(launch_row_lists(P));
   bool use_win = false;
   if (win) {
     IB_TRY(launch_window_points(P));
@@ -300,6 +302,7 @@ void free_problem(Problem* P) {
   dfree(P->X); dfree(P->springs); dfree(P->kappa); dfree(P->rest);
   dfree(P->adj_ptr); dfree(P->adj_spring); dfree(P->adj_other);
   dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->U64); dfree(P->U32);
+  dfree(P->G64); dfree(P->rc_pt); dfree(P->rc_w); dfree(P->rc_start); dfree(P->rc_cnt);
   dfree(P->Mcoarse); dfree(P->V); dfree(P->Z); dfree(P->Z64); dfree(P->H); dfree(P->givens);
   dfree(P->dots); dfree(P->scal); dfree(P->x64); dfree(P->b64); dfree(P->t64); dfree(P->t64b);
   dfree(P->dev_err); dfree(P->count);
@@ -365,6 +368,11 @@ int allocate(Problem& P) {
     IB_TRY(dalloc(&P.X, 2ul * np));
     IB_TRY(dalloc(&P.F, 2ul * np));
     IB_TRY(dalloc(&P.U64, 2ul * np));
+    if (P.windows && ns > 0) {
+      IB_TRY(dalloc(&P.G64, 2ul * np));
+      IB_TRY(dalloc(&P.rc_pt, 32ul * np));
+      IB_TRY(dalloc(&P.rc_w, 32ul * np));
+    }
     if (fp32) IB_TRY(dalloc(&P.U32, 2ul * np));
     IB_TRY(dalloc(&P.adj_ptr, (size_t)np + 1));
   }
@@ -807,6 +815,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   P.sigma = params->time_method == IB_EXPLICIT ? 0.0 : stiffness(*params, n_springs, kappa);
   P.stiff_sigma = stiff_threshold();
   if (const char* e = std::getenv("IB_WINDOWS")) P.windows = e[0] != '0';
+  if (const char* e = std::getenv("IB_ROW_LISTS")) P.row_lists = e[0] != '0';
   int Nc = params->box > 4 ? params->box : 4;
   for (int N = params->N; N >= Nc; N /= 2) {
     LevelInfo L;

@@ -308,10 +308,13 @@ __device__ void gj_invert_cols(double* M, int n, int* err) {
     }
     const double inv = 1.0 / piv;
     for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[i * n + k];
+    // row k's entry of this thread's column, read by every thread of the column
+    // before any of them overwrites it (the thread whose rows include k does)
+    double mkj = 0.0;
+    if (r0 < R) mkj = (jc == k ? 1.0 : M[k * n + jc]) * inv;
     __syncthreads();
     // row k scaled (its pivot entry becomes 1/pivot); other rows updated
     if (r0 < R) {
-      const double mkj = (jc == k ? 1.0 : M[k * n + jc]) * inv;
       for (int i = r0; i < n; i += R) {
         if (i == k) M[k * n + jc] = mkj;
         else if (jc == k) M[i * n + k] = -f[i] * mkj;

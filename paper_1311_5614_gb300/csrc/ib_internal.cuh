@@ -9,6 +9,8 @@
 // & (N - 1) because every level size is a power of two.
 #pragma once
 
+#include <cstdlib>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -284,6 +286,19 @@ struct Problem {
   float* K32 = nullptr;       // [3][ns]
   double* F = nullptr;        // [np][2] spring force at X
   double* U64 = nullptr;      // [2][np] interpolated velocity scratch
+  double* G64 = nullptr;      // [2][np] J U per point (the operator's spread by row lists)
+  // Level-0 row lists, rebuilt at every set-up with the assembled rows: for each
+  // structure row (slot), the points whose spread patch covers it, in point order,
+  // with their spread weight.  The right-hand side's spread, the FP64 operator's
+  // spread and the level-0 row assembly gather through them, one writer per row,
+  // so their sums run in a fixed order (no floating-point atomics).
+  bool rows_ready = false;
+  bool row_lists = true;      // IB_ROW_LISTS=0 (read at ib_setup): the scatter forms with atomics
+  int cap_rc = 0;             // rows the count/start arrays hold
+  int* rc_start = nullptr;    // [cap_rc + 1]
+  int* rc_cnt = nullptr;      // [cap_rc]
+  int* rc_pt = nullptr;       // [32 np] point of each entry
+  double* rc_w = nullptr;     // [32 np] its weight phi_x phi_y
   float* U32 = nullptr;       // [2][np]
 
   // coarsest level
@@ -346,13 +361,26 @@ struct KScope {
   ~KScope();
 };
 
+// Whether new device allocations are filled with all-ones bytes (NaN as float or
+// double, -1 as int): IB_POISON=1 in the environment, for tests that look for
+// reads of memory nothing has written.
+inline bool poison_allocations() {
+  static const bool on = [] {
+    const char* e = std::getenv("IB_POISON");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 // Device allocation with the library's error reporting (count 0: NULL).
 template <typename T>
 int dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return IB_OK;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess && poison_allocations()) e = cudaMemset((void*)*p, 0xFF, count * sizeof(T));
   if (e != cudaSuccess) {
+    if (*p) cudaFree((void*)*p);
     *p = nullptr;
     cudaGetLastError();
     return fail(IB_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
@@ -427,6 +455,8 @@ int launch_pressure_mean_remove(Problem& P, double* w);
 inline bool op_elastic(const Problem& P) { return P.np > 0 && P.ns > 0 && P.prm.time_method == IB_IMPLICIT; }
 int launch_zero_walls(Problem& P, double* w);  // no-slip walls: w = 0 on the wall faces
 int launch_ring_prepare(Problem& P, int level); // ... the wall boxes' inverses (once)
+int launch_row_lists(Problem& P);               // level-0 row lists (see Problem::rows_ready)
+int launch_spread_rows(Problem& P, const double* vals, long sk, long sc, double scale, double* y);
 int launch_ring_copy(Problem& P, int level);    // ... into their slots (every set-up)
 int launch_wall_rhs(Problem& P, double* b);    // ... and the moving lid's ghost term
 

@@ -255,6 +255,24 @@ __global__ void k_spread_JU(Patches<T> pat, Springs<T> sp, const T* __restrict__
   }
 }
 
+// (J U)_k per point into G [2][np] (the spread then gathers it by rows).
+__global__ void k_point_JU(Springs<double> sp, const double* __restrict__ U, double* __restrict__ G) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= sp.np) return;
+  int np = sp.np, ns = sp.ns;
+  double ux = U[k], uy = U[np + k];
+  double gx = 0, gy = 0;
+  for (int q = sp.adj_ptr[k]; q < sp.adj_ptr[k + 1]; ++q) {
+    int s = sp.adj_spring[q], o = sp.adj_other[q];
+    double dx = U[o] - ux, dy = U[np + o] - uy;
+    double kxx = sp.K[s], kxy = sp.K[ns + s], kyy = sp.K[2 * ns + s];
+    gx += kxx * dx + kxy * dy;
+    gy += kxy * dx + kyy * dy;
+  }
+  G[k] = gx;
+  G[np + k] = gy;
+}
+
 // Mark every box whose velocity rows meet a spread patch: those are the boxes
 // whose block A_BB can contain elasticity (structure boxes).
 __global__ void k_mark(Patches<double> pat, int np, int N, int b, int nb, int* flag) {
@@ -444,6 +462,7 @@ int launch_spring_force_jacobian(Problem& P) {
 int launch_spread_force(Problem& P, double* b) {
   if (P.np == 0) return IB_OK;
   LevelInfo& L0 = P.lev[0];
+  if (P.rows_ready) return launch_spread_rows(P, P.F, 2, 1, -1.0 / (L0.h * L0.h), b);
   KScope ks(P, IB_KC_OTHER, P.np * (16.0 + 2 * (8 * 8 + 8) + 32 * 16.0));
   k_spread_force<<<nblk(P.np), TPB, 0, P.stream>>>(L0.pat64, P.F, P.np, L0.N, 1.0 / (L0.h * L0.h), b);
   IB_LAUNCH_CHECK();
@@ -499,6 +518,16 @@ int launch_elastic(Problem& P, int level, const T* w, T* y, double coef, T* U) {
     KScope ks(P, IB_KC_INTERP, 2.0 * P.np * (25 * sT + 8));
     k_interp<T><<<nblk(2L * P.np), TPB, 0, P.stream>>>(pat, w, P.np, L.N, U);
     IB_LAUNCH_CHECK();
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (level == 0 && P.rows_ready) {  // J U per point, then the spread as a gather by rows
+      {
+        KScope ks(P, IB_KC_SPREAD, P.np * (2 * sT + 8 + 2.0 * P.ns / P.np * (5 * sT + 8)));
+        k_point_JU<<<nblk(P.np), TPB, 0, P.stream>>>(springs_view<double>(P), U, P.G64);
+        IB_LAUNCH_CHECK();
+      }
+      return launch_spread_rows(P, P.G64, 1, P.np, coef, y);
+    }
   }
   {
     // per point: own U, per spring U_other + K + adjacency, 16 weights + 4 bases,

@@ -125,6 +125,174 @@ __global__ void k_window_points(Patches<double> pat, Springs<double> sp, int N, 
   }
 }
 
+// ---- level-0 row lists: for each structure row, the points whose spread patch
+// covers it.  Thread = (point k, row component c, spread node): count, then fill
+// after a scan, then sort each row's entries by point (a point covers a row once).
+__global__ void k_rc_count(Patches<double> pat, int np, int N, const int* __restrict__ rowslot, int* cnt,
+                           int* err) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 32L * np) return;
+  const int k = (int)(t >> 5), rem = (int)(t & 31), c = rem >> 4, a = rem & 3, bb = (rem >> 2) & 3;
+  const double ws = pat.w_at(0, c, 0, a, k) * pat.w_at(0, c, 1, bb, k);
+  if (ws == 0.0) return;
+  const int ri = wrapi(pat.b_at(0, c, 0, k) + a, N), rj = wrapi(pat.b_at(0, c, 1, k) + bb, N);
+  const int s = rowslot[(size_t)c * N * N + (size_t)rj * N + ri];
+  if (s < 0) {
+    atomicOr(err, DEV_ERR_INDEX);
+    return;
+  }
+  atomicAdd(&cnt[s], 1);
+}
+
+// Exclusive scan of cnt[0, n) into start[0, n] by one block: each thread sums a
+// contiguous chunk, the chunk sums are scanned in shared memory, then each thread
+// writes its chunk's offsets.
+__global__ void __launch_bounds__(1024) k_scan_block(const int* __restrict__ cnt, int n, int* __restrict__ start) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, per = (n + 1023) / 1024;
+  const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+  int s = 0;
+  for (int i = b0; i < b1; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = t ? part[t - 1] : 0;
+  for (int i = b0; i < b1; ++i) {
+    start[i] = run;
+    run += cnt[i];
+  }
+  if (t == 1023) start[n] = part[1023];
+}
+
+__global__ void k_rc_fill(Patches<double> pat, int np, int N, const int* __restrict__ rowslot,
+                          const int* __restrict__ start, int* fill, int* pt, double* wt) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 32L * np) return;
+  const int k = (int)(t >> 5), rem = (int)(t & 31), c = rem >> 4, a = rem & 3, bb = (rem >> 2) & 3;
+  const double ws = pat.w_at(0, c, 0, a, k) * pat.w_at(0, c, 1, bb, k);
+  if (ws == 0.0) return;
+  const int ri = wrapi(pat.b_at(0, c, 0, k) + a, N), rj = wrapi(pat.b_at(0, c, 1, k) + bb, N);
+  const int s = rowslot[(size_t)c * N * N + (size_t)rj * N + ri];
+  if (s < 0) return;
+  const int pos = start[s] + atomicAdd(&fill[s], 1);
+  pt[pos] = k;
+  wt[pos] = ws;
+}
+
+__global__ void k_rc_sort(const int* __restrict__ start, int nrows, int* pt, double* wt) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nrows) return;
+  const int e0 = start[s], e1 = start[s + 1];
+  for (int e = e0 + 1; e < e1; ++e) {
+    const int k = pt[e];
+    const double w = wt[e];
+    int q = e - 1;
+    while (q >= e0 && pt[q] > k) {
+      pt[q + 1] = pt[q];
+      wt[q + 1] = wt[q];
+      --q;
+    }
+    pt[q + 1] = k;
+    wt[q + 1] = w;
+  }
+}
+
+// y[row] += scale * sum over the row's entries of weight * vals[k sk + c sc] (c the
+// row's component), one thread per structure row: the spread S of a per-point
+// field as a gather in a fixed order.
+__global__ void k_spread_rows(const int* __restrict__ slot_row, int nrows, int N, const int* __restrict__ start,
+                              const int* __restrict__ pt, const double* __restrict__ wt,
+                              const double* __restrict__ vals, long sk, long sc, double scale, double* y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nrows) return;
+  const int r = slot_row[s], c = r / (N * N);
+  double acc = 0.0;
+  for (int e = start[s]; e < start[s + 1]; ++e) acc += wt[e] * vals[(size_t)pt[e] * sk + (size_t)c * sc];
+  y[r] += scale * acc;
+}
+
+// Level-0 windows by rows: thread = (structure row, column component cc); the
+// row's entries (points k in order), each coupling of k (J_kk, then its springs'
+// blocks in adjacency order) and each interpolation node of the coupled point, in
+// that fixed order, add into the thread's half of the row window, kept in shared
+// memory (no other thread touches it), which the block then writes out: the same
+// sums as k_window_points, without atomics.  A block holds WROWS consecutive rows,
+// whose windows are contiguous in Ew.
+constexpr int WROWS = 16;
+__global__ void __launch_bounds__(2 * WROWS) k_window_rows(const int* __restrict__ slot_row, int nrows, int N,
+                                                           const int* __restrict__ start, const int* __restrict__ pt,
+                                                           const double* __restrict__ wt, Patches<double> pat,
+                                                           Springs<double> sp, double* __restrict__ Ew, int* err) {
+  __shared__ double sw[2 * WROWS * WSQ];
+  const int tid = threadIdx.x, s0 = blockIdx.x * WROWS;
+  const int s = s0 + (tid >> 1), cc = tid & 1;
+  double* mine = sw + tid * WSQ;  // the half-window (row s, component cc): s * WIN + cc * WSQ in Ew
+  for (int e = 0; e < WSQ; ++e) mine[e] = 0.0;
+  bool outside = false;
+  if (s < nrows) {
+    const int r = slot_row[s], n = N * N, c = r / n, rr = r - c * n, ri = rr % N, rj = rr / N;
+    const int ns = sp.ns;
+    for (int e = start[s]; e < start[s + 1]; ++e) {
+      const int k = pt[e];
+      const double ws = wt[e];
+      const int a0 = sp.adj_ptr[k], deg = sp.adj_ptr[k + 1] - a0;
+      for (int q = 0; q <= deg; ++q) {
+        int l;
+        double Jc;  // J[c][cc]
+        if (q == 0) {
+          l = k;
+          Jc = 0.0;
+          for (int a = a0; a < a0 + deg; ++a) {
+            const int s2 = sp.adj_spring[a];
+            Jc -= (c == cc) ? sp.K[(c == 0 ? 0 : 2) * ns + s2] : sp.K[ns + s2];
+          }
+        } else {
+          const int s2 = sp.adj_spring[a0 + q - 1];
+          l = sp.adj_other[a0 + q - 1];
+          Jc = (c == cc) ? sp.K[(c == 0 ? 0 : 2) * ns + s2] : sp.K[ns + s2];
+        }
+        const double jv = ws * Jc;
+        if (jv == 0.0) continue;
+        // the coupled point's interpolation patch, loaded once
+        const int ix0 = pat.b_at(1, cc, 0, l), iy0 = pat.b_at(1, cc, 1, l);
+        double wx[PATCH], wy[PATCH];
+        int di[PATCH], dj[PATCH];
+#pragma unroll
+        for (int a = 0; a < PATCH; ++a) {
+          wx[a] = pat.w_at(1, cc, 0, a, l);
+          wy[a] = pat.w_at(1, cc, 1, a, l);
+          di[a] = sdiff(wrapi(ix0 + a, N), ri, N);
+          dj[a] = sdiff(wrapi(iy0 + a, N), rj, N);
+        }
+#pragma unroll
+        for (int cb = 0; cb < PATCH; ++cb) {
+          if (wy[cb] == 0.0) continue;
+#pragma unroll
+          for (int ca = 0; ca < PATCH; ++ca) {
+            const double wi = wx[ca] * wy[cb];
+            if (wi == 0.0) continue;
+            if (di[ca] < -WR || di[ca] > WR || dj[cb] < -WR || dj[cb] > WR) {
+              outside = true;
+              continue;
+            }
+            mine[(dj[cb] + WR) * WD + di[ca] + WR] += jv * wi;
+          }
+        }
+      }
+    }
+  }
+  if (outside) atomicOr(err, DEV_ERR_WINDOW);
+  __syncthreads();
+  const int rows = nrows - s0 < WROWS ? nrows - s0 : WROWS;
+  double* dst = Ew + (size_t)s0 * WIN;
+  for (int e = tid; e < rows * WIN; e += 2 * WROWS) dst[e] = sw[e];
+}
+
 // Prolongation weights of coarse column C along one direction (sec. 3.1): fine
 // index 2C + o, o in [-1, 2].  Normal direction (faces): 1/2, 1, 1/2 at o = -1, 0, 1;
 // centred direction (cell rows): 1/4, 3/4, 3/4, 1/4 at o = -1, 0, 1, 2.
@@ -343,12 +511,58 @@ int launch_mark_rows(Problem& P, int level) {
 int launch_window_points(Problem& P) {
   LevelInfo& L = P.lev[0];
   if (L.n_rows == 0) return IB_OK;
-  IB_CUDA_TRY(cudaMemsetAsync(L.Ew64, 0, sizeof(double) * WIN * (size_t)L.n_rows, P.stream));
+  if (!P.rows_ready)  // the row form writes every entry; the point form adds into zeros
+    IB_CUDA_TRY(cudaMemsetAsync(L.Ew64, 0, sizeof(double) * WIN * (size_t)L.n_rows, P.stream));
   Springs<double> sp;
   sp.np = P.np; sp.ns = P.ns; sp.adj_ptr = P.adj_ptr; sp.adj_spring = P.adj_spring;
   sp.adj_other = P.adj_other; sp.K = P.K64;
   KScope ks(P, IB_KC_SETUP, 0.0);
-  k_window_points<<<nblk(256L * P.np), TPB, 0, P.stream>>>(L.pat64, sp, L.N, L.rowslot, L.Ew64, P.dev_err);
+  if (P.rows_ready)  // one writer per row half: a fixed summation order
+    k_window_rows<<<(L.n_rows + WROWS - 1) / WROWS, 2 * WROWS, 0, P.stream>>>(L.slot_row, L.n_rows, L.N, P.rc_start, P.rc_pt,
+                                                             P.rc_w, L.pat64, sp, L.Ew64, P.dev_err);
+  else
+    k_window_points<<<nblk(256L * P.np), TPB, 0, P.stream>>>(L.pat64, sp, L.N, L.rowslot, L.Ew64, P.dev_err);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
+// Level-0 row lists (Problem::rows_ready): count the entries of each structure row,
+// scan, fill, sort each row by point.
+int launch_row_lists(Problem& P) {
+  LevelInfo& L = P.lev[0];
+  P.rows_ready = false;
+  if (!P.row_lists || !P.rc_pt || L.n_rows == 0) return IB_OK;
+  if (P.cap_rc < L.n_rows) {
+    dfree(P.rc_start);
+    dfree(P.rc_cnt);
+    P.cap_rc = L.cap_rows > L.n_rows ? L.cap_rows : L.n_rows;
+    IB_TRY(dalloc(&P.rc_start, (size_t)P.cap_rc + 1));
+    IB_TRY(dalloc(&P.rc_cnt, (size_t)P.cap_rc));
+  }
+  const int nr = L.n_rows;
+  KScope ks(P, IB_KC_SETUP, 32.0 * P.np * 40.0);
+  IB_CUDA_TRY(cudaMemsetAsync(P.rc_cnt, 0, sizeof(int) * nr, P.stream));
+  k_rc_count<<<nblk(32L * P.np), TPB, 0, P.stream>>>(L.pat64, P.np, L.N, L.rowslot, P.rc_cnt, P.dev_err);
+  IB_LAUNCH_CHECK();
+  k_scan_block<<<1, 1024, 0, P.stream>>>(P.rc_cnt, nr, P.rc_start);
+  IB_LAUNCH_CHECK();
+  IB_CUDA_TRY(cudaMemsetAsync(P.rc_cnt, 0, sizeof(int) * nr, P.stream));
+  k_rc_fill<<<nblk(32L * P.np), TPB, 0, P.stream>>>(L.pat64, P.np, L.N, L.rowslot, P.rc_start, P.rc_cnt,
+                                                    P.rc_pt, P.rc_w);
+  IB_LAUNCH_CHECK();
+  k_rc_sort<<<nblk(nr), TPB, 0, P.stream>>>(P.rc_start, nr, P.rc_pt, P.rc_w);
+  IB_LAUNCH_CHECK();
+  P.rows_ready = true;
+  return IB_OK;
+}
+
+// y[row] += scale * (S vals)[row] on the level-0 structure rows by the row lists.
+int launch_spread_rows(Problem& P, const double* vals, long sk, long sc, double scale, double* y) {
+  LevelInfo& L = P.lev[0];
+  if (L.n_rows == 0) return IB_OK;
+  KScope ks(P, IB_KC_SPREAD, (double)L.n_rows * 24.0 + 32.0 * P.np * 20.0);
+  k_spread_rows<<<nblk(L.n_rows), TPB, 0, P.stream>>>(L.slot_row, L.n_rows, L.N, P.rc_start, P.rc_pt, P.rc_w,
+                                                       vals, sk, sc, scale, y);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
