@@ -117,7 +117,7 @@ typedef struct {
   double mu;          /* viscosity (> 0) */
   double dt;          /* backward-Euler step (> 0) */
   int32_t delta;      /* IB_DELTA_PESKIN4 or IB_DELTA_COS4 (sec. 2.2) */
-  int32_t box;        /* box size b in {1, 2, 4, 8} (sec. 6) */
+  int32_t box;        /* box size b in {1, 2, 4, 8, 16} (sec. 6) */
   int32_t nu1, nu2;   /* pre/post smoothing sweeps, 0..8 (Algorithm 1) */
   int32_t precision;  /* IB_FP64, IB_FP32_PRECOND or IB_MIXED_PRECOND (see above) */
   int32_t jacobian;   /* IB_JAC_CLAMPED (default) or IB_JAC_EXACT spring Jacobian */

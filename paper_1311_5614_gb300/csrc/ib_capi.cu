@@ -94,8 +94,8 @@ double stiff_threshold() {
 
 int validate(const ib_params* p) {
   if (!p) return fail(IB_ERR_INVALID_ARG, "params is NULL");
-  if (!(p->box == 1 || p->box == 2 || p->box == 4 || p->box == 8))
-    return fail(IB_ERR_INVALID_ARG, "box must be 1, 2, 4 or 8");
+  if (!(p->box == 1 || p->box == 2 || p->box == 4 || p->box == 8 || p->box == 16))
+    return fail(IB_ERR_INVALID_ARG, "box must be 1, 2, 4, 8 or 16");
   int nc = p->box > 4 ? p->box : 4;
   if (!is_pow2(p->N) || p->N < 2 * nc || p->N > (1 << 14))
     return fail(IB_ERR_INVALID_ARG, "N must be a power of two with 2*max(4, box) <= N <= 16384");
@@ -303,7 +303,7 @@ void free_problem(Problem* P) {
   dfree(P->adj_ptr); dfree(P->adj_spring); dfree(P->adj_other);
   dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->U64); dfree(P->U32);
   dfree(P->G64); dfree(P->rc_pt); dfree(P->rc_w); dfree(P->rc_start); dfree(P->rc_cnt);
-  dfree(P->Mcoarse); dfree(P->V); dfree(P->Z); dfree(P->Z64); dfree(P->H); dfree(P->givens);
+  dfree(P->Mcoarse); dfree(P->inv_ws); dfree(P->inv_perm); dfree(P->V); dfree(P->Z); dfree(P->Z64); dfree(P->H); dfree(P->givens);
   dfree(P->dots); dfree(P->scal); dfree(P->x64); dfree(P->b64); dfree(P->t64); dfree(P->t64b);
   dfree(P->dev_err); dfree(P->count);
   dfree(P->nn_sch); dfree(P->nn_x); dfree(P->nn_y); dfree(P->nn_r); dfree(P->nn_dz); dfree(P->nn_adz);

@@ -171,154 +171,79 @@ __global__ void k_coarse_fill(double* M, int N, StokesCoef<double> c, int nz, in
   M[e] = v;
 }
 
-// In-place Gauss-Jordan inversion with partial pivoting by one CTA (row-major
-// n x n storage; applied to a column-major A it returns A^{-1} in column-major
-// order).  Row interchanges are undone by the reverse sequence of column
-// interchanges at the end.  M may live in global or shared memory.
+// Largest order inverted in shared memory (one CTA per matrix, n^2 doubles of
+// dynamic shared memory up to 160 KB, so n <= 143 in practice); larger matrices
+// take the blocked form below, up to INV_MAXN_BLOCKED.
 constexpr int INV_MAXN = 256;
-__device__ void gj_invert(double* M, int n, int* err) {
-  __shared__ double f[INV_MAXN];
-  __shared__ int perm[INV_MAXN];
-  __shared__ double rv[32];
-  __shared__ int ri[32];
-  __shared__ int prow;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = (bd + 31) >> 5;
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + tid; i < n; i += bd) {
-      double a = fabs(M[(size_t)i * n + k]);
-      if (a > best) { best = a; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b0 = rv[0];
-      int i0 = ri[0];
-      for (int q = 1; q < nw; ++q)
-        if (rv[q] > b0 || (rv[q] == b0 && ri[q] < i0)) { b0 = rv[q]; i0 = ri[q]; }
-      if (i0 >= n) i0 = k;
-      prow = i0;
-      perm[k] = i0;
-    }
-    __syncthreads();
-    const int p = prow;
-    if (p != k) {
-      for (int j = tid; j < n; j += bd) {
-        double t = M[(size_t)k * n + j];
-        M[(size_t)k * n + j] = M[(size_t)p * n + j];
-        M[(size_t)p * n + j] = t;
-      }
-    }
-    __syncthreads();
-    double piv = M[(size_t)k * n + k];
-    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-      if (tid == 0) atomicOr(err, DEV_ERR_SINGULAR);
-      piv = 1.0;
-    }
-    __syncthreads();
-    const double inv = 1.0 / piv;
-    for (int j = tid; j < n; j += bd) {
-      double v = (j == k) ? 1.0 : M[(size_t)k * n + j];
-      M[(size_t)k * n + j] = v * inv;
-    }
-    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[(size_t)i * n + k];
-    __syncthreads();
-    for (int i = tid; i < n; i += bd)
-      if (i != k) M[(size_t)i * n + k] = 0.0;
-    __syncthreads();
-    for (long e = tid; e < (long)n * n; e += bd) {
-      int i = (int)(e / n), j = (int)(e % n);
-      if (i != k) M[e] -= f[i] * M[(size_t)k * n + j];
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    int p = perm[k];
-    if (p != k) {
-      for (int i = tid; i < n; i += bd) {
-        double t = M[(size_t)i * n + k];
-        M[(size_t)i * n + k] = M[(size_t)i * n + p];
-        M[(size_t)i * n + p] = t;
-      }
-    }
-    __syncthreads();
-  }
-}
+constexpr int INV_MAXN_BLOCKED = 1024;
 
-// One matrix per CTA, worked on in global memory (large n).
-__global__ void k_invert(double* Ms, int n, int* err) { gj_invert(Ms + (size_t)blockIdx.x * n * n, n, err); }
+// Pivot row of column `col` among rows first..n-1 of the row-major matrix A (row
+// stride ld): the largest magnitude, the lowest row on ties; found by one warp, the
+// magnitudes compared as integers (a non-negative double orders like its bit
+// pattern, so the FP64 pipe is left to the elimination; a NaN compares above every
+// finite value and is then caught as a non-finite pivot).  Lane 0 holds the result.
+__device__ __forceinline__ int warp_pivot_row(const double* A, int ld, int col, int first, int n, int lane) {
+  unsigned long long best = 0ull;
+  int bi = n;
+  for (int i = first + lane; i < n; i += 32) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ld + col]));
+    if (bi == n || a > best) { best = a; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+  }
+  return bi < n ? bi : first;
+}
 
 // Gauss-Jordan with partial pivoting on a matrix in shared memory, organised for
 // the rank-1 update: thread t owns column t % n for the rows congruent to t / n
-// modulo R = blockDim / n (blockDim >= n), so the update needs no index division and the pivot
-// column is written in the same pass (M[i][k] = -f_i / pivot).
+// modulo R = blockDim / n (blockDim >= n), so the update needs no index division and
+// the pivot column is written in the same pass (M[i][k] = -f_i / pivot).  The row
+// interchange of step k is folded into that pass: f_i and the scaled pivot row are
+// read from the rows before the interchange (rows k and p trade places), so a step
+// is one pivot search by warp 0 (which also forms the one reciprocal), one read
+// pass and one update pass, three barriers.
 __device__ void gj_invert_cols(double* M, int n, int* err) {
   __shared__ double f[INV_MAXN];
   __shared__ int perm[INV_MAXN];
-  __shared__ double rv[32];
-  __shared__ int ri[32];
+  __shared__ double sinv;
   __shared__ int prow;
   const int tid = threadIdx.x, bd = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = (bd + 31) >> 5;
   const int R = bd / n > 0 ? bd / n : 1;
   const int jc = tid % n, r0 = tid / n;
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + tid; i < n; i += bd) {
-      const double a = fabs(M[i * n + k]);
-      if (a > best) { best = a; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b0 = rv[0];
-      int i0 = ri[0];
-      for (int q = 1; q < nw; ++q)
-        if (rv[q] > b0 || (rv[q] == b0 && ri[q] < i0)) { b0 = rv[q]; i0 = ri[q]; }
-      if (i0 >= n) i0 = k;
-      prow = i0;
-      perm[k] = i0;
+    if (tid < 32) {
+      const int p = warp_pivot_row(M, n, k, k, n, tid);
+      if (tid == 0) {
+        double piv = M[p * n + k];
+        if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+          atomicOr(err, DEV_ERR_SINGULAR);
+          piv = 1.0;
+        }
+        prow = p;
+        perm[k] = p;
+        sinv = 1.0 / piv;
+      }
     }
     __syncthreads();
     const int p = prow;
-    if (p != k)
-      for (int j = tid; j < n; j += bd) {
-        const double t = M[k * n + j];
-        M[k * n + j] = M[p * n + j];
-        M[p * n + j] = t;
-      }
-    __syncthreads();
-    double piv = M[k * n + k];
-    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-      if (tid == 0) atomicOr(err, DEV_ERR_SINGULAR);
-      piv = 1.0;
+    const double inv = sinv;
+    // after the interchange row k is the old row p and row p the old row k
+    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[(i == p ? k : i) * n + k];
+    double mkj = 0.0, okj = 0.0;
+    if (r0 < R) {
+      mkj = (jc == k ? 1.0 : M[p * n + jc]) * inv;
+      okj = M[k * n + jc];
     }
-    const double inv = 1.0 / piv;
-    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[i * n + k];
-    // row k's entry of this thread's column, read by every thread of the column
-    // before any of them overwrites it (the thread whose rows include k does)
-    double mkj = 0.0;
-    if (r0 < R) mkj = (jc == k ? 1.0 : M[k * n + jc]) * inv;
     __syncthreads();
     // row k scaled (its pivot entry becomes 1/pivot); other rows updated
     if (r0 < R) {
       for (int i = r0; i < n; i += R) {
         if (i == k) M[k * n + jc] = mkj;
         else if (jc == k) M[i * n + k] = -f[i] * mkj;
-        else M[i * n + jc] -= f[i] * mkj;
+        else M[i * n + jc] = (i == p ? okj : M[i * n + jc]) - f[i] * mkj;
       }
     }
     __syncthreads();
@@ -331,6 +256,178 @@ __device__ void gj_invert_cols(double* M, int n, int* err) {
         M[i * n + k] = M[i * n + p];
         M[i * n + p] = t;
       }
+    __syncthreads();
+  }
+}
+
+// Blocked Gauss-Jordan for matrices too large for shared memory (the 8 x 8 and
+// 16 x 16 boxes, the coarsest level of 16 x 16 boxes): the columns go in panels of
+// GJ_PW.  k_bgj_panel runs the panel's Gauss-Jordan steps, with partial pivoting,
+// on the panel's columns staged in shared memory, interchanging whole rows in
+// global memory as it goes, and saves the pivot rows of every other column (after
+// the interchanges, before any elimination) in U.  The steps change another column
+// x only through its pivot-row entries: with Q the panel's final columns,
+//   x_i <- [i not a pivot row of the panel] x_i + sum_s Q[i][s] x_{k0+s},
+// which k_bgj_update applies to all other columns at once, a rank-GJ_PW product
+// tiled 64 x 64 over the matrix.  These are the row operations of the unblocked
+// elimination, grouped by panel; the pivots are the same.  k_bgj_unperm finally
+// undoes the row interchanges as column interchanges.
+constexpr int GJ_PW = 16;
+constexpr int GJ_PANEL_THREADS = 512;
+
+__global__ void __launch_bounds__(GJ_PANEL_THREADS) k_bgj_panel(double* Ms, int n, int k0, int pw, double* U,
+                                                                int* perms, int* err) {
+  extern __shared__ double sP[];  // [n][GJ_PW] the panel, then f[n]
+  double* f = sP + (size_t)n * GJ_PW;
+  __shared__ double sinv;
+  __shared__ int prow;
+  double* M = Ms + (size_t)blockIdx.x * n * n;
+  int* perm = perms + (size_t)blockIdx.x * n;
+  double* Um = U + (size_t)blockIdx.x * GJ_PW * n;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int e = tid; e < n * GJ_PW; e += bd) {
+    const int i = e / GJ_PW, c = e - i * GJ_PW;
+    sP[e] = c < pw ? M[(size_t)i * n + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int R = bd / GJ_PW, c = tid % GJ_PW, r0 = tid / GJ_PW;
+  for (int s = 0; s < pw; ++s) {
+    const int k = k0 + s;
+    if (tid < 32) {
+      const int p = warp_pivot_row(sP, GJ_PW, s, k, n, tid);
+      if (tid == 0) {
+        double piv = sP[(size_t)p * GJ_PW + s];
+        if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+          atomicOr(err, DEV_ERR_SINGULAR);
+          piv = 1.0;
+        }
+        prow = p;
+        perm[k] = p;
+        sinv = 1.0 / piv;
+      }
+    }
+    __syncthreads();
+    const int p = prow;
+    if (p != k) {  // whole rows: the panel here, the other columns in global memory
+      for (int j = tid; j < n; j += bd) {
+        if (j >= k0 && j < k0 + pw) continue;  // stale copy of the panel, rewritten below
+        const double t = M[(size_t)k * n + j];
+        M[(size_t)k * n + j] = M[(size_t)p * n + j];
+        M[(size_t)p * n + j] = t;
+      }
+      if (tid < GJ_PW) {
+        const double t = sP[(size_t)k * GJ_PW + tid];
+        sP[(size_t)k * GJ_PW + tid] = sP[(size_t)p * GJ_PW + tid];
+        sP[(size_t)p * GJ_PW + tid] = t;
+      }
+    }
+    __syncthreads();
+    const double inv = sinv;
+    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : sP[(size_t)i * GJ_PW + s];
+    const double mkc = (c < pw) ? (c == s ? 1.0 : sP[(size_t)k * GJ_PW + c]) * inv : 0.0;
+    __syncthreads();
+    if (c < pw) {
+      for (int i = r0; i < n; i += R) {
+        double* e = sP + (size_t)i * GJ_PW + c;
+        if (i == k) *e = mkc;
+        else if (c == s) *e = -f[i] * mkc;
+        else *e -= f[i] * mkc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * pw; e += bd) {
+    const int i = e / pw, cc = e - i * pw;
+    M[(size_t)i * n + k0 + cc] = sP[(size_t)i * GJ_PW + cc];
+  }
+  for (int e = tid; e < pw * n; e += bd) {
+    const int s = e / n, j = e - s * n;
+    Um[(size_t)s * n + j] = (j >= k0 && j < k0 + pw) ? 0.0 : M[(size_t)(k0 + s) * n + j];
+  }
+}
+
+// grid (column tiles, row tiles, matrices): a 64 x 64 tile per CTA, 4 x 4 entries
+// per thread, the panel's rows of the tile and the saved pivot rows staged in shared memory.
+__global__ void __launch_bounds__(256) k_bgj_update(double* Ms, int n, int k0, int pw, const double* U, int z0) {
+  __shared__ double sQ[64][GJ_PW + 1];
+  __shared__ double sU[GJ_PW][64];
+  const int z = z0 + blockIdx.z;
+  double* M = Ms + (size_t)z * n * n;
+  const double* Um = U + (size_t)z * GJ_PW * n;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64, tid = threadIdx.x;
+  for (int e = tid; e < 64 * GJ_PW; e += 256) {
+    const int r = e / GJ_PW, s = e - r * GJ_PW, i = i0 + r;
+    sQ[r][s] = (i < n && s < pw) ? M[(size_t)i * n + k0 + s] : 0.0;
+  }
+  for (int e = tid; e < GJ_PW * 64; e += 256) {
+    const int s = e >> 6, cc = e & 63, j = j0 + cc;
+    sU[s][cc] = (j < n && s < pw) ? Um[(size_t)s * n + j] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.0;
+#pragma unroll
+  for (int s = 0; s < GJ_PW; ++s) {
+    double qa[4], ub[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) qa[a] = sQ[ty + 16 * a][s];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ub[q] = sU[s][tx + 16 * q];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][q] = fma(qa[a], ub[q], acc[a][q]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= n) continue;
+    const bool pivot_row = i >= k0 && i < k0 + pw;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx + 16 * q;
+      if (j >= n || (j >= k0 && j < k0 + pw)) continue;
+      double* e = M + (size_t)i * n + j;
+      *e = (pivot_row ? 0.0 : *e) + acc[a][q];
+    }
+  }
+}
+
+// Column j of the result is column idx[j] of the eliminated matrix, idx being
+// 0..n-1 put through the column interchanges k <-> perm[k], k = n-1 down to 0.
+// grid (groups of 8 rows, matrices z0 + y).
+__global__ void k_bgj_unperm(double* Ms, int n, const int* perms, int z0) {
+  extern __shared__ double sRow[];  // one row [n], then perm [n] and idx [n] as ints
+  int* sp = reinterpret_cast<int*>(sRow + n);
+  int* idx = sp + n;
+  const int z = z0 + blockIdx.y;
+  double* M = Ms + (size_t)z * n * n;
+  const int* perm = perms + (size_t)z * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    sp[j] = perm[j];
+    idx[j] = j;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = sp[k];
+      if (p != k) {
+        const int t = idx[k];
+        idx[k] = idx[p];
+        idx[p] = t;
+      }
+    }
+  __syncthreads();
+  const int r_end = min(n, (int)(blockIdx.x + 1) * 8);
+  for (int i = blockIdx.x * 8; i < r_end; ++i) {
+    double* row = M + (size_t)i * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) sRow[j] = row[j];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = sRow[idx[j]];
     __syncthreads();
   }
 }
@@ -550,14 +647,62 @@ int launch_struct_fill(Problem& P, int level) {
   return IB_OK;
 }
 
+// The blocked Gauss-Jordan over count matrices: per panel of GJ_PW columns one
+// panel launch (a CTA per matrix) and one update launch (64 x 64 tiles of every
+// matrix), then the column interchanges.  Its workspace (saved pivot rows and
+// pivot indices) grows on demand and is kept with the problem.
+int launch_invert_blocked(Problem& P, double* M, int n, int count) {
+  const size_t ws = (size_t)count * GJ_PW * n, wp = (size_t)count * n;
+  if (ws > P.inv_ws_cap) {
+    dfree(P.inv_ws);
+    P.inv_ws_cap = 0;
+    IB_TRY(dalloc(&P.inv_ws, ws));
+    P.inv_ws_cap = ws;
+  }
+  if (wp > P.inv_perm_cap) {
+    dfree(P.inv_perm);
+    P.inv_perm_cap = 0;
+    IB_TRY(dalloc(&P.inv_perm, wp));
+    P.inv_perm_cap = wp;
+  }
+  const size_t smem_panel = (size_t)n * (GJ_PW + 1) * sizeof(double);
+  const size_t smem_unperm = (size_t)n * (sizeof(double) + 2 * sizeof(int));
+  static std::once_flag once;
+  cudaError_t ae = cudaSuccess;
+  std::call_once(once, [&] {
+    const int mx = (int)((size_t)INV_MAXN_BLOCKED * (GJ_PW + 1) * sizeof(double));
+    ae = cudaFuncSetAttribute(k_bgj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  });
+  IB_CUDA_TRY(ae);
+  const int tiles = (n + 63) / 64;
+  for (int k0 = 0; k0 < n; k0 += GJ_PW) {
+    const int pw = n - k0 < GJ_PW ? n - k0 : GJ_PW;
+    k_bgj_panel<<<count, GJ_PANEL_THREADS, smem_panel, P.stream>>>(M, n, k0, pw, P.inv_ws, P.inv_perm,
+                                                                   P.dev_err);
+    IB_LAUNCH_CHECK();
+    for (int z0 = 0; z0 < count; z0 += 65535) {
+      const int nz = count - z0 < 65535 ? count - z0 : 65535;
+      k_bgj_update<<<dim3(tiles, tiles, nz), 256, 0, P.stream>>>(M, n, k0, pw, P.inv_ws, z0);
+      IB_LAUNCH_CHECK();
+    }
+  }
+  for (int z0 = 0; z0 < count; z0 += 65535) {
+    const int nz = count - z0 < 65535 ? count - z0 : 65535;
+    k_bgj_unperm<<<dim3((n + 7) / 8, nz), 256, smem_unperm, P.stream>>>(M, n, P.inv_perm, z0);
+    IB_LAUNCH_CHECK();
+  }
+  return IB_OK;
+}
+
 // Invert count n x n matrices stored back to back: 5 x 5 in registers (one per
 // thread), n^2 doubles that fit in shared memory staged there (one CTA each),
-// larger ones in global memory.
+// larger ones by the blocked form in global memory.
 int launch_invert(Problem& P, double* M, int n, int count) {
   if (count <= 0) return IB_OK;
-  if (n > INV_MAXN) return fail(IB_ERR_INVALID_ARG, "matrix too large for the device inverse");
-  KScope ks(P, IB_KC_SETUP, 2.0 * count * n * n * 8.0);
   size_t smem = (size_t)n * n * sizeof(double);
+  if (smem > 160u * 1024u ? n > INV_MAXN_BLOCKED : n > INV_MAXN)
+    return fail(IB_ERR_INVALID_ARG, "matrix too large for the device inverse");
+  KScope ks(P, IB_KC_SETUP, 2.0 * count * n * n * 8.0);
   if (n == 5) {
     k_invert5<<<nblk(count, 128), 128, 0, P.stream>>>(M, count, P.dev_err);
   } else if (smem <= 160u * 1024u) {
@@ -570,7 +715,7 @@ int launch_invert(Problem& P, double* M, int n, int count) {
     int threads = n <= 32 ? 64 : (n <= 64 ? 128 : 256);
     k_invert_sm<<<count, threads, smem, P.stream>>>(M, n, P.dev_err);
   } else {
-    k_invert<<<count, 1024, 0, P.stream>>>(M, n, P.dev_err);
+    IB_TRY(launch_invert_blocked(P, M, n, count));
   }
   IB_LAUNCH_CHECK();
   return IB_OK;

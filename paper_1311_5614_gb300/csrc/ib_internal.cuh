@@ -305,6 +305,10 @@ struct Problem {
   int nc = 0;                 // 3 Nc^2
   int nborder = 0;            // null-space border columns (1 or 3)
   double* Mcoarse = nullptr;  // [(nc + nborder)^2] bordered inverse, column-major
+  double* inv_ws = nullptr;   // blocked inversion: saved pivot rows, [count][16][n]
+  size_t inv_ws_cap = 0;
+  int* inv_perm = nullptr;    // blocked inversion: pivot rows, [count][n]
+  size_t inv_perm_cap = 0;
 
   // Krylov (FP64)
   double* V = nullptr;        // [m + 1][n]

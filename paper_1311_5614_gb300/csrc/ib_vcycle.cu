@@ -920,8 +920,11 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
       else
         IB_BOXN(4, 4);
       break;
-    default:
+    case 8:
       IB_BOXN(8, 1);
+      break;
+    default:  // 16 x 16 boxes: 800 unknowns, one CTA of 800 threads per box
+      IB_BOXN(16, 1);
       break;
   }
 #undef IB_BOXN
