@@ -560,14 +560,15 @@ def run_unet(args):
     return 0
 
 
-CAVITY_CASES = [(N, b, a) for N in (64, 256, 1024) for b in (4, 8) for a in (6.0, 60.0, 600.0, 3000.0)]
+CAVITY_CASES = ([(N, b, a) for N in (64, 256, 1024) for b in (4, 8) for a in (6.0, 60.0, 600.0, 3000.0)]
+                + [(N, 16, a) for N in (64, 256) for a in (6.0, 60.0, 600.0, 3000.0)])
 
 
 def run_cavity(args):
     """The paper's own problem on the GPU (sec. 4, the refinement study of sec. 6):
     the lid-driven cavity with the thick annulus, steady Stokes, cosine kernel, zero
     rest length, stiffness alpha = 6, 60, 600, 3000 (non-stiff ... very stiff), box
-    sizes 4 and 8, V(1,1), MG-GMRES from zero to a 1e-6 residual reduction (100
+    sizes 4 and 8 (and 16 at N = 64 and 256), V(1,1), MG-GMRES from zero to a 1e-6 residual reduction (100
     iterations at most), at N = 64, 256 and 1024.  Right-hand side from the library
     (ib_rhs: the lid's ghost term and -S F(X)); each case is solved warmup + steps
     times and its median FGMRES device time reported (events inside ib_solve).  The
@@ -616,7 +617,7 @@ def run_cavity_time(args):
     time method at 0.9 of its stability limit (dt = 0.9 alpha_exp / gamma; 40 steps
     run and the work extrapolated to t = 1, as the paper does), at relative
     stiffness gamma dt / alpha_exp = 1, 10, 100, 500 for the implicit step, box
-    sizes 4 and 8, MG-GMRES to 1e-6 per step.  The efficiency factor is the ratio of
+    sizes 4, 8 and 16, MG-GMRES to 1e-6 per step.  The efficiency factor is the ratio of
     the explicit method's work to the implicit one's, counted in MG-GMRES
     iterations (the paper's measure) and in GPU time (set-up + solve per step, CUDA
     events inside ib_solve_step).  alpha_exp = 3.93 at N = 64 is the paper's Table 1
@@ -628,7 +629,7 @@ def run_cavity_time(args):
     torch.cuda.set_device(args.local_rank)
     N, T, dt_i, a_exp = 64, 1.0, 1.0 / 40.0, 3.93
     rows = []
-    for b in (4, 8):
+    for b in (4, 8, 16):
         for rel in (1.0, 10.0, 100.0, 500.0):
             gamma = rel * a_exp / dt_i
             res = {"box": b, "rel_stiffness": rel, "gamma": gamma}

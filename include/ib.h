@@ -222,11 +222,39 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * per-row point lists in a fixed order, and every reduction sums in a fixed
  * order.  IB_ROW_LISTS=0 (read at ib_setup) takes the scatter forms with FP64
  * atomic additions instead (about 1 ms less set-up on a 1024^2 grid with 32 768
- * points; results then vary at the rounding level).  IB_POISON=1 (read at the
+ * points; results then vary at the rounding level).
+ * With IB_FP32_PRECOND, a step below the stiffness threshold (IB_STIFF_SIGMA)
+ * eliminates its structure boxes (n <= 4) in FP32, the inverses kept and applied
+ * in FP64 as before; a solve that escalates to the mixed V-cycle re-forms and
+ * inverts them in FP64 first.  IB_INV32=0 (read at ib_setup) always inverts in
+ * FP64.  IB_POISON=1 (read at the
  * library's first allocation) fills every new device allocation with all-ones
  * bytes (NaN), a test aid that makes reads of unwritten memory show. */
 IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,
                   ib_stats* stats);
+
+/* One implicit step with the spring force taken at the new positions: the
+ * backward-Euler step whose force is F(X^{n+1}) rather than its linearisation
+ * about X^n, solved by Newton's method (sec. 8 names Newton's method for nonlinear
+ * force laws; each iteration is a linearised system of the form ib_solve_step
+ * solves).  S and S^* stay at X^n (lagged, sec. 2.3); iteration k evaluates the
+ * springs' force and Jacobian at X^k = X^n + dt S^* u^k (u^0 = 0) and solves
+ *   [mu Lap - (rho/dt) + dt S J(X^k) S^*] u - G p = -(rho/dt) u^n - S [F(X^k) - J(X^k)(X^k - X^n)],
+ *   D u = 0
+ * with the MG-preconditioned FGMRES of ib_solve_step; the first iterate is
+ * ib_solve_step's result.  Iterates until max |X^{k+1} - X^k| <= tol_newton * h
+ * (after at least two solves) or max_newton solves.  The converged step does not
+ * depend on the Jacobian variant (IB_JAC_EXACT converges quadratically, the
+ * clamped one linearly).  Arguments as for ib_solve_step (device pointers, X
+ * updated in place to X^{n+1}); stats: iters summed over the solves, t_setup_ms
+ * and t_solve_ms summed, the other fields from the last solve.  newton (host
+ * memory, two doubles, may be NULL): newton[0] = solves done, newton[1] = the last
+ * max |X^{k+1} - X^k| / h.  Errors: IB_ERR_INVALID_ARG (max_newton < 1,
+ * tol_newton < 0, the explicit-time method, NULL X with points) and those of
+ * ib_solve_step; IB_ERR_NOT_CONVERGED if a linear solve stops at max_iters (the
+ * iteration ends there). */
+IB_API int ib_solve_step_newton(ib_problem* prob, const double* u_n, double* up, double* X,
+                                int32_t max_newton, double tol_newton, ib_stats* stats, double* newton);
 
 /* Solve A_0 x = b for a given right-hand side with the current hierarchy (the
  * points of ib_setup or the last ib_update_points / ib_solve_step), by the same

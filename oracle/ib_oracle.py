@@ -20,7 +20,9 @@ implicit-time immersed boundary method"):
 * the V-cycle of Algorithm 1 with the box (Vanka) smoother of sec. 5 and the
   n x n "big boxes" of sec. 6, exact coarsest solve on N_c = max(4, n);
 * flexible GMRES with the V-cycle as right preconditioner, sec. 3.3;
-* the position update X^{n+1} = X^n + dt S^* u^{n+1}, Eq. 20.
+* the position update X^{n+1} = X^n + dt S^* u^{n+1}, Eq. 20;
+* the same step with the spring force taken at X^{n+1} (a nonlinear step),
+  solved by Newton's method over linearised systems of the same form (sec. 8).
 
 Everything is assembled as explicit sparse matrices (scipy CSR) and applied
 with plain matrix-vector products; box matrices are principal submatrices of
@@ -421,14 +423,16 @@ def level_sizes(N, b):
     return out
 
 
-def fine_elasticity(prob, X=None):
-    """E_0 = S J S^* on the finest grid (the block alpha S A_f S^* of the paper's system)."""
+def fine_elasticity(prob, X=None, Xj=None):
+    """E_0 = S J S^* on the finest grid (the block alpha S A_f S^* of the paper's system).
+    S at the points X; the springs' Jacobian J at Xj (default: X as well)."""
     X = prob.X if X is None else X
+    Xj = X if Xj is None else Xj
     N, L = prob.N, prob.L
     h = L / N
     S = spread_matrix(X, N, L, prob.delta)
     Ss = interp_matrix(S, h)
-    Jm = spring_jacobian(X, prob.springs, prob.kappa, prob.rest, L, prob.clamped)
+    Jm = spring_jacobian(Xj, prob.springs, prob.kappa, prob.rest, L, prob.clamped)
     return (S @ Jm @ Ss).tocsr(), S, Ss, Jm
 
 
@@ -441,10 +445,11 @@ def with_elasticity(Astokes, E, dt, N):
     return (Astokes + dt * Ebig).tocsr()
 
 
-def build_hierarchy(prob, X=None):
-    """Levels N, N/2, ..., N_c with A_l = Stokes_l + dt E_l, E_{l+1} = R E_l P."""
+def build_hierarchy(prob, X=None, Xj=None):
+    """Levels N, N/2, ..., N_c with A_l = Stokes_l + dt E_l, E_{l+1} = R E_l P (S at X,
+    the springs' Jacobian at Xj, default X)."""
     sizes = level_sizes(prob.N, prob.box)
-    E, S, Ss, Jm = fine_elasticity(prob, X)
+    E, S, Ss, Jm = fine_elasticity(prob, X, Xj)
     levels = []
     for li, N in enumerate(sizes):
         h = prob.L / N
@@ -752,6 +757,69 @@ def solve_step(prob, u_n=None, order="color4", X=None):
     Np = X.shape[0]
     Xn = X + prob.dt * np.stack([U[:Np], U[Np:]], axis=1)
     return StepResult(w=w, X=Xn, solve=res, b=b)
+
+
+@dataclass
+class NewtonResult:
+    w: np.ndarray          # [u|v|p] at t^{n+1}, zero-mean pressure
+    X: np.ndarray          # X^{n+1}
+    iters: int             # Newton iterations (linear solves)
+    changes: list          # max |X^{k+1} - X^k| / h after each iteration (the first: the step)
+    linear_iters: list     # FGMRES iterations of each linear solve
+
+
+def solve_step_newton(prob, u_n=None, order="color4", X=None, max_newton=20, tol=1e-9):
+    """The backward-Euler step with the spring force at the new positions, solved by
+    Newton's method (sec. 8 names Newton's method for nonlinear force laws; it
+    solves a sequence of linearised systems of the form of the linearised step).
+
+    Unknowns u^{n+1}, p^{n+1}; S and S^* stay at X^n (lagged, sec. 2.3); with
+    X(u) = X^n + dt S^* u the equations are
+        mu Lap u - (rho/dt) u - G p + S F(X(u)) = -(rho/dt) u^n,   D u = 0.
+    Iteration k linearises F about X^k = X(u^k):
+        F(X) ~ F(X^k) + J(X^k) (X - X^k),  X - X^k = dt S^* (u - u^k),
+    so u^{k+1} solves the linearised step's operator with J(X^k) in place of J(X^n)
+    and the right-hand side -(rho/dt) u^n - S [F(X^k) - J(X^k)(X^k - X^n)]
+    (X^k - X^n = dt S^* u^k).  u^0 = 0, X^0 = X^n: the first iterate is the
+    linearised step.  Stops when max |X^{k+1} - X^k| <= tol h (k >= 1) or after
+    max_newton solves.  The fixed point does not depend on J (its terms cancel), so
+    the clamped Jacobian converges to the same step, only more slowly."""
+    Xn = prob.X if X is None else np.asarray(X, dtype=np.float64)
+    N, L = prob.N, prob.L
+    h = L / N
+    n2 = 2 * N * N
+    Np = Xn.shape[0]
+    S = spread_matrix(Xn, N, L, prob.delta)
+    Ss = interp_matrix(S, h)
+    Xk = Xn.copy()
+    changes, lin = [], []
+    w = None
+    for k in range(max_newton):
+        levels, _ = build_hierarchy(prob, Xn, Xj=Xk)
+        for lev in levels[:-1]:
+            prepare_boxes(lev, prob.box)
+        Fk = spring_force(Xk, prob.springs, prob.kappa, prob.rest, L)
+        Jk = spring_jacobian(Xk, prob.springs, prob.kappa, prob.rest, L, prob.clamped)
+        d = np.array([_min_image(Xk[i] - Xn[i], L) for i in range(Np)]).reshape(Np, 2)
+        Ft = np.concatenate([Fk[:, 0], Fk[:, 1]]) - Jk @ np.concatenate([d[:, 0], d[:, 1]])
+        b = np.zeros(3 * N * N)
+        b[:n2] = -(S @ Ft)
+        if u_n is not None and prob.rho != 0.0:
+            b[:n2] -= (prob.rho / prob.dt) * np.asarray(u_n, dtype=np.float64).ravel()[:n2]
+
+        def M(v):
+            return vcycle(levels, v, np.zeros_like(v), prob.nu1, prob.nu2, prob.rho, order)
+
+        res = fgmres(levels[0].A, b, M, prob.tol, prob.max_iters)
+        lin.append(res.iters)
+        w = remove_pressure_mean(res.x, N)
+        U = Ss @ w[:n2]
+        Xnew = Xn + prob.dt * np.stack([U[:Np], U[Np:]], axis=1)
+        changes.append(float(np.abs(Xnew - Xk).max() / h))
+        Xk = Xnew
+        if k >= 1 and changes[-1] <= tol:
+            break
+    return NewtonResult(w=w, X=Xk, iters=len(changes), changes=changes, linear_iters=lin)
 
 
 def direct_solve(A, b, N, rho):

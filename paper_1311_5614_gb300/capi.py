@@ -74,6 +74,8 @@ _SIGS = {
     "ib_vcycle": (ctypes.c_int, [_P, _P, _P]),
     "ib_rhs": (ctypes.c_int, [_P, _P, _P]),
     "ib_solve_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ib_stats)]),
+    "ib_solve_step_newton": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.POINTER(ib_stats), ctypes.POINTER(ctypes.c_double)]),
     "ib_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ib_stats)]),
     "ib_num_levels": (ctypes.c_int, [_P]),
     "ib_level_size": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -217,6 +219,24 @@ def ib_solve_step(prob, u_n, up, X, n_points, raise_on_not_converged=False):
     if code != IB_OK and (code != IB_ERR_NOT_CONVERGED or raise_on_not_converged):
         _check(code)
     return st.as_dict()
+
+
+def ib_solve_step_newton(prob, u_n, up, X, n_points, max_newton=20, tol_newton=1e-9,
+                         raise_on_not_converged=False):
+    """One implicit step with the spring force at the new positions (Newton's method);
+    returns the ib_stats as a dict plus newton_iters and newton_change."""
+    n = ib_level_size(prob, 0)
+    st = ib_stats()
+    nw = (ctypes.c_double * 2)()
+    code = lib().ib_solve_step_newton(prob, _dev_ptr(u_n, 2 * n * n, "u_n"), _dev_ptr(up, 3 * n * n, "up"),
+                                      _dev_ptr(X, 2 * n_points, "X") if n_points else None, int(max_newton),
+                                      float(tol_newton), ctypes.byref(st), nw)
+    if code != IB_OK and (code != IB_ERR_NOT_CONVERGED or raise_on_not_converged):
+        _check(code)
+    d = st.as_dict()
+    d["newton_iters"] = int(nw[0])
+    d["newton_change"] = float(nw[1])
+    return d
 
 
 def ib_solve(prob, b, x, raise_on_not_converged=False):
@@ -516,6 +536,11 @@ class IBSolver:
 
     def solve_step(self, u_n, up, X, raise_on_not_converged=False):
         return ib_solve_step(self.handle, u_n, up, X, self.n_points, raise_on_not_converged)
+
+    def solve_step_newton(self, u_n, up, X, max_newton=20, tol_newton=1e-9, raise_on_not_converged=False):
+        """One implicit step with the spring force at X^{n+1}, by Newton's method."""
+        return ib_solve_step_newton(self.handle, u_n, up, X, self.n_points, max_newton, tol_newton,
+                                    raise_on_not_converged)
 
     def solve(self, b, x, raise_on_not_converged=False):
         """x = A_0^{-1} b by MG-preconditioned FGMRES (the points do not move)."""

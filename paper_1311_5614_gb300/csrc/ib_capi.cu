@@ -265,8 +265,13 @@ int setup_hierarchy(Problem& P) {
   } else {
     for (int l = 0; l < ns; ++l) IB_TRY(launch_assemble_struct(P, l));
   }
+  // a step of the FP32 V-cycle that is not stiff eliminates its structure boxes in
+  // FP32 (the inverses are stored, and applied, in FP64); an escalation to the
+  // mixed V-cycle re-forms them in FP64 (reform_struct64)
+  const bool inv32 = P.inv32 && P.prm.precision == IB_FP32_PRECOND && P.sigma < P.stiff_sigma;
   bool all_done = false;
-  IB_TRY(launch_invert_struct_all(P, &all_done));
+  IB_TRY(launch_invert_struct_all(P, &all_done, inv32));
+  P.struct_inv32 = inv32 && all_done;
   if (!all_done)
     for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_form));
   if (P.prm.walls)
@@ -278,6 +283,27 @@ int setup_hierarchy(Problem& P) {
   IB_TRY(launch_invert(P, P.Mcoarse, P.nc + P.nborder, 1));
   IB_TRY(vcycle_reset_rE(P));
   if (P.nn_sch) IB_TRY(learned_struct_channel(P));
+  return check_dev_err(P);
+}
+
+// The structure-box blocks of this step formed again and inverted in FP64, for a
+// solve that escalates from the FP32 V-cycle to the mixed one after a set-up that
+// eliminated them in FP32 (the same sequence as in setup_hierarchy).
+int reform_struct64(Problem& P) {
+  const int ns = P.nlev - 1;
+  for (int l = 0; l < ns; ++l) IB_TRY(launch_struct_fill(P, l));
+  if (P.win_step) {
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_struct_from_windows(P, l));
+  } else {
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_assemble_struct(P, l));
+  }
+  bool all_done = false;
+  IB_TRY(launch_invert_struct_all(P, &all_done, false));
+  if (!all_done)
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, P.nB, P.lev[l].n_form));
+  if (P.prm.walls)
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_ring_copy(P, l));
+  P.struct_inv32 = false;
   return check_dev_err(P);
 }
 
@@ -301,7 +327,8 @@ void free_problem(Problem* P) {
   P->gstream = nullptr;
   dfree(P->X); dfree(P->springs); dfree(P->kappa); dfree(P->rest);
   dfree(P->adj_ptr); dfree(P->adj_spring); dfree(P->adj_other);
-  dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->U64); dfree(P->U32);
+  dfree(P->K64); dfree(P->K32); dfree(P->F); dfree(P->Fs); dfree(P->U64); dfree(P->U32);
+  dfree(P->Xn); dfree(P->Xk); dfree(P->Dk); dfree(P->Gk);
   dfree(P->G64); dfree(P->rc_pt); dfree(P->rc_w); dfree(P->rc_start); dfree(P->rc_cnt);
   dfree(P->Mcoarse); dfree(P->inv_ws); dfree(P->inv_perm); dfree(P->V); dfree(P->Z); dfree(P->Z64); dfree(P->H); dfree(P->givens);
   dfree(P->dots); dfree(P->scal); dfree(P->x64); dfree(P->b64); dfree(P->t64); dfree(P->t64b);
@@ -367,6 +394,7 @@ int allocate(Problem& P) {
   if (np > 0) {
     IB_TRY(dalloc(&P.X, 2ul * np));
     IB_TRY(dalloc(&P.F, 2ul * np));
+    if (ns > 0) IB_TRY(dalloc(&P.Fs, 2ul * ns));
     IB_TRY(dalloc(&P.U64, 2ul * np));
     if (P.windows && ns > 0) {
       IB_TRY(dalloc(&P.G64, 2ul * np));
@@ -552,6 +580,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       return IB_OK;
     }
     if (total >= P.prm.max_iters) break;
+    if (st->escalated_at >= 0 && P.struct_inv32) IB_TRY(reform_struct64(P));
     int mav = std::min(P.max_m, P.prm.max_iters - total);
     const int cycle_start = total;
     IB_TRY(launch_fill<double>(P, g, (size_t)m + 1, 0.0));
@@ -735,6 +764,114 @@ int solve_step_impl(Problem& P, const double* u_n, double* up, double* X, ib_sta
   return rc;
 }
 
+// One implicit step with the spring force taken at the new positions (a nonlinear
+// backward-Euler step, the body of ib_solve_step_newton), solved by Newton's method:
+// S and S* stay at X^n (lagged, as in the linearised step), the springs' force and
+// Jacobian are evaluated at the iterate X^k = X^n + dt S*^n u^k, and iteration k
+// solves the linearised step's system with J(X^k) and the right-hand side
+// -(rho/dt) u^n - S [F(X^k) - J(X^k)(X^k - X^n)].  u^0 = 0: the first iterate is the
+// linearised step.  Stops when max |X^{k+1} - X^k| <= tol h (k >= 1) or after
+// max_newton solves.
+int newton_step_impl(Problem& P, const double* u_n, double* up, double* X, int max_newton, double tol,
+                     ib_stats* stats, double* newton) {
+  if (max_newton < 1) return fail(IB_ERR_INVALID_ARG, "max_newton must be >= 1");
+  if (!(tol >= 0.0)) return fail(IB_ERR_INVALID_ARG, "tol_newton must be >= 0");
+  if (P.prm.time_method == IB_EXPLICIT)
+    return fail(IB_ERR_INVALID_ARG, "the Newton step needs the implicit-time method");
+  if (P.np > 0 && !X) return fail(IB_ERR_INVALID_ARG, "X is NULL");
+  ib_stats local;
+  ib_stats* st = stats ? stats : &local;
+  std::memset(st, 0, sizeof(*st));
+  st->escalated_at = -1;
+  const size_t n = 3ul * P.prm.N * P.prm.N, np2 = 2ul * P.np;
+  if (P.np == 0 || P.ns == 0) {  // no springs: nothing nonlinear
+    const int rc = solve_step_impl(P, u_n, up, X, st);
+    if (newton) { newton[0] = 1.0; newton[1] = 0.0; }
+    return rc;
+  }
+  if (!P.Xn) IB_TRY(dalloc(&P.Xn, np2));
+  if (!P.Xk) IB_TRY(dalloc(&P.Xk, np2));
+  if (!P.Dk) IB_TRY(dalloc(&P.Dk, np2));
+  if (!P.Gk) IB_TRY(dalloc(&P.Gk, np2));
+  IB_CUDA_TRY(cudaMemcpyAsync(P.Xn, X, sizeof(double) * np2, cudaMemcpyDeviceToDevice, P.stream));
+  std::vector<double> xa(np2), xb(np2);
+  const double h = P.prm.L / P.prm.N, Lp = P.prm.L;
+  double change = 0.0, t_setup = 0.0, t_solve = 0.0;
+  int k = 0, total_iters = 0, rc = IB_OK;
+  struct ClearXs {  // the springs go back to P.X on every exit
+    Problem& P;
+    ~ClearXs() { P.Xs = nullptr; }
+  } clear_xs{P};
+  for (; k < max_newton; ++k) {
+    IB_CUDA_TRY(cudaMemcpyAsync(P.X, P.Xn, sizeof(double) * np2, cudaMemcpyDeviceToDevice, P.stream));
+    P.Xs = k == 0 ? nullptr : P.Xk;
+    IB_CUDA_TRY(cudaEventRecord(P.ev[0], P.stream));
+    rc = setup_hierarchy(P);
+    if (rc != IB_OK) { st->status = rc; return rc; }
+    IB_TRY(launch_fill<double>(P, P.b64, n, 0.0));
+    if (k > 0) IB_TRY(launch_newton_force(P));
+    IB_TRY(launch_spread_force(P, P.b64));
+    if (u_n && P.prm.rho != 0.0) {
+      const long n2 = 2L * P.prm.N * P.prm.N;
+      KScope ks(P, IB_KC_OTHER, 3.0 * n2 * 8.0);
+      k_axpy_n<<<(int)((n2 + 255) / 256), 256, 0, P.stream>>>(-P.prm.rho / P.prm.dt, u_n, P.b64, n2);
+      IB_LAUNCH_CHECK();
+    }
+    if (P.prm.walls) IB_TRY(launch_wall_rhs(P, P.b64));
+    IB_CUDA_TRY(cudaEventRecord(P.ev[1], P.stream));
+    ib_stats sk;
+    std::memset(&sk, 0, sizeof(sk));
+    sk.escalated_at = -1;
+    rc = P.prm.precision != IB_FP32_PRECOND ? fgmres<double>(P, P.b64, P.x64, &sk)
+                                            : fgmres<float>(P, P.b64, P.x64, &sk);
+    IB_CUDA_TRY(cudaEventRecord(P.ev[2], P.stream));
+    total_iters += sk.iters;
+    st->restarts += sk.restarts;
+    st->rel_res_true = sk.rel_res_true;
+    st->rel_res_est = sk.rel_res_est;
+    st->escalated_at = sk.escalated_at;
+    if (rc != IB_OK && rc != IB_ERR_NOT_CONVERGED) { st->status = rc; return rc; }
+    IB_TRY(launch_pressure_mean_remove(P, P.x64));
+    IB_TRY(launch_move_points(P, P.x64));  // P.X = X^{k+1} (interpolation at X^n)
+    IB_CUDA_TRY(cudaMemcpyAsync(xa.data(), P.X, sizeof(double) * np2, cudaMemcpyDeviceToHost, P.stream));
+    IB_CUDA_TRY(cudaMemcpyAsync(xb.data(), k == 0 ? P.Xn : P.Xk, sizeof(double) * np2, cudaMemcpyDeviceToHost,
+                                P.stream));
+    IB_CUDA_TRY(cudaMemcpyAsync(P.Xk, P.X, sizeof(double) * np2, cudaMemcpyDeviceToDevice, P.stream));
+    IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, P.ev[0], P.ev[1]);
+    cudaEventElapsedTime(&b, P.ev[1], P.ev[2]);
+    t_setup += a;
+    t_solve += b;
+    change = 0.0;
+    for (size_t i = 0; i < np2; ++i) {
+      double d = xa[i] - xb[i];
+      d -= Lp * std::rint(d / Lp);
+      change = std::max(change, std::fabs(d));
+    }
+    change /= h;
+    if (rc == IB_ERR_NOT_CONVERGED) { ++k; break; }
+    if (k >= 1 && change <= tol) { ++k; break; }
+  }
+  std::string msg = g_err;
+  IB_CUDA_TRY(cudaMemcpyAsync(up, P.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  IB_CUDA_TRY(cudaMemcpyAsync(X, P.X, sizeof(double) * np2, cudaMemcpyDeviceToDevice, P.stream));
+  IB_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  st->iters = total_iters;
+  st->t_setup_ms = (float)t_setup;
+  st->t_solve_ms = (float)t_solve;
+  int nsb = 0;
+  for (int l = 0; l < P.nlev - 1; ++l) nsb += P.lev[l].n_struct;
+  st->n_struct_boxes = nsb;
+  st->status = rc;
+  if (newton) {
+    newton[0] = (double)k;
+    newton[1] = change;
+  }
+  g_err = msg;
+  return rc;
+}
+
 }  // namespace
 }  // namespace ib
 
@@ -816,6 +953,7 @@ int ib_setup(const ib_params* params, int32_t n_points, const double* X, int32_t
   P.stiff_sigma = stiff_threshold();
   if (const char* e = std::getenv("IB_WINDOWS")) P.windows = e[0] != '0';
   if (const char* e = std::getenv("IB_ROW_LISTS")) P.row_lists = e[0] != '0';
+  if (const char* e = std::getenv("IB_INV32")) P.inv32 = e[0] != '0';
   int Nc = params->box > 4 ? params->box : 4;
   for (int N = params->N; N >= Nc; N /= 2) {
     LevelInfo L;
@@ -1021,6 +1159,13 @@ int ib_solve_step(ib_problem* H, const double* u_n, double* up, double* X, ib_st
   g_err.clear();
   if (!H || !up) return fail(IB_ERR_INVALID_ARG, "NULL argument");
   return solve_step_impl(H->P, u_n, up, X, stats);
+}
+
+int ib_solve_step_newton(ib_problem* H, const double* u_n, double* up, double* X, int32_t max_newton,
+                         double tol_newton, ib_stats* stats, double* newton) {
+  g_err.clear();
+  if (!H || !up) return fail(IB_ERR_INVALID_ARG, "NULL argument");
+  return newton_step_impl(H->P, u_n, up, X, max_newton, tol_newton, stats, newton);
 }
 
 int ib_solve(ib_problem* H, const double* b, double* x, ib_stats* stats) {

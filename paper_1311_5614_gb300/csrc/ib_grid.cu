@@ -177,16 +177,24 @@ __global__ void k_coarse_fill(double* M, int N, StokesCoef<double> c, int nz, in
 constexpr int INV_MAXN = 256;
 constexpr int INV_MAXN_BLOCKED = 1024;
 
+// Magnitude of x as an integer key: a non-negative float or double orders like its
+// bit pattern.
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+  return (unsigned long long)__double_as_longlong(fabs(x));
+}
+__device__ __forceinline__ unsigned long long mag_key(float x) { return (unsigned long long)__float_as_uint(fabsf(x)); }
+
 // Pivot row of column `col` among rows first..n-1 of the row-major matrix A (row
 // stride ld): the largest magnitude, the lowest row on ties; found by one warp, the
-// magnitudes compared as integers (a non-negative double orders like its bit
-// pattern, so the FP64 pipe is left to the elimination; a NaN compares above every
-// finite value and is then caught as a non-finite pivot).  Lane 0 holds the result.
-__device__ __forceinline__ int warp_pivot_row(const double* A, int ld, int col, int first, int n, int lane) {
+// magnitudes compared as integer keys (so the floating-point pipe is left to the
+// elimination; a NaN compares above every finite value and is then caught as a
+// non-finite pivot).  Lane 0 holds the result.
+template <typename TE>
+__device__ __forceinline__ int warp_pivot_row(const TE* A, int ld, int col, int first, int n, int lane) {
   unsigned long long best = 0ull;
   int bi = n;
   for (int i = first + lane; i < n; i += 32) {
-    const unsigned long long a = (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ld + col]));
+    const unsigned long long a = mag_key(A[(size_t)i * ld + col]);
     if (bi == n || a > best) { best = a; bi = i; }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -205,10 +213,11 @@ __device__ __forceinline__ int warp_pivot_row(const double* A, int ld, int col, 
 // read from the rows before the interchange (rows k and p trade places), so a step
 // is one pivot search by warp 0 (which also forms the one reciprocal), one read
 // pass and one update pass, three barriers.
-__device__ void gj_invert_cols(double* M, int n, int* err) {
-  __shared__ double f[INV_MAXN];
+template <typename TE>
+__device__ void gj_invert_cols(TE* M, int n, int* err) {
+  __shared__ TE f[INV_MAXN];
   __shared__ int perm[INV_MAXN];
-  __shared__ double sinv;
+  __shared__ TE sinv;
   __shared__ int prow;
   const int tid = threadIdx.x, bd = blockDim.x;
   const int R = bd / n > 0 ? bd / n : 1;
@@ -217,33 +226,37 @@ __device__ void gj_invert_cols(double* M, int n, int* err) {
     if (tid < 32) {
       const int p = warp_pivot_row(M, n, k, k, n, tid);
       if (tid == 0) {
-        double piv = M[p * n + k];
+        TE piv = M[p * n + k];
         if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
           atomicOr(err, DEV_ERR_SINGULAR);
-          piv = 1.0;
+          piv = TE(1);
         }
         prow = p;
         perm[k] = p;
-        sinv = 1.0 / piv;
+        sinv = TE(1) / piv;
       }
     }
     __syncthreads();
     const int p = prow;
-    const double inv = sinv;
+    const TE inv = sinv;
     // after the interchange row k is the old row p and row p the old row k
-    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : M[(i == p ? k : i) * n + k];
-    double mkj = 0.0, okj = 0.0;
+    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? TE(0) : M[(i == p ? k : i) * n + k];
+    TE mkj = TE(0), okj = TE(0);
     if (r0 < R) {
-      mkj = (jc == k ? 1.0 : M[p * n + jc]) * inv;
+      mkj = (jc == k ? TE(1) : M[p * n + jc]) * inv;
       okj = M[k * n + jc];
     }
     __syncthreads();
-    // row k scaled (its pivot entry becomes 1/pivot); other rows updated
+    // row k scaled (its pivot entry becomes 1/pivot); other rows updated, the
+    // pivot column's entries as 0 - f_i / pivot so that a warp runs one FMA per row
     if (r0 < R) {
       for (int i = r0; i < n; i += R) {
-        if (i == k) M[k * n + jc] = mkj;
-        else if (jc == k) M[i * n + k] = -f[i] * mkj;
-        else M[i * n + jc] = (i == p ? okj : M[i * n + jc]) - f[i] * mkj;
+        if (i == k) {
+          M[k * n + jc] = mkj;
+          continue;
+        }
+        const TE old = (jc == k) ? TE(0) : (i == p ? okj : M[i * n + jc]);
+        M[i * n + jc] = fma(-f[i], mkj, old);
       }
     }
     __syncthreads();
@@ -252,7 +265,7 @@ __device__ void gj_invert_cols(double* M, int n, int* err) {
     const int p = perm[k];
     if (p != k)
       for (int i = tid; i < n; i += bd) {
-        const double t = M[i * n + k];
+        const TE t = M[i * n + k];
         M[i * n + k] = M[i * n + p];
         M[i * n + p] = t;
       }
@@ -440,16 +453,19 @@ struct InvBatch {
   int narr;
 };
 
+// TE: the type of the elimination (the matrices are stored in FP64 either way).
+template <typename TE>
 __global__ void k_invert_batch(InvBatch B, int n, int* err) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TE* sm = reinterpret_cast<TE*>(smraw);
   int l = 0;
   while (l + 1 < B.narr && (int)blockIdx.x >= B.start[l + 1]) ++l;
   double* M = B.M[l] + (size_t)(blockIdx.x - B.start[l]) * n * n;
   const int nn = n * n;
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) sm[e] = M[e];
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) sm[e] = (TE)M[e];
   __syncthreads();
-  gj_invert_cols(sm, n, err);
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = sm[e];
+  gj_invert_cols<TE>(sm, n, err);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = (double)sm[e];
 }
 
 // One matrix per CTA, staged in shared memory (n^2 doubles of dynamic shared memory).
@@ -459,7 +475,7 @@ __global__ void k_invert_sm(double* Ms, int n, int* err) {
   const int nn = n * n;
   for (int e = threadIdx.x; e < nn; e += blockDim.x) sm[e] = M[e];
   __syncthreads();
-  gj_invert_cols(sm, n, err);
+  gj_invert_cols<double>(sm, n, err);
   for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = sm[e];
 }
 
@@ -712,7 +728,7 @@ int launch_invert(Problem& P, double* M, int n, int count) {
       ae = cudaFuncSetAttribute(k_invert_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     });
     IB_CUDA_TRY(ae);
-    int threads = n <= 32 ? 64 : (n <= 64 ? 128 : 256);
+    const int threads = 256;
     k_invert_sm<<<count, threads, smem, P.stream>>>(M, n, P.dev_err);
   } else {
     IB_TRY(launch_invert_blocked(P, M, n, count));
@@ -723,11 +739,12 @@ int launch_invert(Problem& P, double* M, int n, int count) {
 
 // All structure-box inverses of the smoothing levels in one launch (n_B^2 doubles
 // of shared memory per CTA); returns false if they do not fit in shared memory,
-// in which case the caller inverts level by level.
-int launch_invert_struct_all(Problem& P, bool* done) {
+// in which case the caller inverts level by level.  fp32: the elimination in FP32
+// (the inverses stored in FP64 as before).
+int launch_invert_struct_all(Problem& P, bool* done, bool fp32) {
   *done = false;
   const int n = P.nB;
-  const size_t smem = (size_t)n * n * sizeof(double);
+  const size_t smem = (size_t)n * n * (fp32 ? sizeof(float) : sizeof(double));
   if (n == 5 || smem > 160u * 1024u || P.nlev - 1 > 16) return IB_OK;
   InvBatch B;
   std::memset(&B, 0, sizeof(B));
@@ -744,12 +761,17 @@ int launch_invert_struct_all(Problem& P, bool* done) {
   static std::once_flag once;
   cudaError_t ae = cudaSuccess;
   std::call_once(once, [&] {
-    ae = cudaFuncSetAttribute(k_invert_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    ae = cudaFuncSetAttribute(k_invert_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (ae == cudaSuccess)
+      ae = cudaFuncSetAttribute(k_invert_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   });
   IB_CUDA_TRY(ae);
-  const int threads = n <= 32 ? 64 : (n <= 64 ? 128 : 256);
-  KScope ks(P, IB_KC_SETUP, 2.0 * tot * smem);
-  k_invert_batch<<<tot, threads, smem, P.stream>>>(B, n, P.dev_err);
+  const int threads = 256;
+  KScope ks(P, IB_KC_SETUP, 2.0 * tot * n * n * sizeof(double));
+  if (fp32)
+    k_invert_batch<float><<<tot, threads, smem, P.stream>>>(B, n, P.dev_err);
+  else
+    k_invert_batch<double><<<tot, threads, smem, P.stream>>>(B, n, P.dev_err);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }

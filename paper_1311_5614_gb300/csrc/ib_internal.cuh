@@ -264,6 +264,8 @@ struct Problem {
   bool box_form_pinned = false;
   double sigma = 0.0;                 // stiffness ratio dt * max(kappa) / mu of the structure
   double stiff_sigma = 3000.0;        // FP32 mode: from this sigma on, precondition with the mixed V-cycle
+  bool inv32 = true;                  // IB_INV32=0 (read at ib_setup): structure boxes always inverted in FP64
+  bool struct_inv32 = false;          // this set-up's structure-box inverses came from an FP32 elimination
   cudaStream_t gstream = nullptr;                 // private stream the graph is captured on
   long long graph_launches[2][IB_KC_COUNT] = {};
   cudaStream_t stream = nullptr;
@@ -284,7 +286,15 @@ struct Problem {
   int* adj_other = nullptr;   // [2 ns]
   double* K64 = nullptr;      // [3][ns]
   float* K32 = nullptr;       // [3][ns]
-  double* F = nullptr;        // [np][2] spring force at X
+  double* F = nullptr;        // [np][2] spring force at X (gathered per point from Fs)
+  double* Fs = nullptr;       // [ns][2] force of each spring on its first end
+  // Newton steps (ib_solve_step_newton): the points the springs are evaluated at
+  // (NULL: X), X^n, the iterate X^k, and per-point scratch
+  const double* Xs = nullptr;
+  double* Xn = nullptr;       // [np][2]
+  double* Xk = nullptr;       // [np][2]
+  double* Dk = nullptr;       // [2][np] X^k - X^n
+  double* Gk = nullptr;       // [2][np] J(X^k) (X^k - X^n)
   double* U64 = nullptr;      // [2][np] interpolated velocity scratch
   double* G64 = nullptr;      // [2][np] J U per point (the operator's spread by row lists)
   // Level-0 row lists, rebuilt at every set-up with the assembled rows: for each
@@ -403,6 +413,8 @@ int launch_fine_patches(Problem& P);
 int launch_coarse_patches(Problem& P, int level);
 int launch_cast_patches(Problem& P, int level);
 int launch_spring_force_jacobian(Problem& P);
+// F <- F - J (X^k - X^n) at the Newton iterate (F and J evaluated at P.Xs = X^k).
+int launch_newton_force(Problem& P);
 int launch_spread_force(Problem& P, double* b);  // b_vel -= S F
 int launch_move_points(Problem& P, const double* up);
 template <typename T>
@@ -426,7 +438,7 @@ int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool re
 int launch_free_box(Problem& P, int level);
 int launch_struct_fill(Problem& P, int level);
 int launch_invert(Problem& P, double* M, int n, int count);
-int launch_invert_struct_all(Problem& P, bool* done);
+int launch_invert_struct_all(Problem& P, bool* done, bool fp32 = false);
 int launch_coarse_fill(Problem& P);
 template <typename T>
 int launch_fill(Problem& P, T* x, size_t n, T v);

@@ -120,7 +120,7 @@ __global__ void k_cast_d2f(const double* __restrict__ x, float* __restrict__ y, 
 // s = 1 - L0 / l (clamped at 0 for the negative-semidefinite variant).
 __global__ void k_springs(const double* __restrict__ X, const int* __restrict__ ij,
                           const double* __restrict__ kappa, const double* __restrict__ rest,
-                          int ns, double L, int clamped, double* F, double* K64, float* K32,
+                          int ns, double L, int clamped, double* Fs, double* K64, float* K32,
                           int* err) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ns) return;
@@ -142,10 +142,8 @@ __global__ void k_springs(const double* __restrict__ X, const int* __restrict__ 
   } else {
     atomicOr(err, DEV_ERR_NONFINITE);
   }
-  atomicAdd(&F[2 * i], fx);
-  atomicAdd(&F[2 * i + 1], fy);
-  atomicAdd(&F[2 * j], -fx);
-  atomicAdd(&F[2 * j + 1], -fy);
+  Fs[2 * e] = fx;  // on end i; -f on end j (gathered per point by k_point_force)
+  Fs[2 * e + 1] = fy;
   K64[e] = kxx;
   K64[ns + e] = kxy;
   K64[2 * ns + e] = kyy;
@@ -154,6 +152,44 @@ __global__ void k_springs(const double* __restrict__ X, const int* __restrict__ 
     K32[ns + e] = (float)kxy;
     K32[2 * ns + e] = (float)kyy;
   }
+}
+
+// F at each point: the forces of its springs in adjacency order (+f on a spring's
+// first end, -f on its second), one writer per point, so the sum's order is fixed.
+__global__ void k_point_force(const int* __restrict__ adj_ptr, const int* __restrict__ adj_spring,
+                              const int* __restrict__ ij, const double* __restrict__ Fs, int np,
+                              double* __restrict__ F) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  double fx = 0.0, fy = 0.0;
+  for (int q = adj_ptr[k]; q < adj_ptr[k + 1]; ++q) {
+    const int e = adj_spring[q];
+    const double sg = ij[2 * e] == k ? 1.0 : -1.0;
+    fx += sg * Fs[2 * e];
+    fy += sg * Fs[2 * e + 1];
+  }
+  F[2 * k] = fx;
+  F[2 * k + 1] = fy;
+}
+
+// Newton iterate: D = X^k - X^n per point ([2][np], periodic minimum image).
+__global__ void k_newton_disp(const double* __restrict__ Xk, const double* __restrict__ Xn, int np, double L,
+                              double* __restrict__ D) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  double dx = Xk[2 * k] - Xn[2 * k], dy = Xk[2 * k + 1] - Xn[2 * k + 1];
+  dx -= L * rint(dx / L);
+  dy -= L * rint(dy / L);
+  D[k] = dx;
+  D[np + k] = dy;
+}
+
+// F <- F - G (G = J D in [2][np] layout, F interleaved).
+__global__ void k_newton_force(const double* __restrict__ G, int np, double* __restrict__ F) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  F[2 * k] -= G[k];
+  F[2 * k + 1] -= G[np + k];
 }
 
 // b_c -= (S F)_c on the fine grid: delta_h = phi phi / h^2 (point forces).
@@ -449,12 +485,16 @@ int launch_cast_patches(Problem& P, int level) {
 
 int launch_spring_force_jacobian(Problem& P) {
   if (P.np == 0) return IB_OK;
-  IB_CUDA_TRY(cudaMemsetAsync(P.F, 0, sizeof(double) * 2 * P.np, P.stream));
-  if (P.ns == 0) return IB_OK;
+  if (P.ns == 0) {
+    IB_CUDA_TRY(cudaMemsetAsync(P.F, 0, sizeof(double) * 2 * P.np, P.stream));
+    return IB_OK;
+  }
   KScope ks(P, IB_KC_SETUP, P.ns * 100.0);
-  k_springs<<<nblk(P.ns), TPB, 0, P.stream>>>(P.X, P.springs, P.kappa, P.rest, P.ns, P.prm.L,
-                                              P.prm.jacobian == IB_JAC_CLAMPED, P.F, P.K64, P.K32,
+  k_springs<<<nblk(P.ns), TPB, 0, P.stream>>>(P.Xs ? P.Xs : P.X, P.springs, P.kappa, P.rest, P.ns, P.prm.L,
+                                              P.prm.jacobian == IB_JAC_CLAMPED, P.Fs, P.K64, P.K32,
                                               P.dev_err);
+  IB_LAUNCH_CHECK();
+  k_point_force<<<nblk(P.np), TPB, 0, P.stream>>>(P.adj_ptr, P.adj_spring, P.springs, P.Fs, P.np, P.F);
   IB_LAUNCH_CHECK();
   return IB_OK;
 }
@@ -494,6 +534,18 @@ Springs<float> springs_view<float>(Problem& P) {
   s.adj_other = P.adj_other; s.K = P.K32;
   return s;
 }
+int launch_newton_force(Problem& P) {
+  if (P.np == 0 || P.ns == 0 || !P.Xs) return IB_OK;
+  KScope ks(P, IB_KC_OTHER, P.np * 80.0);
+  k_newton_disp<<<nblk(P.np), TPB, 0, P.stream>>>(P.Xs, P.Xn, P.np, P.prm.L, P.Dk);
+  IB_LAUNCH_CHECK();
+  k_point_JU<<<nblk(P.np), TPB, 0, P.stream>>>(springs_view<double>(P), P.Dk, P.Gk);
+  IB_LAUNCH_CHECK();
+  k_newton_force<<<nblk(P.np), TPB, 0, P.stream>>>(P.Gk, P.np, P.F);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
 template <typename T>
 static Patches<T> patches_of(LevelInfo& L);
 template <>

@@ -865,6 +865,93 @@ bool launch_box_form(Problem& P, int l, int form, T* w, const T* b, T* E, int co
   }
 }
 
+// Big boxes (8 x 8 and 16 x 16: 208 and 800 unknowns) in two launches per colour:
+// kv_bigres takes the residuals of the colour's boxes (one CTA per box, into
+// rbox), then kv_bigsolve multiplies them by the box inverses with the rows of a
+// box split over CTAs of 32 rows (8 warps share the sum over the columns), so that
+// a structure box's FP64 product (n_B^2 FMAs) spreads over n_B / 32 SMs instead of
+// one.  Boxes of one colour share no unknowns, so every residual of the colour can
+// be taken before any update, as in the other forms.
+constexpr int BIG_NB_MAX = 800;
+
+template <typename T>
+__global__ void __launch_bounds__(256) kv_bigres(const T* __restrict__ w, const T* __restrict__ b, T* rE,
+                                                 T* __restrict__ rbox, int N, StokesCoef<T> c, int color, int bs,
+                                                 int nB, const int* __restrict__ slot) {
+  pdl_enter();
+  const int nb = N / bs, half = nb >> 1, t = blockIdx.x;
+  const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+  const int sl = slot[J * nb + I];
+  const int nV = 2 * bs * (bs + 1);
+  for (int q = threadIdx.x; q < nB; q += blockDim.x) {
+    int cc, i, j;
+    box_unknown(q, bs, I * bs, J * bs, N, &cc, &i, &j);
+    const int gq = cc * N * N + j * N + i;
+    T r = b[gq] - stokes_row(w, N, c, cc, i, j);
+    if (rE && sl >= 0 && q < nV) {
+      r += rE[gq];
+      rE[gq] = (T)0;
+    }
+    rbox[(size_t)t * nB + q] = r;
+  }
+}
+
+// grid (row chunks of 32, boxes of the colour)
+template <typename T, typename TM>
+__global__ void __launch_bounds__(256) kv_bigsolve(T* w, const T* __restrict__ rbox, int N, int color, int bs,
+                                                   int nB, const int* __restrict__ slot,
+                                                   const double* __restrict__ Ms, const TM* __restrict__ Mf) {
+  __shared__ T rs[BIG_NB_MAX];
+  __shared__ double part[8][32];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int nb = N / bs, half = nb >> 1, t = blockIdx.y;
+  const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+  const int sl = slot[J * nb + I];
+  const int q = blockIdx.x * 32 + lane;
+  pdl_enter();
+  for (int s2 = tid; s2 < nB; s2 += 256) rs[s2] = rbox[(size_t)t * nB + s2];
+  __syncthreads();
+  double d = 0.0;
+  if (q < nB) {
+    if (sl >= 0) {
+      const double* M = Ms + (size_t)sl * nB * nB + q;
+      for (int s2 = wp; s2 < nB; s2 += 8) d += M[(size_t)s2 * nB] * (double)rs[s2];
+    } else {
+      const TM* M = Mf + q;
+      TM dm = 0;
+      for (int s2 = wp; s2 < nB; s2 += 8) dm += M[(size_t)s2 * nB] * (TM)rs[s2];
+      d = (double)dm;
+    }
+  }
+  part[wp][lane] = d;
+  __syncthreads();
+  if (wp == 0 && q < nB) {
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += part[k][lane];
+    int cc, i, j;
+    box_unknown(q, bs, I * bs, J * bs, N, &cc, &i, &j);
+    w[cc * N * N + j * N + i] += (T)sum;
+  }
+}
+
+template <typename T, typename TM>
+int launch_bigbox(Problem& P, int l, T* w, const T* b, T* E, int color) {
+  LevelInfo& L = P.lev[l];
+  const StokesCoef<T> c = coefs<T>(P, l);
+  const int half = L.nb / 2, nbox = half * half, nB = P.nB, bs = P.prm.box;
+  if (nB > BIG_NB_MAX) return fail(IB_ERR_INVALID_ARG, "box too large for the split box kernel");
+  T* rbox = lbuf<T>(L).r;  // 3 N^2 >= nbox * n_B: free during a sweep
+  const bool pdl = use_pdl(P);
+  vlaunch(pdl, kv_bigres<T>, nbox, 256, 0, P.stream, (const T*)w, b, E, rbox, L.N, c, color, bs, nB,
+          (const int*)L.flag);
+  IB_LAUNCH_CHECK();
+  vlaunch(pdl, kv_bigsolve<T, TM>, dim3((nB + 31) / 32, nbox), 256, 0, P.stream, w, (const T*)rbox, L.N, color,
+          bs, nB, (const int*)L.flag, (const double*)L.Mstruct, Mfree_of<TM>(L));
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
 template <typename T, typename TM>
 int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   LevelInfo& L = P.lev[l];
@@ -874,6 +961,9 @@ int launch_boxn(Problem& P, int l, T* w, const T* b, T* E, int color) {
   const double* Ms = L.Mstruct;
   const TM* Mf = Mfree_of<TM>(L);
   // the form the set-up timed fastest on this level, else the size rule
+  // 16 x 16 boxes, and 8 x 8 boxes on levels with fewer boxes per colour than SMs:
+  // the split form
+  if (P.prm.box == 16 || (P.prm.box == 8 && nbox < P.n_sm)) return launch_bigbox<T, TM>(P, l, w, b, E, color);
   const int tuned = l < 32 ? P.box_form[pix<T>()][l] : 0;
   if (tuned != BOXF_RULE && launch_box_form<T, TM>(P, l, tuned, w, b, E, color)) {
     IB_LAUNCH_CHECK();

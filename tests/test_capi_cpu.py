@@ -54,7 +54,7 @@ def test_version_and_defaults(capi):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("N", 48), ("N", 4), ("box", 3), ("mu", 0.0), ("dt", -1.0), ("rho", -1.0), ("tol", 0.0),
+    ("N", 48), ("N", 4), ("box", 3), ("box", 32), ("mu", 0.0), ("dt", -1.0), ("rho", -1.0), ("tol", 0.0),
     ("max_iters", 0), ("max_iters", 1000), ("nu1", 9), ("delta", 5), ("precision", 7), ("L", 0.0),
     ("restart", -1), ("escalate", 2)])
 def test_setup_rejects_bad_params(capi, field, value):
@@ -97,5 +97,6 @@ def test_null_handles_are_rejected(capi):
     assert L.ib_apply(None, 0, None, None) == capi.IB_ERR_INVALID_ARG
     assert L.ib_vcycle(None, None, None) == capi.IB_ERR_INVALID_ARG
     assert L.ib_solve_step(None, None, None, None, None) == capi.IB_ERR_INVALID_ARG
+    assert L.ib_solve_step_newton(None, None, None, None, 5, 1e-9, None, None) == capi.IB_ERR_INVALID_ARG
     assert L.ib_num_levels(None) == 0
     L.ib_destroy(None)

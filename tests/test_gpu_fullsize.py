@@ -67,6 +67,24 @@ def test_sweep_stiff_case_full_size(pkg):
     check_solution(p, A, Ss, up.cpu().numpy(), X.cpu().numpy())
 
 
+def test_sweep_stiff_case_fp32_elimination_then_escalation(pkg, monkeypatch):
+    """The same case held on the FP32 V-cycle (stiffness threshold raised): its
+    structure boxes are eliminated in FP32; the FP32 iteration stalls and escalates
+    mid-solve to the mixed V-cycle, which first re-forms and inverts the boxes in
+    FP64; the step meets the FP64 tolerance on the oracle's operator."""
+    monkeypatch.setenv("IB_STIFF_SIGMA", "1e12")
+    p = W.single_ellipse(N=256, n_points=512, kappa=1e6, dt=1e-2)
+    p.box = 4
+    A, Ss = fine_operator(p)
+    s = pkg.IBSolver.from_problem(p, precision="fp32", max_iters=200)
+    up = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+    X = dev(p.X)
+    st = s.solve_step(None, up, X)
+    s.close()
+    assert st["status"] == 0 and st["escalated_at"] > 0, st
+    check_solution(p, A, Ss, up.cpu().numpy(), X.cpu().numpy())
+
+
 def test_multi_ellipse_1024_apply_and_step(pkg):
     """1024^2 grid, 16 ellipses x 2048 points (seed 1311): the fine operator element
     by element, then one FP32-preconditioned step to the FP64 tolerance."""

@@ -155,3 +155,4 @@ print("ok")
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600,
                          cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     assert out.returncode == 0 and "ok" in out.stdout, out.stdout + out.stderr
+
