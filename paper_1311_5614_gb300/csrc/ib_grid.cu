@@ -468,6 +468,114 @@ __global__ void k_invert_batch(InvBatch B, int n, int* err) {
   for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = (double)sm[e];
 }
 
+// FP32 elimination of NB x NB box matrices (NB = 16 or 56: 2 x 2 and 4 x 4 boxes),
+// one warp per matrix with the matrix in registers: lane t holds columns t and
+// t + 32.  A step broadcasts column k through shared memory, finds the pivot
+// (integer keys, a butterfly so that every lane has it), reads the pivot row and
+// row k of its columns by selecting over the unrolled rows, and updates every row
+// of its columns with the interchange of rows k and p folded in, as in
+// gj_invert_cols; no block barriers.  The column interchanges that undo the row
+// interchanges are applied as the columns are written back.
+template <int NB>
+__global__ void __launch_bounds__(128) k_invert_warp_f32(InvBatch B, int total, int* err) {
+  constexpr int NC = (NB + 31) / 32;
+  __shared__ float fcol[4][NB];
+  __shared__ int sidx[4][NB];
+  __shared__ int spos[4][NB];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int mat = blockIdx.x * 4 + wq;
+  if (mat >= total) return;  // whole warps: no barrier below involves other warps
+  int l = 0;
+  while (l + 1 < B.narr && mat >= B.start[l + 1]) ++l;
+  double* M = B.M[l] + (size_t)(mat - B.start[l]) * NB * NB;
+  float a[NC][NB];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int j = lane + 32 * c;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) a[c][i] = j < NB ? (float)M[i * NB + j] : 0.f;
+  }
+  for (int k = 0; k < NB; ++k) {
+    const int lk = k & 31, ck = k >> 5;
+    if (lane == lk) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        float v = a[0][i];
+#pragma unroll
+        for (int c = 1; c < NC; ++c) v = ck == c ? a[c][i] : v;
+        fcol[wq][i] = v;
+      }
+    }
+    __syncwarp();
+    unsigned key = 0u;
+    int bi = NB;
+    for (int i = k + lane; i < NB; i += 32) {
+      const unsigned v = __float_as_uint(fabsf(fcol[wq][i]));
+      if (bi == NB || v > key) { key = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi < NB && (bi == NB || ok > key || (ok == key && oi < bi))) { key = ok; bi = oi; }
+    }
+    const int p = bi < NB ? bi : k;
+    float piv = fcol[wq][p];
+    if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
+      if (lane == 0) atomicOr(err, DEV_ERR_SINGULAR);
+      piv = 1.f;
+    }
+    const float inv = 1.f / piv;
+    if (lane == 0) sidx[wq][k] = p;
+    float mk[NC], okv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float ap = 0.f, akv = 0.f;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        ap = i == p ? a[c][i] : ap;
+        akv = i == k ? a[c][i] : akv;
+      }
+      mk[c] = (lane + 32 * c == k ? 1.f : ap) * inv;
+      okv[c] = akv;
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const float fi = i == k ? 0.f : fcol[wq][i == p ? k : i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float old = lane + 32 * c == k ? 0.f : (i == p ? okv[c] : a[c][i]);
+        a[c][i] = i == k ? mk[c] : fmaf(-fi, mk[c], old);
+      }
+    }
+    __syncwarp();
+  }
+  // column j of the result is eliminated column idx[j] (idx: 0..NB-1 through the
+  // interchanges k <-> p_k, k = NB-1 down to 0); eliminated column t goes to pos[t]
+  if (lane == 0) {
+    for (int j = 0; j < NB; ++j) spos[wq][j] = j;
+    for (int k = NB - 1; k >= 0; --k) {
+      const int p = sidx[wq][k];
+      if (p != k) {
+        const int t = spos[wq][k];
+        spos[wq][k] = spos[wq][p];
+        spos[wq][p] = t;
+      }
+    }
+  }
+  __syncwarp();
+  for (int j = lane; j < NB; j += 32) sidx[wq][spos[wq][j]] = j;
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int j = lane + 32 * c;
+    if (j >= NB) continue;
+    const int jo = sidx[wq][j];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) M[i * NB + jo] = (double)a[c][i];
+  }
+}
+
 // One matrix per CTA, staged in shared memory (n^2 doubles of dynamic shared memory).
 __global__ void k_invert_sm(double* Ms, int n, int* err) {
   extern __shared__ double sm[];
@@ -768,7 +876,11 @@ int launch_invert_struct_all(Problem& P, bool* done, bool fp32) {
   IB_CUDA_TRY(ae);
   const int threads = 256;
   KScope ks(P, IB_KC_SETUP, 2.0 * tot * n * n * sizeof(double));
-  if (fp32)
+  if (fp32 && n == 56)
+    k_invert_warp_f32<56><<<(tot + 3) / 4, 128, 0, P.stream>>>(B, tot, P.dev_err);
+  else if (fp32 && n == 16)
+    k_invert_warp_f32<16><<<(tot + 3) / 4, 128, 0, P.stream>>>(B, tot, P.dev_err);
+  else if (fp32)
     k_invert_batch<float><<<tot, threads, smem, P.stream>>>(B, n, P.dev_err);
   else
     k_invert_batch<double><<<tot, threads, smem, P.stream>>>(B, n, P.dev_err);

@@ -216,72 +216,91 @@ __global__ void k_spread_rows(const int* __restrict__ slot_row, int nrows, int N
   y[r] += scale * acc;
 }
 
-// Level-0 windows by rows: thread = (structure row, column component cc); the
-// row's entries (points k in order), each coupling of k (J_kk, then its springs'
-// blocks in adjacency order) and each interpolation node of the coupled point, in
-// that fixed order, add into the thread's half of the row window, kept in shared
-// memory (no other thread touches it), which the block then writes out: the same
-// sums as k_window_points, without atomics.  A block holds WROWS consecutive rows,
-// whose windows are contiguous in Ew.
-constexpr int WROWS = 16;
-__global__ void __launch_bounds__(2 * WROWS) k_window_rows(const int* __restrict__ slot_row, int nrows, int N,
-                                                           const int* __restrict__ start, const int* __restrict__ pt,
-                                                           const double* __restrict__ wt, Patches<double> pat,
-                                                           Springs<double> sp, double* __restrict__ Ew, int* err) {
-  __shared__ double sw[2 * WROWS * WSQ];
-  const int tid = threadIdx.x, s0 = blockIdx.x * WROWS;
-  const int s = s0 + (tid >> 1), cc = tid & 1;
-  double* mine = sw + tid * WSQ;  // the half-window (row s, component cc): s * WIN + cc * WSQ in Ew
-  for (int e = 0; e < WSQ; ++e) mine[e] = 0.0;
+// Level-0 windows by rows: one warp per structure row, each half-warp one column
+// component cc of the row's window and each of its 16 lanes one node (a, b) of
+// the 4 x 4 interpolation patch.  The row's entries (points k in order), each
+// coupling of k (J_kk, then its springs' blocks in adjacency order) add, in that
+// fixed order, into the row window kept in shared memory; within a coupling every
+// lane adds to a cell of its own, so each cell's sum runs in the same order as in
+// k_window_points, without atomics.  A block holds WROWS consecutive rows, whose
+// windows are contiguous in Ew.
+constexpr int WROWS = 8;
+__global__ void __launch_bounds__(32 * WROWS) k_window_rows(const int* __restrict__ slot_row, int nrows, int N,
+                                                            const int* __restrict__ start, const int* __restrict__ pt,
+                                                            const double* __restrict__ wt, Patches<double> pat,
+                                                            Springs<double> sp, double* __restrict__ Ew, int* err) {
+  __shared__ double sw[WROWS * WIN];
+  const int tid = threadIdx.x, lane = tid & 31, wr = tid >> 5;
+  const int s0 = blockIdx.x * WROWS, s = s0 + wr;
+  const int cc = lane >> 4, pa = lane & 3, pb = (lane >> 2) & 3;
+  double* mine = sw + wr * WIN + cc * WSQ;  // the half-window (row s, component cc)
+  for (int e = lane; e < WIN; e += 32) sw[wr * WIN + e] = 0.0;
+  __syncwarp();
   bool outside = false;
   if (s < nrows) {
     const int r = slot_row[s], n = N * N, c = r / n, rr = r - c * n, ri = rr % N, rj = rr / N;
     const int ns = sp.ns;
+    const int koff = (c == cc) ? (c == 0 ? 0 : 2) * ns : ns;  // J[c][cc] in K's [3][ns] layout
     for (int e = start[s]; e < start[s + 1]; ++e) {
       const int k = pt[e];
       const double ws = wt[e];
       const int a0 = sp.adj_ptr[k], deg = sp.adj_ptr[k + 1] - a0;
-      for (int q = 0; q <= deg; ++q) {
-        int l;
-        double Jc;  // J[c][cc]
-        if (q == 0) {
-          l = k;
-          Jc = 0.0;
-          for (int a = a0; a < a0 + deg; ++a) {
-            const int s2 = sp.adj_spring[a];
-            Jc -= (c == cc) ? sp.K[(c == 0 ? 0 : 2) * ns + s2] : sp.K[ns + s2];
-          }
-        } else {
-          const int s2 = sp.adj_spring[a0 + q - 1];
-          l = sp.adj_other[a0 + q - 1];
-          Jc = (c == cc) ? sp.K[(c == 0 ? 0 : 2) * ns + s2] : sp.K[ns + s2];
-        }
-        const double jv = ws * Jc;
-        if (jv == 0.0) continue;
-        // the coupled point's interpolation patch, loaded once
-        const int ix0 = pat.b_at(1, cc, 0, l), iy0 = pat.b_at(1, cc, 1, l);
-        double wx[PATCH], wy[PATCH];
-        int di[PATCH], dj[PATCH];
+      // the couplings of k: q = 0 the point itself (J_kk = -sum of its springs'
+      // blocks), q = 1..deg its springs' other ends; up to WQ of them have their
+      // loads issued together, then add in the order q = 0, 1, ...
+      constexpr int WQ = 4;
+      int lq[WQ];
+      double jq[WQ];
+      lq[0] = k;
+      jq[0] = 0.0;
+      if (deg < WQ) {
 #pragma unroll
-        for (int a = 0; a < PATCH; ++a) {
-          wx[a] = pat.w_at(1, cc, 0, a, l);
-          wy[a] = pat.w_at(1, cc, 1, a, l);
-          di[a] = sdiff(wrapi(ix0 + a, N), ri, N);
-          dj[a] = sdiff(wrapi(iy0 + a, N), rj, N);
+        for (int q = 1; q < WQ; ++q) {
+          if (q > deg) break;
+          lq[q] = sp.adj_other[a0 + q - 1];
+          jq[q] = sp.K[koff + sp.adj_spring[a0 + q - 1]];
         }
 #pragma unroll
-        for (int cb = 0; cb < PATCH; ++cb) {
-          if (wy[cb] == 0.0) continue;
+        for (int q = 1; q < WQ; ++q)
+          if (q <= deg) jq[0] -= jq[q];
+      } else {
+        for (int a = a0; a < a0 + deg; ++a) jq[0] -= sp.K[koff + sp.adj_spring[a]];
+      }
+      for (int q0 = 0; q0 <= deg; q0 += WQ) {
+        double wiq[WQ];
+        int cell[WQ];
 #pragma unroll
-          for (int ca = 0; ca < PATCH; ++ca) {
-            const double wi = wx[ca] * wy[cb];
-            if (wi == 0.0) continue;
-            if (di[ca] < -WR || di[ca] > WR || dj[cb] < -WR || dj[cb] > WR) {
-              outside = true;
-              continue;
-            }
-            mine[(dj[cb] + WR) * WD + di[ca] + WR] += jv * wi;
+        for (int u = 0; u < WQ; ++u) {
+          const int q = q0 + u;
+          wiq[u] = 0.0;
+          cell[u] = -1;
+          if (q > deg) continue;
+          int l;
+          if (q0 == 0 && deg < WQ) {
+            l = lq[u];
+          } else if (q == 0) {
+            l = k;
+          } else {
+            l = sp.adj_other[a0 + q - 1];
+            jq[u] = sp.K[koff + sp.adj_spring[a0 + q - 1]];
           }
+          if (q == 0) jq[u] = jq[0];
+          wiq[u] = pat.w_at(1, cc, 0, pa, l) * pat.w_at(1, cc, 1, pb, l);
+          const int di = sdiff(wrapi(pat.b_at(1, cc, 0, l) + pa, N), ri, N);
+          const int dj = sdiff(wrapi(pat.b_at(1, cc, 1, l) + pb, N), rj, N);
+          cell[u] = (di < -WR || di > WR || dj < -WR || dj > WR) ? -2 : (dj + WR) * WD + di + WR;
+        }
+#pragma unroll
+        for (int u = 0; u < WQ; ++u) {
+          const int q = q0 + u;
+          if (q > deg) break;
+          const double jv = ws * jq[u];
+          if (jv == 0.0 || wiq[u] == 0.0) continue;
+          if (cell[u] < 0) {
+            outside = true;
+            continue;
+          }
+          mine[cell[u]] += jv * wiq[u];
         }
       }
     }
@@ -290,7 +309,7 @@ __global__ void __launch_bounds__(2 * WROWS) k_window_rows(const int* __restrict
   __syncthreads();
   const int rows = nrows - s0 < WROWS ? nrows - s0 : WROWS;
   double* dst = Ew + (size_t)s0 * WIN;
-  for (int e = tid; e < rows * WIN; e += 2 * WROWS) dst[e] = sw[e];
+  for (int e = tid; e < rows * WIN; e += 32 * WROWS) dst[e] = sw[e];
 }
 
 // Prolongation weights of coarse column C along one direction (sec. 3.1): fine
@@ -407,13 +426,23 @@ __global__ void k_struct_from_windows(const int* __restrict__ box_of_slot, int n
   if (ws < 0) return;
   const double* row = Ew + (size_t)ws * WIN;
   double* Mb = M + (size_t)s * nB * nB;
-  for (int e = 0; e < WIN; ++e) {
-    const double v = row[e];
-    if (v == 0.0) continue;
-    const int cc = e / WSQ, rem = e - cc * WSQ;
-    const int cj = wrapi(j + rem / WD - WR, N), ci = wrapi(i + rem % WD - WR, N);
-    const int cq = box_local(cc, ci, cj, x0, y0, b, N);
-    if (cq >= 0) Mb[(size_t)cq * nB + q] += coef * v;
+  // the box's velocity columns, each at the window offsets congruent to its
+  // distance from the row modulo N (more than one only on grids narrower than the
+  // window), in the window's order: the same additions as walking the window
+  for (int cq = 0; cq < nv; ++cq) {
+    int cc, ci, cj;
+    box_unknown(cq, b, x0, y0, N, &cc, &ci, &cj);
+    int dx = sdiff(ci, i, N), dy = sdiff(cj, j, N);
+    while (dy - N >= -WR) dy -= N;
+    while (dx - N >= -WR) dx -= N;
+    for (int oy = dy; oy <= WR; oy += N) {
+      if (oy < -WR) continue;
+      for (int ox = dx; ox <= WR; ox += N) {
+        if (ox < -WR) continue;
+        const double v = row[cc * WSQ + (oy + WR) * WD + ox + WR];
+        if (v != 0.0) Mb[(size_t)cq * nB + q] += coef * v;
+      }
+    }
   }
 }
 
@@ -518,7 +547,7 @@ int launch_window_points(Problem& P) {
   sp.adj_other = P.adj_other; sp.K = P.K64;
   KScope ks(P, IB_KC_SETUP, 0.0);
   if (P.rows_ready)  // one writer per row half: a fixed summation order
-    k_window_rows<<<(L.n_rows + WROWS - 1) / WROWS, 2 * WROWS, 0, P.stream>>>(L.slot_row, L.n_rows, L.N, P.rc_start, P.rc_pt,
+    k_window_rows<<<(L.n_rows + WROWS - 1) / WROWS, 32 * WROWS, 0, P.stream>>>(L.slot_row, L.n_rows, L.N, P.rc_start, P.rc_pt,
                                                              P.rc_w, L.pat64, sp, L.Ew64, P.dev_err);
   else
     k_window_points<<<nblk(256L * P.np), TPB, 0, P.stream>>>(L.pat64, sp, L.N, L.rowslot, L.Ew64, P.dev_err);
