@@ -218,9 +218,12 @@ int setup_hierarchy(Problem& P) {
         P.graph_dirty[0] = P.graph_dirty[1] = true;
         dfree(L.Ew64);
         dfree(L.Ew32);
+        dfree(L.crow);
         const int cap = cnt + cnt / 4 + 64;
         IB_TRY(dalloc(&L.Ew64, (size_t)cap * WIN));
         if (P.has32 || P.prm.precision == IB_FP32_PRECOND) IB_TRY(dalloc(&L.Ew32, (size_t)cap * WIN));
+        IB_TRY(dalloc(&L.crow, 4ul * cap));
+        if (!L.ccount) IB_TRY(dalloc(&L.ccount, 4));
         L.cap_rows = cap;
       }
       L.n_rows = cnt;
@@ -262,6 +265,7 @@ int setup_hierarchy(Problem& P) {
     for (int l = 1; l < P.nlev; ++l) IB_TRY(launch_window_galerkin(P, l));
     for (int l = 0; l < ns; ++l) IB_TRY(launch_struct_from_windows(P, l));
     for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_window_cast(P, l));
+    for (int l = 0; l < P.nlev; ++l) IB_TRY(launch_color_rows(P, l));
   } else {
     for (int l = 0; l < ns; ++l) IB_TRY(launch_assemble_struct(P, l));
   }
@@ -316,6 +320,7 @@ void free_problem(Problem* P) {
     dfree(L.v32.w); dfree(L.v32.b); dfree(L.v32.r);
     dfree(L.rE64); dfree(L.rE32);
     dfree(L.box_of_slot); dfree(L.rowslot); dfree(L.slot_row); dfree(L.Ew64); dfree(L.Ew32);
+    dfree(L.crow); dfree(L.ccount);
     dfree(L.Mring);
   }
   dfree(P->Twin);

@@ -217,6 +217,10 @@ struct LevelInfo {
   int* rowslot = nullptr;
   int* slot_row = nullptr;
   int n_rows = 0, cap_rows = 0;
+  // the structure rows (slots) of each colour, rebuilt at every set-up: colour c's
+  // list is crow[c cap_rows ...], ccount[c] long
+  int* crow = nullptr;
+  int* ccount = nullptr;
   double* Ew64 = nullptr;
   float* Ew32 = nullptr;
 };
@@ -428,6 +432,8 @@ int launch_window_galerkin(Problem& P, int level);
 int launch_struct_from_windows(Problem& P, int level);
 int launch_coarse_from_windows(Problem& P);
 int launch_window_cast(Problem& P, int level);
+// The colour lists of a level's structure rows (LevelInfo::crow, ccount).
+int launch_color_rows(Problem& P, int level);
 template <typename T>
 int launch_window_apply(Problem& P, int level, const T* w, T* y, double coef, int color, bool pdl);
 int launch_assemble_coarse(Problem& P);

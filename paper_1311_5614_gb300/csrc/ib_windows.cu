@@ -476,48 +476,83 @@ __global__ void k_window_cast(const double* __restrict__ a, float* __restrict__ 
 // them.  The row count is read from the device (the set-up's counter), so that a
 // captured launch, sized by the storage capacity, stays valid when the count
 // changes from step to step.  Only the programmatic-launch wait orders the reads of w.
+// The colour lists of a level's structure rows: each slot whose row belongs to
+// colour c (a face on a box edge belongs to the boxes on both sides) and is not a
+// no-slip wall face is appended to colour c's list.  The order within a list does
+// not matter: every row is applied by one warp, into its own entry.
+__global__ void k_color_append(const int* __restrict__ slot_row, int nr, int N, int b, int walls, int cap,
+                               int* __restrict__ crow, int* __restrict__ ccount) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nr) return;
+  const int r = slot_row[s], n = N * N, c = r / n, rr = r - c * n, i = rr % N, j = rr / N;
+  if (walls && wall_face(c, i, j)) return;
+#pragma unroll
+  for (int col = 0; col < 4; ++col)
+    if (row_in_color(c, i, j, b, col)) crow[(size_t)col * cap + atomicAdd(&ccount[col], 1)] = s;
+}
+
+// rE (or y) += coef * E_l w on the structure rows of colour `color` (-1: all
+// rows): a warp per row, each lane its window entries e = lane + 32 t; the
+// entries' offsets from the row are decoded once per warp, and rows at least WR
+// cells from the grid's edges gather without wrapping.  The warps stride over the
+// colour's list (or over all slots).
 template <typename T>
 __global__ void __launch_bounds__(256) kv_window_apply(const int* __restrict__ slot_row, const int* __restrict__ nrows_dev,
-                                                       const T* __restrict__ Ew, const T* __restrict__ w, int N,
-                                                       T coef, int b, int color, int walls, T* __restrict__ y) {
-  const int warp = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  int r = -1, c = 0, i = 0, j = 0;
-  if (warp < *nrows_dev) {
-    r = slot_row[warp];
-    const int n = N * N;
-    c = r / n;
-    const int rr = r - c * n;
-    i = rr % N;
-    j = rr / N;
-    if (!row_in_color(c, i, j, b, color) || (walls && wall_face(c, i, j))) r = -1;
-  }
-  pdl_enter();
-  if (r < 0) return;  // the whole warp leaves together
-  const T* row = Ew + (size_t)warp * WIN;
+                                                       const int* __restrict__ crow, const int* __restrict__ ccount,
+                                                       int cap, const T* __restrict__ Ew, const T* __restrict__ w,
+                                                       int N, T coef, int color, int walls, T* __restrict__ y) {
+  constexpr int NT = (WIN + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * (long)blockDim.x) >> 5);
   const size_t n = (size_t)N * N;
-  // every row of E_l sums to zero over each column component (a uniform velocity
-  // is in the kernel of E_l: J annihilates translations, P reproduces constants), so
-  // the entries multiply differences from the component's value at the row's own
-  // index; a structure moving almost rigidly then keeps the accuracy of the
-  // per-point form, which works on velocity differences.  With no-slip walls the
-  // prolongation does not reproduce constants next to a wall, so the coarse rows
-  // need not sum to zero there: the plain sum is taken.
-  const T ref[2] = {walls ? (T)0 : w[(size_t)j * N + i], walls ? (T)0 : w[n + (size_t)j * N + i]};
-  T acc = 0;
-#pragma unroll 4
-  for (int e = lane; e < WIN; e += 32) {
-    const int cc = e / WSQ, rem = e - cc * WSQ;
-    const int dj = rem / WD - WR, di = rem - (rem / WD) * WD - WR;
-    acc += row[e] * (w[cc * n + (size_t)wrapi(j + dj, N) * N + wrapi(i + di, N)] - ref[cc]);
-  }
+  int offc[NT], offd[NT];  // per entry: component and row/column offsets (dj * N + di), -1: none
+  int dis[NT], djs[NT];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[r] += coef * acc;
+  for (int t = 0; t < NT; ++t) {
+    const int e = lane + 32 * t;
+    const int cc = e / WSQ, rem = e - cc * WSQ;
+    djs[t] = rem / WD - WR;
+    dis[t] = rem - (rem / WD) * WD - WR;
+    offc[t] = e < WIN ? cc : -1;
+    offd[t] = djs[t] * N + dis[t];
+  }
+  const int k1 = color < 0 ? *nrows_dev : ccount[color];
+  const int* list = color < 0 ? nullptr : crow + (size_t)color * cap;
+  pdl_enter();
+  for (int k = warp; k < k1; k += nwarps) {
+    const int s = color < 0 ? k : list[k];
+    const int r = slot_row[s], c = (int)(r / n), rr = r - c * (int)n, i = rr % N, j = rr / N;
+    if (color < 0 && walls && wall_face(c, i, j)) continue;  // the whole warp: one row
+    const T* row = Ew + (size_t)s * WIN;
+    // every row of E_l sums to zero over each column component (a uniform velocity
+    // is in the kernel of E_l: J annihilates translations, P reproduces constants),
+    // so the entries multiply differences from the component's value at the row's
+    // own index; a structure moving almost rigidly then keeps the accuracy of the
+    // per-point form, which works on velocity differences.  With no-slip walls the
+    // prolongation does not reproduce constants next to a wall, so the coarse rows
+    // need not sum to zero there: the plain sum is taken.
+    const T ref0 = walls ? (T)0 : w[(size_t)j * N + i], ref1 = walls ? (T)0 : w[n + (size_t)j * N + i];
+    const bool inner = i >= WR && i < N - WR && j >= WR && j < N - WR;
+    const long base = (long)j * N + i;
+    T acc = 0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int cc = offc[t];
+      if (cc < 0) continue;
+      const size_t idx = inner ? (size_t)(cc * (long)n + base + offd[t])
+                               : cc * n + (size_t)wrapi(j + djs[t], N) * N + wrapi(i + dis[t], N);
+      acc += row[lane + 32 * t] * (w[idx] - (cc == 0 ? ref0 : ref1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[r] += coef * acc;
+  }
 }
-template __global__ void kv_window_apply<double>(const int*, const int*, const double*, const double*, int, double,
-                                                 int, int, int, double*);
-template __global__ void kv_window_apply<float>(const int*, const int*, const float*, const float*, int, float, int,
-                                                int, int, float*);
+template __global__ void kv_window_apply<double>(const int*, const int*, const int*, const int*, int, const double*,
+                                                 const double*, int, double, int, int, double*);
+template __global__ void kv_window_apply<float>(const int*, const int*, const int*, const int*, int, const float*,
+                                                const float*, int, float, int, int, float*);
 
 // ---------------------------------------------------------------- launchers
 
@@ -653,18 +688,20 @@ const double* window_of<double>(const LevelInfo& L) { return L.Ew64; }
 template <>
 const float* window_of<float>(const LevelInfo& L) { return L.Ew32; }
 
-// y += coef * E_l w on the structure rows of colour `color` (-1: all).
+// y += coef * E_l w on the structure rows of colour `color` (-1: all).  A colour
+// holds about a third of the rows (those of its boxes and the faces it shares):
+// half the row capacity in warps, striding when a colour holds more.
 template <typename T>
 int launch_window_apply(Problem& P, int level, const T* w, T* y, double coef, int color, bool pdl) {
   LevelInfo& L = P.lev[level];
   if (L.cap_rows == 0) return IB_OK;
   const double sT = sizeof(T);
   // per row: its window, the gathered w values and the read-modify-write of y
-  // (all rows; about a third of them carry a colour)
   const double rows = color < 0 ? L.n_rows : L.n_rows / 3.0;
   KScope ks(P, IB_KC_SPREAD, rows * (WIN * 2.0 * sT + 2 * sT + 4));
+  const long warps = color < 0 ? (long)L.cap_rows : ((long)L.cap_rows + 1) / 2;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)nblk(32L * L.cap_rows));
+  cfg.gridDim = dim3((unsigned)nblk(32L * warps));
   cfg.blockDim = dim3(TPB);
   cfg.stream = P.stream;
   cudaLaunchAttribute at[1];
@@ -673,9 +710,24 @@ int launch_window_apply(Problem& P, int level, const T* w, T* y, double coef, in
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
   IB_CUDA_TRY(cudaLaunchKernelEx(&cfg, kv_window_apply<T>, (const int*)L.slot_row, (const int*)(P.count + 1 + level),
-                                 window_of<T>(L), w, L.N, (T)coef, P.prm.box, color, (int)P.prm.walls, y));
+                                 (const int*)L.crow, (const int*)L.ccount, L.cap_rows, window_of<T>(L), w, L.N,
+                                 (T)coef, color, (int)P.prm.walls, y));
   return IB_OK;
 }
+
+int launch_color_rows(Problem& P, int level) {
+  LevelInfo& L = P.lev[level];
+  const int nr = L.n_rows;
+  if (!L.crow) return IB_OK;
+  IB_CUDA_TRY(cudaMemsetAsync(L.ccount, 0, 4 * sizeof(int), P.stream));
+  if (nr == 0) return IB_OK;
+  KScope ks(P, IB_KC_SETUP, nr * 24.0);
+  k_color_append<<<nblk(nr), TPB, 0, P.stream>>>(L.slot_row, nr, L.N, P.prm.box, (int)P.prm.walls, L.cap_rows,
+                                                 L.crow, L.ccount);
+  IB_LAUNCH_CHECK();
+  return IB_OK;
+}
+
 template int launch_window_apply<double>(Problem&, int, const double*, double*, double, int, bool);
 template int launch_window_apply<float>(Problem&, int, const float*, float*, double, int, bool);
 
