@@ -1028,7 +1028,8 @@ def run_multi1024(args):
                 "solve_ms": float(np.mean([x["t_solve_ms"] for x in step_stats])),
                 "autotune": {"tail_grid": tail[0], "tail_cluster": tail[1], "box_form_by_level": forms_by_level,
                              "box_form_codes": "1 one box per CTA, 2 thread per box row, 3 register-blocked "
-                                               "product, 4/5/6 strip kernel of 8/16/32 boxes, 0 size rule"},
+                                               "product, 4/5/6 strip kernel of 8/16/32 boxes, 7 eight boxes "
+                                               "per 64-thread CTA, 0 size rule"},
                 "profile": {k: {"launches": v[0], "ms": v[1], "bytes": v[2]} for k, v in prof.items()},
                 "forms": forms, "vcycle_large": large}
         print(json.dumps(line), flush=True)

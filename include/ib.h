@@ -295,7 +295,8 @@ IB_API int ib_tail_cluster(const ib_problem* prob, int32_t precision);
  * precision, as the set-up autotuner chose it by timing one colour phase of each form
  * on the problem's own hierarchy: 1 one box per CTA, 2 a thread per box row (several
  * boxes per CTA), 3 the register-blocked product, 4 / 5 / 6 the strip kernel with 8 /
- * 16 / 32 boxes per strip; 0 when no form was timed (the size rule above applies: 1 x 1
+ * 16 / 32 boxes per strip, 7 eight boxes per 64-thread CTA, each thread one row of
+ * all eight (FP32 V-cycle, 4 x 4 boxes); 0 when no form was timed (the size rule above applies: 1 x 1
  * or 8 x 8 boxes, IB_BOX_TUNE=0, or an IB_BOX_* variable set); -1 for an invalid
  * argument.  The environment variable IB_BOX_FORMS (comma-separated codes, finest
  * level first, read at ib_setup) gives the forms instead of timing them (a form that

@@ -809,9 +809,89 @@ inline int strip_width(const Problem& P, int N) {
   return pick;
 }
 
+// FP32 4 x 4 boxes, eight per CTA of 64 threads: the residuals of the eight boxes
+// first (7 rows a thread), then thread q forms row q of all eight free-box solves
+// together, one entry of the shared inverse (read through L1) against the eight
+// residuals read as two vectors, so that a thread spends 11 instructions per 8
+// FMAs instead of 3 per FMA; a structure box's row is then formed again from its
+// FP64 inverse.  The same sums, in the same order, as kv_boxn.
+constexpr int OCT_BPC = 8;
+__global__ void __launch_bounds__(64) kv_boxo(float* w, const float* __restrict__ b, float* rE, int N,
+                                              StokesCoef<float> c, int color, const int* __restrict__ slot,
+                                              const double* __restrict__ Ms, const float* __restrict__ Mf) {
+  constexpr int BS = 4, NB = 2 * BS * (BS + 1) + BS * BS, NV = 2 * BS * (BS + 1);
+  __shared__ __align__(16) float rs[NB][OCT_BPC];
+  __shared__ int sg[OCT_BPC][NB];
+  __shared__ int ssl[OCT_BPC];
+  const int tid = threadIdx.x;
+  const int nb = N / BS, half = nb >> 1, nbox = half * half;
+  const int t0 = blockIdx.x * OCT_BPC;
+  if (tid < OCT_BPC) {
+    const int t = t0 + tid;
+    ssl[tid] = t < nbox ? slot[(2 * (t / half) + (color >> 1)) * nb + 2 * (t % half) + (color & 1)] : -2;
+  }
+  __syncthreads();
+  pdl_enter();
+  for (int e = tid; e < OCT_BPC * NB; e += 64) {
+    const int lb = e / NB, q = e - lb * NB, t = t0 + lb;
+    if (t >= nbox) {
+      rs[q][lb] = 0.f;
+      sg[lb][q] = -1;
+      continue;
+    }
+    const int I = 2 * (t % half) + (color & 1), J = 2 * (t / half) + (color >> 1);
+    int cc, i, j;
+    box_unknown(q, BS, I * BS, J * BS, N, &cc, &i, &j);
+    const int gq = cc * N * N + j * N + i;
+    float r = b[gq] - stokes_row(w, N, c, cc, i, j);
+    if (rE && ssl[lb] >= 0 && q < NV) {
+      r += rE[gq];
+      rE[gq] = 0.f;
+    }
+    rs[q][lb] = r;
+    sg[lb][q] = gq;
+  }
+  __syncthreads();
+  const int q = tid;
+  if (q >= NB) return;
+  float d[OCT_BPC];
+#pragma unroll
+  for (int k = 0; k < OCT_BPC; ++k) d[k] = 0.f;
+  const float* M = Mf + q;
+#pragma unroll 4
+  for (int s2 = 0; s2 < NB; ++s2) {
+    const float m = __ldg(M + s2 * NB);
+    const float4 r0 = *reinterpret_cast<const float4*>(&rs[s2][0]);
+    const float4 r1 = *reinterpret_cast<const float4*>(&rs[s2][4]);
+    d[0] = fmaf(m, r0.x, d[0]);
+    d[1] = fmaf(m, r0.y, d[1]);
+    d[2] = fmaf(m, r0.z, d[2]);
+    d[3] = fmaf(m, r0.w, d[3]);
+    d[4] = fmaf(m, r1.x, d[4]);
+    d[5] = fmaf(m, r1.y, d[5]);
+    d[6] = fmaf(m, r1.z, d[6]);
+    d[7] = fmaf(m, r1.w, d[7]);
+  }
+#pragma unroll
+  for (int lb = 0; lb < OCT_BPC; ++lb) {
+    const int gq = sg[lb][q];
+    if (gq < 0) continue;
+    const int sl = ssl[lb];
+    float dv = d[lb];
+    if (sl >= 0) {
+      const double* Mb = Ms + (size_t)sl * NB * NB + q;
+      double dd = 0.0;
+#pragma unroll 8
+      for (int s2 = 0; s2 < NB; ++s2) dd += Mb[(size_t)s2 * NB] * (double)rs[s2][lb];
+      dv = (float)dd;
+    }
+    w[gq] += dv;
+  }
+}
+
 // Forms of the n x n box kernel (n = 2, 4) the set-up autotuner chooses from.
 enum : int { BOXF_RULE = 0, BOXF_ONE = 1, BOXF_ROWS = 2, BOXF_GEMM = 3, BOXF_STRIP8 = 4, BOXF_STRIP16 = 5,
-             BOXF_STRIP32 = 6 };
+             BOXF_STRIP32 = 6, BOXF_OCT = 7 };
 
 template <typename T>
 constexpr int pix();
@@ -860,6 +940,14 @@ bool launch_box_form(Problem& P, int l, int form, T* w, const T* b, T* E, int co
       return bs == 4 && !P.prm.walls && half % 16 == 0 && launch_strip<T, TM, 16>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
     case BOXF_STRIP32:
       return bs == 4 && !P.prm.walls && half % 32 == 0 && launch_strip<T, TM, 32>(P, pdl, w, b, E, L.N, c, color, L.flag, Ms, Mf);
+    case BOXF_OCT:
+      if constexpr (std::is_same<T, float>::value && std::is_same<TM, float>::value) {
+        if (bs != 4) return false;
+        vlaunch(pdl, kv_boxo, nblk(nbox, OCT_BPC), 64, 0, P.stream, w, b, E, L.N, c, color, (const int*)L.flag, Ms,
+                Mf);
+        return true;
+      }
+      return false;
     default:
       return false;
   }
@@ -1791,7 +1879,8 @@ int vcycle_run(Problem& P);
 
 // Box-kernel autotuner: on every smoothing level with n x n boxes (n = 2, 4), time one
 // colour phase of each applicable form (one box per CTA, a thread per box row, the
-// register-blocked product, the strip kernel at widths 8, 16, 32) on the problem's
+// register-blocked product, the strip kernel at widths 8, 16, 32, eight FP32 boxes
+// per 64-thread CTA) on the problem's
 // own hierarchy with w = b = 0 (the same products and memory traffic, no change of
 // state) and keep the fastest.  Skipped when an IB_BOX_* variable pins the forms.
 template <typename T, typename TM>
@@ -1821,7 +1910,7 @@ int tune_box_forms_t(Problem& P) {
     }
     float best = 1e30f;
     int best_f = BOXF_RULE;
-    for (int f = BOXF_ONE; f <= BOXF_STRIP32; ++f) {
+    for (int f = BOXF_ONE; f <= BOXF_OCT; ++f) {
       if (!launch_box_form<T, TM>(P, l, f, B.w, B.b, (T*)nullptr, 0)) continue;  // warm-up (and applicability)
       cudaEventRecord(e0, P.stream);
       for (int r = 0; r < 4; ++r) launch_box_form<T, TM>(P, l, f, B.w, B.b, (T*)nullptr, r);

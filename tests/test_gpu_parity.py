@@ -408,3 +408,27 @@ def test_long_spring_falls_back_to_point_path(pkg):
     s.vcycle(dev(rhs), z)
     assert rel_elementwise(z.cpu().numpy(), ref) < 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("N", [64, 256])
+def test_vcycle_fp32_eight_box_form(pkg, N, monkeypatch):
+    """The eight-boxes-per-CTA FP32 form (IB_BOX_FORMS code 7) on every smoothing
+    level: within the FP32 bars of the oracle, and bit for bit the V-cycle of the
+    thread-per-row form (code 2), whose sums it forms in the same order."""
+    p = _strip_case(N)
+    rhs = O.rhs_vector(p)
+    ref = _oracle_vcycle(p, rhs)
+    out = {}
+    for form in ("7", "2"):
+        monkeypatch.setenv("IB_BOX_FORMS", ",".join([form] * 16))
+        s = pkg.IBSolver.from_problem(p, precision="fp32")
+        try:
+            assert s.struct_boxes(0) > 0
+            assert s.box_forms("fp32")[0] == int(form)
+            w = torch.zeros(3 * p.N * p.N, dtype=torch.float64, device="cuda")
+            s.vcycle(dev(rhs), w)
+            out[form] = w.cpu().numpy()
+        finally:
+            s.close()
+    assert max(rel_per_component(out["7"], ref, p.N)) <= 2e-5, rel_per_component(out["7"], ref, p.N)
+    assert np.array_equal(out["7"], out["2"])
