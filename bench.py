@@ -58,7 +58,7 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # launch with cold caches, so this is an upper bound of the graph-replayed cycle's
 # traffic).  Valid only for the V-cycle kernel sources it was taken on: reported as
 # null once they change.
-TRAFFIC = {"sources_sha256": "3c9f91d1fa3eecabb0eb2b88eb07a577270e8a0fde90acd1d5dfe0f54e4abf86",
+TRAFFIC = {"sources_sha256": "ee2e6a29d504c1b214cb0cbb1aef37f9adc50996291dd7f619e24a382a622e2b",
            "vcycle1024": 747.8e6}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh", "ib_windows.cu",
                   "ib_async.cuh"]
