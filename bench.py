@@ -58,7 +58,7 @@ CASES = [(k, dt) for dt in (1e-3, 1e-2) for k in (1.0, 1e2, 1e4, 1e6)]
 # launch with cold caches, so this is an upper bound of the graph-replayed cycle's
 # traffic).  Valid only for the V-cycle kernel sources it was taken on: reported as
 # null once they change.
-TRAFFIC = {"sources_sha256": "ee2e6a29d504c1b214cb0cbb1aef37f9adc50996291dd7f619e24a382a622e2b",
+TRAFFIC = {"sources_sha256": "7d15a3a37ad17522a40f3ae3064a068071e95cbd06807e0193cfe1e70bbb0c1b",
            "vcycle1024": 747.8e6}
 VCYCLE_SOURCES = ["ib_internal.cuh", "ib_ops.cuh", "ib_vcycle.cu", "ib_vcycle.cuh", "ib_windows.cu",
                   "ib_async.cuh"]

@@ -275,9 +275,10 @@ int setup_hierarchy(Problem& P) {
   const bool inv32 = P.inv32 && P.prm.precision == IB_FP32_PRECOND && P.sigma < P.stiff_sigma;
   bool all_done = false;
   IB_TRY(launch_invert_struct_all(P, &all_done, inv32));
-  P.struct_inv32 = inv32 && all_done;
+  const bool big = (size_t)nB * nB * sizeof(double) > 160u * 1024u;  // the blocked form (8 x 8, 16 x 16 boxes)
+  P.struct_inv32 = inv32 && (all_done || big);
   if (!all_done)
-    for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_form));
+    for (int l = 0; l < ns; ++l) IB_TRY(launch_invert(P, P.lev[l].Mstruct, nB, P.lev[l].n_form, inv32 && big));
   if (P.prm.walls)
     for (int l = 0; l < ns; ++l) IB_TRY(launch_ring_copy(P, l));
   P.free_ready = true;

@@ -288,19 +288,21 @@ __device__ void gj_invert_cols(TE* M, int n, int* err) {
 constexpr int GJ_PW = 16;
 constexpr int GJ_PANEL_THREADS = 512;
 
-__global__ void __launch_bounds__(GJ_PANEL_THREADS) k_bgj_panel(double* Ms, int n, int k0, int pw, double* U,
-                                                                int* perms, int* err) {
-  extern __shared__ double sP[];  // [n][GJ_PW] the panel, then f[n]
-  double* f = sP + (size_t)n * GJ_PW;
-  __shared__ double sinv;
+template <typename TE>
+__global__ void __launch_bounds__(GJ_PANEL_THREADS) k_bgj_panel(TE* Ms, int n, int k0, int pw, TE* U, int* perms,
+                                                                int* err) {
+  extern __shared__ __align__(16) unsigned char bgj_raw[];
+  TE* sP = reinterpret_cast<TE*>(bgj_raw);  // [n][GJ_PW] the panel, then f[n]
+  TE* f = sP + (size_t)n * GJ_PW;
+  __shared__ TE sinv;
   __shared__ int prow;
-  double* M = Ms + (size_t)blockIdx.x * n * n;
+  TE* M = Ms + (size_t)blockIdx.x * n * n;
   int* perm = perms + (size_t)blockIdx.x * n;
-  double* Um = U + (size_t)blockIdx.x * GJ_PW * n;
+  TE* Um = U + (size_t)blockIdx.x * GJ_PW * n;
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int e = tid; e < n * GJ_PW; e += bd) {
     const int i = e / GJ_PW, c = e - i * GJ_PW;
-    sP[e] = c < pw ? M[(size_t)i * n + k0 + c] : 0.0;
+    sP[e] = c < pw ? M[(size_t)i * n + k0 + c] : TE(0);
   }
   __syncthreads();
   const int R = bd / GJ_PW, c = tid % GJ_PW, r0 = tid / GJ_PW;
@@ -309,14 +311,14 @@ __global__ void __launch_bounds__(GJ_PANEL_THREADS) k_bgj_panel(double* Ms, int 
     if (tid < 32) {
       const int p = warp_pivot_row(sP, GJ_PW, s, k, n, tid);
       if (tid == 0) {
-        double piv = sP[(size_t)p * GJ_PW + s];
-        if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+        TE piv = sP[(size_t)p * GJ_PW + s];
+        if (!(fabs(piv) > TE(0)) || !isfinite(piv)) {
           atomicOr(err, DEV_ERR_SINGULAR);
-          piv = 1.0;
+          piv = TE(1);
         }
         prow = p;
         perm[k] = p;
-        sinv = 1.0 / piv;
+        sinv = TE(1) / piv;
       }
     }
     __syncthreads();
@@ -324,24 +326,24 @@ __global__ void __launch_bounds__(GJ_PANEL_THREADS) k_bgj_panel(double* Ms, int 
     if (p != k) {  // whole rows: the panel here, the other columns in global memory
       for (int j = tid; j < n; j += bd) {
         if (j >= k0 && j < k0 + pw) continue;  // stale copy of the panel, rewritten below
-        const double t = M[(size_t)k * n + j];
+        const TE t = M[(size_t)k * n + j];
         M[(size_t)k * n + j] = M[(size_t)p * n + j];
         M[(size_t)p * n + j] = t;
       }
       if (tid < GJ_PW) {
-        const double t = sP[(size_t)k * GJ_PW + tid];
+        const TE t = sP[(size_t)k * GJ_PW + tid];
         sP[(size_t)k * GJ_PW + tid] = sP[(size_t)p * GJ_PW + tid];
         sP[(size_t)p * GJ_PW + tid] = t;
       }
     }
     __syncthreads();
-    const double inv = sinv;
-    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? 0.0 : sP[(size_t)i * GJ_PW + s];
-    const double mkc = (c < pw) ? (c == s ? 1.0 : sP[(size_t)k * GJ_PW + c]) * inv : 0.0;
+    const TE inv = sinv;
+    for (int i = tid; i < n; i += bd) f[i] = (i == k) ? TE(0) : sP[(size_t)i * GJ_PW + s];
+    const TE mkc = (c < pw) ? (c == s ? TE(1) : sP[(size_t)k * GJ_PW + c]) * inv : TE(0);
     __syncthreads();
     if (c < pw) {
       for (int i = r0; i < n; i += R) {
-        double* e = sP + (size_t)i * GJ_PW + c;
+        TE* e = sP + (size_t)i * GJ_PW + c;
         if (i == k) *e = mkc;
         else if (c == s) *e = -f[i] * mkc;
         else *e -= f[i] * mkc;
@@ -355,37 +357,38 @@ __global__ void __launch_bounds__(GJ_PANEL_THREADS) k_bgj_panel(double* Ms, int 
   }
   for (int e = tid; e < pw * n; e += bd) {
     const int s = e / n, j = e - s * n;
-    Um[(size_t)s * n + j] = (j >= k0 && j < k0 + pw) ? 0.0 : M[(size_t)(k0 + s) * n + j];
+    Um[(size_t)s * n + j] = (j >= k0 && j < k0 + pw) ? TE(0) : M[(size_t)(k0 + s) * n + j];
   }
 }
 
 // grid (column tiles, row tiles, matrices): a 64 x 64 tile per CTA, 4 x 4 entries
 // per thread, the panel's rows of the tile and the saved pivot rows staged in shared memory.
-__global__ void __launch_bounds__(256) k_bgj_update(double* Ms, int n, int k0, int pw, const double* U, int z0) {
-  __shared__ double sQ[64][GJ_PW + 1];
-  __shared__ double sU[GJ_PW][64];
+template <typename TE>
+__global__ void __launch_bounds__(256) k_bgj_update(TE* Ms, int n, int k0, int pw, const TE* U, int z0) {
+  __shared__ TE sQ[64][GJ_PW + 1];
+  __shared__ TE sU[GJ_PW][64];
   const int z = z0 + blockIdx.z;
-  double* M = Ms + (size_t)z * n * n;
-  const double* Um = U + (size_t)z * GJ_PW * n;
+  TE* M = Ms + (size_t)z * n * n;
+  const TE* Um = U + (size_t)z * GJ_PW * n;
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64, tid = threadIdx.x;
   for (int e = tid; e < 64 * GJ_PW; e += 256) {
     const int r = e / GJ_PW, s = e - r * GJ_PW, i = i0 + r;
-    sQ[r][s] = (i < n && s < pw) ? M[(size_t)i * n + k0 + s] : 0.0;
+    sQ[r][s] = (i < n && s < pw) ? M[(size_t)i * n + k0 + s] : TE(0);
   }
   for (int e = tid; e < GJ_PW * 64; e += 256) {
     const int s = e >> 6, cc = e & 63, j = j0 + cc;
-    sU[s][cc] = (j < n && s < pw) ? Um[(size_t)s * n + j] : 0.0;
+    sU[s][cc] = (j < n && s < pw) ? Um[(size_t)s * n + j] : TE(0);
   }
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  TE acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[a][q] = 0.0;
+    for (int q = 0; q < 4; ++q) acc[a][q] = TE(0);
 #pragma unroll
   for (int s = 0; s < GJ_PW; ++s) {
-    double qa[4], ub[4];
+    TE qa[4], ub[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) qa[a] = sQ[ty + 16 * a][s];
 #pragma unroll
@@ -404,8 +407,8 @@ __global__ void __launch_bounds__(256) k_bgj_update(double* Ms, int n, int k0, i
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + tx + 16 * q;
       if (j >= n || (j >= k0 && j < k0 + pw)) continue;
-      double* e = M + (size_t)i * n + j;
-      *e = (pivot_row ? 0.0 : *e) + acc[a][q];
+      TE* e = M + (size_t)i * n + j;
+      *e = (pivot_row ? TE(0) : *e) + acc[a][q];
     }
   }
 }
@@ -413,12 +416,14 @@ __global__ void __launch_bounds__(256) k_bgj_update(double* Ms, int n, int k0, i
 // Column j of the result is column idx[j] of the eliminated matrix, idx being
 // 0..n-1 put through the column interchanges k <-> perm[k], k = n-1 down to 0.
 // grid (groups of 8 rows, matrices z0 + y).
-__global__ void k_bgj_unperm(double* Ms, int n, const int* perms, int z0) {
-  extern __shared__ double sRow[];  // one row [n], then perm [n] and idx [n] as ints
+template <typename TE>
+__global__ void k_bgj_unperm(TE* Ms, int n, const int* perms, int z0) {
+  extern __shared__ __align__(16) unsigned char bgj_row[];
+  TE* sRow = reinterpret_cast<TE*>(bgj_row);  // one row [n], then perm [n] and idx [n] as ints
   int* sp = reinterpret_cast<int*>(sRow + n);
   int* idx = sp + n;
   const int z = z0 + blockIdx.y;
-  double* M = Ms + (size_t)z * n * n;
+  TE* M = Ms + (size_t)z * n * n;
   const int* perm = perms + (size_t)z * n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     sp[j] = perm[j];
@@ -437,7 +442,7 @@ __global__ void k_bgj_unperm(double* Ms, int n, const int* perms, int z0) {
   __syncthreads();
   const int r_end = min(n, (int)(blockIdx.x + 1) * 8);
   for (int i = blockIdx.x * 8; i < r_end; ++i) {
-    double* row = M + (size_t)i * n;
+    TE* row = M + (size_t)i * n;
     for (int j = threadIdx.x; j < n; j += blockDim.x) sRow[j] = row[j];
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = sRow[idx[j]];
@@ -775,7 +780,40 @@ int launch_struct_fill(Problem& P, int level) {
 // panel launch (a CTA per matrix) and one update launch (64 x 64 tiles of every
 // matrix), then the column interchanges.  Its workspace (saved pivot rows and
 // pivot indices) grows on demand and is kept with the problem.
-int launch_invert_blocked(Problem& P, double* M, int n, int count) {
+template <typename TE>
+int run_bgj(Problem& P, TE* M, int n, int count) {
+  const size_t smem_panel = (size_t)n * (GJ_PW + 1) * sizeof(TE);
+  const size_t smem_unperm = (size_t)n * (sizeof(TE) + 2 * sizeof(int));
+  static std::once_flag once;
+  cudaError_t ae = cudaSuccess;
+  std::call_once(once, [&] {
+    const int mx = (int)((size_t)INV_MAXN_BLOCKED * (GJ_PW + 1) * sizeof(TE));
+    ae = cudaFuncSetAttribute(k_bgj_panel<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  });
+  IB_CUDA_TRY(ae);
+  TE* U = reinterpret_cast<TE*>(P.inv_ws);
+  const int tiles = (n + 63) / 64;
+  for (int k0 = 0; k0 < n; k0 += GJ_PW) {
+    const int pw = n - k0 < GJ_PW ? n - k0 : GJ_PW;
+    k_bgj_panel<TE><<<count, GJ_PANEL_THREADS, smem_panel, P.stream>>>(M, n, k0, pw, U, P.inv_perm, P.dev_err);
+    IB_LAUNCH_CHECK();
+    for (int z0 = 0; z0 < count; z0 += 65535) {
+      const int nz = count - z0 < 65535 ? count - z0 : 65535;
+      k_bgj_update<TE><<<dim3(tiles, tiles, nz), 256, 0, P.stream>>>(M, n, k0, pw, U, z0);
+      IB_LAUNCH_CHECK();
+    }
+  }
+  for (int z0 = 0; z0 < count; z0 += 65535) {
+    const int nz = count - z0 < 65535 ? count - z0 : 65535;
+    k_bgj_unperm<TE><<<dim3((n + 7) / 8, nz), 256, smem_unperm, P.stream>>>(M, n, P.inv_perm, z0);
+    IB_LAUNCH_CHECK();
+  }
+  return IB_OK;
+}
+
+// fp32: the elimination in FP32 on a rounded copy of the matrices (a stream-ordered
+// temporary), the inverses written back in FP64.
+int launch_invert_blocked(Problem& P, double* M, int n, int count, bool fp32) {
   const size_t ws = (size_t)count * GJ_PW * n, wp = (size_t)count * n;
   if (ws > P.inv_ws_cap) {
     dfree(P.inv_ws);
@@ -789,39 +827,21 @@ int launch_invert_blocked(Problem& P, double* M, int n, int count) {
     IB_TRY(dalloc(&P.inv_perm, wp));
     P.inv_perm_cap = wp;
   }
-  const size_t smem_panel = (size_t)n * (GJ_PW + 1) * sizeof(double);
-  const size_t smem_unperm = (size_t)n * (sizeof(double) + 2 * sizeof(int));
-  static std::once_flag once;
-  cudaError_t ae = cudaSuccess;
-  std::call_once(once, [&] {
-    const int mx = (int)((size_t)INV_MAXN_BLOCKED * (GJ_PW + 1) * sizeof(double));
-    ae = cudaFuncSetAttribute(k_bgj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  });
-  IB_CUDA_TRY(ae);
-  const int tiles = (n + 63) / 64;
-  for (int k0 = 0; k0 < n; k0 += GJ_PW) {
-    const int pw = n - k0 < GJ_PW ? n - k0 : GJ_PW;
-    k_bgj_panel<<<count, GJ_PANEL_THREADS, smem_panel, P.stream>>>(M, n, k0, pw, P.inv_ws, P.inv_perm,
-                                                                   P.dev_err);
-    IB_LAUNCH_CHECK();
-    for (int z0 = 0; z0 < count; z0 += 65535) {
-      const int nz = count - z0 < 65535 ? count - z0 : 65535;
-      k_bgj_update<<<dim3(tiles, tiles, nz), 256, 0, P.stream>>>(M, n, k0, pw, P.inv_ws, z0);
-      IB_LAUNCH_CHECK();
-    }
-  }
-  for (int z0 = 0; z0 < count; z0 += 65535) {
-    const int nz = count - z0 < 65535 ? count - z0 : 65535;
-    k_bgj_unperm<<<dim3((n + 7) / 8, nz), 256, smem_unperm, P.stream>>>(M, n, P.inv_perm, z0);
-    IB_LAUNCH_CHECK();
-  }
-  return IB_OK;
+  if (!fp32) return run_bgj<double>(P, M, n, count);
+  const size_t nn = (size_t)count * n * n;
+  float* M32 = nullptr;
+  IB_CUDA_TRY(cudaMallocAsync((void**)&M32, nn * sizeof(float), P.stream));
+  int rc = launch_cast<double, float>(P, M, M32, nn);
+  if (rc == IB_OK) rc = run_bgj<float>(P, M32, n, count);
+  if (rc == IB_OK) rc = launch_cast<float, double>(P, M32, M, nn);
+  cudaFreeAsync(M32, P.stream);
+  return rc;
 }
 
 // Invert count n x n matrices stored back to back: 5 x 5 in registers (one per
 // thread), n^2 doubles that fit in shared memory staged there (one CTA each),
 // larger ones by the blocked form in global memory.
-int launch_invert(Problem& P, double* M, int n, int count) {
+int launch_invert(Problem& P, double* M, int n, int count, bool fp32) {
   if (count <= 0) return IB_OK;
   size_t smem = (size_t)n * n * sizeof(double);
   if (smem > 160u * 1024u ? n > INV_MAXN_BLOCKED : n > INV_MAXN)
@@ -839,7 +859,7 @@ int launch_invert(Problem& P, double* M, int n, int count) {
     const int threads = 256;
     k_invert_sm<<<count, threads, smem, P.stream>>>(M, n, P.dev_err);
   } else {
-    IB_TRY(launch_invert_blocked(P, M, n, count));
+    IB_TRY(launch_invert_blocked(P, M, n, count, fp32));
   }
   IB_LAUNCH_CHECK();
   return IB_OK;

@@ -443,7 +443,9 @@ template <typename T>
 int launch_stokes(Problem& P, int level, const T* w, const T* b, T* out, bool residual);
 int launch_free_box(Problem& P, int level);
 int launch_struct_fill(Problem& P, int level);
-int launch_invert(Problem& P, double* M, int n, int count);
+// fp32: matrices too large for shared memory are eliminated in FP32 (the inverses
+// stored in FP64); the others in FP64 regardless.
+int launch_invert(Problem& P, double* M, int n, int count, bool fp32 = false);
 int launch_invert_struct_all(Problem& P, bool* done, bool fp32 = false);
 int launch_coarse_fill(Problem& P);
 template <typename T>

@@ -90,9 +90,11 @@ def test_vcycle_fp64_box16(pkg, name):
         s.close()
 
 
-@pytest.mark.parametrize("prec,bar", [("fp32", 2e-5), ("mixed", 5e-7)])
-def test_vcycle_reduced_precision_box16(pkg, prec, bar):
-    p = make_case("ellipse_64")
+@pytest.mark.parametrize("prec,bar,box", [("fp32", 2e-5, 16), ("mixed", 5e-7, 16), ("fp32", 2e-5, 8)])
+def test_vcycle_reduced_precision_box16(pkg, prec, bar, box):
+    """FP32 (on this non-stiff case its big structure boxes are eliminated in FP32 by
+    the blocked form) and mixed V-cycles within the element-wise bars."""
+    p = make_case("ellipse_64", box)
     rhs = O.rhs_vector(p)
     ref = _oracle_vcycle(p, rhs)
     s = pkg.IBSolver.from_problem(p, precision=prec)
