@@ -224,8 +224,8 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * atomic additions instead (about 1 ms less set-up on a 1024^2 grid with 32 768
  * points; results then vary at the rounding level).
  * With IB_FP32_PRECOND, a step below the stiffness threshold (IB_STIFF_SIGMA)
- * eliminates its structure boxes (n <= 4) in FP32, the inverses kept and applied
- * in FP64 as before; a solve that escalates to the mixed V-cycle re-forms and
+ * eliminates its structure boxes in FP32, the inverses kept and applied in FP64
+ * as before; a solve that escalates to the mixed V-cycle re-forms and
  * inverts them in FP64 first.  IB_INV32=0 (read at ib_setup) always inverts in
  * FP64.  IB_POISON=1 (read at the
  * library's first allocation) fills every new device allocation with all-ones
