@@ -227,7 +227,9 @@ IB_API int ib_rhs(ib_problem* prob, const double* u_n, double* b);
  * eliminates its structure boxes in FP32, the inverses kept and applied in FP64
  * as before; a solve that escalates to the mixed V-cycle re-forms and
  * inverts them in FP64 first.  IB_INV32=0 (read at ib_setup) always inverts in
- * FP64.  IB_POISON=1 (read at the
+ * FP64; IB_INV32=2 (read at every set-up) eliminates in FP32 for every step of
+ * the FP32 and mixed V-cycles, stiff ones included, without the FP64
+ * re-forming.  IB_POISON=1 (read at the
  * library's first allocation) fills every new device allocation with all-ones
  * bytes (NaN), a test aid that makes reads of unwritten memory show. */
 IB_API int ib_solve_step(ib_problem* prob, const double* u_n, double* up, double* X,

@@ -165,6 +165,13 @@ int check_dev_err(Problem& P) {
   return IB_OK;
 }
 
+// IB_INV32=2: the FP32 elimination for every step of the FP32 and mixed V-cycles,
+// stiff ones included, and no FP64 re-forming when a solve escalates.
+bool inv32_always() {
+  const char* e = std::getenv("IB_INV32");
+  return e && e[0] == '2';
+}
+
 // Re-form S, J and everything that depends on them (per step, sec. 8).  With the
 // assembled elasticity rows (ib_windows.cu): mark the structure boxes and rows of
 // every level and read their counts (one synchronisation), assemble the level-0 rows
@@ -272,7 +279,8 @@ int setup_hierarchy(Problem& P) {
   // a step of the FP32 V-cycle that is not stiff eliminates its structure boxes in
   // FP32 (the inverses are stored, and applied, in FP64); an escalation to the
   // mixed V-cycle re-forms them in FP64 (reform_struct64)
-  const bool inv32 = P.inv32 && P.prm.precision == IB_FP32_PRECOND && P.sigma < P.stiff_sigma;
+  const bool inv32 = P.inv32 && P.prm.precision != IB_FP64 &&
+                     (inv32_always() || (P.prm.precision == IB_FP32_PRECOND && P.sigma < P.stiff_sigma));
   bool all_done = false;
   IB_TRY(launch_invert_struct_all(P, &all_done, inv32));
   const bool big = (size_t)nB * nB * sizeof(double) > 160u * 1024u;  // the blocked form (8 x 8, 16 x 16 boxes)
@@ -586,7 +594,7 @@ int fgmres(Problem& P, const double* b, double* x, ib_stats* st) {
       return IB_OK;
     }
     if (total >= P.prm.max_iters) break;
-    if (st->escalated_at >= 0 && P.struct_inv32) IB_TRY(reform_struct64(P));
+    if (st->escalated_at >= 0 && P.struct_inv32 && !inv32_always()) IB_TRY(reform_struct64(P));
     int mav = std::min(P.max_m, P.prm.max_iters - total);
     const int cycle_start = total;
     IB_TRY(launch_fill<double>(P, g, (size_t)m + 1, 0.0));
