@@ -435,15 +435,14 @@ def _box_rows(N, b, color):
     return np.array(sorted(rows))
 
 
-@pytest.mark.parametrize("b", [2, 4])
+@pytest.mark.parametrize("b,N", [(2, 16), (4, 16), (8, 16), (16, 32)])
 @pytest.mark.parametrize("reverse", [False, True])
-def test_colour_sweep_solves_last_colour_boxes_exactly(b, reverse):
+def test_colour_sweep_solves_last_colour_boxes_exactly(b, N, reverse):
     """Four-colour box smoother (sec. 6): n x n boxes (n >= 2) of one colour are
     farther apart than the 5-point stencil reaches, so without structure the last
     colour phase of a sweep solves its boxes' equations exactly: the residual
     vanishes on every unknown of that colour's boxes (colour 2 forward, colour 0
-    reversed) and on no other colour's."""
-    N = 16
+    reversed) and on no other colour's.  Up to the 16 x 16 boxes (800 unknowns)."""
     p = _small_problem(N=N, n=8, kappa=0.0)
     levels, _ = O.build_hierarchy(p)
     lev = levels[0]
